@@ -1,0 +1,127 @@
+"""Pins for the oracle's sequential stepping and MGRIT cycle (Sec. 2.2, 3.3, 3.4)."""
+
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mgrit as mg
+from oracle import semi_lagrangian as sl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ALPHA = {"alpha1": "const", "alpha2": "cos_t", "alpha4": "cos_t_cos_x"}
+
+
+def read_table(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            a, p, m, it = line.split()
+            rows.append((a, int(p), int(m), int(it)))
+    return rows
+
+
+def test_coarsening_rules():
+    """Coarsen until a further level would have fewer than two time points (Sec. 3.4); or stop at <= 8 steps."""
+    assert mg.coarsening_factors(1024, 4) == [4] * 5  # 1024 .. 4 .. 1
+    assert mg.coarsening_factors(2048, 4) == [4] * 5  # .. 8 .. 2
+    assert mg.coarsening_factors(16384, 8, max_coarsest=8) == [8] * 4  # .. 32 .. 4
+    assert mg.coarsening_factors(256, 4, levels=2) == [4]
+    assert mg.coarsening_factors(16384, [16, 4]) == [16, 4, 4, 4, 4, 4]
+
+
+def _small(kind="sin_kx_cos_t", nx=48, nt=64, p=3, m=4, **kw):
+    g = sl.Grid(nx, nt)
+    ws = sl.WaveSpeed(kind, a=0.5, k=1)
+    H = mg.build_hierarchy(g, ws, p, m, **kw)
+    return g, H, W.u0_bumps_1d(nx, W.SEED_C2_BUMPS, 3), W.initial_iterate(nt, nx)
+
+
+def test_ideal_coarse_operator_converges_in_one_iteration():
+    """Psi = Phi^m makes the coarse problem the exact Schur complement: one iteration (Sec. 2.2)."""
+    g, H, u0, U0 = _small(levels=2, coarse="ideal")
+    R = mg.mgrit_solve(H, u0, U0, norm_mode=0)
+    assert R.iterations == 1 and R.history[1] < 1e-13 * R.history[0]
+
+
+def test_integer_courant_converges_in_one_iteration():
+    """alpha = 1, c = 1: phi = 0 and the coarse SL step is the exact m-shift, so Psi = Phi^m."""
+    g = sl.Grid(32, 64, cfl=1.0)
+    H = mg.build_hierarchy(g, sl.WaveSpeed("const"), 3, 4)
+    R = mg.mgrit_solve(H, W.u0_sin4(32), W.initial_iterate(64, 32), norm_mode=0)
+    assert R.iterations == 1
+
+
+@pytest.mark.parametrize("norm_mode", [0, 1])
+def test_fixed_point_is_sequential_solution(norm_mode):
+    """MGRIT solves the same one-step system as sequential stepping (eq. (one-step))."""
+    g, H, u0, U0 = _small()
+    R = mg.mgrit_solve(H, u0, U0, norm_mode=norm_mode)
+    assert R.converged
+    Useq = mg.sequential_solve(H, u0)
+    assert np.linalg.norm(R.U - Useq) / np.linalg.norm(Useq) < 1e-9
+
+
+def test_residual_history_is_contracting():
+    g, H, u0, U0 = _small(kind="cos_t_cos_x", p=1, m=8)
+    R = mg.mgrit_solve(H, u0, U0)
+    h = np.array(R.history)
+    assert np.all(h[2:] < h[1:-1])
+
+
+def test_rediscretised_coarse_operator_diverges_where_the_corrected_one_converges():
+    """Constant alpha, c = 0.85, p = 3, m = 8: the plain coarse SL operator lets the residual grow
+    (rho(c) > 1 in Fig. 2, Sec. 2.3) while the corrected operator converges (Fig. 3)."""
+    g = sl.Grid(64, 1024, cfl=0.85)
+    U0 = W.initial_iterate(1024, 64)
+    res = {}
+    for kind in ("bsl", "sl"):
+        H = mg.build_hierarchy(g, sl.WaveSpeed("const"), 3, 8, levels=2, coarse=kind)
+        res[kind] = mg.mgrit_solve(H, W.u0_sin4(64), U0, max_iter=20 if kind == "bsl" else 6)
+    assert res["bsl"].converged and res["bsl"].iterations <= 18
+    h = res["sl"].history
+    assert not res["sl"].converged and h[-1] > 10.0 * h[1]
+
+
+FAST_T2 = {("alpha1", 1, 4), ("alpha1", 1, 8), ("alpha1", 1, 16), ("alpha2", 1, 16), ("alpha4", 1, 8),
+           ("alpha1", 3, 16), ("alpha4", 3, 16)}
+# Cells where the exact coarse solve (the reading used here) differs from the paper's
+# GMRES-based solve by one iteration; all other cells must match exactly.
+KNOWN_OFF_BY_ONE = {("table2", "alpha4", 3, 4), ("table1", "alpha2", 1, 8), ("table1", "alpha4", 3, 4)}
+
+
+def _table_case(table, a, p, m, expect, levels):
+    nx, nt = 256, 1024
+    g = sl.Grid(nx, nt)
+    H = mg.build_hierarchy(g, sl.WaveSpeed(ALPHA[a]), p, m, levels=levels)
+    R = mg.mgrit_solve(H, W.u0_sin4(nx), W.initial_iterate(nt, nx))
+    if (table, a, p, m) in KNOWN_OFF_BY_ONE:
+        assert abs(R.iterations - expect) <= 1
+    else:
+        assert R.iterations == expect
+
+
+@pytest.mark.parametrize("a,p,m,expect", [r for r in read_table("table2_multilevel_iters.txt") if r[:3] in FAST_T2])
+def test_table2_multilevel_iterations(a, p, m, expect):
+    _table_case("table2", a, p, m, expect, levels=0)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("a,p,m,expect", [r for r in read_table("table2_multilevel_iters.txt") if r[:3] not in FAST_T2])
+def test_table2_multilevel_iterations_slow(a, p, m, expect):
+    _table_case("table2", a, p, m, expect, levels=0)
+
+
+@pytest.mark.parametrize("a,p,m,expect", [r for r in read_table("table1_two_level_iters.txt")
+                                          if r[:3] in {("alpha1", 1, 16), ("alpha4", 1, 16), ("alpha2", 1, 8)}])
+def test_table1_two_level_iterations(a, p, m, expect):
+    _table_case("table1", a, p, m, expect, levels=2)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("a,p,m,expect", read_table("table1_two_level_iters.txt"))
+def test_table1_two_level_iterations_all(a, p, m, expect):
+    _table_case("table1", a, p, m, expect, levels=2)
