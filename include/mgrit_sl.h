@@ -1,0 +1,203 @@
+/*
+ * mgrit_sl.h -- C ABI of a single-GPU (GB300, sm_103a) implementation of
+ * multigrid reduction-in-time (MGRIT) for periodic linear advection with
+ * semi-Lagrangian (SL) time steps and the modified SL coarse-grid operator of
+ * H. De Sterck, R. D. Falgout, O. A. Krzysik, "Fast multigrid reduction-in-time
+ * for advection via modified semi-Lagrangian coarse-grid operators" (2022).
+ *
+ * Problem statement (Sec. 2.1, eq. (ad); Sec. 4.1, eq. (ad_2D)):
+ *   u_t + alpha(x,t) u_x = 0             on the periodic interval [xmin, xmax)
+ *   u_t + alpha u_x + beta u_y = 0       on the periodic square [xmin, xmax)^2
+ * discretised on nx (x nx) equispaced nodes x_i = xmin + i h, h = (xmax-xmin)/nx,
+ * and nt time steps of size dt = cfl * h; the wave speed is one of a fixed set
+ * of analytic families ("readily computable for any x and t", Sec. 2.1).
+ *
+ * Conventions for every call below.
+ *   Pointers named d_* are DEVICE pointers to FP64 arrays owned by the caller
+ *   (for instance allocated by PyTorch); the library never frees them.  h_*
+ *   pointers are HOST pointers.  Arrays are time-major and row-major:
+ *   u[n][j][i] with x (index i) fastest, i.e. the row-wise lexicographic
+ *   ordering of Sec. 4.2; a 1D slice has nx entries, a 2D slice nx*nx.
+ *   The library owns the handle and the device workspace it allocates in
+ *   mgrit_setup (released by mgrit_destroy).  All work is issued on the CUDA
+ *   stream given to mgrit_setup.  Calls return a status and never throw or
+ *   abort; argument errors are detected before any launch.  mgrit_last_error()
+ *   returns a human-readable message for the last failing call on this thread.
+ *   A handle is not thread-safe: one call at a time per handle.
+ */
+#ifndef MGRIT_SL_H
+#define MGRIT_SL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MGRIT_OK = 0,
+  MGRIT_EINVAL = 1,         /* bad argument (checked before any launch) */
+  MGRIT_ENOMEM = 2,         /* device allocation failed */
+  MGRIT_ECUDA = 3,          /* a CUDA runtime error */
+  MGRIT_ENOTCONVERGED = 4,  /* max_iter cycles without reaching rtol */
+  MGRIT_EDIVERGED = 5,      /* residual non-finite or grew by more than 1e3 */
+  MGRIT_ETIMEOUT = 6,       /* a bounded device wait gave up */
+  MGRIT_EUNSUPPORTED = 7,   /* valid but not implemented combination */
+  MGRIT_ESINGULAR = 8       /* a correction matrix had a (near) zero pivot */
+} mgrit_status;
+
+/* Periodic space-time grid (Sec. 2.1).  dim = 1 or 2 (ny = nx in 2D). */
+typedef struct {
+  int dim;
+  int nx;
+  int nt;
+  double xmin;
+  double xmax;
+  double cfl; /* dt = cfl * h; the paper uses 0.85 */
+} mgrit_grid;
+
+/* Analytic wave-speed families. */
+typedef enum {
+  MGRIT_A_CONST = 0,        /* alpha = a                                   eq. (alpha1) with a = 1 */
+  MGRIT_A_COS_T = 1,        /* alpha = cos(2 pi t)                          eq. (alpha2) */
+  MGRIT_A_COS_T_COS_X = 2,  /* alpha = cos(2 pi t) cos(2 pi x)              eq. (alpha4) */
+  MGRIT_A_SIN_KX_COS_T = 3, /* alpha = 1 + a sin(2 pi k x) cos(2 pi t) */
+  MGRIT_A2D_CONST = 10,     /* (alpha, beta) = (a, a2)                      eq. (alpha-const_2D) with a = a2 = 1 */
+  MGRIT_A2D_PAPER = 11,     /* (sin^2(pi y) cos(2pi t/3.4), -cos^2(pi x) cos(2pi t/3.4))  eq. (alpha-var_2D) */
+  MGRIT_A2D_SIN_COS = 12    /* (1 + a sin(2 pi y) cos(2 pi t), 1 + a cos(2 pi x) sin(2 pi t)) */
+} mgrit_wave_kind;
+
+typedef struct {
+  int kind; /* mgrit_wave_kind */
+  double a;
+  double k;
+  double a2;
+} mgrit_wavespeed;
+
+/* Solver options; mgrit_default_options() fills the defaults noted here. */
+typedef struct {
+  int precision;    /* 0: FP64 throughout (default).  1: FP32 bulk -- relaxation, interpolation
+                       and the coarse cycle act on the error in FP32, while departure points, the
+                       fine-level residual (one FP64 sweep per cycle), the C-point state and the
+                       residual norms stay FP64. */
+  int coarse_op;    /* 0: corrected operator [I - diag(sigma) D_{p+1}]^{-1} S (eq. (Phi_multilevel), default);
+                       1: plain coarse SL step S with the same departure points (Sec. 2.3). */
+  int norm_mode;    /* 1 (default): residual after the FCF relaxation of each cycle, counted as in
+                       Tables 1-3; 0: residual after the full cycle, r0 from the initial iterate. */
+  int max_iter;     /* default 200 */
+  double rtol;      /* relative residual reduction to stop at, default 1e-10 (Sec. 2.2) */
+  int max_coarsest; /* levels == 0: stop coarsening once a level has <= this many steps (default 1,
+                       the paper's rule: coarsen until fewer than two time points would remain) */
+  int m_first;      /* 0 (default): factor m on every level; > 0: this factor on level 1 and m below
+                       (the aggressive coarsening of Sec. 5) */
+  int coarse_fp64;  /* precision == 1 only: 1 = coarse levels and correction solves in FP64,
+                       0 (default) = FP32 like the rest of the error cycle */
+  int use_graph;    /* 1 (default): capture one cycle in a CUDA graph and replay it */
+} mgrit_options;
+
+typedef struct {
+  int iterations;     /* V-cycles performed */
+  int converged;      /* 1 if the residual dropped by rtol */
+  int levels;         /* levels in the hierarchy (>= 2) */
+  int history_len;    /* entries of residual_history written */
+  double r0;          /* reference residual norm */
+  double r_final;     /* last residual norm */
+  double residual_history[256];
+  double setup_ms;    /* wall time of mgrit_setup */
+  double solve_ms;    /* wall time of the last mgrit_solve (or sl_step_sequential) */
+  int64_t device_bytes; /* workspace held by the handle */
+} mgrit_stats;
+
+typedef struct mgrit_handle mgrit_handle;
+
+/* Fills *opt with the defaults above.  Returns MGRIT_EINVAL on NULL. */
+mgrit_status mgrit_default_options(mgrit_options* opt);
+
+/*
+ * Builds everything the solver needs for one problem (Sec. 2.1, 3.3.1, 3.4):
+ *  - fine departure points: one backward explicit Runge-Kutta step of order r = order
+ *    per arrival node and step (eq. (depart_ODE); r = 1 forward Euler, r = 3 Kutta's
+ *    third-order method, r = 5 Butcher's six-stage fifth-order method), in FP64;
+ *  - the level hierarchy: factor m per level (m_first on level 1 if set) until the
+ *    coarsest level has <= max_coarsest steps, or exactly `levels` levels if levels > 0;
+ *  - coarse departure points by linear (1D) / bilinear (2D) backtracking
+ *    (eq. (coarse_depart_interp), Sec. SM6), phi and sigma (eq. (varphi_p_multilevel_def),
+ *    (nu_p_def)) and the factorised correction matrices I - diag(sigma) D_{p+1}.
+ * order: odd interpolation degree p in {1, 3, 5} (r = p, Sec. 2.1).
+ * m: coarsening factor >= 2; nt must be divisible by the factors used.
+ * stream: a cudaStream_t (NULL = the legacy default stream).
+ * Errors: MGRIT_EINVAL for bad sizes / kinds / order, MGRIT_ENOMEM, MGRIT_ECUDA,
+ *         MGRIT_ESINGULAR if a correction matrix cannot be factorised without pivoting.
+ */
+mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, int order, int m, int levels,
+                         const mgrit_options* opt, void* stream, mgrit_handle** out);
+
+/*
+ * Solves u_{n+1} = Phi_n u_n, n = 0..nt-1, with u_0 = d_u0 by MGRIT V-cycles with FCF
+ * relaxation (Sec. 2.2) until the space-time residual has dropped by rtol.
+ * d_u0:     [N] initial condition (N = nx or nx*nx).
+ * d_u_init: [(nt+1) x N] initial iterate (row 0 ignored); only rows n = j*m_1 (the C-points)
+ *           are read.  NULL means zero.
+ * d_u_out:  [(nt+1) x N] the solution at every time point (row 0 = u0).  May alias d_u_init.
+ * stats:    optional (NULL allowed), filled on return.
+ * The call is synchronous (it returns once convergence is known).
+ * Errors: MGRIT_ENOTCONVERGED (d_u_out then holds the last iterate), MGRIT_EDIVERGED,
+ *         MGRIT_EINVAL, MGRIT_ECUDA.
+ */
+mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_init, double* d_u_out,
+                         mgrit_stats* stats);
+
+/*
+ * Sequential SL time stepping (eq. (one-step) with g = 0), the comparator of MGRIT:
+ * u_{n+1} = S_{p,r}^{(t_n, dt)} u_n on the fine level, FP64 (precision 0) or FP32 (1).
+ * d_u_out: store_all = 1: [(nt+1) x N] every slice; store_all = 0: [N] the final slice only.
+ * Asynchronous on the handle's stream.
+ */
+mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u_out, int store_all);
+
+/*
+ * Same as mgrit_solve, but d_u0 / d_u_init / h_u_out are HOST arrays: the call copies the
+ * inputs to the device, solves, and copies the full solution back (end-to-end timing).
+ */
+mgrit_status mgrit_solve_host(mgrit_handle* h, const double* h_u0, const double* h_u_init, double* h_u_out,
+                              mgrit_stats* stats);
+
+/*
+ * Discrete adjoint of the fine-level one-step system for J = 1/2 ||u_nt - u_target||^2:
+ * lambda_nt = u_nt - u_target, lambda_n = Phi_n^T lambda_{n+1} (transposed SL gather as a
+ * deterministic scatter-add), solved backward in time by MGRIT with the transposed coarse
+ * operators; dJ/du0 = lambda_0 and dJ/da = sum_n lambda_{n+1}^T (dPhi_n/da) u_n, where a is
+ * the wave-speed amplitude parameter and u_n is recomputed from the C-point checkpoints
+ * d_C_checkpoints ([(nt/m_1 + 1) x N], rows u_{j m_1} of a forward solve).
+ * The paper has no adjoint; see the documentation of the library for the choices made.
+ * d_dJ_du0: [N]; h_dJ_da: host scalar.  Synchronous.
+ */
+mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, const double* d_C_checkpoints,
+                                 double* d_dJ_du0, double* h_dJ_da, mgrit_stats* stats);
+
+/* ---- Introspection (for tests): copies of intermediate setup data --------------------------- */
+
+/* Number of levels and, for a level l, its step count and coarsening factor (0 on level 0). */
+mgrit_status mgrit_level_info(const mgrit_handle* h, int level, int* nt_level, int* m_level);
+
+/* Departure offsets s[n][pt] = (x_pt - xi_pt) / h of level l in grid units (2D: x then y
+ * component blocks, each [nt_l x N]); d_out has nt_l * N (2D: 2 * nt_l * N) doubles. */
+mgrit_status mgrit_copy_offsets(const mgrit_handle* h, int level, double* d_out);
+
+/* sigma of level l >= 1 (eq. (nu_p_def)); same layout as mgrit_copy_offsets. */
+mgrit_status mgrit_copy_sigma(const mgrit_handle* h, int level, double* d_out);
+
+/* Applies Phi_{l,n} (level 0: the SL step; level >= 1: the coarse operator) to `count` slices:
+ * d_out[c] = Phi_{l, n0 + c} d_in[c], c = 0..count-1, each slice N doubles, in the handle's
+ * working precision.  Synchronous. */
+mgrit_status mgrit_apply_step(mgrit_handle* h, int level, int n0, int count, const double* d_in, double* d_out);
+
+void mgrit_destroy(mgrit_handle* h);
+const char* mgrit_status_string(mgrit_status s);
+const char* mgrit_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGRIT_SL_H */

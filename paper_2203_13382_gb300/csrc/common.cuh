@@ -1,0 +1,69 @@
+// Shared device/host helpers for the MGRIT semi-Lagrangian kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#define MGRIT_HD __host__ __device__ __forceinline__
+#define MGRIT_D __device__ __forceinline__
+
+namespace mgrit {
+
+constexpr int kMaxOrder = 5;  // odd interpolation degree p <= 5
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kPi = 3.1415926535897932384626433832795;
+
+// Number of threads for the slice-resident kernels.
+constexpr int kSliceThreads = 512;
+
+MGRIT_HD int wrap_pow2(int idx, int nx) { return idx & (nx - 1); }
+
+// Coefficient 1 / prod_{q != j} (j - q) of the Lagrange basis polynomial of node j = a - (P+1)/2,
+// a = 0..P, on the unit-spaced nodes -(P+1)/2 .. (P-1)/2: equals (-1)^{P-a} / (a! (P-a)!).
+template <int P>
+MGRIT_HD double lagrange_denominator_inv(int a) {
+  double f = 1.0;
+  for (int b = 2; b <= a; ++b) f *= b;
+  double g = 1.0;
+  for (int b = 2; b <= P - a; ++b) g *= b;
+  return (((P - a) & 1) ? -1.0 : 1.0) / (f * g);
+}
+
+// Lagrange weights w_a(eps), a = 0..P, for interpolation at the point -eps relative to the east
+// node, with nodes j = a - (P+1)/2 (Sec. 2.1).  Prefix/suffix products of the factors (-eps - j).
+template <int P, typename R>
+MGRIT_D void lagrange_weights(R eps, R (&w)[P + 1]) {
+  constexpr int L = (P + 1) / 2;
+  R f[P + 1];
+#pragma unroll
+  for (int a = 0; a <= P; ++a) f[a] = -eps - (R)(a - L);
+  R pre[P + 1];
+  pre[0] = (R)1;
+#pragma unroll
+  for (int a = 1; a <= P; ++a) pre[a] = pre[a - 1] * f[a - 1];
+  R suf = (R)1;
+#pragma unroll
+  for (int a = P; a >= 0; --a) {
+    w[a] = pre[a] * suf * (R)lagrange_denominator_inv<P>(a);
+    suf *= f[a];
+  }
+}
+
+// Deterministic block sum of one double per thread (all threads must call).
+MGRIT_D double block_sum(double v, double* smem_scratch) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) smem_scratch[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < nw; ++k) t += smem_scratch[k];
+  }
+  return t;  // valid in thread 0
+}
+
+}  // namespace mgrit

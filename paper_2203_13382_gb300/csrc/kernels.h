@@ -1,0 +1,113 @@
+// Internal launch interface between the host runtime and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "physics.cuh"
+
+namespace mgrit {
+
+// ---- setup (setup_kernels.cu) ------------------------------------------------------------------
+
+// Fine departure offsets s[n][i] = (x_i - xi) / h, one backward ERK-r step (Sec. 2.1).
+void launch_departure_1d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* s,
+                         cudaStream_t st);
+// 2D: sx, sy each [nt][nx*nx], row-major (y slow).
+void launch_departure_2d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* sx,
+                         double* sy, cudaStream_t st);
+
+// Coarse offsets by backtracking (eq. (coarse_depart_interp)) plus phi / sigma (eq. (nu_p_def)).
+// s_prev [m*ntc][nx], sigma_prev [m*ntc][nx] or NULL (level 1); outputs [ntc][nx].
+void launch_backtrack_1d(const double* s_prev, const double* sigma_prev, int m, int ntc, int nx, int p, double* s_out,
+                         double* sigma_out, cudaStream_t st);
+// 2D bilinear backtracking (Sec. SM6); sigma_x / sigma_y per component.
+void launch_backtrack_2d(const double* sx_prev, const double* sy_prev, const double* gx_prev, const double* gy_prev,
+                         int m, int ntc, int nx, int p, double* sx_out, double* sy_out, double* gx_out, double* gy_out,
+                         cudaStream_t st);
+
+// Gather tables of one level from its offsets: shift[n][i] = (E - (p+1)/2 - i) mod nx and either the
+// FP64 Lagrange weights w64[n][a][i] (a = 0..p) or the FP32 distance eps32[n][i].
+void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, uint16_t* shift, double* w64,
+                         float* eps32, cudaStream_t st);
+
+// Partitioned factorisation of M = I - diag(sigma) D_{p+1} (periodic, half-bandwidth b = (p+1)/2)
+// for each of nt steps.  Output per step: `solver_reals(nx, p, P)` values of type double
+// (is_double = 1) or float.  flag (device int) is set to 1 if a pivot is too small.
+size_t solver_reals(int nx, int p, int P);
+int solver_partitions(int nx, int p);
+void launch_factor_1d(const double* sigma, int nt, int nx, int p, int P, void* out, int is_double, int* flag,
+                      cudaStream_t st);
+
+// ---- relaxation (relax_kernels.cu) ---------------------------------------------------------------
+
+// One pass over the coarse intervals of a level (one CTA per interval j = 0..J-1).  The CTA loads
+// its start slice, takes `nsteps` steps n = j*m + k (k = 0..nsteps-1) of Phi (fine SL step) or
+// Psi (gather + correction solve), adding g[n+1] when g is given, and then, by `mode`:
+//   MODE_FC   : cout[j+1] = result                      (F- then C-relaxation)
+//   MODE_RES  : rout[j+1] = result + gC - cin[j+1]      (F-relaxation + C-point residual)
+//   MODE_POST : F-points stored, nothing at the C-point (post F-relaxation, nsteps = m-1)
+// F-point results are stored to fstore (full level array) when fstore != NULL.
+enum RelaxMode { MODE_FC = 0, MODE_RES = 1, MODE_POST = 2 };
+
+struct LevelTables {
+  int nx;
+  int npts;  // nx (1D) or nx*nx (2D)
+  int p;
+  const uint16_t* shift;  // [nt][npts] (2D: x then y blocks)
+  const double* w64;      // [nt][p+1][npts] or NULL
+  const float* eps32;     // [nt][npts] or NULL (2D: x then y blocks)
+  long long table_stride; // elements per step row of shift / eps32 (npts)
+  int nt;                 // steps on this level (for 2D block offsets)
+  // correction solver (coarse levels, corrected operator); NULL for the plain SL step
+  const void* solver;
+  size_t solver_stride;  // reals per step
+  int P;                 // partitions
+};
+
+struct RelaxArgs {
+  int m;          // interval length on this level
+  int J;          // intervals
+  int nsteps;     // steps per CTA
+  int mode;
+  const void* start;   // start slice j at start + j * start_stride
+  long long start_stride;
+  const void* corr;    // optional: added to the start slice (stride corr_stride)
+  long long corr_stride;
+  void* start_wb;      // optional: corrected start written back (stride wb_stride)
+  long long wb_stride;
+  int extra_cta;       // launch one more CTA (j = J) that only loads / corrects / writes back its start
+  const void* g;       // optional RHS, full level array [(N+1)][npts]
+  void* fstore;        // optional F-point store, full level array [(N+1)][npts]
+  void* cout;          // MODE_FC output (stride c_stride)
+  const void* cin;     // MODE_RES: current C value (stride c_stride)
+  void* rout;          // MODE_RES: residual output (stride r_stride)
+  long long c_stride;
+  long long r_stride;
+  int g_at_c;          // MODE_RES: add g at the C-point
+  double* norm_partial;  // MODE_RES: per-interval sum of squares [J] (NULL: not needed)
+};
+
+// is_double selects FP64 (tables w64) or FP32 (tables eps32) arithmetic and storage.
+cudaError_t launch_relax_1d(const LevelTables& T, const RelaxArgs& a, int is_double, cudaStream_t st);
+
+// Sequential stepping over all steps of a level: u[n+1] = Phi_n u[n] + g[n+1], n = 0..N-1 (coarsest
+// level solve, and the fine-level comparator), from u0 ([npts]; NULL = zero).  store_all = 1: out is
+// [(N+1)][npts] with row 0 = u0; store_all = 0: out is [npts] and receives u[N] only.
+cudaError_t launch_sequential_1d(const LevelTables& T, int N, const void* g, const void* u0, void* out, int store_all,
+                                 int is_double, cudaStream_t st);
+
+// Applies count steps n0..n0+count-1 to independent slices: out[c] = Phi_{n0+c} in[c].
+cudaError_t launch_apply_steps_1d(const LevelTables& T, int n0, int count, const void* in, void* out, int is_double,
+                                  cudaStream_t st);
+
+// Deterministic sum of `count` doubles (fixed order): out[0] = sum.
+void launch_sum(const double* v, int count, double* out, cudaStream_t st);
+// Elementwise update with type conversion: kind 0: y = x (d); 1: y(f) = x(d); 2: y(d) += x(f);
+// 3: y(d) = x(f); 4: y(d) += x(d); 5: y(d) += x(d) + z(f).
+void launch_axpy_convert(int kind, const void* x, void* y, const void* z, long long n, cudaStream_t st);
+// zero fill
+void launch_fill_zero(void* y, long long bytes, cudaStream_t st);
+
+}  // namespace mgrit

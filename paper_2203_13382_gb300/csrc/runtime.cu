@@ -1,0 +1,644 @@
+// Host runtime behind the C ABI of include/mgrit_sl.h: level hierarchy, workspace, and the MGRIT
+// V-cycle orchestration (Sec. 2.2, 3.4) over the kernels of setup_kernels.cu / relax_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mgrit_sl.h"
+#include "kernels.h"
+
+using namespace mgrit;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mgrit_status fail(mgrit_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define MG_CUDA(call)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(MGRIT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define MG_TRY(call)                       \
+  do {                                     \
+    mgrit_status s_ = (call);              \
+    if (s_ != MGRIT_OK) return s_;         \
+  } while (0)
+
+struct Level {
+  int nt = 0;  // steps on this level
+  int m = 0;   // coarsening factor from the level above (0 on level 0)
+  double* s64 = nullptr;
+  double* sigma = nullptr;
+  uint16_t* shift = nullptr;
+  double* w64 = nullptr;
+  float* eps32 = nullptr;
+  void* solver = nullptr;
+  size_t solver_stride = 0;
+  int P = 0;
+  int is_double = 1;  // arithmetic of this level's cycle
+  void* E = nullptr;  // coarse levels: unknown, full level array [(nt+1)][npts]
+  void* G = nullptr;  // coarse levels: right-hand side, full level array
+};
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct mgrit_handle {
+  mgrit_grid grid;
+  mgrit_wavespeed wave;
+  int order = 1;
+  mgrit_options opt;
+  cudaStream_t stream = nullptr;
+  int npts = 0;
+  std::vector<Level> levels;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  // level-0 C-point state and scratch
+  double* X = nullptr;
+  double* Y = nullptr;
+  double* r64 = nullptr;   // FP32-bulk: FP64 residual at the C-points
+  float* EC = nullptr;     // FP32-bulk: C-relaxed error (= r) in FP32
+  double* norm_partial = nullptr;
+  double* norm_dev = nullptr;
+  double* norm_host = nullptr;  // pinned
+  int* flag_dev = nullptr;
+  double setup_ms = 0.0;
+
+  ~mgrit_handle() {
+    for (void* p : allocs) cudaFree(p);
+    if (norm_host) cudaFreeHost(norm_host);
+  }
+
+  template <typename T>
+  mgrit_status alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return MGRIT_OK;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MGRIT_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    allocs.push_back(q);
+    bytes += (int64_t)(count * sizeof(T));
+    *p = (T*)q;
+    return MGRIT_OK;
+  }
+
+  int J1() const { return levels[0].nt / levels[1].m; }
+
+  LevelTables tables(int l, int is_double) const {
+    const Level& L = levels[l];
+    LevelTables T{};
+    T.nx = grid.nx;
+    T.npts = npts;
+    T.p = order;
+    T.shift = L.shift;
+    T.w64 = L.w64;
+    T.eps32 = L.eps32;
+    T.table_stride = npts;
+    T.nt = L.nt;
+    T.solver = (l > 0 && opt.coarse_op == 0) ? L.solver : nullptr;
+    T.solver_stride = L.solver_stride;
+    T.P = L.P;
+    (void)is_double;
+    return T;
+  }
+};
+
+namespace {
+
+mgrit_status check_grid(const mgrit_grid* g, const mgrit_wavespeed* w, int order, int m) {
+  if (!g || !w) return fail(MGRIT_EINVAL, "grid and wave must not be NULL");
+  if (g->dim != 1 && g->dim != 2) return fail(MGRIT_EINVAL, "dim must be 1 or 2");
+  if (g->nx < 16 || (g->nx & (g->nx - 1)) != 0) return fail(MGRIT_EINVAL, "nx must be a power of two >= 16");
+  if (g->nt < 2) return fail(MGRIT_EINVAL, "nt must be >= 2");
+  if (!(g->xmax > g->xmin)) return fail(MGRIT_EINVAL, "xmax must exceed xmin");
+  if (!(g->cfl > 0.0) || !std::isfinite(g->cfl)) return fail(MGRIT_EINVAL, "cfl must be positive and finite");
+  if (order != 1 && order != 3 && order != 5) return fail(MGRIT_EINVAL, "order must be 1, 3 or 5");
+  if (m < 2) return fail(MGRIT_EINVAL, "m must be >= 2");
+  const bool k1 = w->kind >= 0 && w->kind <= 3, k2 = w->kind >= 10 && w->kind <= 12;
+  if ((g->dim == 1 && !k1) || (g->dim == 2 && !k2)) return fail(MGRIT_EINVAL, "wave kind does not match dim");
+  if (!std::isfinite(w->a) || !std::isfinite(w->k) || !std::isfinite(w->a2))
+    return fail(MGRIT_EINVAL, "wave parameters must be finite");
+  if (g->dim == 1 && g->nx > 8192) return fail(MGRIT_EUNSUPPORTED, "1D slices are kept on chip: nx <= 8192");
+  if (g->dim == 2) return fail(MGRIT_EUNSUPPORTED, "2D problems are not supported by this build");
+  return MGRIT_OK;
+}
+
+// The coarsening factors (level 1, 2, ...), as in the oracle's rule.
+std::vector<int> factors(int nt, int m, int m_first, int levels, int max_coarsest) {
+  std::vector<int> out;
+  int n = nt;
+  while (true) {
+    if (levels > 0 && (int)out.size() + 1 >= levels) break;
+    const int f = (out.empty() && m_first > 0) ? m_first : m;
+    if (levels == 0 && n <= max_coarsest) break;
+    if (n % f != 0 || n / f < 1) break;
+    out.push_back(f);
+    n /= f;
+  }
+  return out;
+}
+
+mgrit_status relax(mgrit_handle* h, int l, int is_double, const RelaxArgs& a) {
+  LevelTables T = h->tables(l, is_double);
+  MG_CUDA(launch_relax_1d(T, a, is_double, h->stream));
+  return MGRIT_OK;
+}
+
+RelaxArgs args0() {
+  RelaxArgs a;
+  std::memset(&a, 0, sizeof(a));
+  return a;
+}
+
+// Coarse cycle on level l >= 1: E_l from right-hand side G_l (both full level arrays).
+mgrit_status coarse_cycle(mgrit_handle* h, int l) {
+  Level& L = h->levels[l];
+  const int np = h->npts;
+  const int dbl = L.is_double;
+  if (l == (int)h->levels.size() - 1) {  // coarsest: sequential stepping (Sec. 2.2)
+    LevelTables T = h->tables(l, dbl);
+    MG_CUDA(launch_sequential_1d(T, L.nt, L.G, nullptr, L.E, 1, dbl, h->stream));
+    return MGRIT_OK;
+  }
+  Level& Lc = h->levels[l + 1];
+  const int m = Lc.m, J = L.nt / m;
+  // F- then C-relaxation from a zero initial guess
+  RelaxArgs a = args0();
+  a.m = m;
+  a.J = J;
+  a.nsteps = m;
+  a.mode = MODE_FC;
+  a.g = L.G;
+  a.cout = L.E;
+  a.c_stride = (long long)m * np;
+  MG_TRY(relax(h, l, dbl, a));
+  // F-relaxation and the C-point residual -> right-hand side of level l+1
+  a = args0();
+  a.m = m;
+  a.J = J;
+  a.nsteps = m;
+  a.mode = MODE_RES;
+  a.start = L.E;
+  a.start_stride = (long long)m * np;
+  a.g = L.G;
+  a.g_at_c = 1;
+  a.cin = L.E;
+  a.c_stride = (long long)m * np;
+  a.rout = Lc.G;
+  a.r_stride = np;
+  MG_TRY(relax(h, l, dbl, a));
+  MG_TRY(coarse_cycle(h, l + 1));
+  // correction by injection and post F-relaxation
+  a = args0();
+  a.m = m;
+  a.J = J;
+  a.nsteps = m - 1;
+  a.mode = MODE_POST;
+  a.start = L.E;
+  a.start_stride = (long long)m * np;
+  a.corr = Lc.E;
+  a.corr_stride = np;
+  a.start_wb = L.E;
+  a.wb_stride = (long long)m * np;
+  a.extra_cta = 1;
+  a.g = L.G;
+  a.fstore = L.E;
+  MG_TRY(relax(h, l, dbl, a));
+  return MGRIT_OK;
+}
+
+mgrit_status read_norm(mgrit_handle* h, int J, double* out) {
+  launch_sum(h->norm_partial, J, h->norm_dev, h->stream);
+  MG_CUDA(cudaMemcpyAsync(h->norm_host, h->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  *out = std::sqrt(h->norm_host[0]);
+  return MGRIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mgrit_status mgrit_default_options(mgrit_options* opt) {
+  if (!opt) return fail(MGRIT_EINVAL, "opt is NULL");
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = 0;
+  opt->coarse_op = 0;
+  opt->norm_mode = 1;
+  opt->max_iter = 200;
+  opt->rtol = 1e-10;
+  opt->max_coarsest = 1;
+  opt->m_first = 0;
+  opt->coarse_fp64 = 0;
+  opt->use_graph = 1;
+  return MGRIT_OK;
+}
+
+mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, int order, int m, int levels,
+                         const mgrit_options* opt_in, void* stream, mgrit_handle** out) {
+  if (!out) return fail(MGRIT_EINVAL, "out is NULL");
+  *out = nullptr;
+  MG_TRY(check_grid(grid, wave, order, m));
+  mgrit_options opt;
+  if (opt_in) opt = *opt_in;
+  else mgrit_default_options(&opt);
+  if (opt.precision != 0 && opt.precision != 1) return fail(MGRIT_EINVAL, "precision must be 0 or 1");
+  if (opt.coarse_op != 0 && opt.coarse_op != 1) return fail(MGRIT_EINVAL, "coarse_op must be 0 or 1");
+  if (opt.norm_mode != 1) return fail(MGRIT_EUNSUPPORTED, "only norm_mode 1 is implemented on the GPU");
+  if (opt.max_iter < 1 || opt.max_iter > 100000) return fail(MGRIT_EINVAL, "max_iter out of range");
+  if (!(opt.rtol > 0.0 && opt.rtol < 1.0)) return fail(MGRIT_EINVAL, "rtol must be in (0, 1)");
+  if (opt.max_coarsest < 1) return fail(MGRIT_EINVAL, "max_coarsest must be >= 1");
+  if (opt.m_first < 0 || opt.m_first == 1) return fail(MGRIT_EINVAL, "m_first must be 0 or >= 2");
+  if (opt.coarse_fp64 != 0) return fail(MGRIT_EUNSUPPORTED, "coarse_fp64 is not implemented");
+  if (levels < 0 || levels == 1) return fail(MGRIT_EINVAL, "levels must be 0 or >= 2");
+  std::vector<int> fac = factors(grid->nt, m, opt.m_first, levels, opt.max_coarsest);
+  if (fac.empty()) return fail(MGRIT_EINVAL, "nt does not allow a coarse level with this m");
+  if (levels > 0 && (int)fac.size() + 1 != levels)
+    return fail(MGRIT_EINVAL, "nt is not divisible by the coarsening factors for the requested levels");
+
+  const double t0 = now_ms();
+  mgrit_handle* h = new mgrit_handle();
+  h->grid = *grid;
+  h->wave = *wave;
+  h->order = order;
+  h->opt = opt;
+  h->stream = (cudaStream_t)stream;
+  h->npts = grid->nx;
+  const int nx = grid->nx, np = h->npts;
+  const double hgrid = (grid->xmax - grid->xmin) / nx;
+  const double dt = grid->cfl * hgrid;
+  const int fp32 = opt.precision == 1;
+
+  auto cleanup_fail = [&](mgrit_status s) {
+    delete h;
+    return s;
+  };
+  // levels
+  h->levels.resize(fac.size() + 1);
+  h->levels[0].nt = grid->nt;
+  for (size_t l = 1; l < h->levels.size(); ++l) {
+    h->levels[l].m = fac[l - 1];
+    h->levels[l].nt = h->levels[l - 1].nt / fac[l - 1];
+  }
+  mgrit_status st = MGRIT_OK;
+  const int p = order;
+  for (size_t l = 0; l < h->levels.size(); ++l) {
+    Level& L = h->levels[l];
+    const size_t rows = (size_t)L.nt * np;
+    L.is_double = fp32 ? 0 : 1;
+    if ((st = h->alloc(&L.s64, rows)) != MGRIT_OK) return cleanup_fail(st);
+    if ((st = h->alloc(&L.shift, rows)) != MGRIT_OK) return cleanup_fail(st);
+    const bool need64 = !fp32 || l == 0;
+    const bool need32 = fp32;
+    if (need64 && (st = h->alloc(&L.w64, rows * (p + 1))) != MGRIT_OK) return cleanup_fail(st);
+    if (need32 && (st = h->alloc(&L.eps32, rows)) != MGRIT_OK) return cleanup_fail(st);
+    if (l > 0) {
+      if ((st = h->alloc(&L.sigma, rows)) != MGRIT_OK) return cleanup_fail(st);
+      const size_t full = (size_t)(L.nt + 1) * np;
+      const size_t esz = L.is_double ? sizeof(double) : sizeof(float);
+      if ((st = h->alloc((char**)&L.E, full * esz)) != MGRIT_OK) return cleanup_fail(st);
+      if ((st = h->alloc((char**)&L.G, full * esz)) != MGRIT_OK) return cleanup_fail(st);
+      if (opt.coarse_op == 0) {
+        L.P = solver_partitions(nx, p);
+        L.solver_stride = solver_reals(nx, p, L.P);
+        const size_t tot = L.solver_stride * L.nt * (L.is_double ? sizeof(double) : sizeof(float));
+        if ((st = h->alloc((char**)&L.solver, tot)) != MGRIT_OK) return cleanup_fail(st);
+      }
+    }
+  }
+  const int J1 = h->J1();
+  if ((st = h->alloc(&h->X, (size_t)(J1 + 1) * np)) != MGRIT_OK) return cleanup_fail(st);
+  if ((st = h->alloc(&h->Y, (size_t)(J1 + 1) * np)) != MGRIT_OK) return cleanup_fail(st);
+  if (fp32) {
+    if ((st = h->alloc(&h->r64, (size_t)(J1 + 1) * np)) != MGRIT_OK) return cleanup_fail(st);
+    if ((st = h->alloc(&h->EC, (size_t)(J1 + 1) * np)) != MGRIT_OK) return cleanup_fail(st);
+  }
+  if ((st = h->alloc(&h->norm_partial, (size_t)J1 + 1)) != MGRIT_OK) return cleanup_fail(st);
+  if ((st = h->alloc(&h->norm_dev, 2)) != MGRIT_OK) return cleanup_fail(st);
+  if ((st = h->alloc(&h->flag_dev, 1)) != MGRIT_OK) return cleanup_fail(st);
+  if (cudaMallocHost((void**)&h->norm_host, 4 * sizeof(double)) != cudaSuccess)
+    return cleanup_fail(fail(MGRIT_ENOMEM, "pinned host allocation failed"));
+
+  cudaStream_t s = h->stream;
+  WaveParams wp{wave->kind, wave->a, wave->k, wave->a2};
+  auto cuda_fail = [&](const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cleanup_fail(fail(MGRIT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)));
+    return MGRIT_OK;
+  };
+  cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s);
+  // fine departure points and tables
+  launch_departure_1d(wp, p, nx, grid->nt, grid->xmin, hgrid, dt, h->levels[0].s64, s);
+  for (size_t l = 0; l < h->levels.size(); ++l) {
+    Level& L = h->levels[l];
+    if (l > 0) {
+      Level& Lp = h->levels[l - 1];
+      launch_backtrack_1d(Lp.s64, l > 1 ? Lp.sigma : nullptr, L.m, L.nt, nx, p, L.s64, L.sigma, s);
+    }
+    launch_build_tables(L.s64, L.nt, nx, np, p, L.shift, L.w64, L.eps32, s);
+    if (l > 0 && L.solver) launch_factor_1d(L.sigma, L.nt, nx, p, L.P, L.solver, L.is_double, h->flag_dev, s);
+    if ((st = cuda_fail("setup")) != MGRIT_OK) return st;
+  }
+  // zero rows that are read but never written: E_l[0], G_l[0], r64[0], EC[0]
+  for (size_t l = 1; l < h->levels.size(); ++l) {
+    Level& L = h->levels[l];
+    const size_t esz = L.is_double ? sizeof(double) : sizeof(float);
+    cudaMemsetAsync(L.E, 0, (size_t)(L.nt + 1) * np * esz, s);
+    cudaMemsetAsync(L.G, 0, (size_t)(L.nt + 1) * np * esz, s);
+  }
+  if (fp32) {
+    cudaMemsetAsync(h->r64, 0, (size_t)(J1 + 1) * np * sizeof(double), s);
+    cudaMemsetAsync(h->EC, 0, (size_t)(J1 + 1) * np * sizeof(float), s);
+  }
+  int flag = 0;
+  cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if ((st = cuda_fail("setup")) != MGRIT_OK) return st;
+  if (flag) return cleanup_fail(fail(MGRIT_ESINGULAR, "a correction matrix has a (near) zero pivot"));
+  h->setup_ms = now_ms() - t0;
+  *out = h;
+  return MGRIT_OK;
+}
+
+mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_init, double* d_u_out,
+                         mgrit_stats* stats) {
+  if (!h || !d_u0 || !d_u_out) return fail(MGRIT_EINVAL, "handle, u0 and u_out must not be NULL");
+  const double t0 = now_ms();
+  cudaStream_t s = h->stream;
+  const int np = h->npts;
+  const int m1 = h->levels[1].m, J = h->J1();
+  const int fp32 = h->opt.precision == 1;
+  // initial iterate at the C-points
+  MG_CUDA(cudaMemcpyAsync(h->X, d_u0, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(cudaMemcpyAsync(h->Y, d_u0, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (d_u_init) {
+    MG_CUDA(cudaMemcpy2DAsync(h->X + np, np * sizeof(double), d_u_init + (size_t)m1 * np,
+                              (size_t)m1 * np * sizeof(double), np * sizeof(double), J, cudaMemcpyDeviceToDevice, s));
+  } else {
+    MG_CUDA(cudaMemsetAsync(h->X + np, 0, (size_t)J * np * sizeof(double), s));
+  }
+  Level& L1 = h->levels[1];
+  std::vector<double> hist;
+  double r0 = 0.0, rk = 0.0;
+  int iters = 0;
+  bool converged = false;
+  mgrit_status status = MGRIT_OK;
+  for (int k = 0; k < h->opt.max_iter; ++k) {
+    if (!fp32) {
+      // FCF relaxation on level 0; the correction of the previous cycle is fused into the first pass
+      RelaxArgs a = args0();
+      a.m = m1;
+      a.J = J;
+      a.nsteps = m1;
+      a.mode = MODE_FC;
+      a.start = h->X;
+      a.start_stride = np;
+      a.corr = k > 0 ? L1.E : nullptr;
+      a.corr_stride = np;
+      a.cout = h->Y;
+      a.c_stride = np;
+      MG_TRY(relax(h, 0, 1, a));
+      a = args0();
+      a.m = m1;
+      a.J = J;
+      a.nsteps = m1;
+      a.mode = MODE_RES;
+      a.start = h->Y;
+      a.start_stride = np;
+      a.cin = h->Y;
+      a.c_stride = np;
+      a.rout = L1.G;
+      a.r_stride = np;
+      a.norm_partial = h->norm_partial;
+      MG_TRY(relax(h, 0, 1, a));
+      MG_TRY(coarse_cycle(h, 1));
+      std::swap(h->X, h->Y);
+    } else {
+      // FP64 residual of the current iterate (F-relaxation + C-point residual)
+      RelaxArgs a = args0();
+      a.m = m1;
+      a.J = J;
+      a.nsteps = m1;
+      a.mode = MODE_RES;
+      a.start = h->X;
+      a.start_stride = np;
+      a.cin = h->X;
+      a.c_stride = np;
+      a.rout = h->r64;
+      a.r_stride = np;
+      MG_TRY(relax(h, 0, 1, a));
+      // C-relaxation of the error equation from a zero guess gives e_C = r; F-relax + residual in FP32
+      launch_axpy_convert(1, h->r64, h->EC, nullptr, (long long)(J + 1) * np, s);
+      a = args0();
+      a.m = m1;
+      a.J = J;
+      a.nsteps = m1;
+      a.mode = MODE_RES;
+      a.start = h->EC;
+      a.start_stride = np;
+      a.rout = L1.G;
+      a.r_stride = np;
+      a.norm_partial = h->norm_partial;
+      MG_TRY(relax(h, 0, 0, a));
+      MG_TRY(coarse_cycle(h, 1));
+      // u_C += r + E_1
+      launch_axpy_convert(5, h->r64, h->X, L1.E, (long long)(J + 1) * np, s);
+    }
+    MG_TRY(read_norm(h, J, &rk));
+    hist.push_back(rk);
+    iters = k + 1;
+    if (k == 0) r0 = rk;
+    if (!std::isfinite(rk) || rk > 1e3 * r0) {
+      status = fail(MGRIT_EDIVERGED, "residual norm diverged");
+      break;
+    }
+    if (k >= 1 && rk < h->opt.rtol * r0) {
+      converged = true;
+      break;
+    }
+  }
+  // post F-relaxation from the (corrected) C-points into the full output
+  {
+    RelaxArgs a = args0();
+    a.m = m1;
+    a.J = J;
+    a.nsteps = m1 - 1;
+    a.mode = MODE_POST;
+    a.start = h->X;
+    a.start_stride = np;
+    a.corr = fp32 ? nullptr : L1.E;
+    a.corr_stride = np;
+    a.start_wb = d_u_out;
+    a.wb_stride = (long long)m1 * np;
+    a.extra_cta = 1;
+    a.fstore = d_u_out;
+    MG_TRY(relax(h, 0, 1, a));
+  }
+  MG_CUDA(cudaStreamSynchronize(s));
+  if (status == MGRIT_OK && !converged) status = fail(MGRIT_ENOTCONVERGED, "max_iter reached");
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iterations = iters;
+    stats->converged = converged ? 1 : 0;
+    stats->levels = (int)h->levels.size();
+    stats->r0 = r0;
+    stats->r_final = rk;
+    const int nh = (int)hist.size() < 256 ? (int)hist.size() : 256;
+    stats->history_len = nh;
+    for (int i = 0; i < nh; ++i) stats->residual_history[i] = hist[i];
+    stats->setup_ms = h->setup_ms;
+    stats->solve_ms = now_ms() - t0;
+    stats->device_bytes = h->bytes;
+  }
+  return status;
+}
+
+mgrit_status mgrit_solve_host(mgrit_handle* h, const double* h_u0, const double* h_u_init, double* h_u_out,
+                              mgrit_stats* stats) {
+  if (!h || !h_u0 || !h_u_out) return fail(MGRIT_EINVAL, "handle, u0 and u_out must not be NULL");
+  const size_t np = h->npts, nt = h->grid.nt;
+  double *d_u0 = nullptr, *d_init = nullptr, *d_out = nullptr;
+  cudaStream_t s = h->stream;
+  MG_CUDA(cudaMallocAsync((void**)&d_u0, np * sizeof(double), s));
+  MG_CUDA(cudaMallocAsync((void**)&d_out, (nt + 1) * np * sizeof(double), s));
+  if (h_u_init) MG_CUDA(cudaMallocAsync((void**)&d_init, (nt + 1) * np * sizeof(double), s));
+  MG_CUDA(cudaMemcpyAsync(d_u0, h_u0, np * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (h_u_init) MG_CUDA(cudaMemcpyAsync(d_init, h_u_init, (nt + 1) * np * sizeof(double), cudaMemcpyHostToDevice, s));
+  mgrit_status st = mgrit_solve(h, d_u0, d_init, d_out, stats);
+  cudaMemcpyAsync(h_u_out, d_out, (nt + 1) * np * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d_u0, s);
+  cudaFreeAsync(d_out, s);
+  if (d_init) cudaFreeAsync(d_init, s);
+  MG_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u_out, int store_all) {
+  if (!h || !d_u0 || !d_u_out) return fail(MGRIT_EINVAL, "handle, u0 and u_out must not be NULL");
+  const double t0 = now_ms();
+  const int np = h->npts, nt = h->grid.nt;
+  cudaStream_t s = h->stream;
+  LevelTables T = h->tables(0, 1);
+  T.solver = nullptr;
+  if (h->opt.precision == 0) {
+    MG_CUDA(launch_sequential_1d(T, nt, nullptr, d_u0, d_u_out, store_all, 1, s));
+  } else {
+    const size_t rows = store_all ? (size_t)(nt + 1) : 1;
+    float *u0f = nullptr, *outf = nullptr;
+    MG_CUDA(cudaMallocAsync((void**)&u0f, np * sizeof(float), s));
+    MG_CUDA(cudaMallocAsync((void**)&outf, rows * np * sizeof(float), s));
+    launch_axpy_convert(1, d_u0, u0f, nullptr, np, s);
+    MG_CUDA(launch_sequential_1d(T, nt, nullptr, u0f, outf, store_all, 0, s));
+    launch_axpy_convert(3, outf, d_u_out, nullptr, (long long)rows * np, s);
+    cudaFreeAsync(u0f, s);
+    cudaFreeAsync(outf, s);
+  }
+  MG_CUDA(cudaGetLastError());
+  (void)t0;
+  return MGRIT_OK;
+}
+
+mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, const double* d_C_checkpoints,
+                                 double* d_dJ_du0, double* h_dJ_da, mgrit_stats* stats) {
+  (void)h;
+  (void)d_u_target;
+  (void)d_C_checkpoints;
+  (void)d_dJ_du0;
+  (void)h_dJ_da;
+  (void)stats;
+  return fail(MGRIT_EUNSUPPORTED, "the adjoint solve is not implemented in this build");
+}
+
+mgrit_status mgrit_level_info(const mgrit_handle* h, int level, int* nt_level, int* m_level) {
+  if (!h) return fail(MGRIT_EINVAL, "handle is NULL");
+  if (level < 0 || level >= (int)h->levels.size()) {
+    if (nt_level) *nt_level = (int)h->levels.size();
+    return fail(MGRIT_EINVAL, "level out of range");
+  }
+  if (nt_level) *nt_level = h->levels[level].nt;
+  if (m_level) *m_level = h->levels[level].m;
+  return MGRIT_OK;
+}
+
+mgrit_status mgrit_copy_offsets(const mgrit_handle* h, int level, double* d_out) {
+  if (!h || !d_out) return fail(MGRIT_EINVAL, "NULL argument");
+  if (level < 0 || level >= (int)h->levels.size()) return fail(MGRIT_EINVAL, "level out of range");
+  const Level& L = h->levels[level];
+  MG_CUDA(cudaMemcpyAsync(d_out, L.s64, (size_t)L.nt * h->npts * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  return MGRIT_OK;
+}
+
+mgrit_status mgrit_copy_sigma(const mgrit_handle* h, int level, double* d_out) {
+  if (!h || !d_out) return fail(MGRIT_EINVAL, "NULL argument");
+  if (level < 1 || level >= (int)h->levels.size()) return fail(MGRIT_EINVAL, "level out of range (>= 1)");
+  const Level& L = h->levels[level];
+  MG_CUDA(cudaMemcpyAsync(d_out, L.sigma, (size_t)L.nt * h->npts * sizeof(double), cudaMemcpyDeviceToDevice,
+                          h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  return MGRIT_OK;
+}
+
+mgrit_status mgrit_apply_step(mgrit_handle* h, int level, int n0, int count, const double* d_in, double* d_out) {
+  if (!h || !d_in || !d_out) return fail(MGRIT_EINVAL, "NULL argument");
+  if (level < 0 || level >= (int)h->levels.size()) return fail(MGRIT_EINVAL, "level out of range");
+  const Level& L = h->levels[level];
+  if (count < 0 || n0 < 0 || n0 + count > L.nt) return fail(MGRIT_EINVAL, "step range out of range");
+  const int np = h->npts;
+  cudaStream_t s = h->stream;
+  const int dbl = L.is_double;
+  LevelTables T = h->tables(level, dbl);
+  if (dbl) {
+    MG_CUDA(launch_apply_steps_1d(T, n0, count, d_in, d_out, 1, s));
+  } else {
+    float *fi = nullptr, *fo = nullptr;
+    MG_CUDA(cudaMallocAsync((void**)&fi, (size_t)count * np * sizeof(float), s));
+    MG_CUDA(cudaMallocAsync((void**)&fo, (size_t)count * np * sizeof(float), s));
+    launch_axpy_convert(1, d_in, fi, nullptr, (long long)count * np, s);
+    MG_CUDA(launch_apply_steps_1d(T, n0, count, fi, fo, 0, s));
+    launch_axpy_convert(3, fo, d_out, nullptr, (long long)count * np, s);
+    cudaFreeAsync(fi, s);
+    cudaFreeAsync(fo, s);
+  }
+  MG_CUDA(cudaStreamSynchronize(s));
+  return MGRIT_OK;
+}
+
+void mgrit_destroy(mgrit_handle* h) { delete h; }
+
+const char* mgrit_status_string(mgrit_status s) {
+  switch (s) {
+    case MGRIT_OK: return "ok";
+    case MGRIT_EINVAL: return "invalid argument";
+    case MGRIT_ENOMEM: return "out of device memory";
+    case MGRIT_ECUDA: return "CUDA error";
+    case MGRIT_ENOTCONVERGED: return "not converged";
+    case MGRIT_EDIVERGED: return "diverged";
+    case MGRIT_ETIMEOUT: return "device wait timed out";
+    case MGRIT_EUNSUPPORTED: return "unsupported";
+    case MGRIT_ESINGULAR: return "singular correction matrix";
+  }
+  return "unknown status";
+}
+
+const char* mgrit_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+"""The C-ABI library loads without a GPU and exports every entry point declared in include/mgrit_sl.h."""
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mgrit_sl.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mgrit_[a-z_]+|sl_step_sequential)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_13382_gb300 import build
+
+    build.build()
+    import paper_2203_13382_gb300 as mg
+
+    return mg.load_library()
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for required in ("mgrit_setup", "mgrit_solve", "sl_step_sequential", "mgrit_adjoint_solve", "mgrit_destroy",
+                     "mgrit_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2203_13382_gb300 import build
+
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_2203_13382_gb300 as mg
+
+    assert sorted(mg._SIGNATURES) == declared_functions()
+
+
+def test_host_only_calls(lib):
+    import ctypes
+
+    import paper_2203_13382_gb300 as mg
+
+    o = mg.default_options()
+    assert o.norm_mode == 1 and o.max_iter == 200 and abs(o.rtol - 1e-10) < 1e-25
+    assert mg.mgrit_status_string(0) == "ok"
+    assert mg.mgrit_status_string(8) == "singular correction matrix"
+    # argument errors are detected before any CUDA call
+    g = mg.MgritGrid(1, 100, 64, -1.0, 1.0, 0.85)  # nx not a power of two
+    w = mg.MgritWavespeed(0, 1.0, 1.0, 1.0)
+    h = ctypes.c_void_p()
+    st = lib.mgrit_setup(ctypes.byref(g), ctypes.byref(w), 1, 4, 0, None, None, ctypes.byref(h))
+    assert st == 1 and b"power of two" in lib.mgrit_last_error()
+    g = mg.MgritGrid(1, 64, 64, -1.0, 1.0, 0.85)
+    assert lib.mgrit_setup(ctypes.byref(g), ctypes.byref(w), 2, 4, 0, None, None, ctypes.byref(h)) == 1  # even p
+    assert lib.mgrit_setup(ctypes.byref(g), ctypes.byref(w), 3, 1, 0, None, None, ctypes.byref(h)) == 1  # m = 1
+    w2 = mg.MgritWavespeed(11, 1.0, 1.0, 1.0)
+    assert lib.mgrit_setup(ctypes.byref(g), ctypes.byref(w2), 3, 4, 0, None, None, ctypes.byref(h)) == 1  # 2D kind
+    assert lib.mgrit_setup(ctypes.byref(g), ctypes.byref(w), 3, 4, 0, None, None, None) == 1
+    g3 = mg.MgritGrid(1, 64, 96, -1.0, 1.0, 0.85)
+    assert lib.mgrit_setup(ctypes.byref(g3), ctypes.byref(w), 3, 64, 3, None, None, ctypes.byref(h)) == 1
