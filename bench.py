@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark: space-time DOF/s of MGRIT solves to a 1e-10 relative residual on one GB300.
+
+Workload (the paper's 1D variable-speed setting with the synthetic wave speed and initial data of this
+project): u_t + alpha u_x = 0 on periodic [-1, 1), alpha = 1 + 0.5 sin(2 pi x) cos(2 pi t), nx = 4096,
+nt = 16384, dt = 0.85 h, SL order p = r = 3, coarsening m = 8 on every level until at most 8 coarse
+steps remain (5 levels), u0 = three seeded Gaussian bumps, random U[0,1] initial iterate.
+
+One step = one complete solve through the library: mgrit_setup (departure points, backtracking,
+sigma, factorisations) + mgrit_solve to 1e-10 + mgrit_destroy, with u0 and the initial iterate
+already resident in HBM.  value = DOF / time per step (DOF = nx * nt), summed over ranks.
+
+Also reported: the same-GPU sequential SL stepping comparator, the roofline of the dominant kernel,
+the CPU oracle on a bounded sample of the workload, an end-to-end figure through the host-buffer
+entry point, SM clocks sampled during the timed region, and the number of kernels launched.
+
+`--impl reference` times the CPU oracle (the method restated in numpy from the paper) on a bounded
+sample of the same workload and prints the same JSON line with "impl": "reference".
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "space-time DOF/s to 1e-10 rel. residual vs sequential SL stepping, same GB300"
+WORKLOAD = {
+    "workload": "advection1d_alpha_1+0.5sin2pix_cos2pit_nx4096_nt16384_p3_m8_max8coarsest",
+    "nx": 4096,
+    "nt": 16384,
+    "order": 3,
+    "m": 8,
+    "wave": "sin_kx_cos_t",
+    "a": 0.5,
+    "k": 1.0,
+    "max_coarsest": 8,
+    "cfl": 0.85,
+    "u0": "3 gaussian bumps, seed 20260001",
+    "rtol": 1e-10,
+}
+CPU_SAMPLE_NT = 512  # bounded oracle sample: the first 512 time steps of the same problem
+REF_SAMPLE_NT = 256
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 peak derived from unit counts: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def peaks():
+    hbm, src = 6800.0, "fallback"
+    if os.path.exists(MEASURED):
+        with open(MEASURED) as f:
+            d = json.load(f)
+        hbm, src = float(d.get("hbm_gbs", hbm)), "measured"
+    return hbm, src
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.path.join("/tmp", f"clocks_{os.getpid()}.csv"), "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.out.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# roofline of the dominant kernel
+# ------------------------------------------------------------------------------------------------
+
+def phase_work(phase: str, wl: dict, levels: list[tuple[int, int]], launches: int) -> dict | None:
+    """Algorithmic bytes and flops per launch of a level-0 pass (one launch = one sweep of nt steps)."""
+    nx, nt, p = wl["nx"], wl["nt"], wl["order"]
+    J = nt // wl["m"]
+    pts = nx * nt
+    if phase in ("fine64_res", "fine64_fc", "fine64_post"):
+        # per point-step: 2 B shift + (p+1) FP64 weights; per interval: start slice, C value in, C value out
+        byts = pts * (2 + 8 * (p + 1)) + 3 * J * nx * 8
+        if phase == "fine64_post":
+            byts = pts * (2 + 8 * (p + 1)) + pts * 8 + J * nx * 16  # writes every slice of the solution
+        flops = pts * 2 * (p + 1)
+        return {"bytes": byts, "flops": flops, "fp": 64}
+    if phase == "fine32_res":
+        byts = pts * (2 + 4) + 2 * J * nx * 4
+        flops = pts * (2 * (p + 1) + 3 * (p + 1))
+        return {"bytes": byts, "flops": flops, "fp": 32}
+    return None
+
+
+def roofline(stats: dict, wl: dict, hbm_peak: float, hbm_src: str, steps: int, traffic: dict | None) -> dict:
+    ms, nl = stats["phase_ms"], stats["phase_launches"]
+    ranked = sorted(((ms[k], k) for k in ms if nl[k] > 0 and k not in ("sequential",)), reverse=True)
+    dom = None
+    for _, k in ranked:
+        if phase_work(k, wl, [], nl[k]) is not None:
+            dom = k
+            break
+    top = ranked[0][1] if ranked else None
+    if dom is None:
+        return {"bound": None, "kernel": top}
+    w = phase_work(dom, wl, [], nl[dom])
+    avg_s = ms[dom] / nl[dom] / 1e3
+    t_hbm = w["bytes"] / (hbm_peak * 1e9)
+    t_alu = w["flops"] / (FP64_PEAK_TFLOPS * 1e12) if w["fp"] == 64 else 0.0
+    out = {"kernel": f"k_relax_1d ({dom})", "phase_share": ms[dom] / max(sum(ms.values()), 1e-30),
+           "top_phase": top, "avg_launch_ms": avg_s * 1e3}
+    if t_alu > t_hbm:
+        out.update({"bound": "alu", "achieved": w["flops"] / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"})
+    else:
+        out.update({"bound": "hbm", "achieved": w["bytes"] / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "peak_source": f"{hbm_src} hbm_gbs"})
+    out["frac"] = out["achieved"] / out["peak"]
+    out["algorithmic_bytes"] = w["bytes"]
+    out["algorithmic_flops"] = w["flops"]
+    out["traffic"] = (traffic or {}).get(dom)
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# the CPU oracle (reference arm and cpu_baseline)
+# ------------------------------------------------------------------------------------------------
+
+def oracle_sample(nt_sample: int) -> tuple[float, int]:
+    """Oracle MGRIT solve of the workload truncated to its first nt_sample steps; returns (seconds, iterations)."""
+    from oracle import mgrit as omg
+    from oracle import semi_lagrangian as osl
+
+    wl = WORKLOAD
+    t0 = time.perf_counter()
+    H = omg.build_hierarchy(osl.Grid(wl["nx"], nt_sample, cfl=wl["cfl"]), osl.WaveSpeed(wl["wave"], a=wl["a"], k=wl["k"]),
+                            wl["order"], wl["m"], max_coarsest=wl["max_coarsest"])
+    R = omg.mgrit_solve(H, W.u0_bumps_1d(wl["nx"], W.SEED_C2_BUMPS, 3), W.initial_iterate(nt_sample, wl["nx"]),
+                        rtol=wl["rtol"])
+    return time.perf_counter() - t0, R.iterations
+
+
+def cores_used() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", "1"))
+
+
+def run_reference(args) -> None:
+    rank, _, world = rank_info()
+    if rank != 0:
+        return
+    wl = WORKLOAD
+    dof = wl["nx"] * REF_SAMPLE_NT
+    for _ in range(args.warmup):
+        oracle_sample(REF_SAMPLE_NT)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        _, its = oracle_sample(REF_SAMPLE_NT)
+    el = time.perf_counter() - t0
+    value = dof * args.steps / el
+    sample = f"oracle MGRIT solve to 1e-10 of the first {REF_SAMPLE_NT} of {wl['nt']} time steps (nx={wl['nx']})"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**wl, "sample_nt": REF_SAMPLE_NT}, "iterations": its,
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores_used(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# the GPU arm
+# ------------------------------------------------------------------------------------------------
+
+def run_ours(args) -> None:
+    import torch
+
+    import paper_2203_13382_gb300 as mg
+
+    rank, local_rank, world = rank_info()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    wl = WORKLOAD
+    nx, nt = wl["nx"], wl["nt"]
+    dof = nx * nt
+    prec = 1 if args.precision == "fp32bulk" else 0
+    u0_h = W.u0_bumps_1d(nx, W.SEED_C2_BUMPS, 3)
+    U_h = W.initial_iterate(nt, nx)
+    u0 = torch.from_numpy(u0_h).cuda()
+    U0 = torch.from_numpy(U_h).cuda()
+    u_out = torch.empty(nt + 1, nx, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_step(profile: int):
+        h = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
+                           max_coarsest=wl["max_coarsest"], precision=prec, rtol=wl["rtol"], profile=profile)
+        _, st = h.solve(u0, U0, u_out)
+        h.destroy()
+        return st
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        one_step(1)
+    barrier()
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(local_rank)
+    gpu_id = str(getattr(props, "uuid", local_rank))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(one_step(1))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * dof / (ms / 1e3)
+
+    # phase sums over the timed steps
+    agg_ms = {k: sum(s["phase_ms"][k] for s in stats) for k in stats[0]["phase_ms"]}
+    agg_nl = {k: sum(s["phase_launches"][k] for s in stats) for k in stats[0]["phase_launches"]}
+    launches = int(sum(s["kernel_launches"] for s in stats))
+    iters = [s["iterations"] for s in stats]
+    hbm, hbm_src = peaks()
+    traffic = None
+    if os.path.exists(os.path.join(ROOT, "profiles", "traffic.json")):
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get(args.precision)
+    roof = roofline({"phase_ms": agg_ms, "phase_launches": agg_nl}, wl, hbm, hbm_src, args.steps, traffic)
+
+    # comparator: sequential SL stepping on the same GPU (steps only, and including the departure points)
+    h = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
+                       max_coarsest=wl["max_coarsest"], precision=0, profile=1)
+    h.sequential(u0, store_all=False)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    nseq = max(2, args.steps // 2)
+    s0.record(stream)
+    for _ in range(nseq):
+        seq_last = h.sequential(u0, store_all=False)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1) / nseq
+    _, st_prof = h.solve(u0, U0, u_out)
+    dep_ms = st_prof["phase_ms"]["departure"]
+    tab_ms = st_prof["phase_ms"]["tables"] * nt / sum(h.level_info(l)[0] for l in range(h.nlevels))
+    h.destroy()
+    seq_full_ms = seq_ms + dep_ms + tab_ms
+    fixed_point = float((seq_last - u_out[-1]).norm() / seq_last.norm())
+
+    # end to end through the host-buffer entry point (inputs from pinned host memory, solution back)
+    u0_pin = torch.from_numpy(u0_h).pin_memory()
+    U_pin = torch.from_numpy(U_h).pin_memory()
+    out_pin = torch.empty(nt + 1, nx, dtype=torch.float64).pin_memory()
+    ne2e = max(2, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ne2e):
+        he = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
+                            max_coarsest=wl["max_coarsest"], precision=prec, rtol=wl["rtol"])
+        he.solve_host(u0_pin.numpy(), U_pin.numpy(), out_pin.numpy())
+        he.destroy()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ne2e
+    J = nt // wl["m"]
+    e2e = {"value": world * dof / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": nx * 8 + J * nx * 8,
+           "d2h_bytes_per_step": (nt + 1) * nx * 8,
+           "path": "mgrit_setup + mgrit_solve_host (pinned host buffers) + mgrit_destroy, wall clock"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        secs, cpu_its = oracle_sample(CPU_SAMPLE_NT)
+        cpu = {"value": nx * CPU_SAMPLE_NT / secs, "unit": "DOF/s", "cores": cores_used(), "kind": "oracle",
+               "sample": f"oracle MGRIT solve to 1e-10 of the first {CPU_SAMPLE_NT} of {nt} time steps "
+                         f"(nx={nx}; {cpu_its} iterations, {secs:.1f} s)"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
+            "config": {**wl, "precision": args.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2: per-step gather tables alone exceed 2 GB"},
+            "iterations": iters[0], "iterations_all_steps": sorted(set(iters)),
+            "comparator": {"sequential_dof_per_s": dof / (seq_full_ms / 1e3),
+                           "sequential_ms": seq_full_ms, "sequential_steps_only_ms": seq_ms,
+                           "sequential_includes": "FP64 departure points + level-0 gather tables + nt SL steps",
+                           "mgrit_over_sequential": (dof / (ms / 1e3)) / (dof / (seq_full_ms / 1e3)),
+                           "fixed_point_rel_diff_final_slice": fixed_point},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "phases_ms_per_step": {k: v / args.steps for k, v in agg_ms.items() if agg_nl[k]},
+            "phase_launches_per_step": {k: v // args.steps for k, v in agg_nl.items() if v},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32bulk", "fp64"], default="fp32bulk")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -92,8 +92,26 @@ typedef struct {
                        (the aggressive coarsening of Sec. 5) */
   int coarse_fp64;  /* precision == 1 only: 1 = coarse levels and correction solves in FP64,
                        0 (default) = FP32 like the rest of the error cycle */
-  int use_graph;    /* 1 (default): capture one cycle in a CUDA graph and replay it */
+  int use_graph;    /* reserved (must be 0 or 1) */
+  int profile;      /* 1: time each phase with CUDA events on the handle's stream (mgrit_stats.phase_ms) */
 } mgrit_options;
+
+/* Phases timed when mgrit_options.profile = 1 (indices into mgrit_stats.phase_ms / phase_launches). */
+enum {
+  MGRIT_PHASE_DEPARTURE = 0,  /* fine ERK departure points */
+  MGRIT_PHASE_BACKTRACK = 1,  /* coarse departure points, phi, sigma */
+  MGRIT_PHASE_TABLES = 2,     /* gather tables */
+  MGRIT_PHASE_FACTOR = 3,     /* correction-matrix factorisation */
+  MGRIT_PHASE_FINE64_FC = 4,  /* level 0, FP64 F+C relaxation pass */
+  MGRIT_PHASE_FINE64_RES = 5, /* level 0, FP64 F-relaxation + C-point residual pass */
+  MGRIT_PHASE_FINE64_POST = 6,/* level 0, FP64 final F-relaxation into the output */
+  MGRIT_PHASE_FINE32_RES = 7, /* level 0, FP32 error propagation + residual pass */
+  MGRIT_PHASE_COARSE = 8,     /* relaxation passes on levels 1 .. L-2 */
+  MGRIT_PHASE_COARSEST = 9,   /* sequential solve on the coarsest level */
+  MGRIT_PHASE_MISC = 10,      /* norms and elementwise updates */
+  MGRIT_PHASE_SEQUENTIAL = 11,/* sl_step_sequential */
+  MGRIT_NUM_PHASES = 12
+};
 
 typedef struct {
   int iterations;     /* V-cycles performed */
@@ -104,8 +122,11 @@ typedef struct {
   double r_final;     /* last residual norm */
   double residual_history[256];
   double setup_ms;    /* wall time of mgrit_setup */
-  double solve_ms;    /* wall time of the last mgrit_solve (or sl_step_sequential) */
+  double solve_ms;    /* wall time of the last mgrit_solve */
   int64_t device_bytes; /* workspace held by the handle */
+  int64_t kernel_launches;  /* kernels launched by this handle: mgrit_setup plus this call */
+  double phase_ms[12];      /* profile = 1: summed event time per phase (setup phases from mgrit_setup) */
+  int phase_launches[12];   /* kernels per phase (setup phases from mgrit_setup, others from this call) */
 } mgrit_stats;
 
 typedef struct mgrit_handle mgrit_handle;

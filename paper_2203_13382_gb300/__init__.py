@@ -48,14 +48,21 @@ class MgritWavespeed(ctypes.Structure):
 class MgritOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("coarse_op", ctypes.c_int), ("norm_mode", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("rtol", ctypes.c_double), ("max_coarsest", ctypes.c_int),
-                ("m_first", ctypes.c_int), ("coarse_fp64", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("m_first", ctypes.c_int), ("coarse_fp64", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+PHASES = ["departure", "backtrack", "tables", "factor", "fine64_fc", "fine64_res", "fine64_post", "fine32_res",
+          "coarse", "coarsest", "misc", "sequential"]
 
 
 class MgritStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("levels", ctypes.c_int),
                 ("history_len", ctypes.c_int), ("r0", ctypes.c_double), ("r_final", ctypes.c_double),
                 ("residual_history", ctypes.c_double * 256), ("setup_ms", ctypes.c_double),
-                ("solve_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+                ("solve_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("phase_ms", ctypes.c_double * 12),
+                ("phase_launches", ctypes.c_int * 12)]
 
     def as_dict(self) -> dict:
         return {
@@ -68,6 +75,9 @@ class MgritStats(ctypes.Structure):
             "setup_ms": self.setup_ms,
             "solve_ms": self.solve_ms,
             "device_bytes": self.device_bytes,
+            "kernel_launches": self.kernel_launches,
+            "phase_ms": {PHASES[i]: self.phase_ms[i] for i in range(12)},
+            "phase_launches": {PHASES[i]: self.phase_launches[i] for i in range(12)},
         }
 
 

@@ -37,8 +37,9 @@ void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, u
 // (is_double = 1) or float.  flag (device int) is set to 1 if a pivot is too small.
 size_t solver_reals(int nx, int p, int P);
 int solver_partitions(int nx, int p);
-void launch_factor_1d(const double* sigma, int nt, int nx, int p, int P, void* out, int is_double, int* flag,
-                      cudaStream_t st);
+// Returns the number of kernel launches issued.
+int launch_factor_1d(const double* sigma, int nt, int nx, int p, int P, void* out, int is_double, int* flag,
+                     cudaStream_t st);
 
 // ---- relaxation (relax_kernels.cu) ---------------------------------------------------------------
 

@@ -78,10 +78,57 @@ struct mgrit_handle {
   double* norm_host = nullptr;  // pinned
   int* flag_dev = nullptr;
   double setup_ms = 0.0;
+  // launch accounting and optional per-phase event timing
+  int64_t setup_launches = 0, call_launches = 0;
+  int setup_phase_launches[MGRIT_NUM_PHASES] = {};
+  double setup_phase_ms[MGRIT_NUM_PHASES] = {};
+  int phase_launches[MGRIT_NUM_PHASES] = {};
+  double phase_ms[MGRIT_NUM_PHASES] = {};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used;  // (phase, index of the start event)
+  size_t ev_next = 0;
 
   ~mgrit_handle() {
     for (void* p : allocs) cudaFree(p);
     if (norm_host) cudaFreeHost(norm_host);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
+
+  void reset_call_counters() {
+    call_launches = 0;
+    for (int i = 0; i < MGRIT_NUM_PHASES; ++i) {
+      phase_launches[i] = 0;
+      phase_ms[i] = 0.0;
+    }
+    ev_used.clear();
+    ev_next = 0;
+  }
+
+  // Record a phase boundary; returns the event index or -1 (profiling off / pool exhausted).
+  int phase_begin() {
+    if (!opt.profile || ev_next + 2 > ev_pool.size()) return -1;
+    const int i = (int)ev_next;
+    ev_next += 2;
+    cudaEventRecord(ev_pool[i], stream);
+    return i;
+  }
+  void phase_end(int phase, int ev, int launches) {
+    call_launches += launches;
+    phase_launches[phase] += launches;
+    if (ev >= 0) {
+      cudaEventRecord(ev_pool[ev + 1], stream);
+      ev_used.push_back({phase, ev});
+    }
+  }
+  // After a stream synchronisation: accumulate the recorded phase times.
+  void collect_phase_times() {
+    for (auto& pr : ev_used) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev_pool[pr.second], ev_pool[pr.second + 1]) == cudaSuccess)
+        phase_ms[pr.first] += ms;
+    }
+    ev_used.clear();
+    ev_next = 0;
   }
 
   template <typename T>
@@ -156,9 +203,11 @@ std::vector<int> factors(int nt, int m, int m_first, int levels, int max_coarses
   return out;
 }
 
-mgrit_status relax(mgrit_handle* h, int l, int is_double, const RelaxArgs& a) {
+mgrit_status relax(mgrit_handle* h, int l, int is_double, const RelaxArgs& a, int phase) {
   LevelTables T = h->tables(l, is_double);
+  const int ev = h->phase_begin();
   MG_CUDA(launch_relax_1d(T, a, is_double, h->stream));
+  h->phase_end(phase, ev, 1);
   return MGRIT_OK;
 }
 
@@ -175,7 +224,9 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   const int dbl = L.is_double;
   if (l == (int)h->levels.size() - 1) {  // coarsest: sequential stepping (Sec. 2.2)
     LevelTables T = h->tables(l, dbl);
+    const int ev = h->phase_begin();
     MG_CUDA(launch_sequential_1d(T, L.nt, L.G, nullptr, L.E, 1, dbl, h->stream));
+    h->phase_end(MGRIT_PHASE_COARSEST, ev, 1);
     return MGRIT_OK;
   }
   Level& Lc = h->levels[l + 1];
@@ -189,7 +240,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   a.g = L.G;
   a.cout = L.E;
   a.c_stride = (long long)m * np;
-  MG_TRY(relax(h, l, dbl, a));
+  MG_TRY(relax(h, l, dbl, a, MGRIT_PHASE_COARSE));
   // F-relaxation and the C-point residual -> right-hand side of level l+1
   a = args0();
   a.m = m;
@@ -204,7 +255,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   a.c_stride = (long long)m * np;
   a.rout = Lc.G;
   a.r_stride = np;
-  MG_TRY(relax(h, l, dbl, a));
+  MG_TRY(relax(h, l, dbl, a, MGRIT_PHASE_COARSE));
   MG_TRY(coarse_cycle(h, l + 1));
   // correction by injection and post F-relaxation
   a = args0();
@@ -221,12 +272,14 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   a.extra_cta = 1;
   a.g = L.G;
   a.fstore = L.E;
-  MG_TRY(relax(h, l, dbl, a));
+  MG_TRY(relax(h, l, dbl, a, MGRIT_PHASE_COARSE));
   return MGRIT_OK;
 }
 
 mgrit_status read_norm(mgrit_handle* h, int J, double* out) {
+  const int ev = h->phase_begin();
   launch_sum(h->norm_partial, J, h->norm_dev, h->stream);
+  h->phase_end(MGRIT_PHASE_MISC, ev, 1);
   MG_CUDA(cudaMemcpyAsync(h->norm_host, h->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   MG_CUDA(cudaStreamSynchronize(h->stream));
   *out = std::sqrt(h->norm_host[0]);
@@ -248,7 +301,8 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->max_coarsest = 1;
   opt->m_first = 0;
   opt->coarse_fp64 = 0;
-  opt->use_graph = 1;
+  opt->use_graph = 0;
+  opt->profile = 0;
   return MGRIT_OK;
 }
 
@@ -345,17 +399,37 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     if (e != cudaSuccess) return cleanup_fail(fail(MGRIT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)));
     return MGRIT_OK;
   };
+  if (opt.profile) {
+    h->ev_pool.resize(4096);
+    for (auto& e : h->ev_pool)
+      if (cudaEventCreate(&e) != cudaSuccess) return cleanup_fail(fail(MGRIT_ECUDA, "cudaEventCreate failed"));
+  }
+  h->reset_call_counters();
   cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s);
   // fine departure points and tables
-  launch_departure_1d(wp, p, nx, grid->nt, grid->xmin, hgrid, dt, h->levels[0].s64, s);
+  {
+    const int ev = h->phase_begin();
+    launch_departure_1d(wp, p, nx, grid->nt, grid->xmin, hgrid, dt, h->levels[0].s64, s);
+    h->phase_end(MGRIT_PHASE_DEPARTURE, ev, 1);
+  }
   for (size_t l = 0; l < h->levels.size(); ++l) {
     Level& L = h->levels[l];
     if (l > 0) {
       Level& Lp = h->levels[l - 1];
+      const int ev = h->phase_begin();
       launch_backtrack_1d(Lp.s64, l > 1 ? Lp.sigma : nullptr, L.m, L.nt, nx, p, L.s64, L.sigma, s);
+      h->phase_end(MGRIT_PHASE_BACKTRACK, ev, 1);
     }
-    launch_build_tables(L.s64, L.nt, nx, np, p, L.shift, L.w64, L.eps32, s);
-    if (l > 0 && L.solver) launch_factor_1d(L.sigma, L.nt, nx, p, L.P, L.solver, L.is_double, h->flag_dev, s);
+    {
+      const int ev = h->phase_begin();
+      launch_build_tables(L.s64, L.nt, nx, np, p, L.shift, L.w64, L.eps32, s);
+      h->phase_end(MGRIT_PHASE_TABLES, ev, 1);
+    }
+    if (l > 0 && L.solver) {
+      const int ev = h->phase_begin();
+      const int nl = launch_factor_1d(L.sigma, L.nt, nx, p, L.P, L.solver, L.is_double, h->flag_dev, s);
+      h->phase_end(MGRIT_PHASE_FACTOR, ev, nl);
+    }
     if ((st = cuda_fail("setup")) != MGRIT_OK) return st;
   }
   // zero rows that are read but never written: E_l[0], G_l[0], r64[0], EC[0]
@@ -373,25 +447,37 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
   if ((st = cuda_fail("setup")) != MGRIT_OK) return st;
   if (flag) return cleanup_fail(fail(MGRIT_ESINGULAR, "a correction matrix has a (near) zero pivot"));
+  h->collect_phase_times();
+  h->setup_launches = h->call_launches;
+  for (int i = 0; i < MGRIT_NUM_PHASES; ++i) {
+    h->setup_phase_launches[i] = h->phase_launches[i];
+    h->setup_phase_ms[i] = h->phase_ms[i];
+  }
+  h->reset_call_counters();
   h->setup_ms = now_ms() - t0;
   *out = h;
   return MGRIT_OK;
 }
 
-mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_init, double* d_u_out,
-                         mgrit_stats* stats) {
-  if (!h || !d_u0 || !d_u_out) return fail(MGRIT_EINVAL, "handle, u0 and u_out must not be NULL");
+}  // extern "C"
+
+namespace {
+
+// The MGRIT iteration.  u0 / u_init may be host or device pointers (kinds given); u_out is on the device.
+mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_kind, const double* d_u_init,
+                        cudaMemcpyKind init_kind, double* d_u_out, mgrit_stats* stats) {
   const double t0 = now_ms();
   cudaStream_t s = h->stream;
   const int np = h->npts;
   const int m1 = h->levels[1].m, J = h->J1();
   const int fp32 = h->opt.precision == 1;
+  h->reset_call_counters();
   // initial iterate at the C-points
-  MG_CUDA(cudaMemcpyAsync(h->X, d_u0, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  MG_CUDA(cudaMemcpyAsync(h->Y, d_u0, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(cudaMemcpyAsync(h->X, d_u0, np * sizeof(double), u0_kind, s));
+  MG_CUDA(cudaMemcpyAsync(h->Y, h->X, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (d_u_init) {
     MG_CUDA(cudaMemcpy2DAsync(h->X + np, np * sizeof(double), d_u_init + (size_t)m1 * np,
-                              (size_t)m1 * np * sizeof(double), np * sizeof(double), J, cudaMemcpyDeviceToDevice, s));
+                              (size_t)m1 * np * sizeof(double), np * sizeof(double), J, init_kind, s));
   } else {
     MG_CUDA(cudaMemsetAsync(h->X + np, 0, (size_t)J * np * sizeof(double), s));
   }
@@ -415,7 +501,7 @@ mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_
       a.corr_stride = np;
       a.cout = h->Y;
       a.c_stride = np;
-      MG_TRY(relax(h, 0, 1, a));
+      MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_FC));
       a = args0();
       a.m = m1;
       a.J = J;
@@ -428,7 +514,7 @@ mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_
       a.rout = L1.G;
       a.r_stride = np;
       a.norm_partial = h->norm_partial;
-      MG_TRY(relax(h, 0, 1, a));
+      MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_RES));
       MG_TRY(coarse_cycle(h, 1));
       std::swap(h->X, h->Y);
     } else {
@@ -444,9 +530,13 @@ mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_
       a.c_stride = np;
       a.rout = h->r64;
       a.r_stride = np;
-      MG_TRY(relax(h, 0, 1, a));
+      MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_RES));
       // C-relaxation of the error equation from a zero guess gives e_C = r; F-relax + residual in FP32
-      launch_axpy_convert(1, h->r64, h->EC, nullptr, (long long)(J + 1) * np, s);
+      {
+        const int ev = h->phase_begin();
+        launch_axpy_convert(1, h->r64, h->EC, nullptr, (long long)(J + 1) * np, s);
+        h->phase_end(MGRIT_PHASE_MISC, ev, 1);
+      }
       a = args0();
       a.m = m1;
       a.J = J;
@@ -457,10 +547,14 @@ mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_
       a.rout = L1.G;
       a.r_stride = np;
       a.norm_partial = h->norm_partial;
-      MG_TRY(relax(h, 0, 0, a));
+      MG_TRY(relax(h, 0, 0, a, MGRIT_PHASE_FINE32_RES));
       MG_TRY(coarse_cycle(h, 1));
       // u_C += r + E_1
-      launch_axpy_convert(5, h->r64, h->X, L1.E, (long long)(J + 1) * np, s);
+      {
+        const int ev = h->phase_begin();
+        launch_axpy_convert(5, h->r64, h->X, L1.E, (long long)(J + 1) * np, s);
+        h->phase_end(MGRIT_PHASE_MISC, ev, 1);
+      }
     }
     MG_TRY(read_norm(h, J, &rk));
     hist.push_back(rk);
@@ -490,9 +584,10 @@ mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_
     a.wb_stride = (long long)m1 * np;
     a.extra_cta = 1;
     a.fstore = d_u_out;
-    MG_TRY(relax(h, 0, 1, a));
+    MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_POST));
   }
   MG_CUDA(cudaStreamSynchronize(s));
+  h->collect_phase_times();
   if (status == MGRIT_OK && !converged) status = fail(MGRIT_ENOTCONVERGED, "max_iter reached");
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -507,26 +602,36 @@ mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_
     stats->setup_ms = h->setup_ms;
     stats->solve_ms = now_ms() - t0;
     stats->device_bytes = h->bytes;
+    stats->kernel_launches = h->setup_launches + h->call_launches;
+    for (int i = 0; i < MGRIT_NUM_PHASES; ++i) {
+      stats->phase_ms[i] = h->setup_phase_ms[i] + h->phase_ms[i];
+      stats->phase_launches[i] = h->setup_phase_launches[i] + h->phase_launches[i];
+    }
   }
   return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_init, double* d_u_out,
+                         mgrit_stats* stats) {
+  if (!h || !d_u0 || !d_u_out) return fail(MGRIT_EINVAL, "handle, u0 and u_out must not be NULL");
+  return solve_impl(h, d_u0, cudaMemcpyDeviceToDevice, d_u_init, cudaMemcpyDeviceToDevice, d_u_out, stats);
 }
 
 mgrit_status mgrit_solve_host(mgrit_handle* h, const double* h_u0, const double* h_u_init, double* h_u_out,
                               mgrit_stats* stats) {
   if (!h || !h_u0 || !h_u_out) return fail(MGRIT_EINVAL, "handle, u0 and u_out must not be NULL");
   const size_t np = h->npts, nt = h->grid.nt;
-  double *d_u0 = nullptr, *d_init = nullptr, *d_out = nullptr;
+  double* d_out = nullptr;
   cudaStream_t s = h->stream;
-  MG_CUDA(cudaMallocAsync((void**)&d_u0, np * sizeof(double), s));
   MG_CUDA(cudaMallocAsync((void**)&d_out, (nt + 1) * np * sizeof(double), s));
-  if (h_u_init) MG_CUDA(cudaMallocAsync((void**)&d_init, (nt + 1) * np * sizeof(double), s));
-  MG_CUDA(cudaMemcpyAsync(d_u0, h_u0, np * sizeof(double), cudaMemcpyHostToDevice, s));
-  if (h_u_init) MG_CUDA(cudaMemcpyAsync(d_init, h_u_init, (nt + 1) * np * sizeof(double), cudaMemcpyHostToDevice, s));
-  mgrit_status st = mgrit_solve(h, d_u0, d_init, d_out, stats);
+  // the initial iterate is read only at the C-points, straight from host memory
+  mgrit_status st = solve_impl(h, h_u0, cudaMemcpyHostToDevice, h_u_init, cudaMemcpyHostToDevice, d_out, stats);
   cudaMemcpyAsync(h_u_out, d_out, (nt + 1) * np * sizeof(double), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(d_u0, s);
   cudaFreeAsync(d_out, s);
-  if (d_init) cudaFreeAsync(d_init, s);
   MG_CUDA(cudaStreamSynchronize(s));
   return st;
 }
@@ -538,6 +643,8 @@ mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u
   cudaStream_t s = h->stream;
   LevelTables T = h->tables(0, 1);
   T.solver = nullptr;
+  h->reset_call_counters();
+  const int ev = h->phase_begin();
   if (h->opt.precision == 0) {
     MG_CUDA(launch_sequential_1d(T, nt, nullptr, d_u0, d_u_out, store_all, 1, s));
   } else {
@@ -551,6 +658,7 @@ mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u
     cudaFreeAsync(u0f, s);
     cudaFreeAsync(outf, s);
   }
+  h->phase_end(MGRIT_PHASE_SEQUENTIAL, ev, h->opt.precision == 0 ? 1 : 3);
   MG_CUDA(cudaGetLastError());
   (void)t0;
   return MGRIT_OK;

@@ -470,8 +470,8 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_1d(const double* __re
   }
 }
 
-void launch_factor_1d(const double* sigma, int nt, int nx, int p, int P, void* out, int is_double, int* flag,
-                      cudaStream_t st) {
+int launch_factor_1d(const double* sigma, int nt, int nx, int p, int P, void* out, int is_double, int* flag,
+                     cudaStream_t st) {
   const int b = (p + 1) / 2;
   const int s = nx / P, q = s - b;
   const size_t per = (size_t)(2 * b + 1) * q * P + (size_t)2 * b * nx;
@@ -484,8 +484,9 @@ void launch_factor_1d(const double* sigma, int nt, int nx, int p, int P, void* o
   const int chunk = 256;
   double* scratch = nullptr;
   const int nchunk = nt < chunk ? nt : chunk;
-  if (cudaMallocAsync((void**)&scratch, per * nchunk * sizeof(double), st) != cudaSuccess) return;
-  for (int n0 = 0; n0 < nt; n0 += chunk) {
+  if (cudaMallocAsync((void**)&scratch, per * nchunk * sizeof(double), st) != cudaSuccess) return 0;
+  int launches = 0;
+  for (int n0 = 0; n0 < nt; n0 += chunk, ++launches) {
     const int cnt = (nt - n0) < chunk ? (nt - n0) : chunk;
     if (is_double)
       k_factor_1d<double><<<cnt, kFactorThreads, smem, st>>>(sigma + (size_t)n0 * nx, nx, p, P,
@@ -495,6 +496,7 @@ void launch_factor_1d(const double* sigma, int nt, int nx, int p, int P, void* o
                                                          (float*)out + (size_t)n0 * stride, stride, scratch, flag);
   }
   cudaFreeAsync(scratch, st);
+  return launches;
 }
 
 }  // namespace mgrit

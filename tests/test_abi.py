@@ -56,7 +56,7 @@ def test_host_only_calls(lib):
     import paper_2203_13382_gb300 as mg
 
     o = mg.default_options()
-    assert o.norm_mode == 1 and o.max_iter == 200 and abs(o.rtol - 1e-10) < 1e-25
+    assert o.norm_mode == 1 and o.max_iter == 200 and abs(o.rtol - 1e-10) < 1e-25 and o.profile == 0
     assert mg.mgrit_status_string(0) == "ok"
     assert mg.mgrit_status_string(8) == "singular correction matrix"
     # argument errors are detected before any CUDA call
@@ -73,3 +73,28 @@ def test_host_only_calls(lib):
     assert lib.mgrit_setup(ctypes.byref(g), ctypes.byref(w), 3, 4, 0, None, None, None) == 1
     g3 = mg.MgritGrid(1, 64, 96, -1.0, 1.0, 0.85)
     assert lib.mgrit_setup(ctypes.byref(g3), ctypes.byref(w), 3, 64, 3, None, None, ctypes.byref(h)) == 1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors of the C structs have the C sizes and field offsets (compiled with gcc here)."""
+    import ctypes
+    import shutil
+
+    import paper_2203_13382_gb300 as mg
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "mgrit_sl.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(mgrit_grid), sizeof(mgrit_wavespeed),"
+        " sizeof(mgrit_options), sizeof(mgrit_stats), offsetof(mgrit_stats, device_bytes),"
+        " offsetof(mgrit_stats, phase_ms), offsetof(mgrit_options, profile));return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(mg.MgritGrid), ctypes.sizeof(mg.MgritWavespeed), ctypes.sizeof(mg.MgritOptions),
+            ctypes.sizeof(mg.MgritStats), mg.MgritStats.device_bytes.offset, mg.MgritStats.phase_ms.offset,
+            mg.MgritOptions.profile.offset]
+    assert got == want
