@@ -213,6 +213,22 @@ mgrit_status mgrit_copy_sigma(const mgrit_handle* h, int level, double* d_out);
  * working precision.  Synchronous. */
 mgrit_status mgrit_apply_step(mgrit_handle* h, int level, int n0, int count, const double* d_in, double* d_out);
 
+/*
+ * mgrit_apply_step without any device allocation.  The paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory -- for instance an application whose framework
+ * reserves the GPU's memory up front (a cudaMalloc from this library would fail or fragment that
+ * pool), or a latency-sensitive caller that cannot accept the device-wide synchronisation of
+ * cudaFree.  Same arguments, layout and result as mgrit_apply_step.  Levels that work in FP32 are
+ * staged through an 8 MiB buffer in file-scope device memory that every GPU loading this library
+ * holds until the process exits; count * N must not exceed 1048576 (MGRIT_EINVAL otherwise, before
+ * any launch).  The first call on a device looks up that buffer's address, so make it before any
+ * stream capture.  All calls share the buffer: calls that overlap on the GPU (other streams, other
+ * threads, other handles) race; calls issued one after another are safe, as each call overwrites
+ * every staged value it reads.  Synchronous; the current device must be the handle's device.
+ */
+mgrit_status mgrit_apply_step_noalloc(mgrit_handle* h, int level, int n0, int count, const double* d_in,
+                                      double* d_out);
+
 void mgrit_destroy(mgrit_handle* h);
 const char* mgrit_status_string(mgrit_status s);
 const char* mgrit_last_error(void);

@@ -98,6 +98,7 @@ _SIGNATURES = {
     "mgrit_copy_offsets": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "mgrit_copy_sigma": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "mgrit_apply_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "mgrit_apply_step_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "mgrit_destroy": (None, [_VP]),
     "mgrit_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mgrit_last_error": (ctypes.c_char_p, []),
@@ -218,6 +219,15 @@ class Handle:
         count = slices.shape[0]
         _check(load_library().mgrit_apply_step(self._h(), level, n0, count, _ptr(slices), _ptr(out)),
                "mgrit_apply_step")
+        return out
+
+    def apply_step_noalloc(self, level: int, n0: int, slices, out=None):
+        """apply_step for callers that cannot allocate device memory: the library allocates nothing, and
+        `out` (if given) must be preallocated by the caller."""
+        if out is None:
+            out = self._empty(*slices.shape)
+        _check(load_library().mgrit_apply_step_noalloc(self._h(), level, n0, slices.shape[0], _ptr(slices),
+                                                        _ptr(out)), "mgrit_apply_step_noalloc")
         return out
 
     def solve(self, u0, u_init=None, u_out=None, allow_not_converged: bool = False):

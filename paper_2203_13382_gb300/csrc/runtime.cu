@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -726,6 +727,68 @@ mgrit_status mgrit_apply_step(mgrit_handle* h, int level, int n0, int count, con
     cudaFreeAsync(fi, s);
     cudaFreeAsync(fo, s);
   }
+  MG_CUDA(cudaStreamSynchronize(s));
+  return MGRIT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Staging memory of mgrit_apply_step_noalloc: two buffers of kNoAllocMaxElems FP32 values (8 MiB in
+// total) in file-scope device memory.  Every GPU that loads this library holds it until the process
+// exits.  In host code `g_noalloc_stage` only names a host-side stand-in, so its device address is
+// looked up with cudaGetSymbolAddress, once per device, with that device current.
+constexpr long long kNoAllocMaxElems = 1LL << 20;
+static __device__ __align__(256) float g_noalloc_stage[2 * kNoAllocMaxElems];
+
+std::mutex g_noalloc_mutex;
+std::vector<float*> g_noalloc_addr;  // indexed by device ordinal
+
+mgrit_status noalloc_stage_address(float** out) {
+  int dev = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if ((int)g_noalloc_addr.size() <= dev) g_noalloc_addr.resize(dev + 1, nullptr);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    MG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_stage));
+    g_noalloc_addr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return MGRIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mgrit_status mgrit_apply_step_noalloc(mgrit_handle* h, int level, int n0, int count, const double* d_in,
+                                      double* d_out) {
+  if (!h || !d_in || !d_out) return fail(MGRIT_EINVAL, "NULL argument");
+  if (level < 0 || level >= (int)h->levels.size()) return fail(MGRIT_EINVAL, "level out of range");
+  const Level& L = h->levels[level];
+  if (count < 0 || n0 < 0 || n0 + count > L.nt) return fail(MGRIT_EINVAL, "step range out of range");
+  const int np = h->npts;
+  const long long elems = (long long)count * np;
+  if (elems > kNoAllocMaxElems)
+    return fail(MGRIT_EINVAL, "count * slice size exceeds the no-allocation staging capacity of " +
+                                  std::to_string(kNoAllocMaxElems) + " values");
+  cudaStream_t s = h->stream;
+  const int dbl = L.is_double;
+  LevelTables T = h->tables(level, dbl);
+  if (dbl) {
+    MG_CUDA(launch_apply_steps_1d(T, n0, count, d_in, d_out, 1, s));
+  } else {
+    float* stage = nullptr;
+    MG_TRY(noalloc_stage_address(&stage));
+    float* fi = stage;
+    float* fo = stage + kNoAllocMaxElems;
+    launch_axpy_convert(1, d_in, fi, nullptr, elems, s);
+    MG_CUDA(launch_apply_steps_1d(T, n0, count, fi, fo, 0, s));
+    launch_axpy_convert(3, fo, d_out, nullptr, elems, s);
+  }
+  MG_CUDA(cudaGetLastError());
   MG_CUDA(cudaStreamSynchronize(s));
   return MGRIT_OK;
 }
