@@ -32,13 +32,12 @@ void launch_backtrack_2d(const double* sx_prev, const double* sy_prev, const dou
 void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, uint16_t* shift, double* w64,
                          float* eps32, cudaStream_t st);
 
-// Partitioned factorisation of M = I - diag(sigma) D_{p+1} (periodic, half-bandwidth b = (p+1)/2)
-// for each of nt steps.  Output per step: `solver_reals(nx, p, P)` values of type double
-// (is_double = 1) or float.  flag (device int) is set to 1 if a pivot is too small.
-size_t solver_reals(int nx, int p, int P);
-int solver_partitions(int nx, int p);
-// Returns the number of kernel launches issued.
-int launch_factor_1d(const double* sigma, int nt, int nx, int p, int P, void* out, int is_double, int* flag,
+// Factorisation of M = I - diag(sigma) D_{p+1} (periodic, half-bandwidth b = (p+1)/2) for each of nt
+// steps (layout: solver_layout.cuh).  Output per step: solver_reals(nx, p) values of type double
+// (is_double = 1) or float.  flag (device int) is set to 1 if a pivot is too small.  Returns the number
+// of kernel launches issued.
+size_t solver_reals(int nx, int p);
+int launch_factor_1d(const double* sigma, int nt, int nx, int p, void* out, int is_double, int* flag,
                      cudaStream_t st);
 
 // ---- relaxation (relax_kernels.cu) ---------------------------------------------------------------
@@ -64,7 +63,6 @@ struct LevelTables {
   // correction solver (coarse levels, corrected operator); NULL for the plain SL step
   const void* solver;
   size_t solver_stride;  // reals per step
-  int P;                 // partitions
 };
 
 struct RelaxArgs {

@@ -9,143 +9,234 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "solver_layout.cuh"
 
 namespace mgrit {
 
 namespace {
 
-template <typename R>
-struct SolverViewC {
-  const R* lu;
-  const R* vw;
-  const R* sinv;
-  const R* ctail;
-  const R* chead;
+// ---- gather tables of one step, loaded into registers ahead of use (software pipelining) ----------
+constexpr int kPts = 8;  // points per thread: nx <= kPts * kSliceThreads = 4096
+
+template <int P, typename R>
+struct GatherRegs;
+
+template <int P>
+struct GatherRegs<P, double> {
+  int base[kPts];
+  double w[kPts][P + 1];
 };
 
-template <typename R>
-__device__ __forceinline__ SolverViewC<R> solver_view_c(const R* base, int nx, int b, int P) {
-  const int s = nx / P, q = s - b;
-  SolverViewC<R> v;
-  v.lu = base;
-  v.vw = v.lu + (size_t)(2 * b + 1) * q * P;
-  v.sinv = v.vw + (size_t)2 * b * nx;
-  v.ctail = v.sinv + (size_t)(b * P) * (b * P);
-  v.chead = v.ctail + (size_t)P * b * b;
-  return v;
-}
+template <int P>
+struct GatherRegs<P, float> {
+  int base[kPts];
+  float eps[kPts];
+};
 
-// dst[i] = sum_a w_a(eps_i) src[(i + shift_i + a) mod nx]  -- the SL gather of step row n.
 template <int P, typename R>
-__device__ __forceinline__ void gather_step(const R* __restrict__ src, R* __restrict__ dst, const LevelTables& T,
-                                            int n) {
+__device__ __forceinline__ void load_gather(GatherRegs<P, R>& g, const LevelTables& T, int n) {
   const int nx = T.nx;
   const uint16_t* __restrict__ sh = T.shift + (size_t)n * nx;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const int base = i + (int)__ldg(sh + i);
-    R w[P + 1];
-    if constexpr (std::is_same<R, double>::value) {
-      const double* __restrict__ wr = T.w64 + (size_t)n * (P + 1) * nx + i;
 #pragma unroll
-      for (int a = 0; a <= P; ++a) w[a] = __ldg(wr + (size_t)a * nx);
-    } else {
-      lagrange_weights<P, float>(__ldg(T.eps32 + (size_t)n * nx + i), w);
+  for (int q = 0; q < kPts; ++q) {
+    const int i = threadIdx.x + q * kSliceThreads;
+    if (i < nx) {
+      g.base[q] = i + (int)__ldg(sh + i);
+      if constexpr (std::is_same<R, double>::value) {
+        const double* __restrict__ wr = T.w64 + (size_t)n * (P + 1) * nx + i;
+#pragma unroll
+        for (int a = 0; a <= P; ++a) g.w[q][a] = __ldg(wr + (size_t)a * nx);
+      } else {
+        g.eps[q] = __ldg(T.eps32 + (size_t)n * nx + i);
+      }
     }
-    R acc = w[0] * src[wrap_pow2(base, nx)];
-#pragma unroll
-    for (int a = 1; a <= P; ++a) acc += w[a] * src[wrap_pow2(base + a, nx)];
-    dst[i] = acc;
   }
 }
 
-// x <- M^{-1} x for M = I - diag(sigma) D_{2B} of one step (data: factorisation, see setup_kernels.cu).
-// scr: shared scratch of at least q (P + 1) + 2 B P reals (may alias the consumed gather source).
+// dst[i] = sum_a w_a(eps_i) src[(i + shift_i + a) mod nx]  -- the SL gather (Sec. 2.1).
+template <int P, typename R>
+__device__ __forceinline__ void apply_gather(const GatherRegs<P, R>& g, const R* __restrict__ src, R* __restrict__ dst,
+                                             int nx) {
+#pragma unroll
+  for (int q = 0; q < kPts; ++q) {
+    const int i = threadIdx.x + q * kSliceThreads;
+    if (i < nx) {
+      R w[P + 1];
+      if constexpr (std::is_same<R, double>::value) {
+#pragma unroll
+        for (int a = 0; a <= P; ++a) w[a] = g.w[q][a];
+      } else {
+        lagrange_weights<P, float>(g.eps[q], w);
+      }
+      const int b = g.base[q];
+      R acc = w[0] * src[wrap_pow2(b, nx)];
+#pragma unroll
+      for (int a = 1; a <= P; ++a) acc += w[a] * src[wrap_pow2(b + a, nx)];
+      dst[i] = acc;
+    }
+  }
+}
+
+// ---- correction solve x <- M^{-1} x, M = I - diag(sigma) D_{2B} (layout: solver_layout.cuh) ----------
+
 template <int B, typename R>
-__device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ scr, const R* __restrict__ data, int nx,
-                                           int P) {
-  const int s = nx / P, q = s - B, nb = B * P, ld = P + 1;
-  const SolverViewC<R> V = solver_view_c<R>(data, nx, B, P);
-  R* yt = scr;           // interior values, transposed [r][k] with leading dimension P + 1
-  R* gS = scr + q * ld;  // separator right-hand sides
-  R* xS = gS + nb;       // separator solution
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const int k = i / s, r = i - k * s - B;
-    if (r >= 0) yt[r * ld + k] = x[i];
-  }
-  __syncthreads();
-  if ((int)threadIdx.x < P) {  // banded forward / backward substitution of each interior block
-    const int k = threadIdx.x;
-    R y[B];
+struct SolverRegs {
+  R lu[kPartRows - B][2 * B + 1];
+};
+
+template <int B, typename R>
+__device__ __forceinline__ void load_solver(SolverRegs<B, R>& s, const R* __restrict__ data, int P) {
+  const int k = threadIdx.x;
+  if (k >= P) return;
 #pragma unroll
-    for (int t = 0; t < B; ++t) y[t] = (R)0;  // y[t] = value of row r-1-t
-    for (int r = 0; r < q; ++r) {
-      R v = yt[r * ld + k];
+  for (int r = 0; r < kPartRows - B; ++r)
+#pragma unroll
+    for (int f = 0; f <= 2 * B; ++f) s.lu[r][f] = __ldg(data + (size_t)rec_lu(B, r, f) * P + k);
+}
+
+// xch: shared scratch of 4 * P * B reals (may alias the consumed gather source).
+template <int B, typename R>
+__device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xch, const SolverRegs<B, R>& sr,
+                                           const R* __restrict__ data, int nx) {
+  constexpr int Q = kPartRows - B;
+  constexpr int BB = B * B;
+  const SolverGeom G = solver_geom(nx, 2 * B - 1);
+  const int P = G.P;
+  const int k = threadIdx.x;
+  const bool act = k < P;
+  const int g0 = k * kPartRows;
+  R* ytail = xch;
+  R* gb0 = xch + P * B;
+  R* gb1 = gb0 + P * B;
+  R* xsb = gb1 + P * B;
+  R y[Q], g[B], ct[BB], ch[BB];
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < BB; ++e) {
+      ct[e] = __ldg(data + (size_t)rec_ct(B, Q, 0, e) * P + k);
+      ch[e] = __ldg(data + (size_t)rec_ch(B, Q, 0, e) * P + k);
+    }
+    // FP32 reads the factor record from registers loaded before the gather; FP64 reads it here
+    auto LU = [&](int r, int f) -> R {
+      if constexpr (std::is_same<R, float>::value) return sr.lu[r][f];
+      else return __ldg(data + (size_t)rec_lu(B, r, f) * P + k);
+    };
+#pragma unroll
+    for (int r = 0; r < Q; ++r) y[r] = x[g0 + B + r];
+#pragma unroll
+    for (int r = 0; r < Q; ++r)
 #pragma unroll
       for (int t = 1; t <= B; ++t)
-        if (r - t >= 0) v -= V.lu[((size_t)(t - 1) * q + r) * P + k] * y[t - 1];
-      yt[r * ld + k] = v;
+        if (r - t >= 0) y[r] -= LU(r, t - 1) * y[r - t];
 #pragma unroll
-      for (int t = B - 1; t >= 1; --t) y[t] = y[t - 1];
-      y[0] = v;
-    }
-#pragma unroll
-    for (int t = 0; t < B; ++t) y[t] = (R)0;  // y[t] = value of row r+1+t
-    for (int r = q - 1; r >= 0; --r) {
-      R v = yt[r * ld + k];
+    for (int r = Q - 1; r >= 0; --r) {
 #pragma unroll
       for (int t = 1; t <= B; ++t)
-        if (r + t < q) v -= V.lu[((size_t)(B + t) * q + r) * P + k] * y[t - 1];
-      v *= V.lu[((size_t)B * q + r) * P + k];
-      yt[r * ld + k] = v;
+        if (r + t < Q) y[r] -= LU(r, B + t) * y[r + t];
+      y[r] *= LU(r, B);
+    }
 #pragma unroll
-      for (int t = B - 1; t >= 1; --t) y[t] = y[t - 1];
-      y[0] = v;
+    for (int a = 0; a < B; ++a) ytail[k * B + a] = y[Q - B + a];
+  }
+  __syncthreads();
+  R cf[2 * BB], fin[BB];
+  if (act) {
+    const int km = (k + P - 1) & (P - 1);
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      R v = x[g0 + a];
+#pragma unroll
+      for (int c = 0; c < B; ++c) v -= ct[a * B + c] * ytail[km * B + c] + ch[a * B + c] * y[c];
+      g[a] = v;
+    }
+    if (G.T > 0) {
+#pragma unroll
+      for (int e = 0; e < 2 * BB; ++e) cf[e] = __ldg(data + G.pcr_off + (size_t)e * P + k);
+    }
+#pragma unroll
+    for (int e = 0; e < BB; ++e) fin[e] = __ldg(data + G.fin_off + (size_t)e * P + k);
+  }
+  // block parallel cyclic reduction on the separators
+  for (int t = 0; t < G.T; ++t) {
+    R cfn[2 * BB];
+    if (act && t + 1 < G.T) {
+      const R* lv = data + G.pcr_off + (size_t)(t + 1) * 2 * BB * P;
+#pragma unroll
+      for (int e = 0; e < 2 * BB; ++e) cfn[e] = __ldg(lv + (size_t)e * P + k);
+    }
+    R* buf = (t & 1) ? gb1 : gb0;
+    if (act) {
+#pragma unroll
+      for (int a = 0; a < B; ++a) buf[k * B + a] = g[a];
+    }
+    __syncthreads();
+    if (act) {
+      const int d = 1 << t;
+      const int km = (k - d) & (P - 1), kp = (k + d) & (P - 1);
+      R gm[B], gp[B];
+#pragma unroll
+      for (int a = 0; a < B; ++a) {
+        gm[a] = buf[km * B + a];
+        gp[a] = buf[kp * B + a];
+      }
+#pragma unroll
+      for (int a = 0; a < B; ++a) {
+        R v = g[a];
+#pragma unroll
+        for (int c = 0; c < B; ++c) v += cf[a * B + c] * gm[c] + cf[BB + a * B + c] * gp[c];
+        g[a] = v;
+      }
+#pragma unroll
+      for (int e = 0; e < 2 * BB; ++e) cf[e] = cfn[e];
+    }
+  }
+  R xs[B];
+  if (act) {
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      R v = (R)0;
+#pragma unroll
+      for (int c = 0; c < B; ++c) v += fin[a * B + c] * g[c];
+      xs[a] = v;
+      xsb[k * B + a] = v;
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nb; e += blockDim.x) {  // separator right-hand sides
-    const int k = e / B, a = e - k * B, km = (k + P - 1) % P;
-    R v = x[k * s + a];
+  if (act) {
+    const int kp = (k + 1) & (P - 1);
+    R xn[B];
 #pragma unroll
-    for (int c = 0; c < B; ++c) {
-      v -= V.ctail[(k * B + a) * B + c] * yt[(q - B + c) * ld + km];
-      v -= V.chead[(k * B + a) * B + c] * yt[c * ld + k];
+    for (int a = 0; a < B; ++a) {
+      xn[a] = xsb[kp * B + a];
+      x[g0 + a] = xs[a];
     }
-    gS[e] = v;
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < nb; r += blockDim.x) {  // separators: inverse of the Schur complement
-    R acc = (R)0;
-    for (int c = 0; c < nb; ++c) acc += V.sinv[(size_t)c * nb + r] * gS[c];
-    xS[r] = acc;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {  // back-substitute the spikes
-    const int k = i / s, r = i - k * s - B;
-    if (r < 0) {
-      x[i] = xS[k * B + r + B];
-    } else {
-      const int kp = (k + 1 == P) ? 0 : k + 1;
-      R v = yt[r * ld + k];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      R v = y[r];
 #pragma unroll
       for (int c = 0; c < B; ++c) {
-        v -= V.vw[(size_t)c * nx + i] * xS[k * B + c];
-        v -= V.vw[(size_t)(B + c) * nx + i] * xS[kp * B + c];
+        v -= __ldg(data + (size_t)rec_v(B, Q, r, c) * P + k) * xs[c];
+        v -= __ldg(data + (size_t)rec_w(B, Q, r, c) * P + k) * xn[c];
       }
-      x[i] = v;
+      x[g0 + B + r] = v;
     }
   }
   __syncthreads();
 }
 
+// One full step src -> dst (Phi, or Psi with the correction solve), given the prefetched gather table.
 template <int P, typename R, bool COARSE>
-__device__ __forceinline__ void full_step(R*& src, R*& dst, const LevelTables& T, int n) {
-  gather_step<P, R>(src, dst, T, n);
+__device__ __forceinline__ void full_step(const GatherRegs<P, R>& gr, R* src, R* dst, const LevelTables& T, int n) {
+  constexpr int B = (P + 1) / 2;
+  SolverRegs<B, R> sr;
+  const R* data = COARSE ? (const R*)T.solver + (size_t)n * T.solver_stride : nullptr;
+  // FP32: issue the loads of the factor record before the gather so their latency overlaps it;
+  // FP64: load it after the gather (register pressure).
+  constexpr bool kEarly = std::is_same<R, float>::value;
+  if constexpr (COARSE && kEarly) load_solver<B, R>(sr, data, T.nx / kPartRows);
+  apply_gather<P, R>(gr, src, dst, T.nx);
   __syncthreads();
-  if constexpr (COARSE) {
-    constexpr int B = (P + 1) / 2;
-    corr_solve<B, R>(dst, src, (const R*)T.solver + (size_t)n * T.solver_stride, T.nx, T.P);
-  }
+  if constexpr (COARSE) corr_solve<B, R>(dst, src, sr, data, T.nx);
 }
 
 template <int P, typename R, bool COARSE>
@@ -170,9 +261,20 @@ __global__ void __launch_bounds__(kSliceThreads) k_relax_1d(LevelTables T, Relax
   __syncthreads();
   if (j >= a.J) return;  // extra CTA: only the correction of the last C-point
   double sq = 0.0;
+  // FP32: the next step's gather table is loaded during the current step; FP64 (ALU bound, and short
+  // of registers for two tables) loads it at the start of its step.
+  constexpr bool kPipe = std::is_same<R, float>::value;
+  GatherRegs<P, R> gcur, gnext;
+  if (kPipe && a.nsteps > 0) load_gather<P, R>(gnext, T, j * a.m);
   for (int k = 0; k < a.nsteps; ++k) {
     const int n = j * a.m + k;
-    full_step<P, R, COARSE>(src, dst, T, n);
+    if constexpr (kPipe) {
+      gcur = gnext;
+      if (k + 1 < a.nsteps) load_gather<P, R>(gnext, T, n + 1);
+    } else {
+      load_gather<P, R>(gcur, T, n);
+    }
+    full_step<P, R, COARSE>(gcur, src, dst, T, n);
     const R* gr = a.g ? (const R*)a.g + (size_t)(n + 1) * nx : nullptr;
     const bool last = (k == a.m - 1);
     if (!last) {
@@ -226,8 +328,17 @@ __global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, 
     if (store_all) out_all[i] = v;
   }
   __syncthreads();
+  constexpr bool kPipe = std::is_same<R, float>::value;
+  GatherRegs<P, R> gcur, gnext;
+  if (kPipe && N > 0) load_gather<P, R>(gnext, T, 0);
   for (int n = 0; n < N; ++n) {
-    full_step<P, R, COARSE>(src, dst, T, n);
+    if constexpr (kPipe) {
+      gcur = gnext;
+      if (n + 1 < N) load_gather<P, R>(gnext, T, n + 1);
+    } else {
+      load_gather<P, R>(gcur, T, n);
+    }
+    full_step<P, R, COARSE>(gcur, src, dst, T, n);
     const R* gr = g ? g + (size_t)(n + 1) * nx : nullptr;
     R* out = store_all ? out_all + (size_t)(n + 1) * nx : (n == N - 1 ? out_all : nullptr);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -251,16 +362,16 @@ __global__ void __launch_bounds__(kSliceThreads) k_apply_1d(LevelTables T, int n
   const int nx = T.nx, c = blockIdx.x;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) src[i] = in[(size_t)c * nx + i];
   __syncthreads();
-  full_step<P, R, COARSE>(src, dst, T, n0 + c);
+  GatherRegs<P, R> gr;
+  load_gather<P, R>(gr, T, n0 + c);
+  full_step<P, R, COARSE>(gr, src, dst, T, n0 + c);
   for (int i = threadIdx.x; i < nx; i += blockDim.x) out[(size_t)c * nx + i] = dst[i];
 }
 
 int buffer_elems(const LevelTables& T, bool coarse) {
   int e = T.nx;
   if (coarse) {
-    const int b = (T.p + 1) / 2;
-    const int s = T.nx / T.P, q = s - b;
-    const int need = q * (T.P + 1) + 2 * b * T.P;
+    const int need = 4 * (T.nx / kPartRows) * ((T.p + 1) / 2);
     if (need > e) e = need;
   }
   return (e + 31) & ~31;

@@ -163,7 +163,6 @@ struct mgrit_handle {
     T.nt = L.nt;
     T.solver = (l > 0 && opt.coarse_op == 0) ? L.solver : nullptr;
     T.solver_stride = L.solver_stride;
-    T.P = L.P;
     (void)is_double;
     return T;
   }
@@ -184,7 +183,7 @@ mgrit_status check_grid(const mgrit_grid* g, const mgrit_wavespeed* w, int order
   if ((g->dim == 1 && !k1) || (g->dim == 2 && !k2)) return fail(MGRIT_EINVAL, "wave kind does not match dim");
   if (!std::isfinite(w->a) || !std::isfinite(w->k) || !std::isfinite(w->a2))
     return fail(MGRIT_EINVAL, "wave parameters must be finite");
-  if (g->dim == 1 && g->nx > 8192) return fail(MGRIT_EUNSUPPORTED, "1D slices are kept on chip: nx <= 8192");
+  if (g->dim == 1 && g->nx > 4096) return fail(MGRIT_EUNSUPPORTED, "1D slices are kept on chip: nx <= 4096");
   if (g->dim == 2) return fail(MGRIT_EUNSUPPORTED, "2D problems are not supported by this build");
   return MGRIT_OK;
 }
@@ -372,8 +371,8 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
       if ((st = h->alloc((char**)&L.E, full * esz)) != MGRIT_OK) return cleanup_fail(st);
       if ((st = h->alloc((char**)&L.G, full * esz)) != MGRIT_OK) return cleanup_fail(st);
       if (opt.coarse_op == 0) {
-        L.P = solver_partitions(nx, p);
-        L.solver_stride = solver_reals(nx, p, L.P);
+        L.P = nx / 8;
+        L.solver_stride = solver_reals(nx, p);
         const size_t tot = L.solver_stride * L.nt * (L.is_double ? sizeof(double) : sizeof(float));
         if ((st = h->alloc((char**)&L.solver, tot)) != MGRIT_OK) return cleanup_fail(st);
       }
@@ -428,7 +427,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     }
     if (l > 0 && L.solver) {
       const int ev = h->phase_begin();
-      const int nl = launch_factor_1d(L.sigma, L.nt, nx, p, L.P, L.solver, L.is_double, h->flag_dev, s);
+      const int nl = launch_factor_1d(L.sigma, L.nt, nx, p, L.solver, L.is_double, h->flag_dev, s);
       h->phase_end(MGRIT_PHASE_FACTOR, ev, nl);
     }
     if ((st = cuda_fail("setup")) != MGRIT_OK) return st;

@@ -3,6 +3,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "physics.cuh"
+#include "solver_layout.cuh"
 
 namespace mgrit {
 
@@ -206,19 +207,8 @@ void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, u
 }
 
 // ------------------------------------------------------------------------------------------------
-// K3: partitioned factorisation of M = I - diag(sigma) D_{p+1} (eq. (Bp_def), (Phi_multilevel))
-//
-// The periodic system is split into P partitions of s = nx/P rows.  The first b rows of each
-// partition are separators S_k, the other q = s - b rows the interior I_k, which couples only to
-// S_k and S_{k+1}.  Per step we store: the banded LU of each interior block (no pivoting), the
-// spikes V_k = A_k^{-1} M[I_k, S_k] and W_k = A_k^{-1} M[I_k, S_{k+1}], the separator couplings to
-// the neighbouring interiors, and the inverse of the (periodic block-tridiagonal) Schur complement
-// on the separators.  Layout (reals) per step:
-//   lu    [(2b+1)][q][P]   rows t < b: L multipliers l_{t+1}; t = b: 1/U_rr; t > b: U_{r, r+t-b}
-//   vw    [2b][nx]         V columns then W columns, indexed by the interior point's global index
-//   sinv  [bP][bP]         column-major inverse of the Schur complement
-//   ctail [P][b][b]        M[S_k + a, (k s - b + c) mod nx]   (couples to the tail of I_{k-1})
-//   chead [P][b][b]        M[S_k + a, k s + b + c]           (couples to the head of I_k)
+// K3: factorisation of M = I - diag(sigma) D_{p+1} for every step of a level (eq. (Bp_def),
+// (Phi_multilevel)); layout and algorithm in solver_layout.cuh.  FP64 arithmetic, stored as R.
 // ------------------------------------------------------------------------------------------------
 
 MGRIT_HD double dstencil(int b, int j) {
@@ -230,273 +220,270 @@ MGRIT_HD double dstencil(int b, int j) {
   return ((b + j) & 1) ? -c : c;
 }
 
-size_t solver_reals(int nx, int p, int P) {
-  const int b = (p + 1) / 2;
-  const int s = nx / P, q = s - b;
-  return (size_t)(2 * b + 1) * q * P + (size_t)2 * b * nx + (size_t)(b * P) * (b * P) + (size_t)2 * P * b * b;
-}
+size_t solver_reals(int nx, int p) { return solver_geom(nx, p).total; }
 
-int solver_partitions(int nx, int p) {
-  const int b = (p + 1) / 2;
-  int P = 32;
-  while (P > 1 && (nx % P != 0 || nx / P < 2 * b + 1)) P >>= 1;
-  return P;
-}
-
-template <typename R>
-struct SolverView {
-  R* lu;
-  R* vw;
-  R* sinv;
-  R* ctail;
-  R* chead;
-};
-
-template <typename R>
-MGRIT_HD SolverView<R> solver_view(R* base, int nx, int b, int P) {
-  const int s = nx / P, q = s - b;
-  SolverView<R> v;
-  v.lu = base;
-  v.vw = v.lu + (size_t)(2 * b + 1) * q * P;
-  v.sinv = v.vw + (size_t)2 * b * nx;
-  v.ctail = v.sinv + (size_t)(b * P) * (b * P);
-  v.chead = v.ctail + (size_t)P * b * b;
-  return v;
-}
-
-constexpr int kFactorThreads = 256;
-constexpr int kMaxSchur = 96;  // b * P <= 3 * 32
-
-// Solve A_k x = rhs in place (interior block of partition k) using the stored LU (FP64 copy).
-__device__ void interior_solve_fp64(const double* lu, int b, int q, int P, int k, double* x /*len q, stride 1*/) {
-  for (int r = 0; r < q; ++r) {
-    double v = x[r];
-    for (int t = 1; t <= b && r - t >= 0; ++t) v -= lu[((size_t)(t - 1) * q + r) * P + k] * x[r - t];
-    x[r] = v;
+// In-place inverse of a B x B matrix (row-major) by Gauss-Jordan with partial pivoting; false if singular.
+template <int B>
+__device__ bool small_inverse(double (&A)[B][B]) {
+  int perm[B];
+  for (int kk = 0; kk < B; ++kk) {
+    int pr = kk;
+    for (int r = kk + 1; r < B; ++r)
+      if (fabs(A[r][kk]) > fabs(A[pr][kk])) pr = r;
+    perm[kk] = pr;
+    if (!(fabs(A[pr][kk]) > 1e-300)) return false;
+    if (pr != kk)
+      for (int c = 0; c < B; ++c) {
+        const double t = A[kk][c];
+        A[kk][c] = A[pr][c];
+        A[pr][c] = t;
+      }
+    const double pv = A[kk][kk];
+    A[kk][kk] = 1.0;
+    for (int c = 0; c < B; ++c) A[kk][c] /= pv;
+    for (int r = 0; r < B; ++r) {
+      if (r == kk) continue;
+      const double f = A[r][kk];
+      A[r][kk] = 0.0;
+      for (int c = 0; c < B; ++c) A[r][c] -= f * A[kk][c];
+    }
   }
-  for (int r = q - 1; r >= 0; --r) {
-    double v = x[r];
-    for (int t = 1; t <= b && r + t < q; ++t) v -= lu[((size_t)(b + t) * q + r) * P + k] * x[r + t];
-    x[r] = v * lu[((size_t)b * q + r) * P + k];
-  }
+  for (int kk = B - 1; kk >= 0; --kk)
+    if (perm[kk] != kk)
+      for (int r = 0; r < B; ++r) {
+        const double t = A[r][kk];
+        A[r][kk] = A[r][perm[kk]];
+        A[r][perm[kk]] = t;
+      }
+  return true;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kFactorThreads) k_factor_1d(const double* __restrict__ sigma_all, int nx, int p,
-                                                              int P, R* __restrict__ out_all, size_t stride,
-                                                              double* __restrict__ scratch_all, int* flag) {
-  const int n = blockIdx.x;
-  const int b = (p + 1) / 2;
-  const int s = nx / P, q = s - b;
-  const int nb = b * P;
-  const double* sigma = sigma_all + (size_t)n * nx;
-  R* out = out_all + (size_t)n * stride;  // (chunk-relative step n)
-  SolverView<R> V = solver_view<R>(out, nx, b, P);
-  // FP64 working copies in global scratch: lu [(2b+1)][q][P], spikes [2b][nx]
-  double* lu = scratch_all + (size_t)blockIdx.x * ((size_t)(2 * b + 1) * q * P + (size_t)2 * b * nx);
-  double* sp = lu + (size_t)(2 * b + 1) * q * P;
-  extern __shared__ double S[];  // [nb][nb] row-major Schur complement
-  __shared__ int perm[kMaxSchur];
-  __shared__ double piv_s;
-  __shared__ int piv_row;
+template <int B>
+__device__ void mat_mul(const double (&X)[B][B], const double (&Y)[B][B], double (&Z)[B][B]) {
+  for (int a = 0; a < B; ++a)
+    for (int c = 0; c < B; ++c) {
+      double v = 0.0;
+      for (int e = 0; e < B; ++e) v += X[a][e] * Y[e][c];
+      Z[a][c] = v;
+    }
+}
 
-  auto Mval = [&](int row, int col) -> double {  // entry M[row, col] (indices mod nx)
-    int off = col - row;
-    off = ((off % nx) + nx) % nx;
-    if (off > nx / 2) off -= nx;
-    const double dv = dstencil(b, off);
-    return (off == 0 ? 1.0 : 0.0) - sigma[((row % nx) + nx) % nx] * dv;
+// One CTA per step, one thread per partition k < P.
+template <int B, typename R>
+__global__ void __launch_bounds__(512) k_factor_1d(const double* __restrict__ sigma_all, int nx, R* __restrict__ out_all, size_t stride,
+                            int* flag) {
+  constexpr int Q = kPartRows - B;
+  const SolverGeom G = solver_geom(nx, 2 * B - 1);
+  const int P = G.P;
+  const double* sigma = sigma_all + (size_t)blockIdx.x * nx;
+  R* out = out_all + (size_t)blockIdx.x * stride;
+  extern __shared__ double sh[];  // exchange: 3 blocks of B x B per partition
+  const int k = threadIdx.x;
+  const bool active = k < P;
+  const int g0 = k * kPartRows;
+  auto Mval = [&](int row, int off) -> double {  // M[row, row + off], |off| <= B
+    const int rr = ((row % nx) + nx) % nx;
+    return (off == 0 ? 1.0 : 0.0) - sigma[rr] * dstencil(B, off);
   };
-
-  // 1) banded LU of each interior block (one thread per partition)
-  for (int k = threadIdx.x; k < P; k += blockDim.x) {
-    const int g0 = k * s + b;
-    double Uw[3][4];  // last b rows of U: Uw[t][c] = U[r-1-t][r-1-t+c], c = 0..b
-    for (int r = 0; r < q; ++r) {
-      double a[7];  // a[c + b] = A[r][r + c], c = -b..b
-      for (int c = -b; c <= b; ++c) a[c + b] = (r + c >= 0 && r + c < q) ? Mval(g0 + r, g0 + r + c) : 0.0;
-      for (int t = b; t >= 1; --t) {  // eliminate columns r-t (left to right)
+  double Lb[B][B] = {}, Db[B][B] = {}, Ub[B][B] = {};  // ctail / Mss / chead, then the Schur blocks
+  double Vh[B][B] = {}, Wh[B][B] = {};                  // head rows of the spikes
+  bool ok = true;
+  if (active) {
+    // 1) banded LU of the interior block (rows g0 + B + r)
+    double l[Q][B], U[Q][B + 1];
+    for (int r = 0; r < Q; ++r) {
+      double a[2 * B + 1];
+      for (int c = -B; c <= B; ++c) a[c + B] = (r + c >= 0 && r + c < Q) ? Mval(g0 + B + r, c) : 0.0;
+      for (int t = B; t >= 1; --t) {
         if (r - t < 0) {
-          lu[((size_t)(t - 1) * q + r) * P + k] = 0.0;
+          l[r][t - 1] = 0.0;
           continue;
         }
-        const double* Ur = Uw[t - 1];  // row r - t of U
-        const double l = a[b - t] / Ur[0];
-        lu[((size_t)(t - 1) * q + r) * P + k] = l;
-        for (int c = 1; c <= b; ++c) {  // columns r - t + c
+        const double lt = a[B - t] / U[r - t][0];
+        l[r][t - 1] = lt;
+        for (int c = 1; c <= B; ++c) {
           const int col = -t + c;
-          if (col <= b) a[col + b] -= l * Ur[c];
+          if (col <= B) a[col + B] -= lt * U[r - t][c];
         }
       }
-      const double diag = a[b];
-      if (!(fabs(diag) > 1e-13)) atomicExch(flag, 1);
-      lu[((size_t)b * q + r) * P + k] = 1.0 / diag;
-      for (int t = 1; t <= b; ++t) lu[((size_t)(b + t) * q + r) * P + k] = a[b + t];
-      for (int t = b - 1; t >= 1; --t)
-        for (int c = 0; c <= b; ++c) Uw[t][c] = Uw[t - 1][c];
-      for (int c = 0; c <= b; ++c) Uw[0][c] = a[b + c];
+      if (!(fabs(a[B]) > 1e-13)) ok = false;
+      for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
     }
-  }
-  __syncthreads();
-  // 2) spikes V (columns of S_k) and W (columns of S_{k+1})
-  for (int task = threadIdx.x; task < P * 2 * b; task += blockDim.x) {
-    const int k = task % P, col = task / P;  // col < b: V column col; else W column col - b
-    const int g0 = k * s + b;
-    double* dst = sp + (size_t)col * nx;
-    // build rhs in dst at the interior points of partition k
-    for (int r = 0; r < q; ++r) {
-      double v = 0.0;
-      if (col < b) {
-        const int off = (k * s + col) - (g0 + r);  // column in S_k
-        if (off >= -b) v = -sigma[g0 + r] * dstencil(b, off);
-      } else {
-        const int cc = col - b;
-        const int off = q - r + cc;  // column (k+1) s + cc relative to g0 + r
-        if (off <= b) v = -sigma[g0 + r] * dstencil(b, off);
+    auto solve = [&](double (&x)[Q]) {
+      for (int r = 0; r < Q; ++r)
+        for (int t = 1; t <= B; ++t)
+          if (r - t >= 0) x[r] -= l[r][t - 1] * x[r - t];
+      for (int r = Q - 1; r >= 0; --r) {
+        for (int t = 1; t <= B; ++t)
+          if (r + t < Q) x[r] -= U[r][t] * x[r + t];
+        x[r] /= U[r][0];
       }
-      dst[g0 + r] = v;
-    }
-    // forward / backward substitution along the contiguous interior range of dst
-    for (int r = 0; r < q; ++r) {
-      double v = dst[g0 + r];
-      for (int t = 1; t <= b && r - t >= 0; ++t) v -= lu[((size_t)(t - 1) * q + r) * P + k] * dst[g0 + r - t];
-      dst[g0 + r] = v;
-    }
-    for (int r = q - 1; r >= 0; --r) {
-      double v = dst[g0 + r];
-      for (int t = 1; t <= b && r + t < q; ++t) v -= lu[((size_t)(b + t) * q + r) * P + k] * dst[g0 + r + t];
-      dst[g0 + r] = v * lu[((size_t)b * q + r) * P + k];
-    }
-    // separator slots of this column: zero
-    if (k == 0) {
-      for (int kk = 0; kk < P; ++kk)
-        for (int a = 0; a < b; ++a) dst[kk * s + a] = 0.0;
-    }
-  }
-  __syncthreads();
-  // 3) couplings and the Schur complement on the separators
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) S[e] = 0.0;
-  __syncthreads();
-  for (int task = threadIdx.x; task < P * b; task += blockDim.x) {
-    const int k = task / b, a = task % b;
-    const int row = k * s + a;
-    const int km = (k + P - 1) % P, kp = (k + 1) % P;
-    double ct[3], ch[3];
-    for (int c = 0; c < b; ++c) {
-      ct[c] = Mval(row, k * s - b + c);  // tail of I_{k-1} (wraps for k = 0)
-      ch[c] = Mval(row, k * s + b + c);  // head of I_k
-      V.ctail[((size_t)k * b + a) * b + c] = (R)ct[c];
-      V.chead[((size_t)k * b + a) * b + c] = (R)ch[c];
-    }
-    for (int c = 0; c < b; ++c) {
-      // x_{S_{k-1}} coefficient: -ctail * V_{k-1}(tail rows)
-      double Lc = 0.0, Dc = Mval(row, k * s + c), Uc = 0.0;
-      for (int c2 = 0; c2 < b; ++c2) {
-        const int tail = km * s + b + (q - b + c2);  // global index of tail row c2 of I_{k-1}
-        const int head = k * s + b + c2;             // head row c2 of I_k
-        Lc -= ct[c2] * sp[(size_t)c * nx + tail];
-        Dc -= ct[c2] * sp[(size_t)(b + c) * nx + tail];
-        Dc -= ch[c2] * sp[(size_t)c * nx + head];
-        Uc -= ch[c2] * sp[(size_t)(b + c) * nx + head];
+    };
+    // 2) spikes V = A^{-1} M[I_k, S_k], W = A^{-1} M[I_k, S_{k+1}]
+    double V[Q][B], W[Q][B];
+    for (int c = 0; c < B; ++c) {
+      double xv[Q], xw[Q];
+      for (int r = 0; r < Q; ++r) {
+        const int ov = c - B - r;  // column g0 + c of S_k
+        const int ow = Q - r + c;  // column g0 + 8 + c of S_{k+1}
+        xv[r] = (ov >= -B) ? -sigma[g0 + B + r] * dstencil(B, ov) : 0.0;
+        xw[r] = (ow <= B) ? -sigma[g0 + B + r] * dstencil(B, ow) : 0.0;
       }
-      atomicAdd(&S[(size_t)(k * b + a) * nb + km * b + c], Lc);
-      atomicAdd(&S[(size_t)(k * b + a) * nb + k * b + c], Dc);
-      atomicAdd(&S[(size_t)(k * b + a) * nb + kp * b + c], Uc);
+      solve(xv);
+      solve(xw);
+      for (int r = 0; r < Q; ++r) {
+        V[r][c] = xv[r];
+        W[r][c] = xw[r];
+      }
     }
+    // 3) couplings of the separator rows
+    for (int a = 0; a < B; ++a)
+      for (int c = 0; c < B; ++c) {
+        Lb[a][c] = (c >= a) ? Mval(g0 + a, c - B - a) : 0.0;  // ctail
+        Ub[a][c] = (c <= a) ? Mval(g0 + a, B + c - a) : 0.0;  // chead
+        Db[a][c] = Mval(g0 + a, c - a);                       // M[S_k, S_k]
+        Vh[a][c] = V[a][c];
+        Wh[a][c] = W[a][c];
+      }
+    for (int r = 0; r < Q; ++r) {
+      for (int t = 0; t < B; ++t) out[(size_t)rec_lu(B, r, t) * P + k] = (R)l[r][t];
+      out[(size_t)rec_lu(B, r, B) * P + k] = (R)(1.0 / U[r][0]);
+      for (int t = 1; t <= B; ++t) out[(size_t)rec_lu(B, r, B + t) * P + k] = (R)U[r][t];
+      for (int c = 0; c < B; ++c) {
+        out[(size_t)rec_v(B, Q, r, c) * P + k] = (R)V[r][c];
+        out[(size_t)rec_w(B, Q, r, c) * P + k] = (R)W[r][c];
+      }
+    }
+    for (int a = 0; a < B; ++a)
+      for (int c = 0; c < B; ++c) {
+        out[(size_t)rec_ct(B, Q, a, c) * P + k] = (R)Lb[a][c];
+        out[(size_t)rec_ch(B, Q, a, c) * P + k] = (R)Ub[a][c];
+        // tail rows of V and W go to partition k + 1
+        sh[((size_t)k * 2 + 0) * B * B + a * B + c] = V[Q - B + a][c];
+        sh[((size_t)k * 2 + 1) * B * B + a * B + c] = W[Q - B + a][c];
+      }
   }
   __syncthreads();
-  // 4) in-place Gauss-Jordan inversion of S (row-major in smem) with partial pivoting
-  for (int kk = 0; kk < nb; ++kk) {
-    if (threadIdx.x == 0) {
-      int pr = kk;
-      double best = fabs(S[(size_t)kk * nb + kk]);
-      for (int r = kk + 1; r < nb; ++r) {
-        const double v = fabs(S[(size_t)r * nb + kk]);
-        if (v > best) {
-          best = v;
-          pr = r;
+  if (active) {
+    // 4) Schur complement blocks: L_k (x_{S_{k-1}}), D_k (x_{S_k}), U_k (x_{S_{k+1}})
+    const int km = (k + P - 1) % P;
+    double Ln[B][B], Dn[B][B], Un[B][B];
+    for (int a = 0; a < B; ++a)
+      for (int c = 0; c < B; ++c) {
+        double lv = 0.0, dv = Db[a][c], uv = 0.0;
+        for (int c2 = 0; c2 < B; ++c2) {
+          const double vt = sh[((size_t)km * 2 + 0) * B * B + c2 * B + c];
+          const double wt = sh[((size_t)km * 2 + 1) * B * B + c2 * B + c];
+          lv -= Lb[a][c2] * vt;
+          dv -= Lb[a][c2] * wt;
+          dv -= Ub[a][c2] * Vh[c2][c];
+          uv -= Ub[a][c2] * Wh[c2][c];
         }
+        Ln[a][c] = lv;
+        Dn[a][c] = dv;
+        Un[a][c] = uv;
       }
-      piv_row = pr;
-      perm[kk] = pr;
-      if (!(best > 1e-300)) atomicExch(flag, 1);
-    }
-    __syncthreads();
-    const int pr = piv_row;
-    if (pr != kk)
-      for (int c = threadIdx.x; c < nb; c += blockDim.x) {
-        const double t = S[(size_t)kk * nb + c];
-        S[(size_t)kk * nb + c] = S[(size_t)pr * nb + c];
-        S[(size_t)pr * nb + c] = t;
+    for (int a = 0; a < B; ++a)
+      for (int c = 0; c < B; ++c) {
+        Lb[a][c] = Ln[a][c];
+        Db[a][c] = Dn[a][c];
+        Ub[a][c] = Un[a][c];
       }
-    __syncthreads();
-    if (threadIdx.x == 0) piv_s = S[(size_t)kk * nb + kk];
-    __syncthreads();
-    const double pv = piv_s;
-    for (int c = threadIdx.x; c < nb; c += blockDim.x)
-      S[(size_t)kk * nb + c] = (c == kk ? 1.0 : S[(size_t)kk * nb + c]) / pv;
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-      const int r = e / nb, c = e % nb;
-      if (r == kk) continue;
-      const double f = S[(size_t)r * nb + kk];
-      if (c == kk) continue;
-      S[e] -= f * S[(size_t)kk * nb + c];
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
-      if (r == kk) continue;
-      S[(size_t)r * nb + kk] = -S[(size_t)r * nb + kk] * S[(size_t)kk * nb + kk];
-    }
-    __syncthreads();
   }
-  // undo the row interchanges as column interchanges, in reverse order
-  for (int kk = nb - 1; kk >= 0; --kk) {
-    const int pr = perm[kk];
-    if (pr != kk)
-      for (int r = threadIdx.x; r < nb; r += blockDim.x) {
-        const double t = S[(size_t)r * nb + kk];
-        S[(size_t)r * nb + kk] = S[(size_t)r * nb + pr];
-        S[(size_t)r * nb + pr] = t;
-      }
+  __syncthreads();
+  // 5) block PCR factorisation
+  for (int t = 0; t < G.T; ++t) {
+    const int d = 1 << t;
+    if (active)
+      for (int a = 0; a < B; ++a)
+        for (int c = 0; c < B; ++c) {
+          sh[((size_t)k * 3 + 0) * B * B + a * B + c] = Lb[a][c];
+          sh[((size_t)k * 3 + 1) * B * B + a * B + c] = Db[a][c];
+          sh[((size_t)k * 3 + 2) * B * B + a * B + c] = Ub[a][c];
+        }
     __syncthreads();
+    double Lm[B][B], Dm[B][B], Um[B][B], Lp[B][B], Dp[B][B], Up[B][B];
+    if (active) {
+      const int km = ((k - d) % P + P) % P, kp = (k + d) % P;
+      for (int a = 0; a < B; ++a)
+        for (int c = 0; c < B; ++c) {
+          Lm[a][c] = sh[((size_t)km * 3 + 0) * B * B + a * B + c];
+          Dm[a][c] = sh[((size_t)km * 3 + 1) * B * B + a * B + c];
+          Um[a][c] = sh[((size_t)km * 3 + 2) * B * B + a * B + c];
+          Lp[a][c] = sh[((size_t)kp * 3 + 0) * B * B + a * B + c];
+          Dp[a][c] = sh[((size_t)kp * 3 + 1) * B * B + a * B + c];
+          Up[a][c] = sh[((size_t)kp * 3 + 2) * B * B + a * B + c];
+        }
+    }
+    __syncthreads();
+    if (active) {
+      ok = ok && small_inverse<B>(Dm) && small_inverse<B>(Dp);
+      double al[B][B], ga[B][B], t1[B][B];
+      mat_mul<B>(Lb, Dm, al);
+      mat_mul<B>(Ub, Dp, ga);
+      for (int a = 0; a < B; ++a)
+        for (int c = 0; c < B; ++c) {
+          al[a][c] = -al[a][c];
+          ga[a][c] = -ga[a][c];
+        }
+      R* pc = out + G.pcr_off + (size_t)t * 2 * B * B * P;
+      for (int a = 0; a < B; ++a)
+        for (int c = 0; c < B; ++c) {
+          pc[(size_t)(a * B + c) * P + k] = (R)al[a][c];
+          pc[(size_t)(B * B + a * B + c) * P + k] = (R)ga[a][c];
+        }
+      double nD[B][B];
+      mat_mul<B>(al, Um, t1);
+      for (int a = 0; a < B; ++a)
+        for (int c = 0; c < B; ++c) nD[a][c] = Db[a][c] + t1[a][c];
+      mat_mul<B>(ga, Lp, t1);
+      for (int a = 0; a < B; ++a)
+        for (int c = 0; c < B; ++c) nD[a][c] += t1[a][c];
+      mat_mul<B>(al, Lm, t1);
+      for (int a = 0; a < B; ++a)
+        for (int c = 0; c < B; ++c) Lb[a][c] = t1[a][c];
+      mat_mul<B>(ga, Up, t1);
+      for (int a = 0; a < B; ++a)
+        for (int c = 0; c < B; ++c) {
+          Ub[a][c] = t1[a][c];
+          Db[a][c] = nD[a][c];
+        }
+    }
   }
-  // 5) write out: LU, spikes (global point layout), Schur inverse (column-major)
-  for (size_t e = threadIdx.x; e < (size_t)(2 * b + 1) * q * P; e += blockDim.x) V.lu[e] = (R)lu[e];
-  for (size_t e = threadIdx.x; e < (size_t)2 * b * nx; e += blockDim.x) V.vw[e] = (R)sp[e];
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    V.sinv[(size_t)c * nb + r] = (R)S[e];
+  if (active) {
+    double F[B][B];
+    for (int a = 0; a < B; ++a)
+      for (int c = 0; c < B; ++c) F[a][c] = Lb[a][c] + Db[a][c] + Ub[a][c];
+    ok = ok && small_inverse<B>(F);
+    for (int a = 0; a < B; ++a)
+      for (int c = 0; c < B; ++c) out[G.fin_off + (size_t)(a * B + c) * P + k] = (R)F[a][c];
+    if (!ok) atomicExch(flag, 1);
   }
 }
 
-int launch_factor_1d(const double* sigma, int nt, int nx, int p, int P, void* out, int is_double, int* flag,
+int launch_factor_1d(const double* sigma, int nt, int nx, int p, void* out, int is_double, int* flag,
                      cudaStream_t st) {
-  const int b = (p + 1) / 2;
-  const int s = nx / P, q = s - b;
-  const size_t per = (size_t)(2 * b + 1) * q * P + (size_t)2 * b * nx;
-  const size_t stride = solver_reals(nx, p, P);
-  const int nb = b * P;
-  const size_t smem = (size_t)nb * nb * sizeof(double);
-  cudaFuncSetAttribute(k_factor_1d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(k_factor_1d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  // process in chunks to bound the FP64 scratch
-  const int chunk = 256;
-  double* scratch = nullptr;
-  const int nchunk = nt < chunk ? nt : chunk;
-  if (cudaMallocAsync((void**)&scratch, per * nchunk * sizeof(double), st) != cudaSuccess) return 0;
-  int launches = 0;
-  for (int n0 = 0; n0 < nt; n0 += chunk, ++launches) {
-    const int cnt = (nt - n0) < chunk ? (nt - n0) : chunk;
-    if (is_double)
-      k_factor_1d<double><<<cnt, kFactorThreads, smem, st>>>(sigma + (size_t)n0 * nx, nx, p, P,
-                                                          (double*)out + (size_t)n0 * stride, stride, scratch, flag);
-    else
-      k_factor_1d<float><<<cnt, kFactorThreads, smem, st>>>(sigma + (size_t)n0 * nx, nx, p, P,
-                                                         (float*)out + (size_t)n0 * stride, stride, scratch, flag);
+  const SolverGeom G = solver_geom(nx, p);
+  const int threads = ((G.P + 31) / 32) * 32;
+  const size_t smem = (size_t)G.P * 3 * G.B * G.B * sizeof(double);
+  const size_t stride = G.total;
+#define MGRIT_FACTOR(BB)                                                                                  \
+  if (is_double) {                                                                                        \
+    cudaFuncSetAttribute(k_factor_1d<BB, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    k_factor_1d<BB, double><<<nt, threads, smem, st>>>(sigma, nx, (double*)out, stride, flag);            \
+  } else {                                                                                                \
+    cudaFuncSetAttribute(k_factor_1d<BB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    k_factor_1d<BB, float><<<nt, threads, smem, st>>>(sigma, nx, (float*)out, stride, flag);             \
   }
-  cudaFreeAsync(scratch, st);
-  return launches;
+  if (G.B == 1) {
+    MGRIT_FACTOR(1)
+  } else if (G.B == 2) {
+    MGRIT_FACTOR(2)
+  } else {
+    MGRIT_FACTOR(3)
+  }
+#undef MGRIT_FACTOR
+  return 1;
 }
 
 }  // namespace mgrit
