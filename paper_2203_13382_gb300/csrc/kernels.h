@@ -63,6 +63,10 @@ struct LevelTables {
   // correction solver (coarse levels, corrected operator); NULL for the plain SL step
   const void* solver;
   size_t solver_stride;  // reals per step
+  // FP32 coarse levels: bytes of the per-step reduction coefficients staged into shared memory by a
+  // TMA bulk copy (0 = read from global memory); err: device flag set to 1 if a bounded wait gave up.
+  unsigned stage_bytes;
+  int* err;
 };
 
 struct RelaxArgs {

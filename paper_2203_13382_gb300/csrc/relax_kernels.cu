@@ -22,9 +22,8 @@ template <int P, typename R>
 struct GatherRegs;
 
 template <int P>
-struct GatherRegs<P, double> {
-  int base[kPts];
-  double w[kPts][P + 1];
+struct GatherRegs<P, double> {  // FP64 streams its table loads inside the gather (register pressure)
+  int n;
 };
 
 template <int P>
@@ -35,18 +34,18 @@ struct GatherRegs<P, float> {
 
 template <int P, typename R>
 __device__ __forceinline__ void load_gather(GatherRegs<P, R>& g, const LevelTables& T, int n) {
+  if constexpr (std::is_same<R, double>::value) {
+    g.n = n;
+    return;
+  }
   const int nx = T.nx;
   const uint16_t* __restrict__ sh = T.shift + (size_t)n * nx;
 #pragma unroll
   for (int q = 0; q < kPts; ++q) {
     const int i = threadIdx.x + q * kSliceThreads;
-    if (i < nx) {
-      g.base[q] = i + (int)__ldg(sh + i);
-      if constexpr (std::is_same<R, double>::value) {
-        const double* __restrict__ wr = T.w64 + (size_t)n * (P + 1) * nx + i;
-#pragma unroll
-        for (int a = 0; a <= P; ++a) g.w[q][a] = __ldg(wr + (size_t)a * nx);
-      } else {
+    if constexpr (!std::is_same<R, double>::value) {
+      if (i < nx) {
+        g.base[q] = i + (int)__ldg(sh + i);
         g.eps[q] = __ldg(T.eps32 + (size_t)n * nx + i);
       }
     }
@@ -55,20 +54,24 @@ __device__ __forceinline__ void load_gather(GatherRegs<P, R>& g, const LevelTabl
 
 // dst[i] = sum_a w_a(eps_i) src[(i + shift_i + a) mod nx]  -- the SL gather (Sec. 2.1).
 template <int P, typename R>
-__device__ __forceinline__ void apply_gather(const GatherRegs<P, R>& g, const R* __restrict__ src, R* __restrict__ dst,
-                                             int nx) {
-#pragma unroll
+__device__ __forceinline__ void apply_gather(const GatherRegs<P, R>& g, const LevelTables& T, const R* __restrict__ src,
+                                             R* __restrict__ dst) {
+  const int nx = T.nx;
+#pragma unroll 2
   for (int q = 0; q < kPts; ++q) {
     const int i = threadIdx.x + q * kSliceThreads;
     if (i < nx) {
       R w[P + 1];
+      int b;
       if constexpr (std::is_same<R, double>::value) {
+        const double* __restrict__ wr = T.w64 + (size_t)g.n * (P + 1) * nx + i;
 #pragma unroll
-        for (int a = 0; a <= P; ++a) w[a] = g.w[q][a];
+        for (int a = 0; a <= P; ++a) w[a] = __ldg(wr + (size_t)a * nx);
+        b = i + (int)__ldg(T.shift + (size_t)g.n * nx + i);
       } else {
         lagrange_weights<P, float>(g.eps[q], w);
+        b = g.base[q];
       }
-      const int b = g.base[q];
       R acc = w[0] * src[wrap_pow2(b, nx)];
 #pragma unroll
       for (int a = 1; a <= P; ++a) acc += w[a] * src[wrap_pow2(b + a, nx)];
@@ -95,9 +98,11 @@ __device__ __forceinline__ void load_solver(SolverRegs<B, R>& s, const R* __rest
 }
 
 // xch: shared scratch of 4 * P * B reals (may alias the consumed gather source).
+// pcr_src: the coefficient block [pcr_off, total) of this step, either in global memory (data +
+// pcr_off) or staged in shared memory.
 template <int B, typename R>
 __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xch, const SolverRegs<B, R>& sr,
-                                           const R* __restrict__ data, int nx) {
+                                           const R* __restrict__ data, const R* pcr_src, int nx) {
   constexpr int Q = kPartRows - B;
   constexpr int BB = B * B;
   const SolverGeom G = solver_geom(nx, 2 * B - 1);
@@ -151,18 +156,18 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
     }
     if (G.T > 0) {
 #pragma unroll
-      for (int e = 0; e < 2 * BB; ++e) cf[e] = __ldg(data + G.pcr_off + (size_t)e * P + k);
+      for (int e = 0; e < 2 * BB; ++e) cf[e] = pcr_src[(size_t)e * P + k];
     }
 #pragma unroll
-    for (int e = 0; e < BB; ++e) fin[e] = __ldg(data + G.fin_off + (size_t)e * P + k);
+    for (int e = 0; e < BB; ++e) fin[e] = pcr_src[(G.fin_off - G.pcr_off) + (size_t)e * P + k];
   }
   // block parallel cyclic reduction on the separators
   for (int t = 0; t < G.T; ++t) {
     R cfn[2 * BB];
     if (act && t + 1 < G.T) {
-      const R* lv = data + G.pcr_off + (size_t)(t + 1) * 2 * BB * P;
+      const R* lv = pcr_src + (size_t)(t + 1) * 2 * BB * P;
 #pragma unroll
-      for (int e = 0; e < 2 * BB; ++e) cfn[e] = __ldg(lv + (size_t)e * P + k);
+      for (int e = 0; e < 2 * BB; ++e) cfn[e] = lv[(size_t)e * P + k];
     }
     R* buf = (t & 1) ? gb1 : gb0;
     if (act) {
@@ -224,20 +229,73 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
   __syncthreads();
 }
 
+// Shared-memory staging of the reduction coefficients of one coarse step (FP32 levels).
+struct Stage {
+  void* buf;       // shared buffer of T.stage_bytes, or nullptr
+  uint64_t* bar;   // mbarrier completing the bulk copy
+  uint32_t phase;  // parity of the next completion
+};
+
 // One full step src -> dst (Phi, or Psi with the correction solve), given the prefetched gather table.
+// Returns false if a bounded wait gave up (the caller then stops; the flag T.err is set).
 template <int P, typename R, bool COARSE>
-__device__ __forceinline__ void full_step(const GatherRegs<P, R>& gr, R* src, R* dst, const LevelTables& T, int n) {
+__device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R* dst, const LevelTables& T, int n,
+                                          Stage& stg) {
   constexpr int B = (P + 1) / 2;
   SolverRegs<B, R> sr;
   const R* data = COARSE ? (const R*)T.solver + (size_t)n * T.solver_stride : nullptr;
+  const R* pcr_src = nullptr;
+  if constexpr (COARSE) {
+    const SolverGeom G = solver_geom(T.nx, T.p);
+    pcr_src = data + G.pcr_off;
+    if (stg.buf && threadIdx.x == 0) {  // TMA: stage this step's reduction coefficients
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(stg.bar, T.stage_bytes);
+      bulk_copy_g2s(stg.buf, pcr_src, T.stage_bytes, stg.bar);
+    }
+  }
   // FP32: issue the loads of the factor record before the gather so their latency overlaps it;
-  // FP64: load it after the gather (register pressure).
+  // FP64: they are read inside the solve (register pressure).
   constexpr bool kEarly = std::is_same<R, float>::value;
   if constexpr (COARSE && kEarly) load_solver<B, R>(sr, data, T.nx / kPartRows);
-  apply_gather<P, R>(gr, src, dst, T.nx);
+  apply_gather<P, R>(gr, T, src, dst);
   __syncthreads();
-  if constexpr (COARSE) corr_solve<B, R>(dst, src, sr, data, T.nx);
+  if constexpr (COARSE) {
+    if (stg.buf) {
+      const bool ok = mbar_wait_bounded(stg.bar, stg.phase, kWaitLimitCycles);
+      stg.phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          atomicExch(T.err, 1);
+          mbar_wait_bounded(stg.bar, stg.phase ^ 1u, kWaitLimitCycles);  // let the copy in flight land
+        }
+        return false;
+      }
+      pcr_src = (const R*)stg.buf;
+    }
+    corr_solve<B, R>(dst, src, sr, data, pcr_src, T.nx);
+  }
+  return true;
 }
+
+// Carves the staging buffer and its barrier out of dynamic shared memory after `used` bytes and
+// initialises the barrier (all threads must call; includes a barrier).
+__device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, unsigned bytes) {
+  Stage s;
+  s.phase = 0;
+  if (bytes == 0) {
+    s.buf = nullptr;
+    s.bar = nullptr;
+    return s;
+  }
+  const size_t off = (used + 127) & ~(size_t)127;
+  s.buf = smem + off;
+  s.bar = reinterpret_cast<uint64_t*>(smem + off + ((bytes + 127) & ~127u));
+  if (threadIdx.x == 0) mbar_init(s.bar, 1);
+  __syncthreads();
+  return s;
+}
+
 
 template <int P, typename R, bool COARSE>
 __global__ void __launch_bounds__(kSliceThreads) k_relax_1d(LevelTables T, RelaxArgs a, int buf) {
@@ -247,6 +305,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_relax_1d(LevelTables T, Relax
   double* red = reinterpret_cast<double*>(dst + buf);
   const int nx = T.nx;
   const int j = blockIdx.x;
+  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), COARSE ? T.stage_bytes : 0u);
   {
     const R* st = a.start ? (const R*)a.start + (size_t)j * a.start_stride : nullptr;
     const R* co = a.corr ? (const R*)a.corr + (size_t)j * a.corr_stride : nullptr;
@@ -274,7 +333,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_relax_1d(LevelTables T, Relax
     } else {
       load_gather<P, R>(gcur, T, n);
     }
-    full_step<P, R, COARSE>(gcur, src, dst, T, n);
+    if (!full_step<P, R, COARSE>(gcur, src, dst, T, n, stg)) return;
     const R* gr = a.g ? (const R*)a.g + (size_t)(n + 1) * nx : nullptr;
     const bool last = (k == a.m - 1);
     if (!last) {
@@ -322,6 +381,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, 
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
   const int nx = T.nx;
+  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), COARSE ? T.stage_bytes : 0u);
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const R v = u0 ? u0[i] : (R)0;
     src[i] = v;
@@ -338,7 +398,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, 
     } else {
       load_gather<P, R>(gcur, T, n);
     }
-    full_step<P, R, COARSE>(gcur, src, dst, T, n);
+    if (!full_step<P, R, COARSE>(gcur, src, dst, T, n, stg)) return;
     const R* gr = g ? g + (size_t)(n + 1) * nx : nullptr;
     R* out = store_all ? out_all + (size_t)(n + 1) * nx : (n == N - 1 ? out_all : nullptr);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -360,11 +420,12 @@ __global__ void __launch_bounds__(kSliceThreads) k_apply_1d(LevelTables T, int n
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
   const int nx = T.nx, c = blockIdx.x;
+  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), COARSE ? T.stage_bytes : 0u);
   for (int i = threadIdx.x; i < nx; i += blockDim.x) src[i] = in[(size_t)c * nx + i];
   __syncthreads();
   GatherRegs<P, R> gr;
   load_gather<P, R>(gr, T, n0 + c);
-  full_step<P, R, COARSE>(gr, src, dst, T, n0 + c);
+  if (!full_step<P, R, COARSE>(gr, src, dst, T, n0 + c, stg)) return;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) out[(size_t)c * nx + i] = dst[i];
 }
 
@@ -378,14 +439,16 @@ int buffer_elems(const LevelTables& T, bool coarse) {
 }
 
 template <typename R>
-size_t smem_bytes(int buf) {
-  return 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double);
+size_t smem_bytes(int buf, unsigned stage) {
+  size_t b = 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double);
+  if (stage) b = ((b + 127) & ~(size_t)127) + ((stage + 127) & ~127u) + 16;
+  return b;
 }
 
 template <typename R, bool COARSE>
 cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
-  const size_t sm = smem_bytes<R>(buf);
+  const size_t sm = smem_bytes<R>(buf, COARSE ? T.stage_bytes : 0u);
   const int grid = a.J + (a.extra_cta ? 1 : 0);
   if (grid <= 0) return cudaSuccess;
 #define MGRIT_LAUNCH_RELAX(PP)                                                                             \
@@ -406,7 +469,7 @@ template <typename R, bool COARSE>
 cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, const void* u0, void* u, int store_all,
                                 cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
-  const size_t sm = smem_bytes<R>(buf);
+  const size_t sm = smem_bytes<R>(buf, COARSE ? T.stage_bytes : 0u);
 #define MGRIT_LAUNCH_SEQ(PP)                                                                               \
   {                                                                                                        \
     auto kern = k_sequential_1d<PP, R, COARSE>;                                                            \
@@ -424,7 +487,7 @@ cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, cons
 template <typename R, bool COARSE>
 cudaError_t apply_dispatch(const LevelTables& T, int n0, int count, const void* in, void* out, cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
-  const size_t sm = smem_bytes<R>(buf);
+  const size_t sm = smem_bytes<R>(buf, COARSE ? T.stage_bytes : 0u);
 #define MGRIT_LAUNCH_APPLY(PP)                                                                             \
   {                                                                                                        \
     auto kern = k_apply_1d<PP, R, COARSE>;                                                                 \

@@ -2,6 +2,7 @@
 // V-cycle orchestration (Sec. 2.2, 3.4) over the kernels of setup_kernels.cu / relax_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -78,6 +79,7 @@ struct mgrit_handle {
   double* norm_dev = nullptr;
   double* norm_host = nullptr;  // pinned
   int* flag_dev = nullptr;
+  int* err_dev = nullptr;  // set by kernels whose bounded wait gave up
   double setup_ms = 0.0;
   // launch accounting and optional per-phase event timing
   int64_t setup_launches = 0, call_launches = 0;
@@ -163,7 +165,18 @@ struct mgrit_handle {
     T.nt = L.nt;
     T.solver = (l > 0 && opt.coarse_op == 0) ? L.solver : nullptr;
     T.solver_stride = L.solver_stride;
-    (void)is_double;
+    T.err = err_dev;
+    T.stage_bytes = 0;
+    if (T.solver && !is_double) {
+      // TMA staging of the reduction coefficients: needs P = nx/8 >= 4 (16-byte alignment of every
+      // step's block and of its size) and room in shared memory next to the two slice buffers.
+      const int P = grid.nx / 8, B = (order + 1) / 2;
+      int T_ = 0;
+      while ((1 << T_) < P) ++T_;
+      const size_t bytes = (size_t)(T_ * 2 * B * B + B * B) * P * sizeof(float);
+      const size_t slices = 2 * (size_t)std::max(grid.nx, 4 * P * B) * sizeof(float) + 64 * sizeof(double);
+      if (P >= 4 && bytes % 16 == 0 && slices + bytes + 512 <= 220 * 1024) T.stage_bytes = (unsigned)bytes;
+    }
     return T;
   }
 };
@@ -281,7 +294,11 @@ mgrit_status read_norm(mgrit_handle* h, int J, double* out) {
   launch_sum(h->norm_partial, J, h->norm_dev, h->stream);
   h->phase_end(MGRIT_PHASE_MISC, ev, 1);
   MG_CUDA(cudaMemcpyAsync(h->norm_host, h->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  MG_CUDA(cudaMemcpyAsync(h->norm_host + 1, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   MG_CUDA(cudaStreamSynchronize(h->stream));
+  int err = 0;
+  std::memcpy(&err, h->norm_host + 1, sizeof(int));
+  if (err) return fail(MGRIT_ETIMEOUT, "a bounded device wait gave up (TMA staging did not complete)");
   *out = std::sqrt(h->norm_host[0]);
   return MGRIT_OK;
 }
@@ -388,6 +405,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   if ((st = h->alloc(&h->norm_partial, (size_t)J1 + 1)) != MGRIT_OK) return cleanup_fail(st);
   if ((st = h->alloc(&h->norm_dev, 2)) != MGRIT_OK) return cleanup_fail(st);
   if ((st = h->alloc(&h->flag_dev, 1)) != MGRIT_OK) return cleanup_fail(st);
+  if ((st = h->alloc(&h->err_dev, 1)) != MGRIT_OK) return cleanup_fail(st);
   if (cudaMallocHost((void**)&h->norm_host, 4 * sizeof(double)) != cudaSuccess)
     return cleanup_fail(fail(MGRIT_ENOMEM, "pinned host allocation failed"));
 
@@ -406,6 +424,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   }
   h->reset_call_counters();
   cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s);
+  cudaMemsetAsync(h->err_dev, 0, sizeof(int), s);
   // fine departure points and tables
   {
     const int ev = h->phase_begin();

@@ -11,14 +11,55 @@ namespace mgrit {
 // K1: fine departure offsets (Sec. 2.1 eq. (depart_ODE); Sec. 4.1 eq. (SL2D_char1-2))
 // ------------------------------------------------------------------------------------------------
 
-__global__ void k_departure_1d(WaveParams w, Tableau T, int nx, int nt, double xmin, double h, double dt,
+// sin and cos of a small angle: Taylor polynomials (truncation below 3e-19 for |t| < 1/8), else sincos.
+MGRIT_D void small_sincos(double t, double& st, double& ct) {
+  if (fabs(t) < 0.125) {
+    const double t2 = t * t;
+    st = t * (1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040 + t2 * (1.0 / 362880)))));
+    ct = 1.0 + t2 * (-0.5 + t2 * (1.0 / 24 + t2 * (-1.0 / 720 + t2 * (1.0 / 40320 + t2 * (-1.0 / 3628800)))));
+  } else {
+    sincos(t, &st, &ct);
+  }
+}
+
+// One block row of arrival nodes of one step n (blockIdx.y).  The time factors of the ERK stages are
+// shared by the block; the spatial factor at a stage point x_i - d is formed from the node's
+// sin / cos by the angle-addition formula with a small-angle series, since d is a fraction of dt.
+__global__ void k_departure_1d(WaveParams w, Tableau T, int nx, double xmin, double h, double dt,
                                double* __restrict__ s) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nx * nt) return;
-  const int n = (int)(idx / nx), i = (int)(idx % nx);
-  const double x = xmin + h * i;
+  __shared__ double tf[6];
+  const int n = blockIdx.y;
   const double t1 = (n + 1) * dt;
-  s[idx] = erk_displacement_1d(w, T, x, t1, dt) / h;
+  if ((int)threadIdx.x < T.stages) tf[threadIdx.x] = cos(kTwoPi * (t1 - T.c[threadIdx.x] * dt));
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  const double x = xmin + h * i;
+  const double kw = (w.kind == 3) ? kTwoPi * w.k : kTwoPi;  // spatial wavenumber
+  double Sx = 0.0, Cx = 1.0;
+  if (w.kind >= 2) sincos(kw * x, &Sx, &Cx);
+  double k[6];
+  for (int st = 0; st < T.stages; ++st) {
+    double d = 0.0;  // x - (stage point)
+    for (int j = 0; j < st; ++j)
+      if (T.A[st][j] != 0.0) d = d + dt * T.A[st][j] * k[j];
+    double a;
+    if (w.kind == 0) {
+      a = w.a;
+    } else if (w.kind == 1) {
+      a = tf[st];
+    } else {
+      double sth, cth;
+      small_sincos(kw * d, sth, cth);
+      if (w.kind == 2) a = tf[st] * (Cx * cth + Sx * sth);       // cos(2 pi t) cos(2 pi (x - d))
+      else a = 1.0 + w.a * (Sx * cth - Cx * sth) * tf[st];     // 1 + a sin(2 pi k (x - d)) cos(2 pi t)
+    }
+    k[st] = a;
+  }
+  double dsum = 0.0;
+  for (int st = 0; st < T.stages; ++st)
+    if (T.b[st] != 0.0) dsum = dsum + T.b[st] * k[st];
+  s[(size_t)n * nx + i] = dt * dsum / h;
 }
 
 __global__ void k_departure_2d(WaveParams w, Tableau T, int nx, int nt, double xmin, double h, double dt,
@@ -38,9 +79,9 @@ __global__ void k_departure_2d(WaveParams w, Tableau T, int nx, int nt, double x
 
 void launch_departure_1d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* s,
                          cudaStream_t st) {
-  const long long tot = (long long)nx * nt;
   const int bs = 256;
-  k_departure_1d<<<(unsigned)((tot + bs - 1) / bs), bs, 0, st>>>(w, make_tableau(r), nx, nt, xmin, h, dt, s);
+  dim3 grid((unsigned)((nx + bs - 1) / bs), (unsigned)nt);
+  k_departure_1d<<<grid, bs, 0, st>>>(w, make_tableau(r), nx, xmin, h, dt, s);
 }
 
 void launch_departure_2d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* sx,
