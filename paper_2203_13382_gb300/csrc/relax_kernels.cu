@@ -97,6 +97,32 @@ __device__ __forceinline__ void load_solver(SolverRegs<B, R>& s, const R* __rest
     for (int f = 0; f <= 2 * B; ++f) s.lu[r][f] = __ldg(data + (size_t)rec_lu(B, r, f) * P + k);
 }
 
+// The 8 values of one partition (8-aligned) in shared memory, moved as vectors (fewer bank conflicts).
+template <typename R>
+__device__ __forceinline__ void load_part(const R* p, R (&v)[kPartRows]) {
+  if constexpr (std::is_same<R, float>::value) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double2 a = reinterpret_cast<const double2*>(p)[c];
+      v[2 * c] = a.x;
+      v[2 * c + 1] = a.y;
+    }
+  }
+}
+template <typename R>
+__device__ __forceinline__ void store_part(R* p, const R (&v)[kPartRows]) {
+  if constexpr (std::is_same<R, float>::value) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) reinterpret_cast<double2*>(p)[c] = make_double2(v[2 * c], v[2 * c + 1]);
+  }
+}
+
 // xch: shared scratch of 4 * P * B reals (may alias the consumed gather source).
 // pcr_src: the coefficient block [pcr_off, total) of this step, either in global memory (data +
 // pcr_off) or staged in shared memory.
@@ -114,8 +140,9 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
   R* gb0 = xch + P * B;
   R* gb1 = gb0 + P * B;
   R* xsb = gb1 + P * B;
-  R y[Q], g[B], ct[BB], ch[BB];
+  R y[Q], g[B], ct[BB], ch[BB], xp[kPartRows];
   if (act) {
+    load_part<R>(x + g0, xp);
 #pragma unroll
     for (int e = 0; e < BB; ++e) {
       ct[e] = __ldg(data + (size_t)rec_ct(B, Q, 0, e) * P + k);
@@ -127,7 +154,7 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
       else return __ldg(data + (size_t)rec_lu(B, r, f) * P + k);
     };
 #pragma unroll
-    for (int r = 0; r < Q; ++r) y[r] = x[g0 + B + r];
+    for (int r = 0; r < Q; ++r) y[r] = xp[B + r];
 #pragma unroll
     for (int r = 0; r < Q; ++r)
 #pragma unroll
@@ -149,7 +176,7 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
     const int km = (k + P - 1) & (P - 1);
 #pragma unroll
     for (int a = 0; a < B; ++a) {
-      R v = x[g0 + a];
+      R v = xp[a];
 #pragma unroll
       for (int c = 0; c < B; ++c) v -= ct[a * B + c] * ytail[km * B + c] + ch[a * B + c] * y[c];
       g[a] = v;
@@ -213,7 +240,7 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
 #pragma unroll
     for (int a = 0; a < B; ++a) {
       xn[a] = xsb[kp * B + a];
-      x[g0 + a] = xs[a];
+      xp[a] = xs[a];
     }
 #pragma unroll
     for (int r = 0; r < Q; ++r) {
@@ -223,8 +250,9 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
         v -= __ldg(data + (size_t)rec_v(B, Q, r, c) * P + k) * xs[c];
         v -= __ldg(data + (size_t)rec_w(B, Q, r, c) * P + k) * xn[c];
       }
-      x[g0 + B + r] = v;
+      xp[B + r] = v;
     }
+    store_part<R>(x + g0, xp);
   }
   __syncthreads();
 }
@@ -297,8 +325,9 @@ __device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, un
 }
 
 
+// Fine-level kernels keep three CTAs per SM resident (register cap 42) to hide gather latency.
 template <int P, typename R, bool COARSE>
-__global__ void __launch_bounds__(kSliceThreads) k_relax_1d(LevelTables T, RelaxArgs a, int buf) {
+__global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : 3) k_relax_1d(LevelTables T, RelaxArgs a, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
@@ -333,14 +362,31 @@ __global__ void __launch_bounds__(kSliceThreads) k_relax_1d(LevelTables T, Relax
     } else {
       load_gather<P, R>(gcur, T, n);
     }
-    if (!full_step<P, R, COARSE>(gcur, src, dst, T, n, stg)) return;
     const R* gr = a.g ? (const R*)a.g + (size_t)(n + 1) * nx : nullptr;
+    // FP32: the right-hand side of this step is loaded before the step so its latency is hidden
+    R gpre[kPts];
+    if constexpr (kPipe) {
+      if (gr) {
+#pragma unroll
+        for (int q = 0; q < kPts; ++q) {
+          const int i = threadIdx.x + q * kSliceThreads;
+          gpre[q] = (i < nx) ? gr[i] : (R)0;
+        }
+      }
+    }
+    if (!full_step<P, R, COARSE>(gcur, src, dst, T, n, stg)) return;
     const bool last = (k == a.m - 1);
     if (!last) {
       R* fs = a.fstore ? (R*)a.fstore + (size_t)(n + 1) * nx : nullptr;
-      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < kPts; ++q) {
+        const int i = threadIdx.x + q * kSliceThreads;
+        if (i >= nx) continue;
         R v = dst[i];
-        if (gr) v += gr[i];
+        if (gr) {
+          if constexpr (kPipe) v += gpre[q];
+          else v += gr[i];
+        }
         dst[i] = v;
         if (fs) fs[i] = v;
       }
