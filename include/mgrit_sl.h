@@ -184,14 +184,19 @@ mgrit_status mgrit_solve_host(mgrit_handle* h, const double* h_u0, const double*
                               mgrit_stats* stats);
 
 /*
- * Discrete adjoint of the fine-level one-step system for J = 1/2 ||u_nt - u_target||^2:
- * lambda_nt = u_nt - u_target, lambda_n = Phi_n^T lambda_{n+1} (transposed SL gather as a
- * deterministic scatter-add), solved backward in time by MGRIT with the transposed coarse
- * operators; dJ/du0 = lambda_0 and dJ/da = sum_n lambda_{n+1}^T (dPhi_n/da) u_n, where a is
- * the wave-speed amplitude parameter and u_n is recomputed from the C-point checkpoints
- * d_C_checkpoints ([(nt/m_1 + 1) x N], rows u_{j m_1} of a forward solve).
- * The paper has no adjoint; see the documentation of the library for the choices made.
- * d_dJ_du0: [N]; h_dJ_da: host scalar.  Synchronous.
+ * Discrete adjoint of the fine-level one-step system for J = 1/2 ||u_nt - u_target||^2.  The paper has no
+ * adjoint; this follows from its one-step system (eq. (one-step)): lambda_nt = u_nt - u_target,
+ * lambda_n = Phi_n^T lambda_{n+1}, solved backward in time by MGRIT (the reversed problem
+ * mu_k = lambda_{nt-k} with the transposed operators; coarse levels use Psi^T = S^T M^{-T} of the
+ * forward hierarchy; S^T is applied as a deterministic transposed gather, M^{-T} by the same
+ * partitioned solver factorising M^T), same cycle and stopping rule as mgrit_solve, from a zero
+ * initial iterate.  Outputs dJ/du0 = lambda_0 and dJ/da = sum_n lambda_{n+1}^T (dPhi_n/da) u_n, where a
+ * is wave.a of the kinds with an amplitude (MGRIT_A_CONST: alpha = a; MGRIT_A_SIN_KX_COS_T) and dJ/da
+ * is 0 for the others; dPhi/da acts through d s/d a of a tangent-linear ERK step, and u_n is recomputed
+ * from the checkpoints.
+ * d_C_checkpoints: [(nt/m_1 + 1) x N] the C-point rows u_{j m_1} of a converged forward solve.
+ * d_dJ_du0: [N]; h_dJ_da: host scalar.  FP64 handles (precision 0), 1D.  Synchronous.
+ * stats (optional) describes the adjoint MGRIT solve.
  */
 mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, const double* d_C_checkpoints,
                                  double* d_dJ_du0, double* h_dJ_da, mgrit_stats* stats);

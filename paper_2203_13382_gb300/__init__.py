@@ -254,6 +254,15 @@ class Handle:
                "mgrit_solve_host")
         return u_out, st.as_dict()
 
+    def adjoint(self, u_target, checkpoints):
+        """Discrete adjoint (mgrit_adjoint_solve): returns (dJ/du0, dJ/da, stats of the adjoint MGRIT)."""
+        dJdu0 = self._empty(self.npts)
+        dJda = ctypes.c_double()
+        st = MgritStats()
+        _check(load_library().mgrit_adjoint_solve(self._h(), _ptr(u_target), _ptr(checkpoints), _ptr(dJdu0),
+                                                   ctypes.byref(dJda), ctypes.byref(st)), "mgrit_adjoint_solve")
+        return dJdu0, dJda.value, st.as_dict()
+
     def sequential(self, u0, u_out=None, store_all: bool = True):
         if u_out is None:
             u_out = self._empty(self.grid.nt + 1, self.npts) if store_all else self._empty(self.npts)

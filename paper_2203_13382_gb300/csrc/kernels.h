@@ -38,7 +38,13 @@ void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, u
 // of kernel launches issued.
 size_t solver_reals(int nx, int p);
 int launch_factor_1d(const double* sigma, int nt, int nx, int p, void* out, int is_double, int* flag,
-                     cudaStream_t st);
+                     cudaStream_t st, int transpose = 0);
+
+// Adjoint support: per step the range of floor(s) (window of the transposed gather), and d s / d a by
+// the tangent-linear ERK step.
+void launch_floor_range(const double* s, int nt, int nx, int2* out, cudaStream_t st);
+void launch_departure_da_1d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* ds,
+                            cudaStream_t st);
 
 // ---- relaxation (relax_kernels.cu) ---------------------------------------------------------------
 
@@ -67,6 +73,11 @@ struct LevelTables {
   // TMA bulk copy (0 = read from global memory); err: device flag set to 1 if a bounded wait gave up.
   unsigned stage_bytes;
   int* err;
+  // adjoint: trans = 1 applies Phi^T (coarse: (M^{-1} S)^T = S^T M^{-T}, `solver` then holds the
+  // factorisation of M^T); reverse = 1 maps step n to table row nt - 1 - n; frange[row] = floor range.
+  int trans;
+  int reverse;
+  const int2* frange;
 };
 
 struct RelaxArgs {
@@ -105,10 +116,15 @@ cudaError_t launch_sequential_1d(const LevelTables& T, int N, const void* g, con
 cudaError_t launch_apply_steps_1d(const LevelTables& T, int n0, int count, const void* in, void* out, int is_double,
                                   cudaStream_t st);
 
+// dJ/da contributions of the intervals of level 0 (FP64): CTA j recomputes u_n, n = j m .. j m + m - 1,
+// from the checkpoint C[j] and adds lambda_{n+1}^T (dPhi_n/da) u_n with lambda_{n+1} = mu[nt - n - 1].
+cudaError_t launch_gradient_a_1d(const LevelTables& T, const double* s64, const double* ds, const double* C,
+                                 const double* mu, int nt, int m, double* partial, cudaStream_t st);
+
 // Deterministic sum of `count` doubles (fixed order): out[0] = sum.
 void launch_sum(const double* v, int count, double* out, cudaStream_t st);
 // Elementwise update with type conversion: kind 0: y = x (d); 1: y(f) = x(d); 2: y(d) += x(f);
-// 3: y(d) = x(f); 4: y(d) += x(d); 5: y(d) += x(d) + z(f).
+// 3: y(d) = x(f); 4: y(d) += x(d); 5: y(d) += x(d) + z(f); 6: y(d) = x(d) - z(d).
 void launch_axpy_convert(int kind, const void* x, void* y, const void* z, long long n, cudaStream_t st);
 // zero fill
 void launch_fill_zero(void* y, long long bytes, cudaStream_t st);

@@ -257,6 +257,55 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
   __syncthreads();
 }
 
+// dst = S^T src for table row `row` (FP64): target k sums, in increasing arrival index i, the weight
+// w_a(eps_i) src[i] of every arrival point i whose stencil node a lands on k.  The candidates form the
+// window i in [k + fmin + L - P, k + fmax + L] (fmin/fmax: range of floor(s) on this step), so the
+// transposed gather is a deterministic gather, not an atomic scatter.
+template <int P>
+__device__ __forceinline__ void apply_gather_T(const LevelTables& T, int row, const double* __restrict__ src,
+                                               double* __restrict__ dst) {
+  constexpr int L = (P + 1) / 2;
+  const int nx = T.nx;
+  const uint16_t* __restrict__ sh = T.shift + (size_t)row * nx;
+  const double* __restrict__ w = T.w64 + (size_t)row * (P + 1) * nx;
+  const int2 fr = T.frange[row];
+  int Wn = P + 1 + (fr.y - fr.x);
+  if (Wn > nx) Wn = nx;
+  for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+    const int start = k + fr.x + L - P;
+    double acc = 0.0;
+    for (int t = 0; t < Wn; ++t) {
+      const int i = wrap_pow2(start + t, nx);
+      const int a = wrap_pow2(k - i - (int)__ldg(sh + i), nx);
+      if (a <= P) acc += __ldg(w + (size_t)a * nx + i) * src[i];
+    }
+    dst[k] = acc;
+  }
+}
+
+// d w_a / d eps of the Lagrange weights (product rule), FP64.
+template <int P>
+__device__ __forceinline__ void lagrange_weights_deps(double eps, double (&dw)[P + 1]) {
+  constexpr int L = (P + 1) / 2;
+  double f[P + 1];
+#pragma unroll
+  for (int a = 0; a <= P; ++a) f[a] = -eps - (double)(a - L);
+#pragma unroll
+  for (int a = 0; a <= P; ++a) {
+    double tot = 0.0;
+#pragma unroll
+    for (int skip = 0; skip <= P; ++skip) {
+      if (skip == a) continue;
+      double term = 1.0;
+#pragma unroll
+      for (int q = 0; q <= P; ++q)
+        if (q != a && q != skip) term *= f[q];
+      tot += term;
+    }
+    dw[a] = -tot * lagrange_denominator_inv<P>(a);
+  }
+}
+
 // Shared-memory staging of the reduction coefficients of one coarse step (FP32 levels).
 struct Stage {
   void* buf;       // shared buffer of T.stage_bytes, or nullptr
@@ -266,10 +315,24 @@ struct Stage {
 
 // One full step src -> dst (Phi, or Psi with the correction solve), given the prefetched gather table.
 // Returns false if a bounded wait gave up (the caller then stops; the flag T.err is set).
-template <int P, typename R, bool COARSE>
+template <int P, typename R, bool COARSE, bool TRANS = false>
 __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R* dst, const LevelTables& T, int n,
                                           Stage& stg) {
   constexpr int B = (P + 1) / 2;
+  if constexpr (TRANS) {  // Phi^T (FP64): coarse levels first solve with M^T in place, then S^T
+    const int row = T.reverse ? T.nt - 1 - n : n;
+    if constexpr (COARSE) {
+      const double* data = (const double*)T.solver + (size_t)row * T.solver_stride;
+      const SolverGeom G = solver_geom(T.nx, T.p);
+      SolverRegs<B, double> sr;
+      corr_solve<B, double>((double*)src, (double*)dst, sr, data, data + G.pcr_off, T.nx);
+    }
+    apply_gather_T<P>(T, row, (const double*)src, (double*)dst);
+    __syncthreads();
+    (void)gr;
+    (void)stg;
+    return true;
+  }
   SolverRegs<B, R> sr;
   const R* data = COARSE ? (const R*)T.solver + (size_t)n * T.solver_stride : nullptr;
   const R* pcr_src = nullptr;
@@ -326,7 +389,7 @@ __device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, un
 
 
 // Fine-level kernels keep three CTAs per SM resident (register cap 42) to hide gather latency.
-template <int P, typename R, bool COARSE>
+template <int P, typename R, bool COARSE, bool TRANS>
 __global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : 3) k_relax_1d(LevelTables T, RelaxArgs a, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* src = reinterpret_cast<R*>(smem_raw);
@@ -374,7 +437,7 @@ __global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : 3) k_relax_1d(Leve
         }
       }
     }
-    if (!full_step<P, R, COARSE>(gcur, src, dst, T, n, stg)) return;
+    if (!full_step<P, R, COARSE, TRANS>(gcur, src, dst, T, n, stg)) return;
     const bool last = (k == a.m - 1);
     if (!last) {
       R* fs = a.fstore ? (R*)a.fstore + (size_t)(n + 1) * nx : nullptr;
@@ -420,7 +483,7 @@ __global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : 3) k_relax_1d(Leve
 }
 
 // u0: [nx] start slice; out: store_all ? [(N+1)][nx] (row 0 = u0) : [nx] (the final slice).
-template <int P, typename R, bool COARSE>
+template <int P, typename R, bool COARSE, bool TRANS>
 __global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, int N, const R* g, const R* u0,
                                                                  R* out_all, int store_all, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -444,7 +507,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, 
     } else {
       load_gather<P, R>(gcur, T, n);
     }
-    if (!full_step<P, R, COARSE>(gcur, src, dst, T, n, stg)) return;
+    if (!full_step<P, R, COARSE, TRANS>(gcur, src, dst, T, n, stg)) return;
     const R* gr = g ? g + (size_t)(n + 1) * nx : nullptr;
     R* out = store_all ? out_all + (size_t)(n + 1) * nx : (n == N - 1 ? out_all : nullptr);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -460,7 +523,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, 
   }
 }
 
-template <int P, typename R, bool COARSE>
+template <int P, typename R, bool COARSE, bool TRANS>
 __global__ void __launch_bounds__(kSliceThreads) k_apply_1d(LevelTables T, int n0, const R* in, R* out, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* src = reinterpret_cast<R*>(smem_raw);
@@ -471,7 +534,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_apply_1d(LevelTables T, int n
   __syncthreads();
   GatherRegs<P, R> gr;
   load_gather<P, R>(gr, T, n0 + c);
-  if (!full_step<P, R, COARSE>(gr, src, dst, T, n0 + c, stg)) return;
+  if (!full_step<P, R, COARSE, TRANS>(gr, src, dst, T, n0 + c, stg)) return;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) out[(size_t)c * nx + i] = dst[i];
 }
 
@@ -491,7 +554,7 @@ size_t smem_bytes(int buf, unsigned stage) {
   return b;
 }
 
-template <typename R, bool COARSE>
+template <typename R, bool COARSE, bool TR>
 cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
   const size_t sm = smem_bytes<R>(buf, COARSE ? T.stage_bytes : 0u);
@@ -499,7 +562,7 @@ cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_
   if (grid <= 0) return cudaSuccess;
 #define MGRIT_LAUNCH_RELAX(PP)                                                                             \
   {                                                                                                        \
-    auto kern = k_relax_1d<PP, R, COARSE>;                                                                 \
+    auto kern = k_relax_1d<PP, R, COARSE, TR>;                                                                 \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
     if (e != cudaSuccess) return e;                                                                        \
     kern<<<grid, kSliceThreads, sm, st>>>(T, a, buf);                                                      \
@@ -511,14 +574,14 @@ cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_
 #undef MGRIT_LAUNCH_RELAX
 }
 
-template <typename R, bool COARSE>
+template <typename R, bool COARSE, bool TR>
 cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, const void* u0, void* u, int store_all,
                                 cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
   const size_t sm = smem_bytes<R>(buf, COARSE ? T.stage_bytes : 0u);
 #define MGRIT_LAUNCH_SEQ(PP)                                                                               \
   {                                                                                                        \
-    auto kern = k_sequential_1d<PP, R, COARSE>;                                                            \
+    auto kern = k_sequential_1d<PP, R, COARSE, TR>;                                                            \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
     if (e != cudaSuccess) return e;                                                                        \
     kern<<<1, kSliceThreads, sm, st>>>(T, N, (const R*)g, (const R*)u0, (R*)u, store_all, buf);            \
@@ -530,13 +593,13 @@ cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, cons
 #undef MGRIT_LAUNCH_SEQ
 }
 
-template <typename R, bool COARSE>
+template <typename R, bool COARSE, bool TR>
 cudaError_t apply_dispatch(const LevelTables& T, int n0, int count, const void* in, void* out, cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
   const size_t sm = smem_bytes<R>(buf, COARSE ? T.stage_bytes : 0u);
 #define MGRIT_LAUNCH_APPLY(PP)                                                                             \
   {                                                                                                        \
-    auto kern = k_apply_1d<PP, R, COARSE>;                                                                 \
+    auto kern = k_apply_1d<PP, R, COARSE, TR>;                                                                 \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
     if (e != cudaSuccess) return e;                                                                        \
     kern<<<count, kSliceThreads, sm, st>>>(T, n0, (const R*)in, (R*)out, buf);                             \
@@ -546,6 +609,48 @@ cudaError_t apply_dispatch(const LevelTables& T, int n0, int count, const void* 
   if (T.p == 3) MGRIT_LAUNCH_APPLY(3)
   MGRIT_LAUNCH_APPLY(5)
 #undef MGRIT_LAUNCH_APPLY
+}
+
+template <int P>
+__global__ void __launch_bounds__(kSliceThreads) k_gradient_a_1d(LevelTables T, const double* __restrict__ s64,
+                                                                 const double* __restrict__ ds,
+                                                                 const double* __restrict__ C,
+                                                                 const double* __restrict__ mu, int nt, int m,
+                                                                 double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* u = reinterpret_cast<double*>(smem_raw);
+  double* v = u + T.nx;
+  double* red = v + T.nx;
+  const int nx = T.nx, j = blockIdx.x;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) u[i] = C[(size_t)j * nx + i];
+  __syncthreads();
+  double acc = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const int n = j * m + k;
+    const double* lam = mu + (size_t)(nt - n - 1) * nx;  // lambda_{n+1}
+    const uint16_t* sh = T.shift + (size_t)n * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double sv = s64[(size_t)n * nx + i];
+      double eps = sv - floor(sv);
+      if (eps >= 1.0) eps -= 1.0;
+      double dw[P + 1];
+      lagrange_weights_deps<P>(eps, dw);
+      const int b = i + (int)sh[i];
+      double t = 0.0;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) t += dw[a] * u[wrap_pow2(b + a, nx)];
+      acc += lam[i] * ds[(size_t)n * nx + i] * t;
+    }
+    GatherRegs<P, double> gr;
+    load_gather<P, double>(gr, T, n);
+    apply_gather<P, double>(gr, T, u, v);
+    __syncthreads();
+    double* t = u;
+    u = v;
+    v = t;
+  }
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[j] = tot;
 }
 
 __global__ void k_sum(const double* __restrict__ v, int count, double* out) {
@@ -566,7 +671,8 @@ __global__ void k_axpy_convert(int kind, const void* __restrict__ x, void* __res
     case 2: ((double*)y)[i] += (double)((const float*)x)[i]; break;
     case 3: ((double*)y)[i] = (double)((const float*)x)[i]; break;
     case 4: ((double*)y)[i] += ((const double*)x)[i]; break;
-    default: ((double*)y)[i] += ((const double*)x)[i] + (double)((const float*)z)[i]; break;
+    case 5: ((double*)y)[i] += ((const double*)x)[i] + (double)((const float*)z)[i]; break;
+    default: ((double*)y)[i] = ((const double*)x)[i] - ((const double*)z)[i]; break;
   }
 }
 
@@ -574,32 +680,65 @@ __global__ void k_axpy_convert(int kind, const void* __restrict__ x, void* __res
 
 cudaError_t launch_relax_1d(const LevelTables& T, const RelaxArgs& a, int is_double, cudaStream_t st) {
   const bool coarse = T.solver != nullptr;
-  if (is_double) return coarse ? relax_dispatch<double, true>(T, a, st) : relax_dispatch<double, false>(T, a, st);
-  return coarse ? relax_dispatch<float, true>(T, a, st) : relax_dispatch<float, false>(T, a, st);
+  if (T.trans) {
+    if (!is_double) return cudaErrorInvalidValue;
+    return coarse ? relax_dispatch<double, true, true>(T, a, st) : relax_dispatch<double, false, true>(T, a, st);
+  }
+  if (is_double)
+    return coarse ? relax_dispatch<double, true, false>(T, a, st) : relax_dispatch<double, false, false>(T, a, st);
+  return coarse ? relax_dispatch<float, true, false>(T, a, st) : relax_dispatch<float, false, false>(T, a, st);
 }
 
 cudaError_t launch_sequential_1d(const LevelTables& T, int N, const void* g, const void* u0, void* u, int store_all,
                                  int is_double, cudaStream_t st) {
   const bool coarse = T.solver != nullptr;
+  if (T.trans) {
+    if (!is_double) return cudaErrorInvalidValue;
+    return coarse ? sequential_dispatch<double, true, true>(T, N, g, u0, u, store_all, st)
+                  : sequential_dispatch<double, false, true>(T, N, g, u0, u, store_all, st);
+  }
   if (is_double)
-    return coarse ? sequential_dispatch<double, true>(T, N, g, u0, u, store_all, st)
-                  : sequential_dispatch<double, false>(T, N, g, u0, u, store_all, st);
-  return coarse ? sequential_dispatch<float, true>(T, N, g, u0, u, store_all, st)
-                : sequential_dispatch<float, false>(T, N, g, u0, u, store_all, st);
+    return coarse ? sequential_dispatch<double, true, false>(T, N, g, u0, u, store_all, st)
+                  : sequential_dispatch<double, false, false>(T, N, g, u0, u, store_all, st);
+  return coarse ? sequential_dispatch<float, true, false>(T, N, g, u0, u, store_all, st)
+                : sequential_dispatch<float, false, false>(T, N, g, u0, u, store_all, st);
 }
 
 cudaError_t launch_apply_steps_1d(const LevelTables& T, int n0, int count, const void* in, void* out, int is_double,
                                   cudaStream_t st) {
   const bool coarse = T.solver != nullptr;
   if (count <= 0) return cudaSuccess;
+  if (T.trans) {
+    if (!is_double) return cudaErrorInvalidValue;
+    return coarse ? apply_dispatch<double, true, true>(T, n0, count, in, out, st)
+                  : apply_dispatch<double, false, true>(T, n0, count, in, out, st);
+  }
   if (is_double)
-    return coarse ? apply_dispatch<double, true>(T, n0, count, in, out, st)
-                  : apply_dispatch<double, false>(T, n0, count, in, out, st);
-  return coarse ? apply_dispatch<float, true>(T, n0, count, in, out, st)
-                : apply_dispatch<float, false>(T, n0, count, in, out, st);
+    return coarse ? apply_dispatch<double, true, false>(T, n0, count, in, out, st)
+                  : apply_dispatch<double, false, false>(T, n0, count, in, out, st);
+  return coarse ? apply_dispatch<float, true, false>(T, n0, count, in, out, st)
+                : apply_dispatch<float, false, false>(T, n0, count, in, out, st);
 }
 
 void launch_sum(const double* v, int count, double* out, cudaStream_t st) { k_sum<<<1, 1024, 0, st>>>(v, count, out); }
+
+cudaError_t launch_gradient_a_1d(const LevelTables& T, const double* s64, const double* ds, const double* C,
+                                 const double* mu, int nt, int m, double* partial, cudaStream_t st) {
+  const size_t sm = 2 * (size_t)T.nx * sizeof(double) + 64 * sizeof(double);
+  const int J = nt / m;
+#define MGRIT_LAUNCH_GRAD(PP)                                                                            \
+  {                                                                                                      \
+    cudaError_t e = cudaFuncSetAttribute(k_gradient_a_1d<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)sm);                                                       \
+    if (e != cudaSuccess) return e;                                                                      \
+    k_gradient_a_1d<PP><<<J, kSliceThreads, sm, st>>>(T, s64, ds, C, mu, nt, m, partial);                 \
+    return cudaGetLastError();                                                                           \
+  }
+  if (T.p == 1) MGRIT_LAUNCH_GRAD(1)
+  if (T.p == 3) MGRIT_LAUNCH_GRAD(3)
+  MGRIT_LAUNCH_GRAD(5)
+#undef MGRIT_LAUNCH_GRAD
+}
 
 void launch_axpy_convert(int kind, const void* x, void* y, const void* z, long long n, cudaStream_t st) {
   if (n <= 0) return;

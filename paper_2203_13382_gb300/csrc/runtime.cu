@@ -51,6 +51,10 @@ struct Level {
   int is_double = 1;  // arithmetic of this level's cycle
   void* E = nullptr;  // coarse levels: unknown, full level array [(nt+1)][npts]
   void* G = nullptr;  // coarse levels: right-hand side, full level array
+  // adjoint (built on first use): floor ranges, factorisation of M^T, d s / d a (level 0)
+  int2* frange = nullptr;
+  void* solverT = nullptr;
+  double* ds = nullptr;
 };
 
 double now_ms() {
@@ -80,6 +84,8 @@ struct mgrit_handle {
   double* norm_host = nullptr;  // pinned
   int* flag_dev = nullptr;
   int* err_dev = nullptr;  // set by kernels whose bounded wait gave up
+  int trans_mode = 0;      // 1 while the reversed, transposed (adjoint) problem is being solved
+  bool adjoint_ready = false;
   double setup_ms = 0.0;
   // launch accounting and optional per-phase event timing
   int64_t setup_launches = 0, call_launches = 0;
@@ -167,6 +173,15 @@ struct mgrit_handle {
     T.solver_stride = L.solver_stride;
     T.err = err_dev;
     T.stage_bytes = 0;
+    T.trans = 0;
+    T.reverse = 0;
+    T.frange = L.frange;
+    if (trans_mode) {
+      T.trans = 1;
+      T.reverse = 1;
+      if (T.solver) T.solver = L.solverT;
+      return T;
+    }
     if (T.solver && !is_double) {
       // TMA staging of the reduction coefficients: needs P = nx/8 >= 4 (16-byte alignment of every
       // step's block and of its size) and room in shared memory next to the two slice buffers.
@@ -683,15 +698,76 @@ mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u
   return MGRIT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Builds the data the adjoint needs on first use: per-step floor ranges of every level, the
+// factorisation of M^T of every coarse step, and d s / d a on level 0.
+mgrit_status ensure_adjoint(mgrit_handle* h) {
+  if (h->adjoint_ready) return MGRIT_OK;
+  cudaStream_t s = h->stream;
+  const int nx = h->grid.nx, np = h->npts, p = h->order;
+  for (size_t l = 0; l < h->levels.size(); ++l) {
+    Level& L = h->levels[l];
+    MG_TRY(h->alloc(&L.frange, (size_t)L.nt));
+    launch_floor_range(L.s64, L.nt, nx, L.frange, s);
+    if (l > 0 && L.solver) {
+      MG_TRY(h->alloc((char**)&L.solverT, L.solver_stride * L.nt * sizeof(double)));
+      launch_factor_1d(L.sigma, L.nt, nx, p, L.solverT, 1, h->flag_dev, s, 1);
+    }
+  }
+  Level& L0 = h->levels[0];
+  MG_TRY(h->alloc(&L0.ds, (size_t)L0.nt * np));
+  const double hg = (h->grid.xmax - h->grid.xmin) / nx;
+  WaveParams wp{h->wave.kind, h->wave.a, h->wave.k, h->wave.a2};
+  launch_departure_da_1d(wp, p, nx, L0.nt, h->grid.xmin, hg, h->grid.cfl * hg, L0.ds, s);
+  int flag = 0;
+  MG_CUDA(cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  if (flag) return fail(MGRIT_ESINGULAR, "a transposed correction matrix has a (near) zero pivot");
+  h->adjoint_ready = true;
+  return MGRIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, const double* d_C_checkpoints,
                                  double* d_dJ_du0, double* h_dJ_da, mgrit_stats* stats) {
-  (void)h;
-  (void)d_u_target;
-  (void)d_C_checkpoints;
-  (void)d_dJ_du0;
-  (void)h_dJ_da;
-  (void)stats;
-  return fail(MGRIT_EUNSUPPORTED, "the adjoint solve is not implemented in this build");
+  if (!h || !d_u_target || !d_C_checkpoints || !d_dJ_du0 || !h_dJ_da)
+    return fail(MGRIT_EINVAL, "NULL argument");
+  if (h->opt.precision != 0) return fail(MGRIT_EUNSUPPORTED, "the adjoint solve needs an FP64 handle (precision 0)");
+  if (h->grid.dim != 1) return fail(MGRIT_EUNSUPPORTED, "the adjoint solve is implemented for 1D problems");
+  MG_TRY(ensure_adjoint(h));
+  cudaStream_t s = h->stream;
+  const int np = h->npts, nt = h->grid.nt, m1 = h->levels[1].m, J = h->J1();
+  double *mu0 = nullptr, *mu = nullptr;
+  MG_CUDA(cudaMallocAsync((void**)&mu0, (size_t)np * sizeof(double), s));
+  MG_CUDA(cudaMallocAsync((void**)&mu, (size_t)(nt + 1) * np * sizeof(double), s));
+  // mu_0 = lambda_nt = u_nt - u_target; u_nt is the last checkpoint (nt is a C-point)
+  launch_axpy_convert(6, d_C_checkpoints + (size_t)J * np, mu0, d_u_target, np, s);
+  // the reversed problem mu_{k+1} = Phi_{nt-1-k}^T mu_k by MGRIT from a zero initial iterate
+  h->trans_mode = 1;
+  mgrit_status st = solve_impl(h, mu0, cudaMemcpyDeviceToDevice, nullptr, cudaMemcpyDeviceToDevice, mu, stats);
+  h->trans_mode = 0;
+  if (st == MGRIT_OK) {
+    // dJ/du0 = lambda_0 = mu_nt
+    cudaMemcpyAsync(d_dJ_du0, mu + (size_t)nt * np, (size_t)np * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    // dJ/da = sum_n lambda_{n+1}^T (dPhi_n/da) u_n, u_n recomputed from the checkpoints
+    LevelTables T0 = h->tables(0, 1);
+    T0.solver = nullptr;
+    const Level& L0 = h->levels[0];
+    cudaError_t e = launch_gradient_a_1d(T0, L0.s64, L0.ds, d_C_checkpoints, mu, nt, m1, h->norm_partial, s);
+    if (e != cudaSuccess) st = fail(MGRIT_ECUDA, std::string("gradient kernel: ") + cudaGetErrorString(e));
+    launch_sum(h->norm_partial, J, h->norm_dev, s);
+    cudaMemcpyAsync(h_dJ_da, h->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+  }
+  cudaFreeAsync(mu0, s);
+  cudaFreeAsync(mu, s);
+  MG_CUDA(cudaStreamSynchronize(s));
+  return st;
 }
 
 mgrit_status mgrit_level_info(const mgrit_handle* h, int level, int* nt_level, int* m_level) {

@@ -1,5 +1,7 @@
 // Setup kernels: departure points, backtracking with phi/sigma, gather tables, and the factorisation
 // of the periodic banded correction matrices.  All arithmetic here is FP64.
+#include <climits>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "physics.cuh"
@@ -89,6 +91,84 @@ void launch_departure_2d(const WaveParams& w, int r, int nx, int nt, double xmin
   const long long tot = (long long)nx * nx * nt;
   const int bs = 256;
   k_departure_2d<<<(unsigned)((tot + bs - 1) / bs), bs, 0, st>>>(w, make_tableau(r), nx, nt, xmin, h, dt, sx, sy);
+}
+
+// Per step: range [min, max] of floor(s) over the arrival points (window of the transposed gather).
+__global__ void k_floor_range(const double* __restrict__ s, int nx, int2* __restrict__ out) {
+  __shared__ int mn[32], mx[32];
+  const double* row = s + (size_t)blockIdx.x * nx;
+  int lo = INT_MAX, hi = INT_MIN;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double v = row[i];
+    double f = floor(v);
+    if (v - f >= 1.0) f += 1.0;
+    const int fi = (int)f;
+    lo = min(lo, fi);
+    hi = max(hi, fi);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    mn[threadIdx.x >> 5] = lo;
+    mx[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      lo = min(lo, mn[w]);
+      hi = max(hi, mx[w]);
+    }
+    out[blockIdx.x] = make_int2(lo, hi);
+  }
+}
+
+void launch_floor_range(const double* s, int nt, int nx, int2* out, cudaStream_t st) {
+  k_floor_range<<<nt, 256, 0, st>>>(s, nx, out);
+}
+
+// d s / d a by the tangent-linear ERK step (a = the amplitude parameter of the wave speed).
+__global__ void k_departure_da_1d(WaveParams w, Tableau T, int nx, double xmin, double h, double dt,
+                                  double* __restrict__ ds) {
+  const int n = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  const double x = xmin + h * i;
+  const double t1 = (n + 1) * dt;
+  double k[6], dk[6];
+  for (int st = 0; st < T.stages; ++st) {
+    double xs = x, dxs = 0.0;
+    for (int j = 0; j < st; ++j)
+      if (T.A[st][j] != 0.0) {
+        xs = xs - dt * T.A[st][j] * k[j];
+        dxs = dxs - dt * T.A[st][j] * dk[j];
+      }
+    const double ts = t1 - T.c[st] * dt;
+    double da = 0.0, dx = 0.0;
+    if (w.kind == 0) {
+      da = 1.0;
+    } else if (w.kind == 2) {
+      dx = -kTwoPi * cos(kTwoPi * ts) * sin(kTwoPi * xs);
+    } else if (w.kind == 3) {
+      const double ct = cos(kTwoPi * ts);
+      da = sin(kTwoPi * w.k * xs) * ct;
+      dx = w.a * kTwoPi * w.k * cos(kTwoPi * w.k * xs) * ct;
+    }
+    k[st] = alpha_1d(w, xs, ts);
+    dk[st] = da + dx * dxs;
+  }
+  double d = 0.0;
+  for (int st = 0; st < T.stages; ++st)
+    if (T.b[st] != 0.0) d = d + T.b[st] * dk[st];
+  ds[(size_t)n * nx + i] = dt * d / h;
+}
+
+void launch_departure_da_1d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* ds,
+                            cudaStream_t st) {
+  const int bs = 256;
+  dim3 grid((unsigned)((nx + bs - 1) / bs), (unsigned)nt);
+  k_departure_da_1d<<<grid, bs, 0, st>>>(w, make_tableau(r), nx, xmin, h, dt, ds);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -310,7 +390,8 @@ __device__ void mat_mul(const double (&X)[B][B], const double (&Y)[B][B], double
 }
 
 // One CTA per step, one thread per partition k < P.
-template <int B, typename R>
+// TRANS: factorise M^T = I - D_{p+1} diag(sigma) instead (entry (row, row+off) uses sigma[row+off]).
+template <int B, typename R, bool TRANS>
 __global__ void __launch_bounds__(512) k_factor_1d(const double* __restrict__ sigma_all, int nx, R* __restrict__ out_all, size_t stride,
                             int* flag) {
   constexpr int Q = kPartRows - B;
@@ -322,8 +403,9 @@ __global__ void __launch_bounds__(512) k_factor_1d(const double* __restrict__ si
   const int k = threadIdx.x;
   const bool active = k < P;
   const int g0 = k * kPartRows;
-  auto Mval = [&](int row, int off) -> double {  // M[row, row + off], |off| <= B
-    const int rr = ((row % nx) + nx) % nx;
+  auto Mval = [&](int row, int off) -> double {  // M[row, row + off] (or M^T), |off| <= B
+    const int src = TRANS ? row + off : row;
+    const int rr = ((src % nx) + nx) % nx;
     return (off == 0 ? 1.0 : 0.0) - sigma[rr] * dstencil(B, off);
   };
   double Lb[B][B] = {}, Db[B][B] = {}, Ub[B][B] = {};  // ctail / Mss / chead, then the Schur blocks
@@ -367,8 +449,8 @@ __global__ void __launch_bounds__(512) k_factor_1d(const double* __restrict__ si
       for (int r = 0; r < Q; ++r) {
         const int ov = c - B - r;  // column g0 + c of S_k
         const int ow = Q - r + c;  // column g0 + 8 + c of S_{k+1}
-        xv[r] = (ov >= -B) ? -sigma[g0 + B + r] * dstencil(B, ov) : 0.0;
-        xw[r] = (ow <= B) ? -sigma[g0 + B + r] * dstencil(B, ow) : 0.0;
+        xv[r] = (ov >= -B) ? Mval(g0 + B + r, ov) : 0.0;
+        xw[r] = (ow <= B) ? Mval(g0 + B + r, ow) : 0.0;
       }
       solve(xv);
       solve(xw);
@@ -503,18 +585,21 @@ __global__ void __launch_bounds__(512) k_factor_1d(const double* __restrict__ si
 }
 
 int launch_factor_1d(const double* sigma, int nt, int nx, int p, void* out, int is_double, int* flag,
-                     cudaStream_t st) {
+                     cudaStream_t st, int transpose) {
   const SolverGeom G = solver_geom(nx, p);
   const int threads = ((G.P + 31) / 32) * 32;
   const size_t smem = (size_t)G.P * 3 * G.B * G.B * sizeof(double);
   const size_t stride = G.total;
-#define MGRIT_FACTOR(BB)                                                                                  \
-  if (is_double) {                                                                                        \
-    cudaFuncSetAttribute(k_factor_1d<BB, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    k_factor_1d<BB, double><<<nt, threads, smem, st>>>(sigma, nx, (double*)out, stride, flag);            \
-  } else {                                                                                                \
-    cudaFuncSetAttribute(k_factor_1d<BB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-    k_factor_1d<BB, float><<<nt, threads, smem, st>>>(sigma, nx, (float*)out, stride, flag);             \
+#define MGRIT_FACTOR(BB)                                                                                         \
+  if (transpose) {                                                                                               \
+    cudaFuncSetAttribute(k_factor_1d<BB, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    k_factor_1d<BB, double, true><<<nt, threads, smem, st>>>(sigma, nx, (double*)out, stride, flag);             \
+  } else if (is_double) {                                                                                        \
+    cudaFuncSetAttribute(k_factor_1d<BB, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    k_factor_1d<BB, double, false><<<nt, threads, smem, st>>>(sigma, nx, (double*)out, stride, flag);            \
+  } else {                                                                                                       \
+    cudaFuncSetAttribute(k_factor_1d<BB, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    k_factor_1d<BB, float, false><<<nt, threads, smem, st>>>(sigma, nx, (float*)out, stride, flag);             \
   }
   if (G.B == 1) {
     MGRIT_FACTOR(1)
