@@ -94,6 +94,10 @@ typedef struct {
                        0 (default) = FP32 like the rest of the error cycle */
   int use_graph;    /* reserved (must be 0 or 1) */
   int profile;      /* 1: time each phase with CUDA events on the handle's stream (mgrit_stats.phase_ms) */
+  int gmres_maxit;  /* 2D coarse correction solves: GMRES from a zero guess with at most this many
+                       iterations (default 10, at most 10) ... */
+  double gmres_rtol;/* ... stopped at this relative residual (default 1e-2): the paper's setting for
+                       multilevel and 2D runs (Sec. 3.4, 4.3).  1D correction solves are exact. */
 } mgrit_options;
 
 /* Phases timed when mgrit_options.profile = 1 (indices into mgrit_stats.phase_ms / phase_launches). */

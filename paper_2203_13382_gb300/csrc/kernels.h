@@ -78,7 +78,12 @@ struct LevelTables {
   int trans;
   int reverse;
   const int2* frange;
+  // 2D: FP64 offsets (x block then y block, [2][nt][npts]) for the on-the-fly FP64 weights; on coarse
+  // levels `solver` then points at sigma ([2][nt][npts], FP64) of the corrected operator.
+  const double* s64;
 };
+
+
 
 struct RelaxArgs {
   int m;          // interval length on this level
@@ -128,5 +133,24 @@ void launch_sum(const double* v, int count, double* out, cudaStream_t st);
 void launch_axpy_convert(int kind, const void* x, void* y, const void* z, long long n, cudaStream_t st);
 // zero fill
 void launch_fill_zero(void* y, long long bytes, cudaStream_t st);
+
+// Work buffers of the 2D passes (one slice per interval, the GMRES basis, reduction partials).
+struct Scratch2d {
+  void* cur;
+  void* nxt;
+  void* basis;     // [J][kmax + 1][npts]
+  int kmax;        // GMRES iterations at most (<= 10)
+  double rtol;     // GMRES relative residual
+  double* partial; // [J][64]
+};
+
+// 2D passes with the same semantics as launch_relax_1d / launch_sequential_1d / launch_apply_steps_1d
+// (kernels2d.cu); coarse steps solve the correction system by GMRES (the paper's inexact solve).
+cudaError_t launch_relax_2d(const LevelTables& T, const RelaxArgs& a, const Scratch2d& S, int is_double,
+                            cudaStream_t st);
+cudaError_t launch_sequential_2d(const LevelTables& T, int N, const void* g, const void* u0, void* out, int store_all,
+                                 const Scratch2d& S, int is_double, cudaStream_t st);
+cudaError_t launch_apply_steps_2d(const LevelTables& T, int n0, int count, const void* in, void* out,
+                                  const Scratch2d& S, int is_double, cudaStream_t st);
 
 }  // namespace mgrit

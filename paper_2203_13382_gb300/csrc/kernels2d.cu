@@ -1,0 +1,343 @@
+// Two-dimensional kernels (Sec. 4 of the paper): the tensor-product SL step (eq. (SL2D_char1-2) and the
+// interpolation of Sec. 4.1) over all coarse intervals at once, and the corrected coarse operator
+// [I - diag(sigma_x)(I (x) D) - diag(sigma_y)(D (x) I)]^{-1} S (eq. (BEOper_2D)) with the paper's inexact
+// solve: GMRES from a zero guess, stopped at relative residual rtol or after kmax iterations (Sec. 4.3).
+//
+// A 2D slice (nx * nx values) does not fit in shared memory, so a relaxation pass is a sequence of
+// launches, one per step index k of the intervals, each updating every interval's slice in global memory.
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mgrit {
+
+namespace {
+
+constexpr int kThreads2d = 256;
+
+// Weights of one axis for element pt of step row n.  FP32: from the stored eps; FP64: from the offset.
+template <int P, typename R>
+__device__ __forceinline__ void axis_weights(const LevelTables& T, int comp, int n, long long pt, R (&w)[P + 1]) {
+  const long long off = ((long long)comp * T.nt + n) * T.npts + pt;
+  if constexpr (std::is_same<R, float>::value) {
+    lagrange_weights<P, float>(__ldg(T.eps32 + off), w);
+  } else {
+    const double s = __ldg(T.s64 + off);
+    double e = s - floor(s);
+    if (e >= 1.0) e -= 1.0;
+    lagrange_weights<P, double>(e, w);
+  }
+}
+
+// dst[j] = S_{n(j)} src[j] (+ g[n(j)+1]) for every interval j (blockIdx.y), n(j) = j*m + k (or the
+// single step n0 when m == 0).
+template <int P, typename R>
+__global__ void __launch_bounds__(kThreads2d) k_step2d(LevelTables T, const R* __restrict__ src, R* __restrict__ dst,
+                                                       int m, int k, int n0, const R* __restrict__ g, int add_g,
+                                                       R* __restrict__ fstore) {
+  const int j = blockIdx.y;
+  const long long N = T.npts;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= N) return;
+  const int n = m > 0 ? j * m + k : n0;
+  const int nx = T.nx;
+  const int i = (int)(pt % nx), jj = (int)(pt / nx);
+  R wx[P + 1], wy[P + 1];
+  axis_weights<P, R>(T, 0, n, pt, wx);
+  axis_weights<P, R>(T, 1, n, pt, wy);
+  const int bx = i + (int)__ldg(T.shift + (long long)n * N + pt);
+  const int by = jj + (int)__ldg(T.shift + ((long long)T.nt + n) * N + pt);
+  const R* s = src + (size_t)j * N;
+  R acc = (R)0;
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const R* row = s + (size_t)wrap_pow2(by + b, nx) * nx;
+    R ra = wx[0] * __ldg(row + wrap_pow2(bx, nx));
+#pragma unroll
+    for (int a = 1; a <= P; ++a) ra += wx[a] * __ldg(row + wrap_pow2(bx + a, nx));
+    acc += wy[b] * ra;
+  }
+  if (add_g && g) acc += g[(size_t)(n + 1) * N + pt];
+  dst[(size_t)j * N + pt] = acc;
+  if (fstore) fstore[(size_t)(n + 1) * N + pt] = acc;
+}
+
+// y = M x with M = I - diag(sx) (I (x) D) - diag(sy) (D (x) I), D = (delta^2)^B (periodic).
+template <int B, typename R>
+__device__ __forceinline__ R apply_M(const R* x, const double* sx, const double* sy, long long pt, int nx) {
+  const int i = (int)(pt % nx), jj = (int)(pt / nx);
+  const R* row = x + (size_t)jj * nx;
+  R dxv = (R)0, dyv = (R)0;
+#pragma unroll
+  for (int o = -B; o <= B; ++o) {
+    // centred binomial stencil (-1)^{B+o} C(2B, B+o)
+    double c = 1.0;
+    for (int t = 1; t <= B + o; ++t) c = c * (2 * B - (B + o) + t) / t;
+    const R d = (R)(((B + o) & 1) ? -c : c);
+    dxv += d * row[wrap_pow2(i + o, nx)];
+    dyv += d * x[(size_t)wrap_pow2(jj + o, nx) * nx + i];
+  }
+  return x[pt] - (R)sx[pt] * dxv - (R)sy[pt] * dyv;
+}
+
+template <typename R>
+__device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, double* red) {
+  double s = 0.0;
+  for (long long q = threadIdx.x; q < N; q += blockDim.x) s += (double)a[q] * (double)b[q];
+  double t = block_sum(s, red);
+  __syncthreads();
+  if (threadIdx.x == 0) red[32] = t;
+  __syncthreads();
+  t = red[32];
+  __syncthreads();
+  return t;
+}
+
+// One CTA per interval j: b (= rhs, in place -> solution) of the system of step n(j) = n0 + j*m.
+// basis: [J][kmax + 1][N] scratch.  GMRES (Arnoldi with modified Gram-Schmidt, Givens rotations), zero
+// initial guess, stop when the least-squares residual <= rtol ||b|| or after kmax iterations.
+template <int B, typename R>
+__global__ void __launch_bounds__(kThreads2d) k_gmres2d(const double* __restrict__ sigma_x,
+                                                        const double* __restrict__ sigma_y, int nx, int n0, int m,
+                                                        R* __restrict__ bx_all, R* __restrict__ basis, int kmax,
+                                                        double rtol) {
+  __shared__ double red[40];
+  __shared__ double H[11][10];
+  __shared__ double cs[10], sn[10], gv[11], yv[10];
+  const long long N = (long long)nx * nx;
+  const int j = blockIdx.x;
+  const int n = n0 + j * m;
+  const double* sx = sigma_x + (size_t)n * N;
+  const double* sy = sigma_y + (size_t)n * N;
+  R* b = bx_all + (size_t)j * N;
+  R* V = basis + (size_t)j * (kmax + 1) * N;
+  const double beta = sqrt(cta_dot<R>(b, b, N, red));
+  if (beta == 0.0) return;  // x = 0
+  for (long long q = threadIdx.x; q < N; q += blockDim.x) V[q] = (R)(b[q] / beta);
+  if (threadIdx.x == 0) {
+    gv[0] = beta;
+    for (int t = 1; t <= kmax; ++t) gv[t] = 0.0;
+  }
+  __syncthreads();
+  int kused = 0;
+  for (int kk = 0; kk < kmax; ++kk) {
+    R* vk = V + (size_t)kk * N;
+    R* w = V + (size_t)(kk + 1) * N;
+    for (long long q = threadIdx.x; q < N; q += blockDim.x) w[q] = apply_M<B, R>(vk, sx, sy, q, nx);
+    __syncthreads();
+    for (int t = 0; t <= kk; ++t) {  // modified Gram-Schmidt
+      const R* vt = V + (size_t)t * N;
+      const double h = cta_dot<R>(vt, w, N, red);
+      for (long long q = threadIdx.x; q < N; q += blockDim.x) w[q] -= (R)h * vt[q];
+      if (threadIdx.x == 0) H[t][kk] = h;
+      __syncthreads();
+    }
+    const double hn = sqrt(cta_dot<R>(w, w, N, red));
+    if (threadIdx.x == 0) {
+      H[kk + 1][kk] = hn;
+      for (int t = 0; t < kk; ++t) {  // previous rotations
+        const double a = H[t][kk], c = H[t + 1][kk];
+        H[t][kk] = cs[t] * a + sn[t] * c;
+        H[t + 1][kk] = -sn[t] * a + cs[t] * c;
+      }
+      const double a = H[kk][kk], c = H[kk + 1][kk];
+      const double r = sqrt(a * a + c * c);
+      cs[kk] = r > 0.0 ? a / r : 1.0;
+      sn[kk] = r > 0.0 ? c / r : 0.0;
+      H[kk][kk] = r;
+      H[kk + 1][kk] = 0.0;
+      gv[kk + 1] = -sn[kk] * gv[kk];
+      gv[kk] = cs[kk] * gv[kk];
+      red[36] = fabs(gv[kk + 1]);
+    }
+    __syncthreads();
+    kused = kk + 1;
+    if (red[36] <= rtol * beta || !(hn > 0.0)) break;
+    for (long long q = threadIdx.x; q < N; q += blockDim.x) w[q] = (R)(w[q] / hn);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {  // back substitution R y = g
+    for (int t = kused - 1; t >= 0; --t) {
+      double v = gv[t];
+      for (int c = t + 1; c < kused; ++c) v -= H[t][c] * yv[c];
+      yv[t] = v / H[t][t];
+    }
+  }
+  __syncthreads();
+  for (long long q = threadIdx.x; q < N; q += blockDim.x) {
+    double x = 0.0;
+    for (int t = 0; t < kused; ++t) x += yv[t] * (double)V[(size_t)t * N + q];
+    b[q] = (R)x;
+  }
+}
+
+template <typename R>
+__global__ void k_add_rows(R* __restrict__ dst, const R* __restrict__ g, int m, int k, int n0, long long N,
+                           R* __restrict__ fstore) {
+  const int j = blockIdx.y;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= N) return;
+  const int n = m > 0 ? j * m + k : n0;
+  R v = dst[(size_t)j * N + pt];
+  if (g) v += g[(size_t)(n + 1) * N + pt];
+  dst[(size_t)j * N + pt] = v;
+  if (fstore) fstore[(size_t)(n + 1) * N + pt] = v;
+}
+
+// cur[j] = start[j] (+ corr[j]) for j = 0 .. count-1; optional write-back.
+template <typename R>
+__global__ void k_load_start(const R* __restrict__ start, long long sstride, const R* __restrict__ corr,
+                             long long cstride, R* __restrict__ wb, long long wbstride, R* __restrict__ cur,
+                             long long N, int J) {
+  const int j = blockIdx.y;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= N) return;
+  R v = start ? start[(size_t)j * sstride + pt] : (R)0;
+  if (corr) v += corr[(size_t)j * cstride + pt];
+  if (wb) wb[(size_t)j * wbstride + pt] = v;
+  if (j < J) cur[(size_t)j * N + pt] = v;
+}
+
+// FC: cout[j+1] = cur[j] (+ g).  RES: rout[j+1] = cur[j] (+ gC) - cin[j+1]; per-interval sum of squares.
+template <typename R>
+__global__ void __launch_bounds__(kThreads2d) k_finish2d(const R* __restrict__ cur, RelaxArgs a, long long N,
+                                                         double* __restrict__ partial, int chunks) {
+  __shared__ double red[33];
+  const int j = blockIdx.y;
+  double sq = 0.0;
+  const int nC = (j + 1) * a.m;
+  const R* gr = a.g ? (const R*)a.g + (size_t)nC * N : nullptr;
+  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < N; pt += (long long)gridDim.x * blockDim.x) {
+    R v = cur[(size_t)j * N + pt];
+    if (a.mode == MODE_FC) {
+      if (gr) v += gr[pt];
+      ((R*)a.cout)[(size_t)(j + 1) * a.c_stride + pt] = v;
+    } else {
+      if (gr && a.g_at_c) v += gr[pt];
+      if (a.cin) v -= ((const R*)a.cin)[(size_t)(j + 1) * a.c_stride + pt];
+      ((R*)a.rout)[(size_t)(j + 1) * a.r_stride + pt] = v;
+      sq += (double)v * (double)v;
+    }
+  }
+  if (a.mode == MODE_RES && partial) {
+    const double t = block_sum(sq, red);
+    if (threadIdx.x == 0) partial[(size_t)j * chunks + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_chunks(const double* __restrict__ partial, int chunks, int J, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= J) return;
+  double s = 0.0;
+  for (int c = 0; c < chunks; ++c) s += partial[(size_t)j * chunks + c];
+  out[j] = s;
+}
+
+template <typename R>
+cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, int m, int k, int n0, int J,
+                     const R* g, R* fstore, cudaStream_t st) {
+  const long long N = T.npts;
+  dim3 grid((unsigned)((N + kThreads2d - 1) / kThreads2d), (unsigned)J);
+  const bool coarse = T.solver != nullptr;
+  const int addg_in_step = coarse ? 0 : 1;
+#define MGRIT_STEP2D(PP) k_step2d<PP, R><<<grid, kThreads2d, 0, st>>>(T, src, dst, m, k, n0, g, addg_in_step, coarse ? nullptr : fstore)
+  if (T.p == 1) MGRIT_STEP2D(1);
+  else if (T.p == 3) MGRIT_STEP2D(3);
+  else MGRIT_STEP2D(5);
+#undef MGRIT_STEP2D
+  if (coarse) {
+    const double* sig = (const double*)T.solver;  // sigma_x block then sigma_y block, [nt][N] each
+    const int B = (T.p + 1) / 2;
+    const int n_first = m > 0 ? k : n0;
+#define MGRIT_GM(BB)                                                                                      \
+  k_gmres2d<BB, R><<<J, kThreads2d, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, dst, (R*)S.basis, \
+                                             S.kmax, S.rtol)
+    if (B == 1) MGRIT_GM(1);
+    else if (B == 2) MGRIT_GM(2);
+    else MGRIT_GM(3);
+#undef MGRIT_GM
+    k_add_rows<R><<<grid, kThreads2d, 0, st>>>(dst, g, m, k, n0, N, fstore);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t relax2d(const LevelTables& T, const RelaxArgs& a, const Scratch2d& S, cudaStream_t st) {
+  const long long N = T.npts;
+  const int J = a.J;
+  R* cur = (R*)S.cur;
+  R* nxt = (R*)S.nxt;
+  dim3 g1((unsigned)((N + kThreads2d - 1) / kThreads2d), (unsigned)(J + (a.extra_cta ? 1 : 0)));
+  k_load_start<R><<<g1, kThreads2d, 0, st>>>((const R*)a.start, a.start_stride, (const R*)a.corr, a.corr_stride,
+                                             (R*)a.start_wb, a.wb_stride, cur, N, J);
+  for (int k = 0; k < a.nsteps; ++k) {
+    const bool last = (k == a.m - 1);
+    cudaError_t e = step_all<R>(T, S, cur, nxt, a.m, k, 0, J, last ? nullptr : (const R*)a.g,
+                                last ? nullptr : (R*)a.fstore, st);
+    if (e != cudaSuccess) return e;
+    R* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  if (a.mode == MODE_FC || a.mode == MODE_RES) {
+    const int chunks = 64;
+    dim3 g2(chunks, (unsigned)J);
+    k_finish2d<R><<<g2, kThreads2d, 0, st>>>(cur, a, N, S.partial, chunks);
+    if (a.mode == MODE_RES && a.norm_partial)
+      k_sum_chunks<<<(J + 255) / 256, 256, 0, st>>>(S.partial, chunks, J, a.norm_partial);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t sequential2d(const LevelTables& T, int Nst, const R* g, const R* u0, R* out, int store_all,
+                         const Scratch2d& S, cudaStream_t st) {
+  const long long N = T.npts;
+  R* cur = (R*)S.cur;
+  R* nxt = (R*)S.nxt;
+  dim3 g1((unsigned)((N + kThreads2d - 1) / kThreads2d), 1u);
+  k_load_start<R><<<g1, kThreads2d, 0, st>>>(u0, 0, nullptr, 0, store_all ? out : nullptr, 0, cur, N, 1);
+  for (int n = 0; n < Nst; ++n) {
+    R* fs = store_all ? out : nullptr;
+    cudaError_t e = step_all<R>(T, S, cur, nxt, 0, 0, n, 1, g, fs, st);
+    if (e != cudaSuccess) return e;
+    R* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  if (!store_all) cudaMemcpyAsync(out, cur, (size_t)N * sizeof(R), cudaMemcpyDeviceToDevice, st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_relax_2d(const LevelTables& T, const RelaxArgs& a, const Scratch2d& S, int is_double,
+                            cudaStream_t st) {
+  return is_double ? relax2d<double>(T, a, S, st) : relax2d<float>(T, a, S, st);
+}
+
+cudaError_t launch_sequential_2d(const LevelTables& T, int N, const void* g, const void* u0, void* out, int store_all,
+                                 const Scratch2d& S, int is_double, cudaStream_t st) {
+  if (is_double)
+    return sequential2d<double>(T, N, (const double*)g, (const double*)u0, (double*)out, store_all, S, st);
+  return sequential2d<float>(T, N, (const float*)g, (const float*)u0, (float*)out, store_all, S, st);
+}
+
+cudaError_t launch_apply_steps_2d(const LevelTables& T, int n0, int count, const void* in, void* out,
+                                  const Scratch2d& S, int is_double, cudaStream_t st) {
+  for (int c = 0; c < count; ++c) {
+    const long long N = T.npts;
+    cudaError_t e;
+    if (is_double)
+      e = step_all<double>(T, S, (double*)in + (size_t)c * N, (double*)out + (size_t)c * N, 0, 0, n0 + c, 1,
+                           nullptr, nullptr, st);
+    else
+      e = step_all<float>(T, S, (float*)in + (size_t)c * N, (float*)out + (size_t)c * N, 0, 0, n0 + c, 1, nullptr,
+                          nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mgrit

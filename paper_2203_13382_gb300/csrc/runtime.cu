@@ -85,6 +85,7 @@ struct mgrit_handle {
   int* flag_dev = nullptr;
   int* err_dev = nullptr;  // set by kernels whose bounded wait gave up
   int trans_mode = 0;      // 1 while the reversed, transposed (adjoint) problem is being solved
+  Scratch2d s2d{};         // 2D work buffers (allocated in mgrit_setup)
   bool adjoint_ready = false;
   double setup_ms = 0.0;
   // launch accounting and optional per-phase event timing
@@ -169,8 +170,9 @@ struct mgrit_handle {
     T.eps32 = L.eps32;
     T.table_stride = npts;
     T.nt = L.nt;
-    T.solver = (l > 0 && opt.coarse_op == 0) ? L.solver : nullptr;
+    T.solver = (l > 0 && opt.coarse_op == 0) ? (grid.dim == 2 ? (const void*)L.sigma : L.solver) : nullptr;
     T.solver_stride = L.solver_stride;
+    T.s64 = L.s64;
     T.err = err_dev;
     T.stage_bytes = 0;
     T.trans = 0;
@@ -182,7 +184,7 @@ struct mgrit_handle {
       if (T.solver) T.solver = L.solverT;
       return T;
     }
-    if (T.solver && !is_double) {
+    if (T.solver && !is_double && grid.dim == 1) {
       // TMA staging of the reduction coefficients: needs P = nx/8 >= 4 (16-byte alignment of every
       // step's block and of its size) and room in shared memory next to the two slice buffers.
       const int P = grid.nx / 8, B = (order + 1) / 2;
@@ -212,7 +214,7 @@ mgrit_status check_grid(const mgrit_grid* g, const mgrit_wavespeed* w, int order
   if (!std::isfinite(w->a) || !std::isfinite(w->k) || !std::isfinite(w->a2))
     return fail(MGRIT_EINVAL, "wave parameters must be finite");
   if (g->dim == 1 && g->nx > 4096) return fail(MGRIT_EUNSUPPORTED, "1D slices are kept on chip: nx <= 4096");
-  if (g->dim == 2) return fail(MGRIT_EUNSUPPORTED, "2D problems are not supported by this build");
+  if (g->dim == 2 && g->nx > 2048) return fail(MGRIT_EUNSUPPORTED, "2D grids: nx <= 2048");
   return MGRIT_OK;
 }
 
@@ -234,7 +236,8 @@ std::vector<int> factors(int nt, int m, int m_first, int levels, int max_coarses
 mgrit_status relax(mgrit_handle* h, int l, int is_double, const RelaxArgs& a, int phase) {
   LevelTables T = h->tables(l, is_double);
   const int ev = h->phase_begin();
-  MG_CUDA(launch_relax_1d(T, a, is_double, h->stream));
+  if (h->grid.dim == 2) MG_CUDA(launch_relax_2d(T, a, h->s2d, is_double, h->stream));
+  else MG_CUDA(launch_relax_1d(T, a, is_double, h->stream));
   h->phase_end(phase, ev, 1);
   return MGRIT_OK;
 }
@@ -253,7 +256,8 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   if (l == (int)h->levels.size() - 1) {  // coarsest: sequential stepping (Sec. 2.2)
     LevelTables T = h->tables(l, dbl);
     const int ev = h->phase_begin();
-    MG_CUDA(launch_sequential_1d(T, L.nt, L.G, nullptr, L.E, 1, dbl, h->stream));
+    if (h->grid.dim == 2) MG_CUDA(launch_sequential_2d(T, L.nt, L.G, nullptr, L.E, 1, h->s2d, dbl, h->stream));
+    else MG_CUDA(launch_sequential_1d(T, L.nt, L.G, nullptr, L.E, 1, dbl, h->stream));
     h->phase_end(MGRIT_PHASE_COARSEST, ev, 1);
     return MGRIT_OK;
   }
@@ -335,6 +339,8 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->coarse_fp64 = 0;
   opt->use_graph = 0;
   opt->profile = 0;
+  opt->gmres_maxit = 10;
+  opt->gmres_rtol = 1e-2;
   return MGRIT_OK;
 }
 
@@ -354,6 +360,8 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   if (opt.max_coarsest < 1) return fail(MGRIT_EINVAL, "max_coarsest must be >= 1");
   if (opt.m_first < 0 || opt.m_first == 1) return fail(MGRIT_EINVAL, "m_first must be 0 or >= 2");
   if (opt.coarse_fp64 != 0) return fail(MGRIT_EUNSUPPORTED, "coarse_fp64 is not implemented");
+  if (opt.gmres_maxit < 1 || opt.gmres_maxit > 10) return fail(MGRIT_EINVAL, "gmres_maxit must be in 1..10");
+  if (!(opt.gmres_rtol >= 0.0 && opt.gmres_rtol < 1.0)) return fail(MGRIT_EINVAL, "gmres_rtol must be in [0, 1)");
   if (levels < 0 || levels == 1) return fail(MGRIT_EINVAL, "levels must be 0 or >= 2");
   std::vector<int> fac = factors(grid->nt, m, opt.m_first, levels, opt.max_coarsest);
   if (fac.empty()) return fail(MGRIT_EINVAL, "nt does not allow a coarse level with this m");
@@ -367,8 +375,8 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   h->order = order;
   h->opt = opt;
   h->stream = (cudaStream_t)stream;
-  h->npts = grid->nx;
-  const int nx = grid->nx, np = h->npts;
+  h->npts = grid->dim == 2 ? grid->nx * grid->nx : grid->nx;
+  const int nx = grid->nx, np = h->npts, dim = grid->dim;
   const double hgrid = (grid->xmax - grid->xmin) / nx;
   const double dt = grid->cfl * hgrid;
   const int fp32 = opt.precision == 1;
@@ -388,11 +396,11 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   const int p = order;
   for (size_t l = 0; l < h->levels.size(); ++l) {
     Level& L = h->levels[l];
-    const size_t rows = (size_t)L.nt * np;
+    const size_t rows = (size_t)L.nt * np * dim;  // 2D: x block then y block
     L.is_double = fp32 ? 0 : 1;
     if ((st = h->alloc(&L.s64, rows)) != MGRIT_OK) return cleanup_fail(st);
     if ((st = h->alloc(&L.shift, rows)) != MGRIT_OK) return cleanup_fail(st);
-    const bool need64 = !fp32 || l == 0;
+    const bool need64 = (!fp32 || l == 0) && dim == 1;  // 2D FP64 weights are formed on the fly
     const bool need32 = fp32;
     if (need64 && (st = h->alloc(&L.w64, rows * (p + 1))) != MGRIT_OK) return cleanup_fail(st);
     if (need32 && (st = h->alloc(&L.eps32, rows)) != MGRIT_OK) return cleanup_fail(st);
@@ -402,7 +410,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
       const size_t esz = L.is_double ? sizeof(double) : sizeof(float);
       if ((st = h->alloc((char**)&L.E, full * esz)) != MGRIT_OK) return cleanup_fail(st);
       if ((st = h->alloc((char**)&L.G, full * esz)) != MGRIT_OK) return cleanup_fail(st);
-      if (opt.coarse_op == 0) {
+      if (opt.coarse_op == 0 && dim == 1) {
         L.P = nx / 8;
         L.solver_stride = solver_reals(nx, p);
         const size_t tot = L.solver_stride * L.nt * (L.is_double ? sizeof(double) : sizeof(float));
@@ -411,6 +419,21 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     }
   }
   const int J1 = h->J1();
+  if (dim == 2) {  // work buffers of the 2D passes
+    size_t jmax = (size_t)J1, jc = 1;
+    for (size_t l = 1; l + 1 < h->levels.size(); ++l)
+      jc = std::max(jc, (size_t)(h->levels[l].nt / h->levels[l + 1].m));
+    jmax = std::max(jmax, jc);
+    const size_t rsz = fp32 ? sizeof(float) : sizeof(double);
+    h->s2d.kmax = opt.gmres_maxit;
+    h->s2d.rtol = opt.gmres_rtol;
+    if ((st = h->alloc((char**)&h->s2d.cur, jmax * np * sizeof(double))) != MGRIT_OK) return cleanup_fail(st);
+    if ((st = h->alloc((char**)&h->s2d.nxt, jmax * np * sizeof(double))) != MGRIT_OK) return cleanup_fail(st);
+    if (opt.coarse_op == 0 &&
+        (st = h->alloc((char**)&h->s2d.basis, jc * (opt.gmres_maxit + 1) * np * rsz)) != MGRIT_OK)
+      return cleanup_fail(st);
+    if ((st = h->alloc(&h->s2d.partial, jmax * 64)) != MGRIT_OK) return cleanup_fail(st);
+  }
   if ((st = h->alloc(&h->X, (size_t)(J1 + 1) * np)) != MGRIT_OK) return cleanup_fail(st);
   if ((st = h->alloc(&h->Y, (size_t)(J1 + 1) * np)) != MGRIT_OK) return cleanup_fail(st);
   if (fp32) {
@@ -443,21 +466,34 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   // fine departure points and tables
   {
     const int ev = h->phase_begin();
-    launch_departure_1d(wp, p, nx, grid->nt, grid->xmin, hgrid, dt, h->levels[0].s64, s);
+    if (dim == 2) {
+      Level& L0 = h->levels[0];
+      launch_departure_2d(wp, p, nx, grid->nt, grid->xmin, hgrid, dt, L0.s64, L0.s64 + (size_t)L0.nt * np, s);
+    } else {
+      launch_departure_1d(wp, p, nx, grid->nt, grid->xmin, hgrid, dt, h->levels[0].s64, s);
+    }
     h->phase_end(MGRIT_PHASE_DEPARTURE, ev, 1);
   }
   for (size_t l = 0; l < h->levels.size(); ++l) {
     Level& L = h->levels[l];
+    const size_t blk = (size_t)L.nt * np;  // one component block
     if (l > 0) {
       Level& Lp = h->levels[l - 1];
+      const size_t pblk = (size_t)Lp.nt * np;
       const int ev = h->phase_begin();
-      launch_backtrack_1d(Lp.s64, l > 1 ? Lp.sigma : nullptr, L.m, L.nt, nx, p, L.s64, L.sigma, s);
+      if (dim == 2)
+        launch_backtrack_2d(Lp.s64, Lp.s64 + pblk, l > 1 ? Lp.sigma : nullptr, l > 1 ? Lp.sigma + pblk : nullptr, L.m,
+                            L.nt, nx, p, L.s64, L.s64 + blk, L.sigma, L.sigma + blk, s);
+      else
+        launch_backtrack_1d(Lp.s64, l > 1 ? Lp.sigma : nullptr, L.m, L.nt, nx, p, L.s64, L.sigma, s);
       h->phase_end(MGRIT_PHASE_BACKTRACK, ev, 1);
     }
     {
       const int ev = h->phase_begin();
-      launch_build_tables(L.s64, L.nt, nx, np, p, L.shift, L.w64, L.eps32, s);
-      h->phase_end(MGRIT_PHASE_TABLES, ev, 1);
+      for (int c = 0; c < dim; ++c)
+        launch_build_tables(L.s64 + c * blk, L.nt, nx, np, p, L.shift + c * blk, L.w64,
+                            L.eps32 ? L.eps32 + c * blk : nullptr, s);
+      h->phase_end(MGRIT_PHASE_TABLES, ev, dim);
     }
     if (l > 0 && L.solver) {
       const int ev = h->phase_begin();
@@ -680,14 +716,16 @@ mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u
   h->reset_call_counters();
   const int ev = h->phase_begin();
   if (h->opt.precision == 0) {
-    MG_CUDA(launch_sequential_1d(T, nt, nullptr, d_u0, d_u_out, store_all, 1, s));
+    if (h->grid.dim == 2) MG_CUDA(launch_sequential_2d(T, nt, nullptr, d_u0, d_u_out, store_all, h->s2d, 1, s));
+    else MG_CUDA(launch_sequential_1d(T, nt, nullptr, d_u0, d_u_out, store_all, 1, s));
   } else {
     const size_t rows = store_all ? (size_t)(nt + 1) : 1;
     float *u0f = nullptr, *outf = nullptr;
     MG_CUDA(cudaMallocAsync((void**)&u0f, np * sizeof(float), s));
     MG_CUDA(cudaMallocAsync((void**)&outf, rows * np * sizeof(float), s));
     launch_axpy_convert(1, d_u0, u0f, nullptr, np, s);
-    MG_CUDA(launch_sequential_1d(T, nt, nullptr, u0f, outf, store_all, 0, s));
+    if (h->grid.dim == 2) MG_CUDA(launch_sequential_2d(T, nt, nullptr, u0f, outf, store_all, h->s2d, 0, s));
+    else MG_CUDA(launch_sequential_1d(T, nt, nullptr, u0f, outf, store_all, 0, s));
     launch_axpy_convert(3, outf, d_u_out, nullptr, (long long)rows * np, s);
     cudaFreeAsync(u0f, s);
     cudaFreeAsync(outf, s);
@@ -785,7 +823,8 @@ mgrit_status mgrit_copy_offsets(const mgrit_handle* h, int level, double* d_out)
   if (!h || !d_out) return fail(MGRIT_EINVAL, "NULL argument");
   if (level < 0 || level >= (int)h->levels.size()) return fail(MGRIT_EINVAL, "level out of range");
   const Level& L = h->levels[level];
-  MG_CUDA(cudaMemcpyAsync(d_out, L.s64, (size_t)L.nt * h->npts * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  MG_CUDA(cudaMemcpyAsync(d_out, L.s64, (size_t)L.nt * h->npts * h->grid.dim * sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->stream));
   MG_CUDA(cudaStreamSynchronize(h->stream));
   return MGRIT_OK;
 }
@@ -794,8 +833,8 @@ mgrit_status mgrit_copy_sigma(const mgrit_handle* h, int level, double* d_out) {
   if (!h || !d_out) return fail(MGRIT_EINVAL, "NULL argument");
   if (level < 1 || level >= (int)h->levels.size()) return fail(MGRIT_EINVAL, "level out of range (>= 1)");
   const Level& L = h->levels[level];
-  MG_CUDA(cudaMemcpyAsync(d_out, L.sigma, (size_t)L.nt * h->npts * sizeof(double), cudaMemcpyDeviceToDevice,
-                          h->stream));
+  MG_CUDA(cudaMemcpyAsync(d_out, L.sigma, (size_t)L.nt * h->npts * h->grid.dim * sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->stream));
   MG_CUDA(cudaStreamSynchronize(h->stream));
   return MGRIT_OK;
 }
@@ -810,13 +849,15 @@ mgrit_status mgrit_apply_step(mgrit_handle* h, int level, int n0, int count, con
   const int dbl = L.is_double;
   LevelTables T = h->tables(level, dbl);
   if (dbl) {
-    MG_CUDA(launch_apply_steps_1d(T, n0, count, d_in, d_out, 1, s));
+    if (h->grid.dim == 2) MG_CUDA(launch_apply_steps_2d(T, n0, count, d_in, d_out, h->s2d, 1, s));
+    else MG_CUDA(launch_apply_steps_1d(T, n0, count, d_in, d_out, 1, s));
   } else {
     float *fi = nullptr, *fo = nullptr;
     MG_CUDA(cudaMallocAsync((void**)&fi, (size_t)count * np * sizeof(float), s));
     MG_CUDA(cudaMallocAsync((void**)&fo, (size_t)count * np * sizeof(float), s));
     launch_axpy_convert(1, d_in, fi, nullptr, (long long)count * np, s);
-    MG_CUDA(launch_apply_steps_1d(T, n0, count, fi, fo, 0, s));
+    if (h->grid.dim == 2) MG_CUDA(launch_apply_steps_2d(T, n0, count, fi, fo, h->s2d, 0, s));
+    else MG_CUDA(launch_apply_steps_1d(T, n0, count, fi, fo, 0, s));
     launch_axpy_convert(3, fo, d_out, nullptr, (long long)count * np, s);
     cudaFreeAsync(fi, s);
     cudaFreeAsync(fo, s);
@@ -872,14 +913,16 @@ mgrit_status mgrit_apply_step_noalloc(mgrit_handle* h, int level, int n0, int co
   const int dbl = L.is_double;
   LevelTables T = h->tables(level, dbl);
   if (dbl) {
-    MG_CUDA(launch_apply_steps_1d(T, n0, count, d_in, d_out, 1, s));
+    if (h->grid.dim == 2) MG_CUDA(launch_apply_steps_2d(T, n0, count, d_in, d_out, h->s2d, 1, s));
+    else MG_CUDA(launch_apply_steps_1d(T, n0, count, d_in, d_out, 1, s));
   } else {
     float* stage = nullptr;
     MG_TRY(noalloc_stage_address(&stage));
     float* fi = stage;
     float* fo = stage + kNoAllocMaxElems;
     launch_axpy_convert(1, d_in, fi, nullptr, elems, s);
-    MG_CUDA(launch_apply_steps_1d(T, n0, count, fi, fo, 0, s));
+    if (h->grid.dim == 2) MG_CUDA(launch_apply_steps_2d(T, n0, count, fi, fo, h->s2d, 0, s));
+    else MG_CUDA(launch_apply_steps_1d(T, n0, count, fi, fo, 0, s));
     launch_axpy_convert(3, fo, d_out, nullptr, elems, s);
   }
   MG_CUDA(cudaGetLastError());
