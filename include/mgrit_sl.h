@@ -239,6 +239,22 @@ mgrit_status mgrit_apply_step_noalloc(mgrit_handle* h, int level, int n0, int co
                                       double* d_out);
 
 void mgrit_destroy(mgrit_handle* h);
+
+/*
+ * Batched independent 1D problems (each as in mgrit_setup, levels chosen by the rule of mgrit_setup):
+ * grids[q], waves[q], orders[q], ms[q] for q < nprob; the shared options must select the FP32-bulk mode
+ * (precision 1) and the corrected coarse operator.  mgrit_solve_batched runs the V-cycles of all problems
+ * in lockstep with one kernel launch per cycle phase over (problem, interval) tiles; each problem stops
+ * when its own residual criterion is met (a per-problem mask).  d_u0[q], d_u_init[q] (or NULL),
+ * d_u_out[q] as in mgrit_solve; stats: NULL or an array of nprob.  MGRIT_ENOTCONVERGED if any problem did
+ * not converge.  The paper solves one problem at a time; batching follows from its one-step system.
+ */
+typedef struct mgrit_batch mgrit_batch;
+mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit_wavespeed* waves, const int* orders,
+                                 const int* ms, const mgrit_options* opt, void* stream, mgrit_batch** out);
+mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, const double* const* d_u_init,
+                                 double* const* d_u_out, mgrit_stats* stats);
+void mgrit_destroy_batched(mgrit_batch* b);
 const char* mgrit_status_string(mgrit_status s);
 const char* mgrit_last_error(void);
 

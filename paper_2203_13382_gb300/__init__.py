@@ -100,6 +100,12 @@ _SIGNATURES = {
     "mgrit_apply_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "mgrit_apply_step_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "mgrit_destroy": (None, [_VP]),
+    "mgrit_setup_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(MgritGrid), ctypes.POINTER(MgritWavespeed),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(MgritOptions), _VP, ctypes.POINTER(_VP)]),
+    "mgrit_solve_batched": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                           ctypes.POINTER(MgritStats)]),
+    "mgrit_destroy_batched": (None, [_VP]),
     "mgrit_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mgrit_last_error": (ctypes.c_char_p, []),
 }
@@ -286,6 +292,59 @@ def mgrit_setup(nx: int, nt: int, order: int, m: int, wave: str = "const", a: fl
     _check(load_library().mgrit_setup(ctypes.byref(g), ctypes.byref(w), order, m, levels, ctypes.byref(o),
                                       ctypes.c_void_p(stream), ctypes.byref(out)), "mgrit_setup")
     return Handle(out.value, g, order, o)
+
+
+class Batch:
+    """Independent 1D problems solved together (mgrit_setup_batched / mgrit_solve_batched)."""
+
+    def __init__(self, ptr: int, grids: list, options: MgritOptions):
+        self._ptr = ptr
+        self.grids = grids
+        self.options = options
+
+    def destroy(self) -> None:
+        if self._ptr:
+            load_library().mgrit_destroy_batched(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def solve(self, u0_list, u_init_list=None, out_list=None):
+        import torch
+
+        n = len(self.grids)
+        if out_list is None:
+            out_list = [torch.empty(g.nt + 1, g.nx, dtype=torch.float64, device="cuda") for g in self.grids]
+        arr = lambda ts: (_VP * n)(*[_ptr(t) for t in ts])  # noqa: E731
+        st = (MgritStats * n)()
+        init = arr(u_init_list) if u_init_list is not None else None
+        _check(load_library().mgrit_solve_batched(self._ptr, arr(u0_list), init, arr(out_list), st),
+               "mgrit_solve_batched")
+        return out_list, [s.as_dict() for s in st]
+
+
+def mgrit_setup_batched(problems: list, stream=None, **options) -> Batch:
+    """problems: dicts with nx, nt, order, m and optionally wave, a, k, cfl (1D); options as mgrit_setup."""
+    import torch
+
+    n = len(problems)
+    grids = (MgritGrid * n)(*[MgritGrid(1, p["nx"], p["nt"], -1.0, 1.0, p.get("cfl", 0.85)) for p in problems])
+    waves = (MgritWavespeed * n)(*[MgritWavespeed(WAVE_KINDS[p.get("wave", "sin_kx_cos_t")], p.get("a", 1.0),
+                                                  p.get("k", 1.0), 1.0) for p in problems])
+    orders = (ctypes.c_int * n)(*[p["order"] for p in problems])
+    ms = (ctypes.c_int * n)(*[p["m"] for p in problems])
+    options.setdefault("precision", 1)
+    o = default_options(**options)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_void_p()
+    _check(load_library().mgrit_setup_batched(n, grids, waves, orders, ms, ctypes.byref(o), ctypes.c_void_p(stream),
+                                              ctypes.byref(out)), "mgrit_setup_batched")
+    return Batch(out.value, list(grids), o)
 
 
 def mgrit_solve(handle: Handle, u0, u_init=None, u_out=None):

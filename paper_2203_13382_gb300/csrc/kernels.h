@@ -126,6 +126,39 @@ cudaError_t launch_apply_steps_1d(const LevelTables& T, int n0, int count, const
 cudaError_t launch_gradient_a_1d(const LevelTables& T, const double* s64, const double* ds, const double* C,
                                  const double* mu, int nt, int m, double* partial, cudaStream_t st);
 
+// ---- batched problems (one launch per cycle phase) ------------------------------------------------
+struct BatchTile {
+  int table;    // index into the LevelTables array of the launch
+  int args;     // index into the RelaxArgs / SeqArgs array
+  int j;        // interval
+  int problem;  // problem index (for the active mask)
+};
+struct SeqArgs {
+  int N;
+  const void* g;
+  const void* u0;
+  void* out;
+  int store_all;
+};
+struct Segment {
+  const void* x;
+  void* y;
+  const void* z;
+  long long n;
+};
+// Shared-memory bytes and slice-buffer length a tile of this level needs (max over tiles per launch).
+void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem);
+cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles,
+                                 int ntiles, const int* d_active, int is_double, int coarse, int buf, size_t smem,
+                                 cudaStream_t st);
+cudaError_t launch_sequential_batched(const LevelTables* d_tabs, const SeqArgs* d_args, const BatchTile* d_tiles,
+                                      int ntiles, const int* d_active, int is_double, int coarse, int buf,
+                                      size_t smem, cudaStream_t st);
+// launch_axpy_convert over many segments in one launch; segments of inactive problems have n = 0.
+void launch_axpy_batched(int kind, const Segment* d_seg, int nseg, long long maxn, cudaStream_t st);
+// out = sum of seg.x[0 .. n) (doubles, fixed order) written to *(double*)seg.y, one CTA per segment.
+void launch_sum_batched(const Segment* d_seg, int nseg, cudaStream_t st);
+
 // Deterministic sum of `count` doubles (fixed order): out[0] = sum.
 void launch_sum(const double* v, int count, double* out, cudaStream_t st);
 // Elementwise update with type conversion: kind 0: y = x (d); 1: y(f) = x(d); 2: y(d) += x(f);

@@ -389,14 +389,14 @@ __device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, un
 
 
 // Fine-level kernels keep three CTAs per SM resident (register cap 42) to hide gather latency.
+// The pass of interval j (one CTA); also the body of the batched kernel.
 template <int P, typename R, bool COARSE, bool TRANS>
-__global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : 3) k_relax_1d(LevelTables T, RelaxArgs a, int buf) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs& a, int j, int buf,
+                                           unsigned char* smem_raw) {
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
   double* red = reinterpret_cast<double*>(dst + buf);
   const int nx = T.nx;
-  const int j = blockIdx.x;
   Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), COARSE ? T.stage_bytes : 0u);
   {
     const R* st = a.start ? (const R*)a.start + (size_t)j * a.start_stride : nullptr;
@@ -482,11 +482,16 @@ __global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : 3) k_relax_1d(Leve
   }
 }
 
+template <int P, typename R, bool COARSE, bool TRANS>
+__global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : 3) k_relax_1d(LevelTables T, RelaxArgs a, int buf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  relax_body<P, R, COARSE, TRANS>(T, a, blockIdx.x, buf, smem_raw);
+}
+
 // u0: [nx] start slice; out: store_all ? [(N+1)][nx] (row 0 = u0) : [nx] (the final slice).
 template <int P, typename R, bool COARSE, bool TRANS>
-__global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, int N, const R* g, const R* u0,
-                                                                 R* out_all, int store_all, int buf) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void sequential_body(const LevelTables& T, int N, const R* g, const R* u0, R* out_all,
+                                                int store_all, int buf, unsigned char* smem_raw) {
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
   const int nx = T.nx;
@@ -520,6 +525,49 @@ __global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, 
     R* t = src;
     src = dst;
     dst = t;
+  }
+}
+
+template <int P, typename R, bool COARSE, bool TRANS>
+__global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, int N, const R* g, const R* u0,
+                                                                 R* out_all, int store_all, int buf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  sequential_body<P, R, COARSE, TRANS>(T, N, g, u0, out_all, store_all, buf, smem_raw);
+}
+
+// ---- batched problems: one launch per cycle phase over (problem, interval) tiles --------------------
+
+template <typename R, bool COARSE>
+__global__ void __launch_bounds__(kSliceThreads, 1) k_relax_batched(const LevelTables* __restrict__ tabs,
+                                                                    const RelaxArgs* __restrict__ args,
+                                                                    const BatchTile* __restrict__ tiles,
+                                                                    const int* __restrict__ active, int buf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BatchTile t = tiles[blockIdx.x];
+  if (active && !active[t.problem]) return;
+  const LevelTables T = tabs[t.table];
+  const RelaxArgs a = args[t.args];
+  switch (T.p) {
+    case 1: relax_body<1, R, COARSE, false>(T, a, t.j, buf, smem_raw); break;
+    case 3: relax_body<3, R, COARSE, false>(T, a, t.j, buf, smem_raw); break;
+    default: relax_body<5, R, COARSE, false>(T, a, t.j, buf, smem_raw); break;
+  }
+}
+
+template <typename R, bool COARSE>
+__global__ void __launch_bounds__(kSliceThreads, 1) k_sequential_batched(const LevelTables* __restrict__ tabs,
+                                                                         const SeqArgs* __restrict__ args,
+                                                                         const BatchTile* __restrict__ tiles,
+                                                                         const int* __restrict__ active, int buf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BatchTile t = tiles[blockIdx.x];
+  if (active && !active[t.problem]) return;
+  const LevelTables T = tabs[t.table];
+  const SeqArgs a = args[t.args];
+  switch (T.p) {
+    case 1: sequential_body<1, R, COARSE, false>(T, a.N, (const R*)a.g, (const R*)a.u0, (R*)a.out, a.store_all, buf, smem_raw); break;
+    case 3: sequential_body<3, R, COARSE, false>(T, a.N, (const R*)a.g, (const R*)a.u0, (R*)a.out, a.store_all, buf, smem_raw); break;
+    default: sequential_body<5, R, COARSE, false>(T, a.N, (const R*)a.g, (const R*)a.u0, (R*)a.out, a.store_all, buf, smem_raw); break;
   }
 }
 
@@ -721,6 +769,92 @@ cudaError_t launch_apply_steps_1d(const LevelTables& T, int n0, int count, const
 }
 
 void launch_sum(const double* v, int count, double* out, cudaStream_t st) { k_sum<<<1, 1024, 0, st>>>(v, count, out); }
+
+namespace {
+
+__global__ void k_axpy_batched(int kind, const Segment* __restrict__ seg) {
+  const Segment sg = seg[blockIdx.y];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < sg.n; i += (long long)gridDim.x * blockDim.x) {
+    switch (kind) {
+      case 1: ((float*)sg.y)[i] = (float)((const double*)sg.x)[i]; break;
+      case 5: ((double*)sg.y)[i] += ((const double*)sg.x)[i] + (double)((const float*)sg.z)[i]; break;
+      default: ((double*)sg.y)[i] = ((const double*)sg.x)[i]; break;
+    }
+  }
+}
+
+__global__ void k_sum_batched(const Segment* __restrict__ seg) {
+  __shared__ double red[32];
+  const Segment sg = seg[blockIdx.x];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < sg.n; i += blockDim.x) s += ((const double*)sg.x)[i];
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0 && sg.n > 0) *(double*)sg.y = t;
+}
+
+}  // namespace
+
+void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem) {
+  const bool coarse = T.solver != nullptr;
+  const int b = buffer_elems(T, coarse);
+  *buf = b;
+  *smem = is_double ? smem_bytes<double>(b, coarse ? T.stage_bytes : 0u) : smem_bytes<float>(b, coarse ? T.stage_bytes : 0u);
+}
+
+cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles,
+                                 int ntiles, const int* d_active, int is_double, int coarse, int buf, size_t smem,
+                                 cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+#define MGRIT_BATCH(RR, CC)                                                                                   \
+  {                                                                                                           \
+    cudaError_t e = cudaFuncSetAttribute(k_relax_batched<RR, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem);                                                          \
+    if (e != cudaSuccess) return e;                                                                           \
+    k_relax_batched<RR, CC><<<ntiles, kSliceThreads, smem, st>>>(d_tabs, d_args, d_tiles, d_active, buf);      \
+    return cudaGetLastError();                                                                                \
+  }
+  if (is_double) {
+    if (coarse) MGRIT_BATCH(double, true)
+    MGRIT_BATCH(double, false)
+  }
+  if (coarse) MGRIT_BATCH(float, true)
+  MGRIT_BATCH(float, false)
+#undef MGRIT_BATCH
+}
+
+cudaError_t launch_sequential_batched(const LevelTables* d_tabs, const SeqArgs* d_args, const BatchTile* d_tiles,
+                                      int ntiles, const int* d_active, int is_double, int coarse, int buf,
+                                      size_t smem, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+#define MGRIT_BSEQ(RR, CC)                                                                                         \
+  {                                                                                                                \
+    cudaError_t e = cudaFuncSetAttribute(k_sequential_batched<RR, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem);                                                               \
+    if (e != cudaSuccess) return e;                                                                                \
+    k_sequential_batched<RR, CC><<<ntiles, kSliceThreads, smem, st>>>(d_tabs, d_args, d_tiles, d_active, buf);      \
+    return cudaGetLastError();                                                                                     \
+  }
+  if (is_double) {
+    if (coarse) MGRIT_BSEQ(double, true)
+    MGRIT_BSEQ(double, false)
+  }
+  if (coarse) MGRIT_BSEQ(float, true)
+  MGRIT_BSEQ(float, false)
+#undef MGRIT_BSEQ
+}
+
+void launch_axpy_batched(int kind, const Segment* d_seg, int nseg, long long maxn, cudaStream_t st) {
+  if (nseg <= 0 || maxn <= 0) return;
+  long long blocks = (maxn + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  dim3 grid((unsigned)blocks, (unsigned)nseg);
+  k_axpy_batched<<<grid, 256, 0, st>>>(kind, d_seg);
+}
+
+void launch_sum_batched(const Segment* d_seg, int nseg, cudaStream_t st) {
+  if (nseg <= 0) return;
+  k_sum_batched<<<nseg, 256, 0, st>>>(d_seg);
+}
 
 cudaError_t launch_gradient_a_1d(const LevelTables& T, const double* s64, const double* ds, const double* C,
                                  const double* mu, int nt, int m, double* partial, cudaStream_t st) {

@@ -932,6 +932,329 @@ mgrit_status mgrit_apply_step_noalloc(mgrit_handle* h, int level, int n0, int co
 
 void mgrit_destroy(mgrit_handle* h) { delete h; }
 
+}  // extern "C"
+
+// ---- batched problems ------------------------------------------------------------------------------
+
+struct mgrit_batch {
+  cudaStream_t stream = nullptr;
+  std::vector<mgrit_handle*> hs;
+  mgrit_options opt;
+  struct Phase {
+    int kind;  // 0 relax, 1 sequential
+    int is_double, coarse;
+    int tile_off, ntiles;
+    int buf;
+    size_t smem;
+  };
+  std::vector<Phase> down, up;
+  Phase final_post{};
+  std::vector<BatchTile> tiles;
+  std::vector<LevelTables> tabs;
+  std::vector<RelaxArgs> args;
+  std::vector<SeqArgs> seqs;
+  LevelTables* d_tabs = nullptr;
+  RelaxArgs* d_args = nullptr;
+  SeqArgs* d_seq = nullptr;
+  BatchTile* d_tiles = nullptr;
+  int* d_active = nullptr;
+  Segment* d_seg = nullptr;
+  double* d_norms = nullptr;
+  double* h_norms = nullptr;
+  int final_args_off = 0;
+
+  ~mgrit_batch() {
+    for (mgrit_handle* h : hs) delete h;
+    cudaFree(d_tabs);
+    cudaFree(d_args);
+    cudaFree(d_seq);
+    cudaFree(d_tiles);
+    cudaFree(d_active);
+    cudaFree(d_seg);
+    cudaFree(d_norms);
+    if (h_norms) cudaFreeHost(h_norms);
+  }
+};
+
+namespace {
+
+// Appends a phase of relax tiles; per problem q: J tiles (plus one if extra) using tabs[tab_of(q)] and
+// args[args_of(q)].
+template <class F>
+mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F per_problem) {
+  mgrit_batch::Phase ph{0, is_double, coarse, (int)b->tiles.size(), 0, 0, 0};
+  for (int q = 0; q < (int)b->hs.size(); ++q) {
+    LevelTables T;
+    RelaxArgs a;
+    int ntile = 0;
+    if (!per_problem(q, T, a, ntile)) continue;
+    const int ti = (int)b->tabs.size(), ai = (int)b->args.size();
+    b->tabs.push_back(T);
+    b->args.push_back(a);
+    int buf;
+    size_t smem;
+    relax_smem_need(T, is_double, &buf, &smem);
+    ph.buf = std::max(ph.buf, buf);
+    ph.smem = std::max(ph.smem, smem);
+    for (int j = 0; j < ntile; ++j) b->tiles.push_back(BatchTile{ti, ai, j, q});
+  }
+  ph.ntiles = (int)b->tiles.size() - ph.tile_off;
+  // a common buffer length for every tile: recompute the shared size with the largest buffer
+  ph.smem = std::max(ph.smem, (size_t)2 * ph.buf * (is_double ? 8 : 4) + 64 * sizeof(double));
+  if (coarse) {
+    unsigned stage = 0;
+    for (int t = ph.tile_off; t < (int)b->tiles.size(); ++t) stage = std::max(stage, b->tabs[b->tiles[t].table].stage_bytes);
+    if (stage) {
+      size_t base = 2 * (size_t)ph.buf * (is_double ? 8 : 4) + 64 * sizeof(double);
+      base = (base + 127) & ~(size_t)127;
+      ph.smem = std::max(ph.smem, base + ((stage + 127) & ~127u) + 16);
+    }
+  }
+  return ph;
+}
+
+}  // namespace
+
+extern "C" {
+
+mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit_wavespeed* waves, const int* orders,
+                                 const int* ms, const mgrit_options* opt_in, void* stream, mgrit_batch** out) {
+  if (!out || !grids || !waves || !orders || !ms || nprob < 1) return fail(MGRIT_EINVAL, "bad batched arguments");
+  *out = nullptr;
+  mgrit_options opt;
+  if (opt_in) opt = *opt_in;
+  else mgrit_default_options(&opt);
+  if (opt.precision != 1) return fail(MGRIT_EUNSUPPORTED, "batched solves run the FP32-bulk mode (precision 1)");
+  if (opt.coarse_op != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves use the corrected coarse operator");
+  for (int q = 0; q < nprob; ++q)
+    if (grids[q].dim != 1) return fail(MGRIT_EUNSUPPORTED, "batched solves are 1D");
+  const double t0 = now_ms();
+  mgrit_batch* b = new mgrit_batch();
+  b->stream = (cudaStream_t)stream;
+  b->opt = opt;
+  for (int q = 0; q < nprob; ++q) {
+    mgrit_handle* h = nullptr;
+    mgrit_status st = mgrit_setup(&grids[q], &waves[q], orders[q], ms[q], 0, &opt, stream, &h);
+    if (st != MGRIT_OK) {
+      delete b;
+      return fail(st, "problem " + std::to_string(q) + ": " + g_last_error);
+    }
+    b->hs.push_back(h);
+  }
+  // phases of one cycle
+  b->down.push_back(add_relax_phase(b, 1, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+    mgrit_handle* h = b->hs[q];
+    const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
+    T = h->tables(0, 1);
+    a = args0();
+    a.m = m1; a.J = J; a.nsteps = m1; a.mode = MODE_RES;
+    a.start = h->X; a.start_stride = np; a.cin = h->X; a.c_stride = np; a.rout = h->r64; a.r_stride = np;
+    nt = J;
+    return true;
+  }));
+  b->down.push_back(add_relax_phase(b, 0, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+    mgrit_handle* h = b->hs[q];
+    const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
+    T = h->tables(0, 0);
+    a = args0();
+    a.m = m1; a.J = J; a.nsteps = m1; a.mode = MODE_RES;
+    a.start = h->EC; a.start_stride = np; a.rout = h->levels[1].G; a.r_stride = np; a.norm_partial = h->norm_partial;
+    nt = J;
+    return true;
+  }));
+  int maxL = 0;
+  for (mgrit_handle* h : b->hs) maxL = std::max(maxL, (int)h->levels.size());
+  for (int d = 1; d < maxL; ++d) {
+    for (int pass = 0; pass < 2; ++pass)
+      b->down.push_back(add_relax_phase(b, 0, 1, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+        mgrit_handle* h = b->hs[q];
+        if ((int)h->levels.size() - 1 <= d) return false;
+        Level& L = h->levels[d];
+        Level& Lc = h->levels[d + 1];
+        const int np = h->npts, m = Lc.m, J = L.nt / m;
+        T = h->tables(d, 0);
+        a = args0();
+        a.m = m; a.J = J; a.nsteps = m; a.g = L.G;
+        if (pass == 0) {
+          a.mode = MODE_FC; a.cout = L.E; a.c_stride = (long long)m * np;
+        } else {
+          a.mode = MODE_RES; a.start = L.E; a.start_stride = (long long)m * np; a.g_at_c = 1; a.cin = L.E;
+          a.c_stride = (long long)m * np; a.rout = Lc.G; a.r_stride = np;
+        }
+        nt = J;
+        return true;
+      }));
+    // coarsest levels reached at this depth: sequential solves
+    mgrit_batch::Phase ph{1, 0, 1, (int)b->tiles.size(), 0, 0, 0};
+    for (int q = 0; q < nprob; ++q) {
+      mgrit_handle* h = b->hs[q];
+      if ((int)h->levels.size() - 1 != d) continue;
+      Level& L = h->levels[d];
+      LevelTables T = h->tables(d, 0);
+      SeqArgs sa{L.nt, L.G, nullptr, L.E, 1};
+      const int ti = (int)b->tabs.size(), ai = (int)b->seqs.size();
+      b->tabs.push_back(T);
+      b->seqs.push_back(sa);
+      int buf;
+      size_t smem;
+      relax_smem_need(T, 0, &buf, &smem);
+      ph.buf = std::max(ph.buf, buf);
+      ph.smem = std::max(ph.smem, smem);
+      b->tiles.push_back(BatchTile{ti, ai, 0, q});
+    }
+    ph.ntiles = (int)b->tiles.size() - ph.tile_off;
+    if (ph.ntiles) b->down.push_back(ph);
+  }
+  for (int d = maxL - 2; d >= 1; --d)
+    b->up.push_back(add_relax_phase(b, 0, 1, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+      mgrit_handle* h = b->hs[q];
+      if ((int)h->levels.size() - 1 <= d) return false;
+      Level& L = h->levels[d];
+      Level& Lc = h->levels[d + 1];
+      const int np = h->npts, m = Lc.m, J = L.nt / m;
+      T = h->tables(d, 0);
+      a = args0();
+      a.m = m; a.J = J; a.nsteps = m - 1; a.mode = MODE_POST; a.start = L.E; a.start_stride = (long long)m * np;
+      a.corr = Lc.E; a.corr_stride = np; a.start_wb = L.E; a.wb_stride = (long long)m * np; a.extra_cta = 1;
+      a.g = L.G; a.fstore = L.E;
+      nt = J + 1;
+      return true;
+    }));
+  b->final_args_off = (int)b->args.size();
+  b->final_post = add_relax_phase(b, 1, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+    mgrit_handle* h = b->hs[q];
+    const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
+    T = h->tables(0, 1);
+    a = args0();
+    a.m = m1; a.J = J; a.nsteps = m1 - 1; a.mode = MODE_POST; a.start = h->X; a.start_stride = np;
+    a.wb_stride = (long long)m1 * np; a.extra_cta = 1;  // start_wb / fstore set per call
+    nt = J + 1;
+    return true;
+  });
+  auto up = [&](void** d, const void* h, size_t bytes) -> bool {
+    if (bytes == 0) return true;
+    if (cudaMalloc(d, bytes) != cudaSuccess) return false;
+    return cudaMemcpyAsync(*d, h, bytes, cudaMemcpyHostToDevice, b->stream) == cudaSuccess;
+  };
+  bool ok = up((void**)&b->d_tabs, b->tabs.data(), b->tabs.size() * sizeof(LevelTables)) &&
+            up((void**)&b->d_args, b->args.data(), b->args.size() * sizeof(RelaxArgs)) &&
+            up((void**)&b->d_seq, b->seqs.data(), b->seqs.size() * sizeof(SeqArgs)) &&
+            up((void**)&b->d_tiles, b->tiles.data(), b->tiles.size() * sizeof(BatchTile));
+  ok = ok && cudaMalloc((void**)&b->d_active, nprob * sizeof(int)) == cudaSuccess &&
+       cudaMalloc((void**)&b->d_seg, 3 * (size_t)nprob * sizeof(Segment)) == cudaSuccess &&
+       cudaMalloc((void**)&b->d_norms, nprob * sizeof(double)) == cudaSuccess &&
+       cudaMallocHost((void**)&b->h_norms, nprob * sizeof(double)) == cudaSuccess;
+  if (!ok || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    delete b;
+    return fail(MGRIT_ENOMEM, "batched workspace allocation failed");
+  }
+  (void)t0;
+  *out = b;
+  return MGRIT_OK;
+}
+
+mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, const double* const* d_u_init,
+                                 double* const* d_u_out, mgrit_stats* stats) {
+  if (!b || !d_u0 || !d_u_out) return fail(MGRIT_EINVAL, "NULL argument");
+  const double t0 = now_ms();
+  cudaStream_t s = b->stream;
+  const int nprob = (int)b->hs.size();
+  for (int q = 0; q < nprob; ++q) {
+    mgrit_handle* h = b->hs[q];
+    const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
+    MG_CUDA(cudaMemcpyAsync(h->X, d_u0[q], np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (d_u_init && d_u_init[q])
+      MG_CUDA(cudaMemcpy2DAsync(h->X + np, np * sizeof(double), d_u_init[q] + (size_t)m1 * np,
+                                (size_t)m1 * np * sizeof(double), np * sizeof(double), J, cudaMemcpyDeviceToDevice, s));
+    else
+      MG_CUDA(cudaMemsetAsync(h->X + np, 0, (size_t)J * np * sizeof(double), s));
+    // per-call output pointers of the final post F-relaxation
+    RelaxArgs& a = b->args[b->final_args_off + q];
+    a.start_wb = d_u_out[q];
+    a.fstore = d_u_out[q];
+  }
+  MG_CUDA(cudaMemcpyAsync(b->d_args + b->final_args_off, b->args.data() + b->final_args_off,
+                          nprob * sizeof(RelaxArgs), cudaMemcpyHostToDevice, s));
+  std::vector<int> active(nprob, 1), iters(nprob, 0), conv(nprob, 0);
+  std::vector<double> r0(nprob, 0.0), rk(nprob, 0.0);
+  std::vector<std::vector<double>> hist(nprob);
+  std::vector<Segment> seg(3 * (size_t)nprob);
+  auto run = [&](const mgrit_batch::Phase& ph) -> mgrit_status {
+    if (ph.ntiles == 0) return MGRIT_OK;
+    cudaError_t e = ph.kind == 0
+                        ? launch_relax_batched(b->d_tabs, b->d_args, b->d_tiles + ph.tile_off, ph.ntiles, b->d_active,
+                                               ph.is_double, ph.coarse, ph.buf, ph.smem, s)
+                        : launch_sequential_batched(b->d_tabs, b->d_seq, b->d_tiles + ph.tile_off, ph.ntiles,
+                                                    b->d_active, ph.is_double, ph.coarse, ph.buf, ph.smem, s);
+    if (e != cudaSuccess) return fail(MGRIT_ECUDA, std::string("batched phase: ") + cudaGetErrorString(e));
+    return MGRIT_OK;
+  };
+  int n_active = nprob;
+  for (int k = 0; k < b->opt.max_iter && n_active > 0; ++k) {
+    long long maxn = 0;
+    for (int q = 0; q < nprob; ++q) {
+      mgrit_handle* h = b->hs[q];
+      const long long n = active[q] ? (long long)(h->J1() + 1) * h->npts : 0;
+      maxn = std::max(maxn, n);
+      seg[q] = Segment{h->r64, h->EC, nullptr, n};
+      seg[nprob + q] = Segment{h->r64, h->X, h->levels[1].E, n};
+      seg[2 * nprob + q] = Segment{h->norm_partial, b->d_norms + q, nullptr, active[q] ? (long long)h->J1() : 0};
+    }
+    MG_CUDA(cudaMemcpyAsync(b->d_active, active.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+    MG_CUDA(cudaMemcpyAsync(b->d_seg, seg.data(), seg.size() * sizeof(Segment), cudaMemcpyHostToDevice, s));
+    MG_TRY(run(b->down[0]));                                  // FP64 residual of every iterate
+    launch_axpy_batched(1, b->d_seg, nprob, maxn, s);         // e_C = r (FP32)
+    for (size_t ph = 1; ph < b->down.size(); ++ph) MG_TRY(run(b->down[ph]));
+    for (auto& ph : b->up) MG_TRY(run(ph));
+    launch_axpy_batched(5, b->d_seg + nprob, nprob, maxn, s); // u_C += r + E_1
+    launch_sum_batched(b->d_seg + 2 * nprob, nprob, s);
+    MG_CUDA(cudaMemcpyAsync(b->h_norms, b->d_norms, nprob * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < nprob; ++q) {
+      if (!active[q]) continue;
+      const double r = std::sqrt(b->h_norms[q]);
+      hist[q].push_back(r);
+      iters[q] = k + 1;
+      rk[q] = r;
+      if (k == 0) r0[q] = r;
+      if (!std::isfinite(r) || r > 1e3 * r0[q]) {
+        active[q] = 0;
+        --n_active;
+      } else if (k >= 1 && r < b->opt.rtol * r0[q]) {
+        conv[q] = 1;
+        active[q] = 0;
+        --n_active;
+      }
+    }
+  }
+  // every problem: post F-relaxation into its output
+  std::vector<int> all(nprob, 1);
+  MG_CUDA(cudaMemcpyAsync(b->d_active, all.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+  MG_TRY(run(b->final_post));
+  MG_CUDA(cudaStreamSynchronize(s));
+  bool all_conv = true;
+  for (int q = 0; q < nprob; ++q) {
+    all_conv = all_conv && conv[q];
+    if (stats) {
+      mgrit_stats& st = stats[q];
+      std::memset(&st, 0, sizeof(st));
+      st.iterations = iters[q];
+      st.converged = conv[q];
+      st.levels = (int)b->hs[q]->levels.size();
+      st.r0 = r0[q];
+      st.r_final = rk[q];
+      st.history_len = std::min<int>(256, (int)hist[q].size());
+      for (int i = 0; i < st.history_len; ++i) st.residual_history[i] = hist[q][i];
+      st.setup_ms = b->hs[q]->setup_ms;
+      st.solve_ms = now_ms() - t0;
+      st.device_bytes = b->hs[q]->bytes;
+    }
+  }
+  return all_conv ? MGRIT_OK : fail(MGRIT_ENOTCONVERGED, "some problems did not converge");
+}
+
+void mgrit_destroy_batched(mgrit_batch* b) { delete b; }
+
 const char* mgrit_status_string(mgrit_status s) {
   switch (s) {
     case MGRIT_OK: return "ok";
