@@ -9,6 +9,8 @@ adjoint solve:
   dJ/du0 = lambda_0,  dJ/da = sum_n lambda_{n+1}^T (dPhi_n/da) u_n.
 dPhi_n/da acts through the departure offsets only: (dPhi u)_i = sum_j w_j'(eps_i) (ds_i/da) u_{E_i+j}
 (E_i is locally constant), with ds/da from differentiating the ERK stages (tangent-linear ERK).
+In 2D (Sec. 4.1) the step is the tensor-product interpolation with weights wx_a(eps) wy_b(nu), so
+(dPhi u)_i = sum_{a,b} [wx_a'(eps_i) dsx_i/da wy_b(nu_i) + wx_a(eps_i) wy_b'(nu_i) dsy_i/da] u_{..}.
 The adjoint MGRIT solve uses the reversed problem mu_k = lambda_{nt-k}, mu_{k+1} = Phi_{nt-1-k}^T mu_k,
 whose coarse operators are the transposed coarse operators Psi^T of the forward hierarchy.
 """
@@ -56,14 +58,45 @@ def sl_transpose_apply_1d(v: np.ndarray, s: np.ndarray, p: int) -> np.ndarray:
     return out
 
 
-class TransposedSolver:
-    """Applies M^{-T} by a sparse LU of M^T (M = I - diag(sigma) D_{p+1})."""
+def sl_transpose_apply_2d(v: np.ndarray, sx: np.ndarray, sy: np.ndarray, p: int) -> np.ndarray:
+    """S^T v in 2D: arrival point (i, j) adds wx_a wy_b v_{j,i} to node ((N + jb) mod ny, (E + ja) mod nx)."""
+    ny, nx = v.shape
+    fx, eps = sl.decompose(sx)
+    fy, nu = sl.decompose(sy)
+    E = np.arange(nx, dtype=np.int64)[None, :] - fx
+    N = np.arange(ny, dtype=np.int64)[:, None] - fy
+    wx = sl.lagrange_weights(eps, p)
+    wy = sl.lagrange_weights(nu, p)
+    st = sl.stencil(p)
+    out = np.zeros_like(v)
+    for b_, jb in enumerate(st):
+        rows = np.mod(N + jb, ny)
+        for a_, ja in enumerate(st):
+            cols = np.mod(E + ja, nx)
+            np.add.at(out, (rows, cols), wy[..., b_] * wx[..., a_] * v)
+    return out
 
-    def __init__(self, M: sp.csc_matrix):
-        self._lu = spla.splu(sp.csc_matrix(M.T))
+
+class TransposedSolver:
+    """Applies M^{-T} (M = I - diag(sigma) D_{p+1}, or its 2D form) to vectors.
+
+    mode "exact": sparse LU of M^T; mode "gmres": the same inexact GMRES as the forward solve
+    (coarse.gmres_zero_guess), applied to M^T.
+    """
+
+    def __init__(self, M: sp.csc_matrix, mode: str = "exact", rtol: float = 1e-2, maxit: int = 10):
+        self.MT = sp.csc_matrix(M.T)
+        self.mode = mode
+        self.rtol = rtol
+        self.maxit = maxit
+        self._lu = spla.splu(self.MT) if mode == "exact" else None
 
     def solve(self, v: np.ndarray) -> np.ndarray:
-        return self._lu.solve(v)
+        shape = v.shape
+        b = v.ravel()
+        if self.mode == "exact":
+            return self._lu.solve(b).reshape(shape)
+        return co.gmres_zero_guess(self.MT, b, self.rtol, self.maxit).reshape(shape)
 
 
 class ReversedTransposed:
@@ -73,8 +106,6 @@ class ReversedTransposed:
     """
 
     def __init__(self, H: mg.Hierarchy):
-        if H.dim != 1:
-            raise NotImplementedError("the oracle adjoint is 1D")
         self.H = H
         self.levels = H.levels
         self._tsolvers: dict[tuple[int, int], TransposedSolver] = {}
@@ -90,9 +121,15 @@ class ReversedTransposed:
         if l > 0 and H.coarse == "bsl":
             key = (l, n)
             if key not in self._tsolvers:
-                self._tsolvers[key] = TransposedSolver(co.correction_matrix_1d(lev.sigma[n], H.p))
+                if H.dim == 1:
+                    M = co.correction_matrix_1d(lev.sigma[n], H.p)
+                else:
+                    M = co.correction_matrix_2d(lev.sigma[0][n], lev.sigma[1][n], H.p)
+                self._tsolvers[key] = TransposedSolver(M, H.solve_mode, H.gmres_rtol, H.gmres_maxit)
             v = self._tsolvers[key].solve(v)
-        return sl_transpose_apply_1d(v, lev.s[n], H.p)
+        if H.dim == 1:
+            return sl_transpose_apply_1d(v, lev.s[n], H.p)
+        return sl_transpose_apply_2d(v, lev.s[0][n], lev.s[1][n], H.p)
 
     def step(self, l: int, k: int, v: np.ndarray) -> np.ndarray:
         return self.step_T(l, self.levels[l].nt - 1 - k, v)
@@ -135,6 +172,58 @@ def dalpha(ws: sl.WaveSpeed, x: np.ndarray, t: float) -> tuple[np.ndarray, np.nd
         ct = math.cos(TWO_PI * t)
         return np.sin(TWO_PI * ws.k * x) * ct, ws.a * TWO_PI * ws.k * np.cos(TWO_PI * ws.k * x) * ct
     raise ValueError(ws.kind)
+
+
+def dvelocity(ws: sl.WaveSpeed, x: np.ndarray, y: np.ndarray, t: float):
+    """Derivatives of the 2D families: ((dvx/da, dvx/dx, dvx/dy), (dvy/da, dvy/dx, dvy/dy)).
+
+    The parameter a is the amplitude of "sin_cos2" (both components) and the x speed of "const2";
+    "paper2" does not depend on it.
+    """
+    z = np.zeros_like(x)
+    if ws.kind == "const2":
+        return (np.ones_like(x), z, z), (z, z, z)
+    if ws.kind == "paper2":
+        ct = math.cos(TWO_PI * t / 3.4)
+        return (z, z, 2.0 * math.pi * np.sin(math.pi * y) * np.cos(math.pi * y) * ct), \
+               (z, 2.0 * math.pi * np.cos(math.pi * x) * np.sin(math.pi * x) * ct, z)
+    if ws.kind == "sin_cos2":
+        ct, st = math.cos(TWO_PI * t), math.sin(TWO_PI * t)
+        return (np.sin(TWO_PI * y) * ct, z, ws.a * TWO_PI * np.cos(TWO_PI * y) * ct), \
+               (np.cos(TWO_PI * x) * st, -ws.a * TWO_PI * np.sin(TWO_PI * x) * st, z)
+    raise ValueError(ws.kind)
+
+
+def departure_offsets_da_2d(grid: sl.Grid, ws: sl.WaveSpeed, n: int, r: int) -> tuple[np.ndarray, np.ndarray]:
+    """(d sx / d a, d sy / d a) for the fine step t_n -> t_{n+1}: departure_offsets_2d's stages differentiated."""
+    A, b, c = sl.erk_tableau(r)
+    X, Y = np.meshgrid(grid.x, grid.x)
+    dt = grid.dt
+    t1 = (n + 1) * dt
+    kx, ky, dkx, dky = [], [], [], []
+    for s in range(len(b)):
+        xs, ys = X.copy(), Y.copy()
+        dxs, dys = np.zeros_like(X), np.zeros_like(Y)
+        for j in range(s):
+            if A[s, j] != 0.0:
+                xs = xs - dt * A[s, j] * kx[j]
+                ys = ys - dt * A[s, j] * ky[j]
+                dxs = dxs - dt * A[s, j] * dkx[j]
+                dys = dys - dt * A[s, j] * dky[j]
+        ts = t1 - c[s] * dt
+        vx, vy = ws.velocity(xs, ys, ts)
+        (ax, xx, xy), (ay, yx, yy) = dvelocity(ws, xs, ys, ts)
+        kx.append(vx)
+        ky.append(vy)
+        dkx.append(ax + xx * dxs + xy * dys)
+        dky.append(ay + yx * dxs + yy * dys)
+    dx = np.zeros_like(X)
+    dy = np.zeros_like(Y)
+    for s in range(len(b)):
+        if b[s] != 0.0:
+            dx = dx + b[s] * dkx[s]
+            dy = dy + b[s] * dky[s]
+    return dt * dx / grid.h, dt * dy / grid.h
 
 
 def departure_offsets_da_1d(grid: sl.Grid, ws: sl.WaveSpeed, n: int, r: int) -> np.ndarray:
@@ -191,6 +280,26 @@ def dphi_da_apply_1d(u: np.ndarray, s: np.ndarray, ds: np.ndarray, p: int) -> np
     return np.sum(dw * u[idx], axis=-1) * ds
 
 
+def dphi_da_apply_2d(u: np.ndarray, sx: np.ndarray, sy: np.ndarray, dsx: np.ndarray, dsy: np.ndarray,
+                     p: int) -> np.ndarray:
+    """(dPhi/da) u in 2D: the product rule on wx_a(eps) wy_b(nu) with d eps/da = dsx, d nu/da = dsy."""
+    ny, nx = u.shape
+    fx, eps = sl.decompose(sx)
+    fy, nu = sl.decompose(sy)
+    E = np.arange(nx, dtype=np.int64)[None, :] - fx
+    N = np.arange(ny, dtype=np.int64)[:, None] - fy
+    wx, wy = sl.lagrange_weights(eps, p), sl.lagrange_weights(nu, p)
+    dwx, dwy = lagrange_weights_deps(eps, p), lagrange_weights_deps(nu, p)
+    st = sl.stencil(p)
+    out = np.zeros_like(u)
+    for b_, jb in enumerate(st):
+        rows = np.mod(N + jb, ny)
+        for a_, ja in enumerate(st):
+            val = u[rows, np.mod(E + ja, nx)]
+            out += (dwx[..., a_] * dsx * wy[..., b_] + wx[..., a_] * dwy[..., b_] * dsy) * val
+    return out
+
+
 # ---------------------------------------------------------------------------
 # objective and gradients
 # ---------------------------------------------------------------------------
@@ -201,7 +310,7 @@ def objective(grid: sl.Grid, ws: sl.WaveSpeed, p: int, u0: np.ndarray, u_target:
     H = mg.Hierarchy(grid, ws, p, [])
     U = mg.sequential_solve(H, u0)
     d = U[-1] - u_target
-    return 0.5 * float(d @ d)
+    return 0.5 * float(np.sum(d * d))
 
 
 def gradients(grid: sl.Grid, ws: sl.WaveSpeed, p: int, u0: np.ndarray, u_target: np.ndarray):
@@ -209,8 +318,19 @@ def gradients(grid: sl.Grid, ws: sl.WaveSpeed, p: int, u0: np.ndarray, u_target:
     H = mg.Hierarchy(grid, ws, p, [])
     U = mg.sequential_solve(H, u0)
     lam = adjoint_sequential(H, U[-1] - u_target)
-    dJda = 0.0
+    return lam[0], dJ_da(H, U, lam)
+
+
+def dJ_da(H: mg.Hierarchy, U: np.ndarray, lam: np.ndarray) -> float:
+    """sum_n lambda_{n+1} . (dPhi_n/da) u_n over the fine steps (U, lam: all nt+1 slices)."""
+    grid, ws, p = H.grid, H.ws, H.p
+    out = 0.0
     for n in range(grid.nt):
-        ds = departure_offsets_da_1d(grid, ws, n, p)
-        dJda += float(lam[n + 1] @ dphi_da_apply_1d(U[n], H.levels[0].s[n], ds, p))
-    return lam[0], dJda
+        if H.dim == 1:
+            ds = departure_offsets_da_1d(grid, ws, n, H.r)
+            out += float(lam[n + 1] @ dphi_da_apply_1d(U[n], H.levels[0].s[n], ds, p))
+        else:
+            dsx, dsy = departure_offsets_da_2d(grid, ws, n, H.r)
+            v = dphi_da_apply_2d(U[n], H.levels[0].s[0][n], H.levels[0].s[1][n], dsx, dsy, p)
+            out += float(np.sum(lam[n + 1] * v))
+    return out
