@@ -192,14 +192,20 @@ mgrit_status mgrit_solve_host(mgrit_handle* h, const double* h_u0, const double*
  * adjoint; this follows from its one-step system (eq. (one-step)): lambda_nt = u_nt - u_target,
  * lambda_n = Phi_n^T lambda_{n+1}, solved backward in time by MGRIT (the reversed problem
  * mu_k = lambda_{nt-k} with the transposed operators; coarse levels use Psi^T = S^T M^{-T} of the
- * forward hierarchy; S^T is applied as a deterministic transposed gather, M^{-T} by the same
- * partitioned solver factorising M^T), same cycle and stopping rule as mgrit_solve, from a zero
- * initial iterate.  Outputs dJ/du0 = lambda_0 and dJ/da = sum_n lambda_{n+1}^T (dPhi_n/da) u_n, where a
- * is wave.a of the kinds with an amplitude (MGRIT_A_CONST: alpha = a; MGRIT_A_SIN_KX_COS_T) and dJ/da
- * is 0 for the others; dPhi/da acts through d s/d a of a tangent-linear ERK step, and u_n is recomputed
- * from the checkpoints.
+ * forward hierarchy), same cycle and stopping rule as mgrit_solve, from a zero initial iterate.
+ * S^T is a deterministic transposed gather (1D: a window of arrival points per node; 2D: the arrival
+ * points grouped by the base node of their tensor-product stencil, Sec. 4.1, in sorted buckets).
+ * M^{-T}: 1D the partitioned banded solver factorising M^T; 2D the same inexact GMRES as the forward
+ * coarse operator (Sec. 4.3), applied to M^T.
+ * Outputs dJ/du0 = lambda_0 and dJ/da = sum_n lambda_{n+1}^T (dPhi_n/da) u_n, where a is wave.a of the
+ * kinds with an amplitude (MGRIT_A_CONST: alpha = a; MGRIT_A_SIN_KX_COS_T; 2D: the x speed of
+ * MGRIT_A2D_CONST and the amplitude of both components of MGRIT_A2D_SIN_COS) and dJ/da is 0 for the
+ * others; dPhi/da acts through d s/d a of a tangent-linear ERK step, and u_n is recomputed from the
+ * checkpoints.
  * d_C_checkpoints: [(nt/m_1 + 1) x N] the C-point rows u_{j m_1} of a converged forward solve.
- * d_dJ_du0: [N]; h_dJ_da: host scalar.  FP64 handles (precision 0), 1D.  Synchronous.
+ * d_dJ_du0: [N]; h_dJ_da: host scalar.  FP64 handles (precision 0), 1D and 2D.  The first call builds
+ * the transposed data (1D: floor ranges and M^T factors; 2D: buckets, 8 bytes per point and step of
+ * every level) and d s/d a (8 bytes per fine point, step and dimension).  Synchronous.
  * stats (optional) describes the adjoint MGRIT solve.
  */
 mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, const double* d_C_checkpoints,

@@ -51,6 +51,40 @@ MGRIT_D void lagrange_weights(R eps, R (&w)[P + 1]) {
   }
 }
 
+// d w_a / d eps of lagrange_weights (product rule over the factors (-eps - j)).
+template <int P>
+MGRIT_D void lagrange_weights_deps(double eps, double (&dw)[P + 1]) {
+  constexpr int L = (P + 1) / 2;
+  double f[P + 1];
+#pragma unroll
+  for (int a = 0; a <= P; ++a) f[a] = -eps - (double)(a - L);
+#pragma unroll
+  for (int a = 0; a <= P; ++a) {
+    double tot = 0.0;
+#pragma unroll
+    for (int skip = 0; skip <= P; ++skip) {
+      if (skip == a) continue;
+      double term = 1.0;
+#pragma unroll
+      for (int q = 0; q <= P; ++q)
+        if (q != a && q != skip) term *= f[q];
+      tot += term;
+    }
+    dw[a] = -tot * lagrange_denominator_inv<P>(a);
+  }
+}
+
+// The single weight w_a(eps) of lagrange_weights (one factor of a 2D tensor-product weight).
+template <int P>
+MGRIT_D double lagrange_basis(double eps, int a) {
+  constexpr int L = (P + 1) / 2;
+  double w = lagrange_denominator_inv<P>(a);
+#pragma unroll
+  for (int c = 0; c <= P; ++c)
+    if (c != a) w *= -eps - (double)(c - L);
+  return w;
+}
+
 // Deterministic block sum of one double per thread (all threads must call).
 MGRIT_D double block_sum(double v, double* smem_scratch) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -45,6 +45,9 @@ int launch_factor_1d(const double* sigma, int nt, int nx, int p, void* out, int 
 void launch_floor_range(const double* s, int nt, int nx, int2* out, cudaStream_t st);
 void launch_departure_da_1d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* ds,
                             cudaStream_t st);
+// 2D: dsx, dsy each [nt][nx*nx].
+void launch_departure_da_2d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* dsx,
+                            double* dsy, cudaStream_t st);
 
 // ---- relaxation (relax_kernels.cu) ---------------------------------------------------------------
 
@@ -81,6 +84,10 @@ struct LevelTables {
   // 2D: FP64 offsets (x block then y block, [2][nt][npts]) for the on-the-fly FP64 weights; on coarse
   // levels `solver` then points at sigma ([2][nt][npts], FP64) of the corrected operator.
   const double* s64;
+  // 2D adjoint: arrival points grouped by the base node of their stencil, per step row:
+  // bperm[row][bstart[row][key] .. bstart[row][key+1]) lists them in increasing order.
+  const int* bstart;  // [nt][npts + 1]
+  const int* bperm;   // [nt][npts]
 };
 
 
@@ -185,5 +192,13 @@ cudaError_t launch_sequential_2d(const LevelTables& T, int N, const void* g, con
                                  const Scratch2d& S, int is_double, cudaStream_t st);
 cudaError_t launch_apply_steps_2d(const LevelTables& T, int n0, int count, const void* in, void* out,
                                   const Scratch2d& S, int is_double, cudaStream_t st);
+
+// 2D adjoint.  Groups the arrival points of every step row by the base node of their stencil
+// (shift: [2][nt][npts] as in LevelTables) into bstart / bperm; deterministic (sorted buckets).
+cudaError_t launch_bucket_build(const uint16_t* shift, int nt, int nx, int* bstart, int* bperm, cudaStream_t st);
+// dJ/da contributions per interval of level 0 (FP64): u_n recomputed from the checkpoints C[j] by fine
+// steps; out[j] = sum_n lambda_{n+1} . (dPhi_n/da) u_n with lambda_{n+1} = mu[nt - n - 1].
+cudaError_t launch_gradient_a_2d(const LevelTables& T, const double* ds, const double* C, const double* mu, int nt,
+                                 int m, int J, const Scratch2d& S, double* out, cudaStream_t st);
 
 }  // namespace mgrit

@@ -63,6 +63,51 @@ __global__ void __launch_bounds__(kThreads2d) k_step2d(LevelTables T, const R* _
   if (fstore) fstore[(size_t)(n + 1) * N + pt] = acc;
 }
 
+// Transposed step dst[j] = S_row^T src[j] (+ g[n(j)+1]), FP64, row = nt-1-n(j) when T.reverse.  Target
+// node (X, Y) receives w_a(eps_i) w_b(nu_i) src_i from every arrival point i whose stencil base node
+// is (X - a, Y - b); the arrival points of each base node are read from the sorted buckets, so the sum
+// has a fixed order (a deterministic scatter-add).
+template <int P>
+__global__ void __launch_bounds__(kThreads2d) k_step2d_T(LevelTables T, const double* __restrict__ src,
+                                                         double* __restrict__ dst, int m, int k, int n0,
+                                                         const double* __restrict__ g, double* __restrict__ fstore) {
+  const int j = blockIdx.y;
+  const long long N = T.npts;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= N) return;
+  const int n = m > 0 ? j * m + k : n0;
+  const int row = T.reverse ? T.nt - 1 - n : n;
+  const int nx = T.nx, mask = nx - 1;
+  const int X = (int)(pt % nx), Y = (int)(pt / nx);
+  const int* bs = T.bstart + (size_t)row * (N + 1);
+  const int* bp = T.bperm + (size_t)row * N;
+  const double* sx = T.s64 + (size_t)row * N;
+  const double* sy = T.s64 + ((size_t)T.nt + row) * N;
+  const double* s = src + (size_t)j * N;
+  double acc = 0.0;
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int rowkey = ((Y - b) & mask) * nx;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int key = rowkey + ((X - a) & mask);
+      const int q1 = __ldg(bs + key + 1);
+      for (int q = __ldg(bs + key); q < q1; ++q) {
+        const int i = __ldg(bp + q);
+        double ex = __ldg(sx + i), ey = __ldg(sy + i);
+        ex -= floor(ex);
+        if (ex >= 1.0) ex -= 1.0;
+        ey -= floor(ey);
+        if (ey >= 1.0) ey -= 1.0;
+        acc += lagrange_basis<P>(ex, a) * lagrange_basis<P>(ey, b) * __ldg(s + i);
+      }
+    }
+  }
+  if (g) acc += g[(size_t)(n + 1) * N + pt];
+  dst[(size_t)j * N + pt] = acc;
+  if (fstore) fstore[(size_t)(n + 1) * N + pt] = acc;
+}
+
 // y = M x with M = I - diag(sx) (I (x) D) - diag(sy) (D (x) I), D = (delta^2)^B (periodic).
 template <int B, typename R>
 __device__ __forceinline__ R apply_M(const R* x, const double* sx, const double* sy, long long pt, int nx) {
@@ -81,6 +126,24 @@ __device__ __forceinline__ R apply_M(const R* x, const double* sx, const double*
   return x[pt] - (R)sx[pt] * dxv - (R)sy[pt] * dyv;
 }
 
+// y = M^T x = x - (I (x) D) diag(sx) x - (D (x) I) diag(sy) x (D is symmetric).
+template <int B, typename R>
+__device__ __forceinline__ R apply_MT(const R* x, const double* sx, const double* sy, long long pt, int nx) {
+  const int i = (int)(pt % nx), jj = (int)(pt / nx);
+  R dxv = (R)0, dyv = (R)0;
+#pragma unroll
+  for (int o = -B; o <= B; ++o) {
+    double c = 1.0;
+    for (int t = 1; t <= B + o; ++t) c = c * (2 * B - (B + o) + t) / t;
+    const R d = (R)(((B + o) & 1) ? -c : c);
+    const long long px = (long long)jj * nx + wrap_pow2(i + o, nx);
+    const long long py = (long long)wrap_pow2(jj + o, nx) * nx + i;
+    dxv += d * (R)sx[px] * x[px];
+    dyv += d * (R)sy[py] * x[py];
+  }
+  return x[pt] - dxv - dyv;
+}
+
 template <typename R>
 __device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, double* red) {
   double s = 0.0;
@@ -94,20 +157,20 @@ __device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, d
   return t;
 }
 
-// One CTA per interval j: b (= rhs, in place -> solution) of the system of step n(j) = n0 + j*m.
-// basis: [J][kmax + 1][N] scratch.  GMRES (Arnoldi with modified Gram-Schmidt, Givens rotations), zero
+// One CTA per interval j: b (= rhs, in place -> solution) of the system of step n(j) = n0 + j*m
+// (row nt_rev - 1 - n(j) when nt_rev > 0; TRANS solves with M^T).  basis: [J][kmax + 1][N] scratch.  GMRES (Arnoldi with modified Gram-Schmidt, Givens rotations), zero
 // initial guess, stop when the least-squares residual <= rtol ||b|| or after kmax iterations.
-template <int B, typename R>
+template <int B, typename R, bool TRANS>
 __global__ void __launch_bounds__(kThreads2d) k_gmres2d(const double* __restrict__ sigma_x,
                                                         const double* __restrict__ sigma_y, int nx, int n0, int m,
-                                                        R* __restrict__ bx_all, R* __restrict__ basis, int kmax,
-                                                        double rtol) {
+                                                        int nt_rev, R* __restrict__ bx_all, R* __restrict__ basis,
+                                                        int kmax, double rtol) {
   __shared__ double red[40];
   __shared__ double H[11][10];
   __shared__ double cs[10], sn[10], gv[11], yv[10];
   const long long N = (long long)nx * nx;
   const int j = blockIdx.x;
-  const int n = n0 + j * m;
+  const int n = nt_rev > 0 ? nt_rev - 1 - (n0 + j * m) : n0 + j * m;
   const double* sx = sigma_x + (size_t)n * N;
   const double* sy = sigma_y + (size_t)n * N;
   R* b = bx_all + (size_t)j * N;
@@ -124,7 +187,8 @@ __global__ void __launch_bounds__(kThreads2d) k_gmres2d(const double* __restrict
   for (int kk = 0; kk < kmax; ++kk) {
     R* vk = V + (size_t)kk * N;
     R* w = V + (size_t)(kk + 1) * N;
-    for (long long q = threadIdx.x; q < N; q += blockDim.x) w[q] = apply_M<B, R>(vk, sx, sy, q, nx);
+    for (long long q = threadIdx.x; q < N; q += blockDim.x)
+      w[q] = TRANS ? apply_MT<B, R>(vk, sx, sy, q, nx) : apply_M<B, R>(vk, sx, sy, q, nx);
     __syncthreads();
     for (int t = 0; t <= kk; ++t) {  // modified Gram-Schmidt
       const R* vt = V + (size_t)t * N;
@@ -241,6 +305,28 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
   dim3 grid((unsigned)((N + kThreads2d - 1) / kThreads2d), (unsigned)J);
   const bool coarse = T.solver != nullptr;
   const int addg_in_step = coarse ? 0 : 1;
+  const int n_first = m > 0 ? k : n0;
+  if (T.trans) {  // Phi^T = S^T M^{-T}: the correction solve (in place on src), then the transposed step
+    if constexpr (std::is_same<R, double>::value) {
+      if (coarse) {
+        const double* sig = (const double*)T.solver;
+        const int B = (T.p + 1) / 2, ntr = T.reverse ? T.nt : 0;
+#define MGRIT_GMT(BB)                                                                                        \
+  k_gmres2d<BB, double, true><<<J, kThreads2d, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, ntr, src, \
+                                                        (double*)S.basis, S.kmax, S.rtol)
+        if (B == 1) MGRIT_GMT(1);
+        else if (B == 2) MGRIT_GMT(2);
+        else MGRIT_GMT(3);
+#undef MGRIT_GMT
+      }
+      if (T.p == 1) k_step2d_T<1><<<grid, kThreads2d, 0, st>>>(T, src, dst, m, k, n0, g, fstore);
+      else if (T.p == 3) k_step2d_T<3><<<grid, kThreads2d, 0, st>>>(T, src, dst, m, k, n0, g, fstore);
+      else k_step2d_T<5><<<grid, kThreads2d, 0, st>>>(T, src, dst, m, k, n0, g, fstore);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
 #define MGRIT_STEP2D(PP) k_step2d<PP, R><<<grid, kThreads2d, 0, st>>>(T, src, dst, m, k, n0, g, addg_in_step, coarse ? nullptr : fstore)
   if (T.p == 1) MGRIT_STEP2D(1);
   else if (T.p == 3) MGRIT_STEP2D(3);
@@ -249,10 +335,9 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
   if (coarse) {
     const double* sig = (const double*)T.solver;  // sigma_x block then sigma_y block, [nt][N] each
     const int B = (T.p + 1) / 2;
-    const int n_first = m > 0 ? k : n0;
 #define MGRIT_GM(BB)                                                                                      \
-  k_gmres2d<BB, R><<<J, kThreads2d, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, dst, (R*)S.basis, \
-                                             S.kmax, S.rtol)
+  k_gmres2d<BB, R, false><<<J, kThreads2d, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, 0, dst, \
+                                                    (R*)S.basis, S.kmax, S.rtol)
     if (B == 1) MGRIT_GM(1);
     else if (B == 2) MGRIT_GM(2);
     else MGRIT_GM(3);
@@ -310,6 +395,137 @@ cudaError_t sequential2d(const LevelTables& T, int Nst, const R* g, const R* u0,
   return cudaGetLastError();
 }
 
+
+// ---- 2D adjoint support -----------------------------------------------------------------------------
+
+// Base node of the stencil of arrival point pt in step row n: ((i + shift_x) mod nx, (j + shift_y) mod nx).
+__device__ __forceinline__ int base_key(const uint16_t* __restrict__ shift, int nt, int n, long long N, int nx,
+                                        long long pt) {
+  const int mask = nx - 1;
+  const int i = (int)(pt % nx), jj = (int)(pt / nx);
+  const int bx = (i + (int)shift[(size_t)n * N + pt]) & mask;
+  const int by = (jj + (int)shift[((size_t)nt + n) * N + pt]) & mask;
+  return by * nx + bx;
+}
+
+// counts[n][1 + key] += 1 (counts zeroed before).
+__global__ void k_bucket_count(const uint16_t* __restrict__ shift, int nt, int nx, int* __restrict__ counts) {
+  const long long N = (long long)nx * nx;
+  const int n = blockIdx.y;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= N) return;
+  atomicAdd(counts + (size_t)n * (N + 1) + 1 + base_key(shift, nt, n, N, nx, pt), 1);
+}
+
+// In-place inclusive scan of each row of length len (one CTA of 1024 threads per row).
+__global__ void __launch_bounds__(1024) k_scan_rows(int* __restrict__ v, long long len) {
+  __shared__ int part[1024];
+  int* row = v + (size_t)blockIdx.x * len;
+  const long long chunk = (len + blockDim.x - 1) / blockDim.x;
+  const long long lo = threadIdx.x * chunk, hi = lo + chunk < len ? lo + chunk : len;
+  int s = 0;
+  for (long long q = lo; q < hi; ++q) s += row[q];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // Hillis-Steele inclusive scan of the chunk sums
+    const int t = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
+  for (long long q = lo; q < hi; ++q) {
+    run += row[q];
+    row[q] = run;
+  }
+}
+
+// perm[n][cursor[n][key]++] = pt (cursor starts as a copy of bstart's first npts entries of the row).
+__global__ void k_bucket_fill(const uint16_t* __restrict__ shift, int nt, int nx, int* __restrict__ cursor,
+                              int* __restrict__ perm) {
+  const long long N = (long long)nx * nx;
+  const int n = blockIdx.y;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= N) return;
+  const int slot = atomicAdd(cursor + (size_t)n * N + base_key(shift, nt, n, N, nx, pt), 1);
+  perm[(size_t)n * N + slot] = (int)pt;
+}
+
+// Sorts every bucket (insertion sort; buckets hold a few points) so that the order is independent of
+// the order of the atomic slot claims.
+__global__ void k_bucket_sort(const int* __restrict__ bstart, int nx, int* __restrict__ perm) {
+  const long long N = (long long)nx * nx;
+  const int n = blockIdx.y;
+  const long long key = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (key >= N) return;
+  const int* bs = bstart + (size_t)n * (N + 1);
+  int* pp = perm + (size_t)n * N;
+  const int lo = bs[key], hi = bs[key + 1];
+  for (int a = lo + 1; a < hi; ++a) {
+    const int v = pp[a];
+    int b = a - 1;
+    while (b >= lo && pp[b] > v) {
+      pp[b + 1] = pp[b];
+      --b;
+    }
+    pp[b + 1] = v;
+  }
+}
+
+__global__ void k_copy_starts(const int* __restrict__ bstart, long long N, int* __restrict__ cursor) {
+  const int n = blockIdx.y;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < N) cursor[(size_t)n * N + q] = bstart[(size_t)n * (N + 1) + q];
+}
+
+// partial[j][chunk] += sum over the chunk's points of lambda_{n+1} (dPhi_n/da) u_n, n = j m + k, u_n = cur[j].
+template <int P>
+__global__ void __launch_bounds__(kThreads2d) k_grad2d(LevelTables T, const double* __restrict__ ds,
+                                                       const double* __restrict__ cur, const double* __restrict__ mu,
+                                                       int nt, int m, int k, double* __restrict__ partial,
+                                                       int chunks) {
+  __shared__ double red[33];
+  const int j = blockIdx.y;
+  const int n = j * m + k;
+  const long long N = T.npts;
+  const int nx = T.nx;
+  const double* lam = mu + (size_t)(nt - n - 1) * N;
+  const double* u = cur + (size_t)j * N;
+  double acc = 0.0;
+  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < N; pt += (long long)gridDim.x * blockDim.x) {
+    const size_t ox = (size_t)n * N + pt, oy = ((size_t)T.nt + n) * N + pt;
+    double ex = T.s64[ox], ey = T.s64[oy];
+    ex -= floor(ex);
+    if (ex >= 1.0) ex -= 1.0;
+    ey -= floor(ey);
+    if (ey >= 1.0) ey -= 1.0;
+    double wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
+    lagrange_weights<P, double>(ex, wx);
+    lagrange_weights<P, double>(ey, wy);
+    lagrange_weights_deps<P>(ex, dwx);
+    lagrange_weights_deps<P>(ey, dwy);
+    const int i = (int)(pt % nx), jj = (int)(pt / nx);
+    const int bx = i + (int)T.shift[ox], by = jj + (int)T.shift[oy];
+    const double dsx = ds[ox], dsy = ds[oy];
+    double val = 0.0;
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {
+      const double* row = u + (size_t)wrap_pow2(by + b, nx) * nx;
+      double rx = 0.0, rdx = 0.0;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        const double v = row[wrap_pow2(bx + a, nx)];
+        rx += wx[a] * v;
+        rdx += dwx[a] * v;
+      }
+      val += wy[b] * dsx * rdx + dwy[b] * dsy * rx;
+    }
+    acc += lam[pt] * val;
+  }
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[(size_t)j * chunks + blockIdx.x] += t;
+}
+
 }  // namespace
 
 cudaError_t launch_relax_2d(const LevelTables& T, const RelaxArgs& a, const Scratch2d& S, int is_double,
@@ -337,6 +553,55 @@ cudaError_t launch_apply_steps_2d(const LevelTables& T, int n0, int count, const
                           nullptr, st);
     if (e != cudaSuccess) return e;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_build(const uint16_t* shift, int nt, int nx, int* bstart, int* bperm, cudaStream_t st) {
+  const long long N = (long long)nx * nx;
+  const int bs = 256;
+  dim3 grid((unsigned)((N + bs - 1) / bs), (unsigned)nt);
+  cudaError_t e = cudaMemsetAsync(bstart, 0, (size_t)nt * (N + 1) * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_bucket_count<<<grid, bs, 0, st>>>(shift, nt, nx, bstart);
+  k_scan_rows<<<nt, 1024, 0, st>>>(bstart, N + 1);
+  int* cursor = nullptr;
+  e = cudaMallocAsync((void**)&cursor, (size_t)nt * N * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_copy_starts<<<grid, bs, 0, st>>>(bstart, N, cursor);
+  k_bucket_fill<<<grid, bs, 0, st>>>(shift, nt, nx, cursor, bperm);
+  k_bucket_sort<<<grid, bs, 0, st>>>(bstart, nx, bperm);
+  cudaFreeAsync(cursor, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient_a_2d(const LevelTables& T, const double* ds, const double* C, const double* mu, int nt,
+                                 int m, int J, const Scratch2d& S, double* out, cudaStream_t st) {
+  const long long N = T.npts;
+  const int chunks = 64;
+  double* cur = (double*)S.cur;
+  double* nxt = (double*)S.nxt;
+  dim3 g1((unsigned)((N + kThreads2d - 1) / kThreads2d), (unsigned)J);
+  k_load_start<double><<<g1, kThreads2d, 0, st>>>(C, N, nullptr, 0, nullptr, 0, cur, N, J);
+  cudaError_t e = cudaMemsetAsync(S.partial, 0, (size_t)J * chunks * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  LevelTables F = T;  // forward fine steps
+  F.solver = nullptr;
+  F.trans = 0;
+  F.reverse = 0;
+  dim3 g2(chunks, (unsigned)J);
+  for (int k = 0; k < m; ++k) {
+    if (T.p == 1) k_grad2d<1><<<g2, kThreads2d, 0, st>>>(T, ds, cur, mu, nt, m, k, S.partial, chunks);
+    else if (T.p == 3) k_grad2d<3><<<g2, kThreads2d, 0, st>>>(T, ds, cur, mu, nt, m, k, S.partial, chunks);
+    else k_grad2d<5><<<g2, kThreads2d, 0, st>>>(T, ds, cur, mu, nt, m, k, S.partial, chunks);
+    if (k + 1 < m) {
+      e = step_all<double>(F, S, cur, nxt, m, k, 0, J, nullptr, nullptr, st);
+      if (e != cudaSuccess) return e;
+      double* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  }
+  k_sum_chunks<<<(J + 255) / 256, 256, 0, st>>>(S.partial, chunks, J, out);
   return cudaGetLastError();
 }
 

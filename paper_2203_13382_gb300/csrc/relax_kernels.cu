@@ -283,29 +283,6 @@ __device__ __forceinline__ void apply_gather_T(const LevelTables& T, int row, co
   }
 }
 
-// d w_a / d eps of the Lagrange weights (product rule), FP64.
-template <int P>
-__device__ __forceinline__ void lagrange_weights_deps(double eps, double (&dw)[P + 1]) {
-  constexpr int L = (P + 1) / 2;
-  double f[P + 1];
-#pragma unroll
-  for (int a = 0; a <= P; ++a) f[a] = -eps - (double)(a - L);
-#pragma unroll
-  for (int a = 0; a <= P; ++a) {
-    double tot = 0.0;
-#pragma unroll
-    for (int skip = 0; skip <= P; ++skip) {
-      if (skip == a) continue;
-      double term = 1.0;
-#pragma unroll
-      for (int q = 0; q <= P; ++q)
-        if (q != a && q != skip) term *= f[q];
-      tot += term;
-    }
-    dw[a] = -tot * lagrange_denominator_inv<P>(a);
-  }
-}
-
 // Shared-memory staging of the reduction coefficients of one coarse step (FP32 levels).
 struct Stage {
   void* buf;       // shared buffer of T.stage_bytes, or nullptr

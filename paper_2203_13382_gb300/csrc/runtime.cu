@@ -54,7 +54,9 @@ struct Level {
   // adjoint (built on first use): floor ranges, factorisation of M^T, d s / d a (level 0)
   int2* frange = nullptr;
   void* solverT = nullptr;
-  double* ds = nullptr;
+  double* ds = nullptr;  // 2D: x block then y block
+  int* bstart = nullptr;  // 2D: arrival points grouped by stencil base node (transposed step)
+  int* bperm = nullptr;
 };
 
 double now_ms() {
@@ -178,10 +180,12 @@ struct mgrit_handle {
     T.trans = 0;
     T.reverse = 0;
     T.frange = L.frange;
+    T.bstart = L.bstart;
+    T.bperm = L.bperm;
     if (trans_mode) {
       T.trans = 1;
       T.reverse = 1;
-      if (T.solver) T.solver = L.solverT;
+      if (T.solver && grid.dim == 1) T.solver = L.solverT;  // 2D: GMRES with M^T on the same sigma
       return T;
     }
     if (T.solver && !is_double && grid.dim == 1) {
@@ -746,6 +750,24 @@ mgrit_status ensure_adjoint(mgrit_handle* h) {
   if (h->adjoint_ready) return MGRIT_OK;
   cudaStream_t s = h->stream;
   const int nx = h->grid.nx, np = h->npts, p = h->order;
+  const double hg = (h->grid.xmax - h->grid.xmin) / nx;
+  WaveParams wp{h->wave.kind, h->wave.a, h->wave.k, h->wave.a2};
+  if (h->grid.dim == 2) {
+    for (size_t l = 0; l < h->levels.size(); ++l) {
+      Level& L = h->levels[l];
+      MG_TRY(h->alloc(&L.bstart, (size_t)L.nt * (np + 1)));
+      MG_TRY(h->alloc(&L.bperm, (size_t)L.nt * np));
+      MG_CUDA(launch_bucket_build(L.shift, L.nt, nx, L.bstart, L.bperm, s));
+    }
+    Level& L0 = h->levels[0];
+    MG_TRY(h->alloc(&L0.ds, (size_t)2 * L0.nt * np));
+    launch_departure_da_2d(wp, p, nx, L0.nt, h->grid.xmin, hg, h->grid.cfl * hg, L0.ds, L0.ds + (size_t)L0.nt * np,
+                           s);
+    MG_CUDA(cudaGetLastError());
+    MG_CUDA(cudaStreamSynchronize(s));
+    h->adjoint_ready = true;
+    return MGRIT_OK;
+  }
   for (size_t l = 0; l < h->levels.size(); ++l) {
     Level& L = h->levels[l];
     MG_TRY(h->alloc(&L.frange, (size_t)L.nt));
@@ -757,8 +779,6 @@ mgrit_status ensure_adjoint(mgrit_handle* h) {
   }
   Level& L0 = h->levels[0];
   MG_TRY(h->alloc(&L0.ds, (size_t)L0.nt * np));
-  const double hg = (h->grid.xmax - h->grid.xmin) / nx;
-  WaveParams wp{h->wave.kind, h->wave.a, h->wave.k, h->wave.a2};
   launch_departure_da_1d(wp, p, nx, L0.nt, h->grid.xmin, hg, h->grid.cfl * hg, L0.ds, s);
   int flag = 0;
   MG_CUDA(cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -777,7 +797,6 @@ mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, cons
   if (!h || !d_u_target || !d_C_checkpoints || !d_dJ_du0 || !h_dJ_da)
     return fail(MGRIT_EINVAL, "NULL argument");
   if (h->opt.precision != 0) return fail(MGRIT_EUNSUPPORTED, "the adjoint solve needs an FP64 handle (precision 0)");
-  if (h->grid.dim != 1) return fail(MGRIT_EUNSUPPORTED, "the adjoint solve is implemented for 1D problems");
   MG_TRY(ensure_adjoint(h));
   cudaStream_t s = h->stream;
   const int np = h->npts, nt = h->grid.nt, m1 = h->levels[1].m, J = h->J1();
@@ -797,7 +816,9 @@ mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, cons
     LevelTables T0 = h->tables(0, 1);
     T0.solver = nullptr;
     const Level& L0 = h->levels[0];
-    cudaError_t e = launch_gradient_a_1d(T0, L0.s64, L0.ds, d_C_checkpoints, mu, nt, m1, h->norm_partial, s);
+    cudaError_t e = h->grid.dim == 2
+                        ? launch_gradient_a_2d(T0, L0.ds, d_C_checkpoints, mu, nt, m1, J, h->s2d, h->norm_partial, s)
+                        : launch_gradient_a_1d(T0, L0.s64, L0.ds, d_C_checkpoints, mu, nt, m1, h->norm_partial, s);
     if (e != cudaSuccess) st = fail(MGRIT_ECUDA, std::string("gradient kernel: ") + cudaGetErrorString(e));
     launch_sum(h->norm_partial, J, h->norm_dev, s);
     cudaMemcpyAsync(h_dJ_da, h->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -171,6 +171,71 @@ void launch_departure_da_1d(const WaveParams& w, int r, int nx, int nt, double x
   k_departure_da_1d<<<grid, bs, 0, st>>>(w, make_tableau(r), nx, xmin, h, dt, ds);
 }
 
+// Derivatives of the 2D velocity: (dvx/da, dvx/dx, dvx/dy) and (dvy/da, dvy/dx, dvy/dy).  The parameter
+// a is the amplitude of kind 12 (both components) and the x speed of kind 10; kind 11 has none.
+MGRIT_D void dvelocity_2d(const WaveParams& w, double x, double y, double t, double (&gx)[3], double (&gy)[3]) {
+  gx[0] = gx[1] = gx[2] = gy[0] = gy[1] = gy[2] = 0.0;
+  if (w.kind == 10) {
+    gx[0] = 1.0;
+  } else if (w.kind == 11) {
+    const double ct = cos(kTwoPi * t / 3.4);
+    gx[2] = 2.0 * kPi * sin(kPi * y) * cos(kPi * y) * ct;
+    gy[1] = 2.0 * kPi * cos(kPi * x) * sin(kPi * x) * ct;
+  } else {
+    const double ct = cos(kTwoPi * t), st = sin(kTwoPi * t);
+    gx[0] = sin(kTwoPi * y) * ct;
+    gx[2] = w.a * kTwoPi * cos(kTwoPi * y) * ct;
+    gy[0] = cos(kTwoPi * x) * st;
+    gy[1] = -w.a * kTwoPi * sin(kTwoPi * x) * st;
+  }
+}
+
+// (d sx / d a, d sy / d a): the stages of erk_displacement_2d differentiated (tangent-linear ERK).
+__global__ void k_departure_da_2d(WaveParams w, Tableau T, int nx, int nt, double xmin, double h, double dt,
+                                  double* __restrict__ dsx, double* __restrict__ dsy) {
+  const long long npts = (long long)nx * nx;
+  const int n = blockIdx.y;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npts) return;
+  const int j = (int)(pt / nx), i = (int)(pt % nx);
+  const double x = xmin + h * i, y = xmin + h * j;
+  const double t1 = (n + 1) * dt;
+  double kx[6], ky[6], dkx[6], dky[6];
+  for (int st = 0; st < T.stages; ++st) {
+    double xs = x, ys = y, dxs = 0.0, dys = 0.0;
+    for (int q = 0; q < st; ++q)
+      if (T.A[st][q] != 0.0) {
+        xs = xs - dt * T.A[st][q] * kx[q];
+        ys = ys - dt * T.A[st][q] * ky[q];
+        dxs = dxs - dt * T.A[st][q] * dkx[q];
+        dys = dys - dt * T.A[st][q] * dky[q];
+      }
+    const double ts = t1 - T.c[st] * dt;
+    double gx[3], gy[3];
+    velocity_2d(w, xs, ys, ts, kx[st], ky[st]);
+    dvelocity_2d(w, xs, ys, ts, gx, gy);
+    dkx[st] = gx[0] + gx[1] * dxs + gx[2] * dys;
+    dky[st] = gy[0] + gy[1] * dxs + gy[2] * dys;
+  }
+  double ax = 0.0, ay = 0.0;
+  for (int st = 0; st < T.stages; ++st)
+    if (T.b[st] != 0.0) {
+      ax = ax + T.b[st] * dkx[st];
+      ay = ay + T.b[st] * dky[st];
+    }
+  const size_t o = (size_t)n * npts + pt;
+  dsx[o] = dt * ax / h;
+  dsy[o] = dt * ay / h;
+}
+
+void launch_departure_da_2d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* dsx,
+                            double* dsy, cudaStream_t st) {
+  const int bs = 256;
+  const long long npts = (long long)nx * nx;
+  dim3 grid((unsigned)((npts + bs - 1) / bs), (unsigned)nt);
+  k_departure_da_2d<<<grid, bs, 0, st>>>(w, make_tableau(r), nx, nt, xmin, h, dt, dsx, dsy);
+}
+
 // ------------------------------------------------------------------------------------------------
 // K2: backtracking (Sec. 3.3.1 eq. (coarse_depart_interp); Sec. SM6) and phi / sigma (eq. (nu_p_def))
 // ------------------------------------------------------------------------------------------------
