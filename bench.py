@@ -303,25 +303,31 @@ def run_ours(args) -> None:
             traffic = json.load(f).get(args.precision)
     roof = roofline({"phase_ms": agg_ms, "phase_launches": agg_nl}, wl, hbm, hbm_src, args.steps, traffic)
 
-    # comparator: sequential SL stepping on the same GPU (steps only, and including the departure points)
-    h = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
-                       max_coarsest=wl["max_coarsest"], precision=0, profile=1)
-    h.sequential(u0, store_all=False)
-    torch.cuda.synchronize()
-    s0 = torch.cuda.Event(enable_timing=True)
-    s1 = torch.cuda.Event(enable_timing=True)
-    nseq = max(2, args.steps // 2)
-    s0.record(stream)
-    for _ in range(nseq):
-        seq_last = h.sequential(u0, store_all=False)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = s0.elapsed_time(s1) / nseq
-    _, st_prof = h.solve(u0, U0, u_out)
-    dep_ms = st_prof["phase_ms"]["departure"]
-    tab_ms = st_prof["phase_ms"]["tables"] * nt / sum(h.level_info(l)[0] for l in range(h.nlevels))
-    h.destroy()
-    seq_full_ms = seq_ms + dep_ms + tab_ms
+    # comparator: sequential SL stepping on the same GPU (one thread-block cluster per slice), FP64 and
+    # FP32; the faster one, plus its departure points and level-0 tables, is the reported comparator
+    seq_ms = {}
+    for name, pr in (("fp64", 0), ("fp32", 1)):
+        h = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
+                           max_coarsest=wl["max_coarsest"], precision=pr, profile=1)
+        h.sequential(u0, store_all=False)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        nseq = max(3, args.steps)
+        s0.record(stream)
+        for _ in range(nseq):
+            last = h.sequential(u0, store_all=False)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms[name] = s0.elapsed_time(s1) / nseq
+        if pr == 0:
+            seq_last = last.clone()
+            _, st_prof = h.solve(u0, U0, u_out)
+            dep_ms = st_prof["phase_ms"]["departure"]
+            tab_ms = st_prof["phase_ms"]["tables"] * nt / sum(h.level_info(l)[0] for l in range(h.nlevels))
+        h.destroy()
+    seq_best = min(seq_ms, key=seq_ms.get)
+    seq_full_ms = seq_ms[seq_best] + dep_ms + tab_ms
     fixed_point = float((seq_last - u_out[-1]).norm() / seq_last.norm())
 
     # end to end through the host-buffer entry point (inputs from pinned host memory, solution back)
@@ -358,8 +364,10 @@ def run_ours(args) -> None:
                        "l2": "inputs larger than L2: per-step gather tables alone exceed 2 GB"},
             "iterations": iters[0], "iterations_all_steps": sorted(set(iters)),
             "comparator": {"sequential_dof_per_s": dof / (seq_full_ms / 1e3),
-                           "sequential_ms": seq_full_ms, "sequential_steps_only_ms": seq_ms,
-                           "sequential_includes": "FP64 departure points + level-0 gather tables + nt SL steps",
+                           "sequential_ms": seq_full_ms, "sequential_precision": seq_best,
+                           "sequential_steps_only_ms": seq_ms,
+                           "sequential_includes": "FP64 departure points + level-0 gather tables + nt SL steps "
+                                                  "(one thread-block cluster per slice)",
                            "mgrit_over_sequential": (dof / (ms / 1e3)) / (dof / (seq_full_ms / 1e3)),
                            "fixed_point_rel_diff_final_slice": fixed_point},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,

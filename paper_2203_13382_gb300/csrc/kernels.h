@@ -124,6 +124,13 @@ cudaError_t launch_relax_1d(const LevelTables& T, const RelaxArgs& a, int is_dou
 cudaError_t launch_sequential_1d(const LevelTables& T, int N, const void* g, const void* u0, void* out, int store_all,
                                  int is_double, cudaStream_t st);
 
+// Fine-level sequential stepping (g = 0, plain SL step) by one thread-block cluster holding the slice in
+// the shared memory of its CTAs (seq_cluster.cu); nx >= 256.  Same arguments and results as
+// launch_sequential_1d; cudaErrorNotSupported when the cluster cannot be formed (the caller then uses
+// the single-CTA kernel).
+cudaError_t launch_sequential_cluster_1d(const LevelTables& T, int N, const void* u0, void* out, int store_all,
+                                         int is_double, cudaStream_t st);
+
 // Applies count steps n0..n0+count-1 to independent slices: out[c] = Phi_{n0+c} in[c].
 cudaError_t launch_apply_steps_1d(const LevelTables& T, int n0, int count, const void* in, void* out, int is_double,
                                   cudaStream_t st);

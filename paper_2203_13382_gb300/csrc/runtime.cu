@@ -719,9 +719,19 @@ mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u
   T.solver = nullptr;
   h->reset_call_counters();
   const int ev = h->phase_begin();
+  // 1D: one thread-block cluster over the slice; the single-CTA kernel where no cluster can be formed
+  auto seq1d = [&](const void* u0, void* out, int dbl) -> cudaError_t {
+    cudaError_t e = h->grid.nx >= 256 ? launch_sequential_cluster_1d(T, nt, u0, out, store_all, dbl, s)
+                                      : cudaErrorNotSupported;
+    if (e == cudaErrorNotSupported) {
+      cudaGetLastError();
+      e = launch_sequential_1d(T, nt, nullptr, u0, out, store_all, dbl, s);
+    }
+    return e;
+  };
   if (h->opt.precision == 0) {
     if (h->grid.dim == 2) MG_CUDA(launch_sequential_2d(T, nt, nullptr, d_u0, d_u_out, store_all, h->s2d, 1, s));
-    else MG_CUDA(launch_sequential_1d(T, nt, nullptr, d_u0, d_u_out, store_all, 1, s));
+    else MG_CUDA(seq1d(d_u0, d_u_out, 1));
   } else {
     const size_t rows = store_all ? (size_t)(nt + 1) : 1;
     float *u0f = nullptr, *outf = nullptr;
@@ -729,7 +739,7 @@ mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u
     MG_CUDA(cudaMallocAsync((void**)&outf, rows * np * sizeof(float), s));
     launch_axpy_convert(1, d_u0, u0f, nullptr, np, s);
     if (h->grid.dim == 2) MG_CUDA(launch_sequential_2d(T, nt, nullptr, u0f, outf, store_all, h->s2d, 0, s));
-    else MG_CUDA(launch_sequential_1d(T, nt, nullptr, u0f, outf, store_all, 0, s));
+    else MG_CUDA(seq1d(u0f, outf, 0));
     launch_axpy_convert(3, outf, d_u_out, nullptr, (long long)rows * np, s);
     cudaFreeAsync(u0f, s);
     cudaFreeAsync(outf, s);
