@@ -24,15 +24,56 @@ MGRIT_D void small_sincos(double t, double& st, double& ct) {
   }
 }
 
-// One block row of arrival nodes of one step n (blockIdx.y).  The time factors of the ERK stages are
-// shared by the block; the spatial factor at a stage point x_i - d is formed from the node's
-// sin / cos by the angle-addition formula with a small-angle series, since d is a fraction of dt.
-__global__ void k_departure_1d(WaveParams w, Tableau T, int nx, double xmin, double h, double dt,
-                               double* __restrict__ s) {
-  __shared__ double tf[6];
-  const int n = blockIdx.y;
-  const double t1 = (n + 1) * dt;
-  if ((int)threadIdx.x < T.stages) tf[threadIdx.x] = cos(kTwoPi * (t1 - T.c[threadIdx.x] * dt));
+// Coefficients of the order-R tableau as compile-time constants (the same tableaux as make_tableau).
+template <int R>
+struct ErkTab {
+  static constexpr int S = R == 1 ? 1 : (R == 3 ? 3 : 6);
+  static constexpr double a(int s, int j) {
+    if (R == 3) return (s == 1 && j == 0) ? 0.5 : (s == 2 && j == 0) ? -1.0 : (s == 2 && j == 1) ? 2.0 : 0.0;
+    if (R == 5) {
+      constexpr double t[6][6] = {{0, 0, 0, 0, 0, 0},
+                                  {0.25, 0, 0, 0, 0, 0},
+                                  {0.125, 0.125, 0, 0, 0, 0},
+                                  {0, -0.5, 1.0, 0, 0, 0},
+                                  {3.0 / 16.0, 0, 0, 9.0 / 16.0, 0, 0},
+                                  {-3.0 / 7.0, 2.0 / 7.0, 12.0 / 7.0, -12.0 / 7.0, 8.0 / 7.0, 0}};
+      return t[s][j];
+    }
+    return 0.0;
+  }
+  static constexpr double b(int s) {
+    if (R == 1) return 1.0;
+    if (R == 3) return s == 1 ? 2.0 / 3.0 : 1.0 / 6.0;
+    constexpr double t[6] = {7.0 / 90.0, 0.0, 32.0 / 90.0, 12.0 / 90.0, 32.0 / 90.0, 7.0 / 90.0};
+    return t[s];
+  }
+  static constexpr double c(int s) {
+    if (R == 3) return s == 0 ? 0.0 : (s == 1 ? 0.5 : 1.0);
+    if (R == 5) {
+      constexpr double t[6] = {0.0, 0.25, 0.25, 0.5, 0.75, 1.0};
+      return t[s];
+    }
+    return 0.0;
+  }
+};
+
+constexpr int kDepSteps = 16;  // time steps per thread of k_departure_1d
+
+// Arrival node i of the steps n0 .. n0 + kDepSteps - 1 (blockIdx.y): the node's sin / cos of the
+// spatial phase are formed once; the spatial factor at a stage point x_i - d is sin / cos(phase - kw d)
+// by the angle-addition formula with a small-angle series (d is a fraction of dt), and the time
+// factors cos(2 pi t) of the stages are shared by the block.
+template <int R>
+__global__ void __launch_bounds__(256) k_departure_1d(WaveParams w, int nx, int nt, double xmin, double h,
+                                                      double dt, double* __restrict__ s) {
+  using Tb = ErkTab<R>;
+  constexpr int S = Tb::S;
+  __shared__ double tf[kDepSteps][S];
+  const int n0 = blockIdx.y * kDepSteps;
+  for (int q = threadIdx.x; q < kDepSteps * S; q += blockDim.x) {
+    const int nb = q / S, st = q % S;
+    tf[nb][st] = cos(kTwoPi * ((n0 + nb + 1) * dt - Tb::c(st) * dt));
+  }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nx) return;
@@ -40,28 +81,35 @@ __global__ void k_departure_1d(WaveParams w, Tableau T, int nx, double xmin, dou
   const double kw = (w.kind == 3) ? kTwoPi * w.k : kTwoPi;  // spatial wavenumber
   double Sx = 0.0, Cx = 1.0;
   if (w.kind >= 2) sincos(kw * x, &Sx, &Cx);
-  double k[6];
-  for (int st = 0; st < T.stages; ++st) {
-    double d = 0.0;  // x - (stage point)
-    for (int j = 0; j < st; ++j)
-      if (T.A[st][j] != 0.0) d = d + dt * T.A[st][j] * k[j];
-    double a;
-    if (w.kind == 0) {
-      a = w.a;
-    } else if (w.kind == 1) {
-      a = tf[st];
-    } else {
-      double sth, cth;
-      small_sincos(kw * d, sth, cth);
-      if (w.kind == 2) a = tf[st] * (Cx * cth + Sx * sth);       // cos(2 pi t) cos(2 pi (x - d))
-      else a = 1.0 + w.a * (Sx * cth - Cx * sth) * tf[st];     // 1 + a sin(2 pi k (x - d)) cos(2 pi t)
+  const double inv_h = 1.0 / h;
+  const int nend = min(kDepSteps, nt - n0);
+  for (int nb = 0; nb < nend; ++nb) {
+    double k[S];
+#pragma unroll
+    for (int st = 0; st < S; ++st) {
+      double d = 0.0;  // x - (stage point)
+#pragma unroll
+      for (int j = 0; j < st; ++j)
+        if (Tb::a(st, j) != 0.0) d = d + dt * Tb::a(st, j) * k[j];
+      double a;
+      if (w.kind == 0) {
+        a = w.a;
+      } else if (w.kind == 1) {
+        a = tf[nb][st];
+      } else {
+        double sth = 0.0, cth = 1.0;
+        if (st > 0) small_sincos(kw * d, sth, cth);
+        if (w.kind == 2) a = tf[nb][st] * (Cx * cth + Sx * sth);  // cos(2 pi t) cos(2 pi (x - d))
+        else a = 1.0 + w.a * (Sx * cth - Cx * sth) * tf[nb][st];  // 1 + a sin(2 pi k (x - d)) cos(2 pi t)
+      }
+      k[st] = a;
     }
-    k[st] = a;
+    double dsum = 0.0;
+#pragma unroll
+    for (int st = 0; st < S; ++st)
+      if (Tb::b(st) != 0.0) dsum = dsum + Tb::b(st) * k[st];
+    s[(size_t)(n0 + nb) * nx + i] = dt * dsum * inv_h;
   }
-  double dsum = 0.0;
-  for (int st = 0; st < T.stages; ++st)
-    if (T.b[st] != 0.0) dsum = dsum + T.b[st] * k[st];
-  s[(size_t)n * nx + i] = dt * dsum / h;
 }
 
 __global__ void k_departure_2d(WaveParams w, Tableau T, int nx, int nt, double xmin, double h, double dt,
@@ -82,8 +130,10 @@ __global__ void k_departure_2d(WaveParams w, Tableau T, int nx, int nt, double x
 void launch_departure_1d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* s,
                          cudaStream_t st) {
   const int bs = 256;
-  dim3 grid((unsigned)((nx + bs - 1) / bs), (unsigned)nt);
-  k_departure_1d<<<grid, bs, 0, st>>>(w, make_tableau(r), nx, xmin, h, dt, s);
+  dim3 grid((unsigned)((nx + bs - 1) / bs), (unsigned)((nt + kDepSteps - 1) / kDepSteps));
+  if (r == 1) k_departure_1d<1><<<grid, bs, 0, st>>>(w, nx, nt, xmin, h, dt, s);
+  else if (r == 3) k_departure_1d<3><<<grid, bs, 0, st>>>(w, nx, nt, xmin, h, dt, s);
+  else k_departure_1d<5><<<grid, bs, 0, st>>>(w, nx, nt, xmin, h, dt, s);
 }
 
 void launch_departure_2d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* sx,
@@ -256,16 +306,28 @@ MGRIT_D double f_poly(double z, int p) {
   return out / fact;
 }
 
-__global__ void k_backtrack_1d(const double* __restrict__ s_prev, const double* __restrict__ sig_prev, int m, int ntc,
-                               int nx, int p, double* __restrict__ s_out, double* __restrict__ sig_out) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)ntc * nx) return;
-  const int n = (int)(idx / nx), i = (int)(idx % nx);
-  const long long base = (long long)m * n * nx;
+// prod_{q=-(p+1)/2}^{(p-1)/2} (q + z) = (p+1)! f_{p+1}(z)  (eq. (fpoly_def) without its constant factor).
+template <int P>
+MGRIT_D double f_prod(double z) {
+  constexpr int L = (P + 1) / 2;
+  double out = 1.0;
+#pragma unroll
+  for (int q = -L; q <= L - 1; ++q) out = out * (q + z);
+  return out;
+}
+
+// One coarse step row n (blockIdx.y) of arrival nodes i.
+template <int P>
+__global__ void k_backtrack_1d(const double* __restrict__ s_prev, const double* __restrict__ sig_prev, int m, int nx,
+                               double* __restrict__ s_out, double* __restrict__ sig_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  const int n = blockIdx.y;
+  const size_t base = (size_t)m * n * nx;
   // position of the coarse characteristic relative to x_i in grid units; c^{(m-1)} = f^{(m-1)}
-  double c = -s_prev[base + (long long)(m - 1) * nx + i];
+  double c = -s_prev[base + (size_t)(m - 1) * nx + i];
   for (int k = m - 2; k >= 0; --k) {
-    const double* row = s_prev + base + (long long)k * nx;
+    const double* row = s_prev + base + (size_t)k * nx;
     const double xE = ceil(c);  // east node of c (the node itself if c lies on one)
     const int E = i + (int)xE;
     const double fE = xE - row[wrap_pow2(E, nx)];
@@ -273,21 +335,34 @@ __global__ void k_backtrack_1d(const double* __restrict__ s_prev, const double* 
     c = (fE - fW) * (c - xE) + fE;
   }
   const double sc = -c;
+  const size_t idx = (size_t)n * nx + i;
   s_out[idx] = sc;
   double ff = 0.0, gs = 0.0;
   for (int k = 0; k < m; ++k) {
-    ff += f_poly(frac_eps(s_prev[base + (long long)k * nx + i]), p);
-    if (sig_prev) gs += sig_prev[base + (long long)k * nx + i];
+    ff += f_prod<P>(frac_eps(s_prev[base + (size_t)k * nx + i]));
+    if (sig_prev) gs += sig_prev[base + (size_t)k * nx + i];
   }
-  const double phi = ((p + 1) & 1 ? -1.0 : 1.0) * (f_poly(frac_eps(sc), p) - ff);
+  double inv_fact = 1.0;
+#pragma unroll
+  for (int b = 2; b <= P + 1; ++b) inv_fact /= b;
+  const double phi = ((P + 1) & 1 ? -1.0 : 1.0) * (f_prod<P>(frac_eps(sc)) - ff) * inv_fact;
   sig_out[idx] = sig_prev ? gs + phi : phi;
 }
 
 void launch_backtrack_1d(const double* s_prev, const double* sigma_prev, int m, int ntc, int nx, int p, double* s_out,
                          double* sigma_out, cudaStream_t st) {
-  const long long tot = (long long)nx * ntc;
   const int bs = 256;
-  k_backtrack_1d<<<(unsigned)((tot + bs - 1) / bs), bs, 0, st>>>(s_prev, sigma_prev, m, ntc, nx, p, s_out, sigma_out);
+  for (int r0 = 0; r0 < ntc; r0 += 65535) {
+    const int rows = min(65535, ntc - r0);
+    dim3 g((unsigned)((nx + bs - 1) / bs), (unsigned)rows);
+    const double* sp = s_prev + (size_t)m * r0 * nx;
+    const double* gp = sigma_prev ? sigma_prev + (size_t)m * r0 * nx : nullptr;
+    double* so = s_out + (size_t)r0 * nx;
+    double* go = sigma_out + (size_t)r0 * nx;
+    if (p == 1) k_backtrack_1d<1><<<g, bs, 0, st>>>(sp, gp, m, nx, so, go);
+    else if (p == 3) k_backtrack_1d<3><<<g, bs, 0, st>>>(sp, gp, m, nx, so, go);
+    else k_backtrack_1d<5><<<g, bs, 0, st>>>(sp, gp, m, nx, so, go);
+  }
 }
 
 // Bilinear fit p2d of Sec. SM6 in grid units relative to the arrival node.
@@ -356,11 +431,13 @@ void launch_backtrack_2d(const double* sx_prev, const double* sy_prev, const dou
 // Gather tables
 // ------------------------------------------------------------------------------------------------
 
+// One step row (blockIdx.y) of one level: shift, and the FP64 weights and / or the FP32 distance.
 template <int P>
-__global__ void k_build_tables(const double* __restrict__ s, long long total, int nx, int npts_row,
-                               uint16_t* __restrict__ shift, double* __restrict__ w64, float* __restrict__ eps32) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
+__global__ void k_build_tables(const double* __restrict__ s, int nx, int npts_row, uint16_t* __restrict__ shift,
+                               double* __restrict__ w64, float* __restrict__ eps32) {
+  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npts_row) return;
+  const size_t row = blockIdx.y, idx = row * npts_row + pt;
   const double sv = s[idx];
   double fl = floor(sv);
   double eps = sv - fl;
@@ -369,14 +446,13 @@ __global__ void k_build_tables(const double* __restrict__ s, long long total, in
     fl += 1.0;
   }
   constexpr int L = (P + 1) / 2;
-  // first stencil node E - L with E = i - floor(s); stored as an offset from i, modulo nx
-  const long long fli = (long long)fl;
-  shift[idx] = (uint16_t)(((-fli - L) % nx + nx) % nx);
+  // first stencil node E - L with E = i - floor(s); stored as an offset from i, modulo nx (a power of two)
+  const int fli = (int)fl;
+  shift[idx] = (uint16_t)((-fli - L) & (nx - 1));
   if (eps32) eps32[idx] = (float)eps;
   if (w64) {
     double w[P + 1];
     lagrange_weights<P, double>(eps, w);
-    const long long row = idx / npts_row, pt = idx % npts_row;
 #pragma unroll
     for (int a = 0; a <= P; ++a) w64[(row * (P + 1) + a) * npts_row + pt] = w[a];
   }
@@ -384,12 +460,18 @@ __global__ void k_build_tables(const double* __restrict__ s, long long total, in
 
 void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, uint16_t* shift, double* w64,
                          float* eps32, cudaStream_t st) {
-  const long long tot = (long long)nt * npts_row;
   const int bs = 256;
-  const unsigned g = (unsigned)((tot + bs - 1) / bs);
-  if (p == 1) k_build_tables<1><<<g, bs, 0, st>>>(s, tot, nx, npts_row, shift, w64, eps32);
-  else if (p == 3) k_build_tables<3><<<g, bs, 0, st>>>(s, tot, nx, npts_row, shift, w64, eps32);
-  else k_build_tables<5><<<g, bs, 0, st>>>(s, tot, nx, npts_row, shift, w64, eps32);
+  // rows in chunks of 65535 (grid y limit)
+  for (int r0 = 0; r0 < nt; r0 += 65535) {
+    const int rows = min(65535, nt - r0);
+    const size_t o = (size_t)r0 * npts_row;
+    dim3 g((unsigned)((npts_row + bs - 1) / bs), (unsigned)rows);
+    double* w = w64 ? w64 + o * (p + 1) : nullptr;
+    float* e = eps32 ? eps32 + o : nullptr;
+    if (p == 1) k_build_tables<1><<<g, bs, 0, st>>>(s + o, nx, npts_row, shift + o, w, e);
+    else if (p == 3) k_build_tables<3><<<g, bs, 0, st>>>(s + o, nx, npts_row, shift + o, w, e);
+    else k_build_tables<5><<<g, bs, 0, st>>>(s + o, nx, npts_row, shift + o, w, e);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
