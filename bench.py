@@ -242,7 +242,10 @@ def run_ours(args) -> None:
 
         dist = dist_mod
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    wl = WORKLOAD
+    wl = dict(WORKLOAD)
+    if args.nt:  # a shorter time axis (profiling captures of a small case); not the benchmark workload
+        wl["nt"] = args.nt
+        wl["workload"] = WORKLOAD["workload"].replace(f"nt{WORKLOAD['nt']}", f"nt{args.nt}")
     nx, nt = wl["nx"], wl["nt"]
     dof = nx * nt
     prec = 1 if args.precision == "fp32bulk" else 0
@@ -303,51 +306,54 @@ def run_ours(args) -> None:
             traffic = json.load(f).get(args.precision)
     roof = roofline({"phase_ms": agg_ms, "phase_launches": agg_nl}, wl, hbm, hbm_src, args.steps, traffic)
 
-    # comparator: sequential SL stepping on the same GPU (one thread-block cluster per slice), FP64 and
-    # FP32; the faster one, plus its departure points and level-0 tables, is the reported comparator
-    seq_ms = {}
-    for name, pr in (("fp64", 0), ("fp32", 1)):
-        h = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
-                           max_coarsest=wl["max_coarsest"], precision=pr, profile=1)
-        h.sequential(u0, store_all=False)
-        torch.cuda.synchronize()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        nseq = max(3, args.steps)
-        s0.record(stream)
-        for _ in range(nseq):
-            last = h.sequential(u0, store_all=False)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        seq_ms[name] = s0.elapsed_time(s1) / nseq
-        if pr == 0:
-            seq_last = last.clone()
-            _, st_prof = h.solve(u0, U0, u_out)
-            dep_ms = st_prof["phase_ms"]["departure"]
-            tab_ms = st_prof["phase_ms"]["tables"] * nt / sum(h.level_info(l)[0] for l in range(h.nlevels))
-        h.destroy()
-    seq_best = min(seq_ms, key=seq_ms.get)
-    seq_full_ms = seq_ms[seq_best] + dep_ms + tab_ms
-    fixed_point = float((seq_last - u_out[-1]).norm() / seq_last.norm())
+    seq_ms, seq_best, seq_full_ms, fixed_point, e2e = {}, None, None, None, None
+    if not args.no_comparator:
+        # comparator: sequential SL stepping on the same GPU (one thread-block cluster per slice), FP64 and
+        # FP32; the faster one, plus its departure points and level-0 tables, is the reported comparator
+        seq_ms = {}
+        for name, pr in (("fp64", 0), ("fp32", 1)):
+            h = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
+                               max_coarsest=wl["max_coarsest"], precision=pr, profile=1)
+            h.sequential(u0, store_all=False)
+            torch.cuda.synchronize()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            nseq = max(3, args.steps)
+            s0.record(stream)
+            for _ in range(nseq):
+                last = h.sequential(u0, store_all=False)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            seq_ms[name] = s0.elapsed_time(s1) / nseq
+            if pr == 0:
+                seq_last = last.clone()
+                _, st_prof = h.solve(u0, U0, u_out)
+                dep_ms = st_prof["phase_ms"]["departure"]
+                tab_ms = st_prof["phase_ms"]["tables"] * nt / sum(h.level_info(l)[0] for l in range(h.nlevels))
+            h.destroy()
+        seq_best = min(seq_ms, key=seq_ms.get)
+        seq_full_ms = seq_ms[seq_best] + dep_ms + tab_ms
+        fixed_point = float((seq_last - u_out[-1]).norm() / seq_last.norm())
 
-    # end to end through the host-buffer entry point (inputs from pinned host memory, solution back)
-    u0_pin = torch.from_numpy(u0_h).pin_memory()
-    U_pin = torch.from_numpy(U_h).pin_memory()
-    out_pin = torch.empty(nt + 1, nx, dtype=torch.float64).pin_memory()
-    ne2e = max(2, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(ne2e):
-        he = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
-                            max_coarsest=wl["max_coarsest"], precision=prec, rtol=wl["rtol"])
-        he.solve_host(u0_pin.numpy(), U_pin.numpy(), out_pin.numpy())
-        he.destroy()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ne2e
-    J = nt // wl["m"]
-    e2e = {"value": world * dof / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": nx * 8 + J * nx * 8,
-           "d2h_bytes_per_step": (nt + 1) * nx * 8,
-           "path": "mgrit_setup + mgrit_solve_host (pinned host buffers) + mgrit_destroy, wall clock"}
+        # end to end through the host-buffer entry point (inputs from pinned host memory, solution back)
+        u0_pin = torch.from_numpy(u0_h).pin_memory()
+        U_pin = torch.from_numpy(U_h).pin_memory()
+        out_pin = torch.empty(nt + 1, nx, dtype=torch.float64).pin_memory()
+        ne2e = max(2, args.steps // 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ne2e):
+            he = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
+                                max_coarsest=wl["max_coarsest"], precision=prec, rtol=wl["rtol"])
+            he.solve_host(u0_pin.numpy(), U_pin.numpy(), out_pin.numpy())
+            he.destroy()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / ne2e
+        J = nt // wl["m"]
+        e2e = {"value": world * dof / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": nx * 8 + J * nx * 8,
+               "d2h_bytes_per_step": (nt + 1) * nx * 8,
+               "path": "mgrit_setup + mgrit_solve_host (pinned host buffers) + mgrit_destroy, wall clock"}
+
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -363,7 +369,7 @@ def run_ours(args) -> None:
             "config": {**wl, "precision": args.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2: per-step gather tables alone exceed 2 GB"},
             "iterations": iters[0], "iterations_all_steps": sorted(set(iters)),
-            "comparator": {"sequential_dof_per_s": dof / (seq_full_ms / 1e3),
+            "comparator": None if args.no_comparator else {"sequential_dof_per_s": dof / (seq_full_ms / 1e3),
                            "sequential_ms": seq_full_ms, "sequential_precision": seq_best,
                            "sequential_steps_only_ms": seq_ms,
                            "sequential_includes": "FP64 departure points + level-0 gather tables + nt SL steps "
@@ -387,6 +393,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32bulk", "fp64"], default="fp32bulk")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true", help="skip the sequential comparator and e2e runs")
+    ap.add_argument("--nt", type=int, default=0, help="override nt (small profiling cases only)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

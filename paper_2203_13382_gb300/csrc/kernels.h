@@ -72,9 +72,13 @@ struct LevelTables {
   // correction solver (coarse levels, corrected operator); NULL for the plain SL step
   const void* solver;
   size_t solver_stride;  // reals per step
-  // FP32 coarse levels: bytes of the per-step reduction coefficients staged into shared memory by a
-  // TMA bulk copy (0 = read from global memory); err: device flag set to 1 if a bounded wait gave up.
-  unsigned stage_bytes;
+  // gather_stage = 1 (FP32 1D levels): each step's eps32 and shift rows (and sigma on otf levels) are
+  // prefetched into shared memory by TMA bulk copies, one step ahead.  otf = 1 (FP32 coarse levels):
+  // `solver` holds sigma as FP32 rows [nt][nx] (solver_stride = nx) and the correction matrix is
+  // factorised on the fly in every application; otf = 0: `solver` holds the stored factorisation
+  // (solver_layout.cuh).  err: device flag set to 1 if a bounded wait gave up.
+  int gather_stage;
+  int otf;
   int* err;
   // adjoint: trans = 1 applies Phi^T (coarse: (M^{-1} S)^T = S^T M^{-T}, `solver` then holds the
   // factorisation of M^T); reverse = 1 maps step n to table row nt - 1 - n; frange[row] = floor range.
@@ -160,8 +164,10 @@ struct Segment {
   const void* z;
   long long n;
 };
-// Shared-memory bytes and slice-buffer length a tile of this level needs (max over tiles per launch).
-void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem);
+// Shared-memory bytes and slice-buffer length a tile of this level needs, and the bytes of its coarse
+// region placed (128-aligned) after the slice buffers; a launch over several tiles takes the largest
+// buffer and the largest region.
+void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem, size_t* region);
 cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles,
                                  int ntiles, const int* d_active, int is_double, int coarse, int buf, size_t smem,
                                  cudaStream_t st);

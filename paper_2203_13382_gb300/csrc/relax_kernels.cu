@@ -27,52 +27,50 @@ struct GatherRegs<P, double> {  // FP64 streams its table loads inside the gathe
 };
 
 template <int P>
-struct GatherRegs<P, float> {
-  int base[kPts];
-  float eps[kPts];
-};
+struct GatherRegs<P, float> {};  // FP32 reads its tables from shared memory (staged by TMA)
 
 template <int P, typename R>
 __device__ __forceinline__ void load_gather(GatherRegs<P, R>& g, const LevelTables& T, int n) {
-  if constexpr (std::is_same<R, double>::value) {
-    g.n = n;
-    return;
-  }
-  const int nx = T.nx;
-  const uint16_t* __restrict__ sh = T.shift + (size_t)n * nx;
-#pragma unroll
-  for (int q = 0; q < kPts; ++q) {
-    const int i = threadIdx.x + q * kSliceThreads;
-    if constexpr (!std::is_same<R, double>::value) {
-      if (i < nx) {
-        g.base[q] = i + (int)__ldg(sh + i);
-        g.eps[q] = __ldg(T.eps32 + (size_t)n * nx + i);
-      }
-    }
-  }
+  if constexpr (std::is_same<R, double>::value) g.n = n;
+  (void)T;
 }
 
-// dst[i] = sum_a w_a(eps_i) src[(i + shift_i + a) mod nx]  -- the SL gather (Sec. 2.1).
-template <int P, typename R>
-__device__ __forceinline__ void apply_gather(const GatherRegs<P, R>& g, const LevelTables& T, const R* __restrict__ src,
-                                             R* __restrict__ dst) {
+// dst[i] = sum_a w_a(eps_i) src[(i + shift_i + a) mod nx]  -- the SL gather (Sec. 2.1), FP64 weights
+// from the w64 table.
+template <int P>
+__device__ __forceinline__ void apply_gather(const GatherRegs<P, double>& g, const LevelTables& T,
+                                             const double* __restrict__ src, double* __restrict__ dst) {
   const int nx = T.nx;
 #pragma unroll 2
   for (int q = 0; q < kPts; ++q) {
     const int i = threadIdx.x + q * kSliceThreads;
     if (i < nx) {
-      R w[P + 1];
-      int b;
-      if constexpr (std::is_same<R, double>::value) {
-        const double* __restrict__ wr = T.w64 + (size_t)g.n * (P + 1) * nx + i;
+      double w[P + 1];
+      const double* __restrict__ wr = T.w64 + (size_t)g.n * (P + 1) * nx + i;
 #pragma unroll
-        for (int a = 0; a <= P; ++a) w[a] = __ldg(wr + (size_t)a * nx);
-        b = i + (int)__ldg(T.shift + (size_t)g.n * nx + i);
-      } else {
-        lagrange_weights<P, float>(g.eps[q], w);
-        b = g.base[q];
-      }
-      R acc = w[0] * src[wrap_pow2(b, nx)];
+      for (int a = 0; a <= P; ++a) w[a] = __ldg(wr + (size_t)a * nx);
+      const int b = i + (int)__ldg(T.shift + (size_t)g.n * nx + i);
+      double acc = w[0] * src[wrap_pow2(b, nx)];
+#pragma unroll
+      for (int a = 1; a <= P; ++a) acc += w[a] * src[wrap_pow2(b + a, nx)];
+      dst[i] = acc;
+    }
+  }
+}
+
+// The same gather in FP32 with the step's eps / shift rows in shared memory; the weights are formed
+// from eps in registers.
+template <int P>
+__device__ __forceinline__ void apply_gather_staged(const float* __restrict__ eps, const uint16_t* __restrict__ sh,
+                                                    const float* __restrict__ src, float* __restrict__ dst, int nx) {
+#pragma unroll 2
+  for (int q = 0; q < kPts; ++q) {
+    const int i = threadIdx.x + q * kSliceThreads;
+    if (i < nx) {
+      float w[P + 1];
+      lagrange_weights<P, float>(eps[i], w);
+      const int b = i + (int)sh[i];
+      float acc = w[0] * src[wrap_pow2(b, nx)];
 #pragma unroll
       for (int a = 1; a <= P; ++a) acc += w[a] * src[wrap_pow2(b + a, nx)];
       dst[i] = acc;
@@ -81,21 +79,6 @@ __device__ __forceinline__ void apply_gather(const GatherRegs<P, R>& g, const Le
 }
 
 // ---- correction solve x <- M^{-1} x, M = I - diag(sigma) D_{2B} (layout: solver_layout.cuh) ----------
-
-template <int B, typename R>
-struct SolverRegs {
-  R lu[kPartRows - B][2 * B + 1];
-};
-
-template <int B, typename R>
-__device__ __forceinline__ void load_solver(SolverRegs<B, R>& s, const R* __restrict__ data, int P) {
-  const int k = threadIdx.x;
-  if (k >= P) return;
-#pragma unroll
-  for (int r = 0; r < kPartRows - B; ++r)
-#pragma unroll
-    for (int f = 0; f <= 2 * B; ++f) s.lu[r][f] = __ldg(data + (size_t)rec_lu(B, r, f) * P + k);
-}
 
 // The 8 values of one partition (8-aligned) in shared memory, moved as vectors (fewer bank conflicts).
 template <typename R>
@@ -127,8 +110,8 @@ __device__ __forceinline__ void store_part(R* p, const R (&v)[kPartRows]) {
 // pcr_src: the coefficient block [pcr_off, total) of this step, either in global memory (data +
 // pcr_off) or staged in shared memory.
 template <int B, typename R>
-__device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xch, const SolverRegs<B, R>& sr,
-                                           const R* __restrict__ data, const R* pcr_src, int nx) {
+__device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xch, const R* __restrict__ data,
+                                           const R* pcr_src, int nx) {
   constexpr int Q = kPartRows - B;
   constexpr int BB = B * B;
   const SolverGeom G = solver_geom(nx, 2 * B - 1);
@@ -148,11 +131,7 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
       ct[e] = __ldg(data + (size_t)rec_ct(B, Q, 0, e) * P + k);
       ch[e] = __ldg(data + (size_t)rec_ch(B, Q, 0, e) * P + k);
     }
-    // FP32 reads the factor record from registers loaded before the gather; FP64 reads it here
-    auto LU = [&](int r, int f) -> R {
-      if constexpr (std::is_same<R, float>::value) return sr.lu[r][f];
-      else return __ldg(data + (size_t)rec_lu(B, r, f) * P + k);
-    };
+    auto LU = [&](int r, int f) -> R { return __ldg(data + (size_t)rec_lu(B, r, f) * P + k); };
 #pragma unroll
     for (int r = 0; r < Q; ++r) y[r] = xp[B + r];
 #pragma unroll
@@ -257,6 +236,279 @@ __device__ __forceinline__ void corr_solve(R* __restrict__ x, R* __restrict__ xc
   __syncthreads();
 }
 
+// ---- on-the-fly correction solve (FP32 coarse levels) ---------------------------------------------
+//
+// x <- M^{-1} x for M = I - diag(sigma) D_{2B}, factorised in every application from the sigma row:
+// the same partitioned algorithm as the stored factorisation (solver_layout.cuh: 8-row partitions,
+// interior banded LU, spikes, separator Schur blocks, block PCR), with the PCR reducing the matrix
+// blocks in lockstep with the right-hand side.  Reads 4 bytes (sigma) per row instead of the stored
+// record; all arithmetic FP32.  X: shared exchange area of (3 B^2 + B) * P floats.
+
+// Coefficient of the centred stencil (delta^2)^B at offset o: (-1)^{B+o} C(2B, B+o).
+template <int B>
+constexpr float dcoef(int o) {
+  int c = 1;
+  for (int t = 1; t <= B + o; ++t) c = c * (2 * B - (B + o) + t) / t;
+  return (o < -B || o > B) ? 0.f : (((B + o) & 1) ? -(float)c : (float)c);
+}
+
+template <int B>
+__device__ __forceinline__ void inv_small(const float (&A)[B * B], float (&R)[B * B]) {
+  if constexpr (B == 1) {
+    R[0] = 1.f / A[0];
+  } else if constexpr (B == 2) {
+    const float id = 1.f / (A[0] * A[3] - A[1] * A[2]);
+    R[0] = A[3] * id;
+    R[1] = -A[1] * id;
+    R[2] = -A[2] * id;
+    R[3] = A[0] * id;
+  } else {  // adjugate / determinant
+    const float c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    const float id = 1.f / (A[0] * c00 + A[1] * c01 + A[2] * c02);
+    R[0] = c00 * id;
+    R[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    R[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    R[3] = c01 * id;
+    R[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    R[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    R[6] = c02 * id;
+    R[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    R[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+  }
+}
+
+// C = A * B (B x B, row-major); acc: C += A * B.
+template <int B>
+__device__ __forceinline__ void mm_small(const float (&A)[B * B], const float (&Bm)[B * B], float (&C)[B * B]) {
+#pragma unroll
+  for (int a = 0; a < B; ++a)
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      float v = 0.f;
+#pragma unroll
+      for (int e = 0; e < B; ++e) v += A[a * B + e] * Bm[e * B + c];
+      C[a * B + c] = v;
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void corr_solve_otf(float* __restrict__ x, const float* __restrict__ sig,
+                                               float* __restrict__ X, int nx) {
+  constexpr int Q = kPartRows - B, BB = B * B;
+  const int P = nx / kPartRows;
+  int T = 0;
+  while ((1 << T) < P) ++T;
+  const int k = threadIdx.x;
+  const bool act = k < P;
+  const int g0 = k * kPartRows;
+  float xp[kPartRows], sg[kPartRows];
+  float y[Q], V[Q][B], W[Q][B];
+  float Lk[BB], Dk[BB], Uk[BB], gk[B];
+  // M[g0 + rr, g0 + rr + o] for |o| <= B
+  auto M = [&](int rr, int o) -> float { return (o == 0 ? 1.f : 0.f) - sg[rr] * dcoef<B>(o); };
+  if (act) {
+    load_part<float>(x + g0, xp);
+    load_part<float>(sig + g0, sg);
+    // 1) banded LU of the interior rows g0 + B + r (no pivoting, as the stored factorisation)
+    float l[Q][B], U[Q][B + 1], piv[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      float a[2 * B + 1];
+#pragma unroll
+      for (int c = -B; c <= B; ++c) a[c + B] = (r + c >= 0 && r + c < Q) ? M(B + r, c) : 0.f;
+#pragma unroll
+      for (int t = B; t >= 1; --t) {
+        if (r - t < 0) continue;
+        const float lt = a[B - t] * piv[r - t];
+        l[r][t - 1] = lt;
+#pragma unroll
+        for (int c = 1; c <= B; ++c)
+          if (-t + c <= B) a[-t + c + B] -= lt * U[r - t][c];
+      }
+      piv[r] = 1.f / a[B];
+#pragma unroll
+      for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
+    }
+    auto solve = [&](float (&v)[Q]) {
+#pragma unroll
+      for (int r = 0; r < Q; ++r)
+#pragma unroll
+        for (int t = 1; t <= B; ++t)
+          if (r - t >= 0) v[r] -= l[r][t - 1] * v[r - t];
+#pragma unroll
+      for (int r = Q - 1; r >= 0; --r) {
+#pragma unroll
+        for (int t = 1; t <= B; ++t)
+          if (r + t < Q) v[r] -= U[r][t] * v[r + t];
+        v[r] *= piv[r];
+      }
+    };
+#pragma unroll
+    for (int r = 0; r < Q; ++r) y[r] = xp[B + r];
+    solve(y);
+    // 2) spikes V = A^{-1} M[I_k, S_k], W = A^{-1} M[I_k, S_{k+1}]
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      float v[Q], w[Q];
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        const int ov = c - B - r, ow = Q - r + c;
+        v[r] = ov >= -B ? M(B + r, ov) : 0.f;
+        w[r] = ow <= B ? M(B + r, ow) : 0.f;
+      }
+      solve(v);
+      solve(w);
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        V[r][c] = v[r];
+        W[r][c] = w[r];
+      }
+    }
+    // tails of V, W, y for partition k + 1
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        X[(size_t)(a * B + c) * P + k] = V[Q - B + a][c];
+        X[(size_t)(BB + a * B + c) * P + k] = W[Q - B + a][c];
+      }
+      X[(size_t)(2 * BB + a) * P + k] = y[Q - B + a];
+    }
+  }
+  __syncthreads();
+  if (act) {
+    // 3) separator row a: ctail (tail of I_{k-1}), Mss (S_k), chead (head of I_k); Schur blocks
+    const int km = (k + P - 1) & (P - 1);
+    float Vt[BB], Wt[BB], yt[B];
+#pragma unroll
+    for (int e = 0; e < BB; ++e) {
+      Vt[e] = X[(size_t)e * P + km];
+      Wt[e] = X[(size_t)(BB + e) * P + km];
+    }
+#pragma unroll
+    for (int a = 0; a < B; ++a) yt[a] = X[(size_t)(2 * BB + a) * P + km];
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      float g = xp[a];
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        float lv = 0.f, dv = M(a, c - a), uv = 0.f;
+#pragma unroll
+        for (int c2 = 0; c2 < B; ++c2) {
+          const float ct = c2 >= a ? M(a, c2 - B - a) : 0.f;
+          const float ch = c2 <= a ? M(a, B + c2 - a) : 0.f;
+          lv -= ct * Vt[c2 * B + c];
+          dv -= ct * Wt[c2 * B + c] + ch * V[c2][c];
+          uv -= ch * W[c2][c];
+        }
+        Lk[a * B + c] = lv;
+        Dk[a * B + c] = dv;
+        Uk[a * B + c] = uv;
+        const float ct = c >= a ? M(a, c - B - a) : 0.f;
+        const float ch = c <= a ? M(a, B + c - a) : 0.f;
+        g -= ct * yt[c] + ch * y[c];
+      }
+      gk[a] = g;
+    }
+  }
+  __syncthreads();
+  // 4) block PCR on (L, D, U | g); exchange per level: D^{-1}, L, U, g of every partition
+  for (int t = 0; t < T; ++t) {
+    const int d = 1 << t;
+    if (act) {
+      float Di[BB];
+      inv_small<B>(Dk, Di);
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        X[(size_t)e * P + k] = Di[e];
+        X[(size_t)(BB + e) * P + k] = Lk[e];
+        X[(size_t)(2 * BB + e) * P + k] = Uk[e];
+      }
+#pragma unroll
+      for (int a = 0; a < B; ++a) X[(size_t)(3 * BB + a) * P + k] = gk[a];
+    }
+    __syncthreads();
+    if (act) {
+      const int km = (k - d) & (P - 1), kp = (k + d) & (P - 1);
+      float Dm[BB], Dp[BB], al[BB], ga[BB], tmp[BB], tmp2[BB];
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        Dm[e] = X[(size_t)e * P + km];
+        Dp[e] = X[(size_t)e * P + kp];
+      }
+      mm_small<B>(Lk, Dm, al);
+      mm_small<B>(Uk, Dp, ga);
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        al[e] = -al[e];
+        ga[e] = -ga[e];
+      }
+#pragma unroll
+      for (int a = 0; a < B; ++a) {
+        float v = gk[a];
+#pragma unroll
+        for (int c = 0; c < B; ++c)
+          v += al[a * B + c] * X[(size_t)(3 * BB + c) * P + km] + ga[a * B + c] * X[(size_t)(3 * BB + c) * P + kp];
+        gk[a] = v;
+      }
+      // D += al U_{k-d} + ga L_{k+d};  L = al L_{k-d};  U = ga U_{k+d}
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        tmp[e] = X[(size_t)(2 * BB + e) * P + km];   // U_{k-d}
+        tmp2[e] = X[(size_t)(BB + e) * P + kp];      // L_{k+d}
+      }
+      float n1[BB], n2[BB];
+      mm_small<B>(al, tmp, n1);
+      mm_small<B>(ga, tmp2, n2);
+#pragma unroll
+      for (int e = 0; e < BB; ++e) Dk[e] += n1[e] + n2[e];
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        tmp[e] = X[(size_t)(BB + e) * P + km];       // L_{k-d}
+        tmp2[e] = X[(size_t)(2 * BB + e) * P + kp];  // U_{k+d}
+      }
+      mm_small<B>(al, tmp, Lk);
+      mm_small<B>(ga, tmp2, Uk);
+    }
+    __syncthreads();
+  }
+  // 5) separators x_S = (L + D + U)^{-1} g, then the interiors
+  float xs[B];
+  if (act) {
+    float F[BB], Fi[BB];
+#pragma unroll
+    for (int e = 0; e < BB; ++e) F[e] = Lk[e] + Dk[e] + Uk[e];
+    inv_small<B>(F, Fi);
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      float v = 0.f;
+#pragma unroll
+      for (int c = 0; c < B; ++c) v += Fi[a * B + c] * gk[c];
+      xs[a] = v;
+      X[(size_t)a * P + k] = v;
+    }
+  }
+  __syncthreads();
+  if (act) {
+    const int kp = (k + 1) & (P - 1);
+    float xn[B];
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      xn[a] = X[(size_t)a * P + kp];
+      xp[a] = xs[a];
+    }
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      float v = y[r];
+#pragma unroll
+      for (int c = 0; c < B; ++c) v -= V[r][c] * xs[c] + W[r][c] * xn[c];
+      xp[B + r] = v;
+    }
+    store_part<float>(x + g0, xp);
+  }
+  __syncthreads();
+}
+
 // dst = S^T src for table row `row` (FP64): target k sums, in increasing arrival index i, the weight
 // w_a(eps_i) src[i] of every arrival point i whose stencil node a lands on k.  The candidates form the
 // window i in [k + fmin + L - P, k + fmax + L] (fmin/fmax: range of floor(s) on this step), so the
@@ -283,89 +535,143 @@ __device__ __forceinline__ void apply_gather_T(const LevelTables& T, int row, co
   }
 }
 
-// Shared-memory staging of the reduction coefficients of one coarse step (FP32 levels).
+// FP32 levels stage each step's tables into shared memory: a double buffer of (eps row, shift row and,
+// for coarse levels factorised on the fly, sigma row), each buffer filled by TMA bulk copies that
+// complete on its mbarrier; then, on coarse levels, the exchange area of the on-the-fly solve.
+// Byte offsets from the 128-aligned start of the region: buffer b starts at b * per_buf with eps at +0,
+// shift at +e, sigma at +e+h; the two barriers at `bars`.
+struct StageLayout {
+  unsigned e, h, per_buf, bars, xch, total, tx;  // tx: bytes copied per step
+};
+MGRIT_HD StageLayout stage_layout(int nx, int p, int otf) {
+  StageLayout o;
+  o.e = ((unsigned)nx * 4u + 127u) & ~127u;
+  o.h = ((unsigned)nx * 2u + 127u) & ~127u;
+  o.per_buf = o.e + o.h + (otf ? o.e : 0u);
+  o.bars = 2 * o.per_buf;
+  o.xch = o.bars + 128;
+  const int B = (p + 1) / 2, P = nx / kPartRows;
+  o.total = o.xch + (otf ? (unsigned)((3 * B * B + B) * P * 4) : 0u);
+  o.tx = (unsigned)nx * (otf ? 10u : 6u);
+  return o;
+}
+
+// Per-CTA state of the table prefetch (scalars only, so it stays in registers): buffer `cur` holds (or
+// receives) the current step's rows; bit b of `phase` is the parity of buffer b's next completion.
 struct Stage {
-  void* buf;       // shared buffer of T.stage_bytes, or nullptr
-  uint64_t* bar;   // mbarrier completing the bulk copy
-  uint32_t phase;  // parity of the next completion
+  unsigned char* base;
+  StageLayout lay;
+  uint32_t phase;
+  int cur;
+  int pending;  // step row whose copy into buffer `cur` is in flight (-1: none)
+  MGRIT_D uint64_t* bar(int b) const { return reinterpret_cast<uint64_t*>(base + lay.bars) + b; }
+  MGRIT_D unsigned char* buf(int b) const { return base + (size_t)b * lay.per_buf; }
+  MGRIT_D const float* eps(int b) const { return reinterpret_cast<const float*>(buf(b)); }
+  MGRIT_D const uint16_t* sh(int b) const { return reinterpret_cast<const uint16_t*>(buf(b) + lay.e); }
+  MGRIT_D const float* sig(int b) const { return reinterpret_cast<const float*>(buf(b) + lay.e + lay.h); }
+  MGRIT_D float* xch() const { return reinterpret_cast<float*>(base + lay.xch); }
 };
 
+// Carves the region out of dynamic shared memory after `used` bytes and initialises the barriers
+// (all threads must call; includes a barrier).  Inactive (base null) unless T.gather_stage.
+__device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, const LevelTables& T, bool coarse) {
+  Stage s;
+  s.base = nullptr;
+  s.phase = 0;
+  s.cur = 0;
+  s.pending = -1;
+  if (!T.gather_stage) return s;
+  s.lay = stage_layout(T.nx, T.p, coarse && T.otf);
+  s.base = smem + ((used + 127) & ~(size_t)127);
+  if (threadIdx.x == 0) {
+    mbar_init(s.bar(0), 1);
+    mbar_init(s.bar(1), 1);
+  }
+  __syncthreads();
+  return s;
+}
+
+// Thread 0: bulk copies of the rows of step `row` into buffer b (all complete on bar(b)).
+__device__ __forceinline__ void stage_issue(const Stage& s, const LevelTables& T, int row, int b, bool otf) {
+  const unsigned nx = (unsigned)T.nx;
+  unsigned char* d = s.buf(b);
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(s.bar(b), s.lay.tx);
+  bulk_copy_g2s(d, T.eps32 + (size_t)row * T.table_stride, nx * 4u, s.bar(b));
+  bulk_copy_g2s(d + s.lay.e, T.shift + (size_t)row * T.table_stride, nx * 2u, s.bar(b));
+  if (otf)
+    bulk_copy_g2s(d + s.lay.e + s.lay.h, (const float*)T.solver + (size_t)row * T.solver_stride, nx * 4u, s.bar(b));
+}
+
+// Waits for buffer `cur` (issuing it first if it was not prefetched) after issuing the next step's
+// copies; false if the bounded wait gave up (T.err set; copies in flight have landed or timed out).
+__device__ __forceinline__ bool stage_acquire(Stage& s, const LevelTables& T, int n, int next_n, bool otf) {
+  const int b = s.cur;
+  if (threadIdx.x == 0) {
+    if (s.pending != n) stage_issue(s, T, n, b, otf);
+    if (next_n >= 0) stage_issue(s, T, next_n, b ^ 1, otf);
+  }
+  const uint32_t par = (s.phase >> b) & 1u;
+  const bool ok = mbar_wait_bounded(s.bar(b), par, kWaitLimitCycles);
+  s.phase ^= 1u << b;
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicExch(T.err, 1);
+      mbar_wait_bounded(s.bar(b), par, kWaitLimitCycles);
+      if (next_n >= 0) mbar_wait_bounded(s.bar(b ^ 1), (s.phase >> (b ^ 1)) & 1u, kWaitLimitCycles);
+    }
+    return false;
+  }
+  return true;
+}
+
 // One full step src -> dst (Phi, or Psi with the correction solve), given the prefetched gather table.
+// next_n: the step this CTA takes after this one (-1: none), whose sigma row is prefetched.
 // Returns false if a bounded wait gave up (the caller then stops; the flag T.err is set).
 template <int P, typename R, bool COARSE, bool TRANS = false>
 __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R* dst, const LevelTables& T, int n,
-                                          Stage& stg) {
+                                          Stage& stg, int next_n) {
   constexpr int B = (P + 1) / 2;
   if constexpr (TRANS) {  // Phi^T (FP64): coarse levels first solve with M^T in place, then S^T
     const int row = T.reverse ? T.nt - 1 - n : n;
     if constexpr (COARSE) {
       const double* data = (const double*)T.solver + (size_t)row * T.solver_stride;
       const SolverGeom G = solver_geom(T.nx, T.p);
-      SolverRegs<B, double> sr;
-      corr_solve<B, double>((double*)src, (double*)dst, sr, data, data + G.pcr_off, T.nx);
+      corr_solve<B, double>((double*)src, (double*)dst, data, data + G.pcr_off, T.nx);
     }
     apply_gather_T<P>(T, row, (const double*)src, (double*)dst);
     __syncthreads();
     (void)gr;
     (void)stg;
+    (void)next_n;
     return true;
   }
-  SolverRegs<B, R> sr;
-  const R* data = COARSE ? (const R*)T.solver + (size_t)n * T.solver_stride : nullptr;
-  const R* pcr_src = nullptr;
-  if constexpr (COARSE) {
-    const SolverGeom G = solver_geom(T.nx, T.p);
-    pcr_src = data + G.pcr_off;
-    if (stg.buf && threadIdx.x == 0) {  // TMA: stage this step's reduction coefficients
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(stg.bar, T.stage_bytes);
-      bulk_copy_g2s(stg.buf, pcr_src, T.stage_bytes, stg.bar);
+  if constexpr (std::is_same<R, float>::value) {  // tables staged by TMA; coarse: factorised on the fly
+    constexpr bool otf = COARSE;
+    if (!stage_acquire(stg, T, n, next_n, otf)) return false;
+    const int b = stg.cur;
+    apply_gather_staged<P>(stg.eps(b), stg.sh(b), (const float*)src, (float*)dst, T.nx);
+    __syncthreads();
+    if constexpr (COARSE) corr_solve_otf<B>((float*)dst, stg.sig(b), stg.xch(), T.nx);
+    stg.cur ^= 1;
+    stg.pending = next_n;
+    (void)gr;
+    return true;
+  } else {
+    (void)stg;
+    (void)next_n;
+    apply_gather<P>(gr, T, src, dst);
+    __syncthreads();
+    if constexpr (COARSE) {
+      const R* data = (const R*)T.solver + (size_t)n * T.solver_stride;
+      const SolverGeom G = solver_geom(T.nx, T.p);
+      corr_solve<B, R>(dst, src, data, data + G.pcr_off, T.nx);
     }
+    return true;
   }
-  // FP32: issue the loads of the factor record before the gather so their latency overlaps it;
-  // FP64: they are read inside the solve (register pressure).
-  constexpr bool kEarly = std::is_same<R, float>::value;
-  if constexpr (COARSE && kEarly) load_solver<B, R>(sr, data, T.nx / kPartRows);
-  apply_gather<P, R>(gr, T, src, dst);
-  __syncthreads();
-  if constexpr (COARSE) {
-    if (stg.buf) {
-      const bool ok = mbar_wait_bounded(stg.bar, stg.phase, kWaitLimitCycles);
-      stg.phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) {
-          atomicExch(T.err, 1);
-          mbar_wait_bounded(stg.bar, stg.phase ^ 1u, kWaitLimitCycles);  // let the copy in flight land
-        }
-        return false;
-      }
-      pcr_src = (const R*)stg.buf;
-    }
-    corr_solve<B, R>(dst, src, sr, data, pcr_src, T.nx);
-  }
-  return true;
 }
 
-// Carves the staging buffer and its barrier out of dynamic shared memory after `used` bytes and
-// initialises the barrier (all threads must call; includes a barrier).
-__device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, unsigned bytes) {
-  Stage s;
-  s.phase = 0;
-  if (bytes == 0) {
-    s.buf = nullptr;
-    s.bar = nullptr;
-    return s;
-  }
-  const size_t off = (used + 127) & ~(size_t)127;
-  s.buf = smem + off;
-  s.bar = reinterpret_cast<uint64_t*>(smem + off + ((bytes + 127) & ~127u));
-  if (threadIdx.x == 0) mbar_init(s.bar, 1);
-  __syncthreads();
-  return s;
-}
-
-
-// Fine-level kernels keep three CTAs per SM resident (register cap 42) to hide gather latency.
+// Fine-level kernels keep two (FP32: shared memory of the staged tables) or three (FP64) CTAs per SM.
 // The pass of interval j (one CTA); also the body of the batched kernel.
 template <int P, typename R, bool COARSE, bool TRANS>
 __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs& a, int j, int buf,
@@ -374,7 +680,7 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
   R* dst = src + buf;
   double* red = reinterpret_cast<double*>(dst + buf);
   const int nx = T.nx;
-  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), COARSE ? T.stage_bytes : 0u);
+  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), T, COARSE);
   {
     const R* st = a.start ? (const R*)a.start + (size_t)j * a.start_stride : nullptr;
     const R* co = a.corr ? (const R*)a.corr + (size_t)j * a.corr_stride : nullptr;
@@ -414,7 +720,7 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
         }
       }
     }
-    if (!full_step<P, R, COARSE, TRANS>(gcur, src, dst, T, n, stg)) return;
+    if (!full_step<P, R, COARSE, TRANS>(gcur, src, dst, T, n, stg, k + 1 < a.nsteps ? n + 1 : -1)) return;
     const bool last = (k == a.m - 1);
     if (!last) {
       R* fs = a.fstore ? (R*)a.fstore + (size_t)(n + 1) * nx : nullptr;
@@ -460,7 +766,8 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
 }
 
 template <int P, typename R, bool COARSE, bool TRANS>
-__global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : 3) k_relax_1d(LevelTables T, RelaxArgs a, int buf) {
+__global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : (std::is_same<R, float>::value ? 2 : 3))
+    k_relax_1d(LevelTables T, RelaxArgs a, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   relax_body<P, R, COARSE, TRANS>(T, a, blockIdx.x, buf, smem_raw);
 }
@@ -472,7 +779,7 @@ __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, con
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
   const int nx = T.nx;
-  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), COARSE ? T.stage_bytes : 0u);
+  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), T, COARSE);
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const R v = u0 ? u0[i] : (R)0;
     src[i] = v;
@@ -489,7 +796,7 @@ __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, con
     } else {
       load_gather<P, R>(gcur, T, n);
     }
-    if (!full_step<P, R, COARSE, TRANS>(gcur, src, dst, T, n, stg)) return;
+    if (!full_step<P, R, COARSE, TRANS>(gcur, src, dst, T, n, stg, n + 1 < N ? n + 1 : -1)) return;
     const R* gr = g ? g + (size_t)(n + 1) * nx : nullptr;
     R* out = store_all ? out_all + (size_t)(n + 1) * nx : (n == N - 1 ? out_all : nullptr);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -554,35 +861,36 @@ __global__ void __launch_bounds__(kSliceThreads) k_apply_1d(LevelTables T, int n
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
   const int nx = T.nx, c = blockIdx.x;
-  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), COARSE ? T.stage_bytes : 0u);
+  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), T, COARSE);
   for (int i = threadIdx.x; i < nx; i += blockDim.x) src[i] = in[(size_t)c * nx + i];
   __syncthreads();
   GatherRegs<P, R> gr;
   load_gather<P, R>(gr, T, n0 + c);
-  if (!full_step<P, R, COARSE, TRANS>(gr, src, dst, T, n0 + c, stg)) return;
+  if (!full_step<P, R, COARSE, TRANS>(gr, src, dst, T, n0 + c, stg, -1)) return;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) out[(size_t)c * nx + i] = dst[i];
 }
 
 int buffer_elems(const LevelTables& T, bool coarse) {
   int e = T.nx;
-  if (coarse) {
+  if (coarse && !T.otf) {  // the stored-factor solve uses the consumed gather source as exchange area
     const int need = 4 * (T.nx / kPartRows) * ((T.p + 1) / 2);
     if (need > e) e = need;
   }
   return (e + 31) & ~31;
 }
 
+// Shared bytes for slice buffers of `buf` elements of type R plus the coarse region of T.
 template <typename R>
-size_t smem_bytes(int buf, unsigned stage) {
+size_t smem_bytes(int buf, const LevelTables& T, bool coarse) {
   size_t b = 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double);
-  if (stage) b = ((b + 127) & ~(size_t)127) + ((stage + 127) & ~127u) + 16;
+  if (T.gather_stage) b = ((b + 127) & ~(size_t)127) + stage_layout(T.nx, T.p, coarse && T.otf).total;
   return b;
 }
 
 template <typename R, bool COARSE, bool TR>
 cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
-  const size_t sm = smem_bytes<R>(buf, COARSE ? T.stage_bytes : 0u);
+  const size_t sm = smem_bytes<R>(buf, T, COARSE);
   const int grid = a.J + (a.extra_cta ? 1 : 0);
   if (grid <= 0) return cudaSuccess;
 #define MGRIT_LAUNCH_RELAX(PP)                                                                             \
@@ -603,7 +911,7 @@ template <typename R, bool COARSE, bool TR>
 cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, const void* u0, void* u, int store_all,
                                 cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
-  const size_t sm = smem_bytes<R>(buf, COARSE ? T.stage_bytes : 0u);
+  const size_t sm = smem_bytes<R>(buf, T, COARSE);
 #define MGRIT_LAUNCH_SEQ(PP)                                                                               \
   {                                                                                                        \
     auto kern = k_sequential_1d<PP, R, COARSE, TR>;                                                            \
@@ -621,7 +929,7 @@ cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, cons
 template <typename R, bool COARSE, bool TR>
 cudaError_t apply_dispatch(const LevelTables& T, int n0, int count, const void* in, void* out, cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
-  const size_t sm = smem_bytes<R>(buf, COARSE ? T.stage_bytes : 0u);
+  const size_t sm = smem_bytes<R>(buf, T, COARSE);
 #define MGRIT_LAUNCH_APPLY(PP)                                                                             \
   {                                                                                                        \
     auto kern = k_apply_1d<PP, R, COARSE, TR>;                                                                 \
@@ -668,7 +976,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_gradient_a_1d(LevelTables T, 
     }
     GatherRegs<P, double> gr;
     load_gather<P, double>(gr, T, n);
-    apply_gather<P, double>(gr, T, u, v);
+    apply_gather<P>(gr, T, u, v);
     __syncthreads();
     double* t = u;
     u = v;
@@ -771,11 +1079,12 @@ __global__ void k_sum_batched(const Segment* __restrict__ seg) {
 
 }  // namespace
 
-void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem) {
+void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem, size_t* region) {
   const bool coarse = T.solver != nullptr;
   const int b = buffer_elems(T, coarse);
   *buf = b;
-  *smem = is_double ? smem_bytes<double>(b, coarse ? T.stage_bytes : 0u) : smem_bytes<float>(b, coarse ? T.stage_bytes : 0u);
+  *smem = is_double ? smem_bytes<double>(b, T, coarse) : smem_bytes<float>(b, T, coarse);
+  *region = T.gather_stage ? stage_layout(T.nx, T.p, coarse && T.otf).total : 0;
 }
 
 cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles,

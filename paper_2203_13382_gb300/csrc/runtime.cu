@@ -45,7 +45,8 @@ struct Level {
   uint16_t* shift = nullptr;
   double* w64 = nullptr;
   float* eps32 = nullptr;
-  void* solver = nullptr;
+  void* solver = nullptr;   // stored factorisation (FP64 coarse levels)
+  float* sig32 = nullptr;   // sigma as FP32 rows (FP32 coarse levels, factorised on the fly)
   size_t solver_stride = 0;
   int P = 0;
   int is_double = 1;  // arithmetic of this level's cycle
@@ -176,7 +177,8 @@ struct mgrit_handle {
     T.solver_stride = L.solver_stride;
     T.s64 = L.s64;
     T.err = err_dev;
-    T.stage_bytes = 0;
+    T.otf = 0;
+    T.gather_stage = 0;
     T.trans = 0;
     T.reverse = 0;
     T.frange = L.frange;
@@ -188,15 +190,13 @@ struct mgrit_handle {
       if (T.solver && grid.dim == 1) T.solver = L.solverT;  // 2D: GMRES with M^T on the same sigma
       return T;
     }
-    if (T.solver && !is_double && grid.dim == 1) {
-      // TMA staging of the reduction coefficients: needs P = nx/8 >= 4 (16-byte alignment of every
-      // step's block and of its size) and room in shared memory next to the two slice buffers.
-      const int P = grid.nx / 8, B = (order + 1) / 2;
-      int T_ = 0;
-      while ((1 << T_) < P) ++T_;
-      const size_t bytes = (size_t)(T_ * 2 * B * B + B * B) * P * sizeof(float);
-      const size_t slices = 2 * (size_t)std::max(grid.nx, 4 * P * B) * sizeof(float) + 64 * sizeof(double);
-      if (P >= 4 && bytes % 16 == 0 && slices + bytes + 512 <= 220 * 1024) T.stage_bytes = (unsigned)bytes;
+    if (grid.dim == 1 && !is_double) {
+      T.gather_stage = 1;  // TMA bulk copies of each step's eps32 / shift rows into shared memory
+      if (l > 0 && opt.coarse_op == 0) {  // coarse: factorised on the fly from sigma (also staged)
+        T.otf = 1;
+        T.solver = L.sig32;
+        T.solver_stride = (size_t)grid.nx;
+      }
     }
     return T;
   }
@@ -416,9 +416,13 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
       if ((st = h->alloc((char**)&L.G, full * esz)) != MGRIT_OK) return cleanup_fail(st);
       if (opt.coarse_op == 0 && dim == 1) {
         L.P = nx / 8;
-        L.solver_stride = solver_reals(nx, p);
-        const size_t tot = L.solver_stride * L.nt * (L.is_double ? sizeof(double) : sizeof(float));
-        if ((st = h->alloc((char**)&L.solver, tot)) != MGRIT_OK) return cleanup_fail(st);
+        if (L.is_double) {
+          L.solver_stride = solver_reals(nx, p);
+          const size_t tot = L.solver_stride * L.nt * sizeof(double);
+          if ((st = h->alloc((char**)&L.solver, tot)) != MGRIT_OK) return cleanup_fail(st);
+        } else if ((st = h->alloc(&L.sig32, (size_t)L.nt * nx)) != MGRIT_OK) {
+          return cleanup_fail(st);
+        }
       }
     }
   }
@@ -503,6 +507,11 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
       const int ev = h->phase_begin();
       const int nl = launch_factor_1d(L.sigma, L.nt, nx, p, L.solver, L.is_double, h->flag_dev, s);
       h->phase_end(MGRIT_PHASE_FACTOR, ev, nl);
+    }
+    if (l > 0 && L.sig32) {
+      const int ev = h->phase_begin();
+      launch_axpy_convert(1, L.sigma, L.sig32, nullptr, (long long)L.nt * nx, s);
+      h->phase_end(MGRIT_PHASE_FACTOR, ev, 1);
     }
     if ((st = cuda_fail("setup")) != MGRIT_OK) return st;
   }
@@ -977,6 +986,7 @@ struct mgrit_batch {
     int tile_off, ntiles;
     int buf;
     size_t smem;
+    size_t region;  // coarse shared region (on-the-fly solve) after the slice buffers
   };
   std::vector<Phase> down, up;
   Phase final_post{};
@@ -1009,11 +1019,17 @@ struct mgrit_batch {
 
 namespace {
 
+size_t batched_smem(int buf, int is_double, size_t region) {
+  size_t b = 2 * (size_t)buf * (is_double ? 8 : 4) + 64 * sizeof(double);
+  if (region) b = ((b + 127) & ~(size_t)127) + region;
+  return b;
+}
+
 // Appends a phase of relax tiles; per problem q: J tiles (plus one if extra) using tabs[tab_of(q)] and
 // args[args_of(q)].
 template <class F>
 mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F per_problem) {
-  mgrit_batch::Phase ph{0, is_double, coarse, (int)b->tiles.size(), 0, 0, 0};
+  mgrit_batch::Phase ph{0, is_double, coarse, (int)b->tiles.size(), 0, 0, 0, 0};
   for (int q = 0; q < (int)b->hs.size(); ++q) {
     LevelTables T;
     RelaxArgs a;
@@ -1023,24 +1039,15 @@ mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F 
     b->tabs.push_back(T);
     b->args.push_back(a);
     int buf;
-    size_t smem;
-    relax_smem_need(T, is_double, &buf, &smem);
+    size_t smem, region;
+    relax_smem_need(T, is_double, &buf, &smem, &region);
     ph.buf = std::max(ph.buf, buf);
-    ph.smem = std::max(ph.smem, smem);
+    ph.region = std::max(ph.region, region);
     for (int j = 0; j < ntile; ++j) b->tiles.push_back(BatchTile{ti, ai, j, q});
   }
   ph.ntiles = (int)b->tiles.size() - ph.tile_off;
-  // a common buffer length for every tile: recompute the shared size with the largest buffer
-  ph.smem = std::max(ph.smem, (size_t)2 * ph.buf * (is_double ? 8 : 4) + 64 * sizeof(double));
-  if (coarse) {
-    unsigned stage = 0;
-    for (int t = ph.tile_off; t < (int)b->tiles.size(); ++t) stage = std::max(stage, b->tabs[b->tiles[t].table].stage_bytes);
-    if (stage) {
-      size_t base = 2 * (size_t)ph.buf * (is_double ? 8 : 4) + 64 * sizeof(double);
-      base = (base + 127) & ~(size_t)127;
-      ph.smem = std::max(ph.smem, base + ((stage + 127) & ~127u) + 16);
-    }
-  }
+  // a common buffer length for every tile, then the largest coarse region after it
+  ph.smem = batched_smem(ph.buf, is_double, ph.region);
   return ph;
 }
 
@@ -1116,7 +1123,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
         return true;
       }));
     // coarsest levels reached at this depth: sequential solves
-    mgrit_batch::Phase ph{1, 0, 1, (int)b->tiles.size(), 0, 0, 0};
+    mgrit_batch::Phase ph{1, 0, 1, (int)b->tiles.size(), 0, 0, 0, 0};
     for (int q = 0; q < nprob; ++q) {
       mgrit_handle* h = b->hs[q];
       if ((int)h->levels.size() - 1 != d) continue;
@@ -1127,13 +1134,14 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
       b->tabs.push_back(T);
       b->seqs.push_back(sa);
       int buf;
-      size_t smem;
-      relax_smem_need(T, 0, &buf, &smem);
+      size_t smem, region;
+      relax_smem_need(T, 0, &buf, &smem, &region);
       ph.buf = std::max(ph.buf, buf);
-      ph.smem = std::max(ph.smem, smem);
+      ph.region = std::max(ph.region, region);
       b->tiles.push_back(BatchTile{ti, ai, 0, q});
     }
     ph.ntiles = (int)b->tiles.size() - ph.tile_off;
+    ph.smem = batched_smem(ph.buf, 0, ph.region);
     if (ph.ntiles) b->down.push_back(ph);
   }
   for (int d = maxL - 2; d >= 1; --d)

@@ -79,6 +79,21 @@ def test_single_steps_match_oracle(case):
             assert rel(y, ref) < 1e-12, (l, n, rel(y, ref))
 
 
+@pytest.mark.parametrize("case", CASES)
+def test_single_steps_fp32_match_oracle(case):
+    """FP32 levels: the gather and the correction matrix factorised on the fly from sigma (FP32)."""
+    H = oracle_hierarchy(*case)
+    h = gpu_handle(*case, precision=1)
+    rng = np.random.default_rng(12)
+    for l in range(H.nlevels):
+        nt_l = H.levels[l].nt
+        for n in sorted(set([0, nt_l // 3, nt_l - 1])):
+            x = rng.standard_normal(case[0])
+            y = h.apply_step(l, n, torch.from_numpy(x[None, :].copy()).cuda()).cpu().numpy()[0]
+            ref = H.step(l, n, x)
+            assert rel(y, ref) < 2e-6, (l, n, rel(y, ref))
+
+
 @pytest.mark.parametrize("case", CASES[:4])
 def test_sequential_matches_oracle(case):
     H = oracle_hierarchy(*case)
