@@ -267,8 +267,9 @@ def run_ours(args) -> None:
         if dist is not None:
             dist.barrier()
 
+    ev = 0 if args.no_phase_events else 1  # per-phase CUDA events inside the timed steps
     for _ in range(args.warmup):
-        one_step(1)
+        one_step(ev)
     barrier()
     torch.cuda.synchronize()
     props = torch.cuda.get_device_properties(local_rank)
@@ -282,9 +283,13 @@ def run_ours(args) -> None:
     e0.record(stream)
     stats = []
     for _ in range(args.steps):
-        stats.append(one_step(1))
+        stats.append(one_step(ev))
     e1.record(stream)
     torch.cuda.synchronize()
+    if not ev:  # phase times from one extra step with events (outside the timed region)
+        prof = one_step(1)
+        for st in stats:
+            st["phase_ms"] = prof["phase_ms"]
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
@@ -395,6 +400,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the sequential comparator and e2e runs")
     ap.add_argument("--nt", type=int, default=0, help="override nt (small profiling cases only)")
+    ap.add_argument("--no-phase-events", action="store_true",
+                    help="time the steps without per-phase events (phase table from one extra step)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -113,6 +113,7 @@ struct RelaxArgs {
   void* cout;          // MODE_FC output (stride c_stride)
   const void* cin;     // MODE_RES: current C value (stride c_stride)
   void* rout;          // MODE_RES: residual output (stride r_stride)
+  float* rout32;       // MODE_RES, FP64 passes: optional FP32 copy of the residual (stride r_stride)
   long long c_stride;
   long long r_stride;
   int g_at_c;          // MODE_RES: add g at the C-point

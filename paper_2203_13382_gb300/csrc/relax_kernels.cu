@@ -17,6 +17,15 @@ namespace {
 
 // ---- gather tables of one step, loaded into registers ahead of use (software pipelining) ----------
 constexpr int kPts = 8;  // points per thread: nx <= kPts * kSliceThreads = 4096
+constexpr int kMaxNx = kPts * kSliceThreads;
+
+// Threads of the slice-resident kernels (one CTA per interval).  Measured on the 4096-point coarse
+// levels: 512 threads at one CTA per SM beat 256 threads at two (longer per-thread gathers and
+// register spills of the on-the-fly solve outweigh the second CTA).
+template <int P, typename R, bool COARSE>
+constexpr int slice_threads() {
+  return kSliceThreads;
+}
 
 template <int P, typename R>
 struct GatherRegs;
@@ -60,12 +69,12 @@ __device__ __forceinline__ void apply_gather(const GatherRegs<P, double>& g, con
 
 // The same gather in FP32 with the step's eps / shift rows in shared memory; the weights are formed
 // from eps in registers.
-template <int P>
+template <int P, int NT>
 __device__ __forceinline__ void apply_gather_staged(const float* __restrict__ eps, const uint16_t* __restrict__ sh,
                                                     const float* __restrict__ src, float* __restrict__ dst, int nx) {
 #pragma unroll 2
-  for (int q = 0; q < kPts; ++q) {
-    const int i = threadIdx.x + q * kSliceThreads;
+  for (int q = 0; q < kMaxNx / NT; ++q) {
+    const int i = threadIdx.x + q * NT;
     if (i < nx) {
       float w[P + 1];
       lagrange_weights<P, float>(eps[i], w);
@@ -291,24 +300,27 @@ __device__ __forceinline__ void mm_small(const float (&A)[B * B], const float (&
     }
 }
 
-template <int B>
+template <int B, int PR>
 __device__ __forceinline__ void corr_solve_otf(float* __restrict__ x, const float* __restrict__ sig,
                                                float* __restrict__ X, int nx) {
-  constexpr int Q = kPartRows - B, BB = B * B;
-  const int P = nx / kPartRows;
+  constexpr int Q = PR - B, BB = B * B;
+  const int P = nx / PR;
   int T = 0;
   while ((1 << T) < P) ++T;
   const int k = threadIdx.x;
   const bool act = k < P;
-  const int g0 = k * kPartRows;
-  float xp[kPartRows], sg[kPartRows];
+  const int g0 = k * PR;
+  float xp[PR], sg[PR];
   float y[Q], V[Q][B], W[Q][B];
   float Lk[BB], Dk[BB], Uk[BB], gk[B];
   // M[g0 + rr, g0 + rr + o] for |o| <= B
   auto M = [&](int rr, int o) -> float { return (o == 0 ? 1.f : 0.f) - sg[rr] * dcoef<B>(o); };
   if (act) {
-    load_part<float>(x + g0, xp);
-    load_part<float>(sig + g0, sg);
+#pragma unroll
+    for (int c = 0; c < PR / kPartRows; ++c) {
+      load_part<float>(x + g0 + c * kPartRows, *reinterpret_cast<float(*)[kPartRows]>(xp + c * kPartRows));
+      load_part<float>(sig + g0 + c * kPartRows, *reinterpret_cast<float(*)[kPartRows]>(sg + c * kPartRows));
+    }
     // 1) banded LU of the interior rows g0 + B + r (no pivoting, as the stored factorisation)
     float l[Q][B], U[Q][B + 1], piv[Q];
 #pragma unroll
@@ -504,10 +516,17 @@ __device__ __forceinline__ void corr_solve_otf(float* __restrict__ x, const floa
       for (int c = 0; c < B; ++c) v -= V[r][c] * xs[c] + W[r][c] * xn[c];
       xp[B + r] = v;
     }
-    store_part<float>(x + g0, xp);
+#pragma unroll
+    for (int c = 0; c < PR / kPartRows; ++c)
+      store_part<float>(x + g0 + c * kPartRows, *reinterpret_cast<const float(*)[kPartRows]>(xp + c * kPartRows));
   }
   __syncthreads();
 }
+
+// Rows per partition of the on-the-fly solve: 16 for B <= 2 (half the partitions of the stored layout,
+// so one PCR level less and half the reduction work), 8 for B = 3 (register budget).
+template <int B>
+constexpr int otf_rows() { return B <= 2 ? 16 : 8; }
 
 // dst = S^T src for table row `row` (FP64): target k sums, in increasing arrival index i, the weight
 // w_a(eps_i) src[i] of every arrival point i whose stencil node a lands on k.  The candidates form the
@@ -536,10 +555,10 @@ __device__ __forceinline__ void apply_gather_T(const LevelTables& T, int row, co
 }
 
 // FP32 levels stage each step's tables into shared memory: a double buffer of (eps row, shift row and,
-// for coarse levels factorised on the fly, sigma row), each buffer filled by TMA bulk copies that
-// complete on its mbarrier; then, on coarse levels, the exchange area of the on-the-fly solve.
-// Byte offsets from the 128-aligned start of the region: buffer b starts at b * per_buf with eps at +0,
-// shift at +e, sigma at +e+h; the two barriers at `bars`.
+// for coarse levels factorised on the fly, sigma row), each buffer filled one step ahead by TMA bulk
+// copies that complete on its mbarrier; then, on coarse levels, the exchange area of the solve.
+// Byte offsets from the 128-aligned start of the region: buffer b starts at b * per_buf with eps at
+// +0, shift at +e, sigma at +e+h; the two barriers at `bars`.
 struct StageLayout {
   unsigned e, h, per_buf, bars, xch, total, tx;  // tx: bytes copied per step
 };
@@ -550,7 +569,7 @@ MGRIT_HD StageLayout stage_layout(int nx, int p, int otf) {
   o.per_buf = o.e + o.h + (otf ? o.e : 0u);
   o.bars = 2 * o.per_buf;
   o.xch = o.bars + 128;
-  const int B = (p + 1) / 2, P = nx / kPartRows;
+  const int B = (p + 1) / 2, P = nx / (B <= 2 ? 16 : 8);  // partitions of the on-the-fly solve
   o.total = o.xch + (otf ? (unsigned)((3 * B * B + B) * P * 4) : 0u);
   o.tx = (unsigned)nx * (otf ? 10u : 6u);
   return o;
@@ -603,8 +622,8 @@ __device__ __forceinline__ void stage_issue(const Stage& s, const LevelTables& T
     bulk_copy_g2s(d + s.lay.e + s.lay.h, (const float*)T.solver + (size_t)row * T.solver_stride, nx * 4u, s.bar(b));
 }
 
-// Waits for buffer `cur` (issuing it first if it was not prefetched) after issuing the next step's
-// copies; false if the bounded wait gave up (T.err set; copies in flight have landed or timed out).
+// Issues the next step's copies (and this step's if it was not prefetched), then waits for buffer
+// `cur`; false if the bounded wait gave up (T.err set; thread 0 lets the copies in flight land first).
 __device__ __forceinline__ bool stage_acquire(Stage& s, const LevelTables& T, int n, int next_n, bool otf) {
   const int b = s.cur;
   if (threadIdx.x == 0) {
@@ -628,7 +647,7 @@ __device__ __forceinline__ bool stage_acquire(Stage& s, const LevelTables& T, in
 // One full step src -> dst (Phi, or Psi with the correction solve), given the prefetched gather table.
 // next_n: the step this CTA takes after this one (-1: none), whose sigma row is prefetched.
 // Returns false if a bounded wait gave up (the caller then stops; the flag T.err is set).
-template <int P, typename R, bool COARSE, bool TRANS = false>
+template <int P, typename R, bool COARSE, bool TRANS, int NT>
 __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R* dst, const LevelTables& T, int n,
                                           Stage& stg, int next_n) {
   constexpr int B = (P + 1) / 2;
@@ -647,12 +666,11 @@ __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R*
     return true;
   }
   if constexpr (std::is_same<R, float>::value) {  // tables staged by TMA; coarse: factorised on the fly
-    constexpr bool otf = COARSE;
-    if (!stage_acquire(stg, T, n, next_n, otf)) return false;
+    if (!stage_acquire(stg, T, n, next_n, COARSE)) return false;
     const int b = stg.cur;
-    apply_gather_staged<P>(stg.eps(b), stg.sh(b), (const float*)src, (float*)dst, T.nx);
+    apply_gather_staged<P, NT>(stg.eps(b), stg.sh(b), (const float*)src, (float*)dst, T.nx);
     __syncthreads();
-    if constexpr (COARSE) corr_solve_otf<B>((float*)dst, stg.sig(b), stg.xch(), T.nx);
+    if constexpr (COARSE) corr_solve_otf<B, otf_rows<B>()>((float*)dst, stg.sig(b), stg.xch(), T.nx);
     stg.cur ^= 1;
     stg.pending = next_n;
     (void)gr;
@@ -673,9 +691,10 @@ __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R*
 
 // Fine-level kernels keep two (FP32: shared memory of the staged tables) or three (FP64) CTAs per SM.
 // The pass of interval j (one CTA); also the body of the batched kernel.
-template <int P, typename R, bool COARSE, bool TRANS>
+template <int P, typename R, bool COARSE, bool TRANS, int NT>
 __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs& a, int j, int buf,
                                            unsigned char* smem_raw) {
+  constexpr int kP = kMaxNx / NT;  // points per thread
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
   double* red = reinterpret_cast<double*>(dst + buf);
@@ -710,31 +729,33 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
     }
     const R* gr = a.g ? (const R*)a.g + (size_t)(n + 1) * nx : nullptr;
     // FP32: the right-hand side of this step is loaded before the step so its latency is hidden
-    R gpre[kPts];
+    R gpre[kP];
     if constexpr (kPipe) {
       if (gr) {
 #pragma unroll
-        for (int q = 0; q < kPts; ++q) {
-          const int i = threadIdx.x + q * kSliceThreads;
+        for (int q = 0; q < kP; ++q) {
+          const int i = threadIdx.x + q * NT;
           gpre[q] = (i < nx) ? gr[i] : (R)0;
         }
       }
     }
-    if (!full_step<P, R, COARSE, TRANS>(gcur, src, dst, T, n, stg, k + 1 < a.nsteps ? n + 1 : -1)) return;
+    if (!full_step<P, R, COARSE, TRANS, NT>(gcur, src, dst, T, n, stg, k + 1 < a.nsteps ? n + 1 : -1)) return;
     const bool last = (k == a.m - 1);
+    R* fs = a.fstore ? (R*)a.fstore + (size_t)(n + 1) * nx : nullptr;
     if (!last) {
-      R* fs = a.fstore ? (R*)a.fstore + (size_t)(n + 1) * nx : nullptr;
+      if (gr || fs) {  // F-point: add the right-hand side and / or store it
 #pragma unroll
-      for (int q = 0; q < kPts; ++q) {
-        const int i = threadIdx.x + q * kSliceThreads;
-        if (i >= nx) continue;
-        R v = dst[i];
-        if (gr) {
-          if constexpr (kPipe) v += gpre[q];
-          else v += gr[i];
+        for (int q = 0; q < kP; ++q) {
+          const int i = threadIdx.x + q * NT;
+          if (i >= nx) continue;
+          R v = dst[i];
+          if (gr) {
+            if constexpr (kPipe) v += gpre[q];
+            else v += gr[i];
+          }
+          dst[i] = v;
+          if (fs) fs[i] = v;
         }
-        dst[i] = v;
-        if (fs) fs[i] = v;
       }
     } else if (a.mode == MODE_FC) {
       R* co = (R*)a.cout + (size_t)(j + 1) * a.c_stride;
@@ -746,13 +767,17 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
     } else {  // MODE_RES
       const R* ci = a.cin ? (const R*)a.cin + (size_t)(j + 1) * a.c_stride : nullptr;
       R* ro = (R*)a.rout + (size_t)(j + 1) * a.r_stride;
+      float* ro32 = a.rout32 ? a.rout32 + (size_t)(j + 1) * a.r_stride : nullptr;
+      R sqt = (R)0;  // FP32 levels accumulate their (FP32) residual in FP32 per thread
       for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         R v = dst[i];
         if (gr && a.g_at_c) v += gr[i];
         if (ci) v -= ci[i];
         ro[i] = v;
-        sq += (double)v * (double)v;
+        if (ro32) ro32[i] = (float)v;
+        if (a.norm_partial) sqt += v * v;
       }
+      sq += (double)sqt;
     }
     __syncthreads();
     R* t = src;
@@ -766,14 +791,16 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
 }
 
 template <int P, typename R, bool COARSE, bool TRANS>
-__global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : (std::is_same<R, float>::value ? 2 : 3))
+__global__ void __launch_bounds__(slice_threads<P, R, COARSE>(),
+                                  COARSE ? (slice_threads<P, R, COARSE>() == 256 ? 2 : 1)
+                                         : (std::is_same<R, float>::value ? 2 : 3))
     k_relax_1d(LevelTables T, RelaxArgs a, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  relax_body<P, R, COARSE, TRANS>(T, a, blockIdx.x, buf, smem_raw);
+  relax_body<P, R, COARSE, TRANS, slice_threads<P, R, COARSE>()>(T, a, blockIdx.x, buf, smem_raw);
 }
 
 // u0: [nx] start slice; out: store_all ? [(N+1)][nx] (row 0 = u0) : [nx] (the final slice).
-template <int P, typename R, bool COARSE, bool TRANS>
+template <int P, typename R, bool COARSE, bool TRANS, int NT>
 __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, const R* g, const R* u0, R* out_all,
                                                 int store_all, int buf, unsigned char* smem_raw) {
   R* src = reinterpret_cast<R*>(smem_raw);
@@ -796,7 +823,7 @@ __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, con
     } else {
       load_gather<P, R>(gcur, T, n);
     }
-    if (!full_step<P, R, COARSE, TRANS>(gcur, src, dst, T, n, stg, n + 1 < N ? n + 1 : -1)) return;
+    if (!full_step<P, R, COARSE, TRANS, NT>(gcur, src, dst, T, n, stg, n + 1 < N ? n + 1 : -1)) return;
     const R* gr = g ? g + (size_t)(n + 1) * nx : nullptr;
     R* out = store_all ? out_all + (size_t)(n + 1) * nx : (n == N - 1 ? out_all : nullptr);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -813,10 +840,12 @@ __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, con
 }
 
 template <int P, typename R, bool COARSE, bool TRANS>
-__global__ void __launch_bounds__(kSliceThreads) k_sequential_1d(LevelTables T, int N, const R* g, const R* u0,
-                                                                 R* out_all, int store_all, int buf) {
+__global__ void __launch_bounds__(slice_threads<P, R, COARSE>()) k_sequential_1d(LevelTables T, int N, const R* g,
+                                                                                 const R* u0, R* out_all,
+                                                                                 int store_all, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  sequential_body<P, R, COARSE, TRANS>(T, N, g, u0, out_all, store_all, buf, smem_raw);
+  sequential_body<P, R, COARSE, TRANS, slice_threads<P, R, COARSE>()>(T, N, g, u0, out_all, store_all, buf,
+                                                                       smem_raw);
 }
 
 // ---- batched problems: one launch per cycle phase over (problem, interval) tiles --------------------
@@ -832,9 +861,9 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_relax_batched(const LevelT
   const LevelTables T = tabs[t.table];
   const RelaxArgs a = args[t.args];
   switch (T.p) {
-    case 1: relax_body<1, R, COARSE, false>(T, a, t.j, buf, smem_raw); break;
-    case 3: relax_body<3, R, COARSE, false>(T, a, t.j, buf, smem_raw); break;
-    default: relax_body<5, R, COARSE, false>(T, a, t.j, buf, smem_raw); break;
+    case 1: relax_body<1, R, COARSE, false, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
+    case 3: relax_body<3, R, COARSE, false, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
+    default: relax_body<5, R, COARSE, false, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
   }
 }
 
@@ -849,14 +878,15 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sequential_batched(const L
   const LevelTables T = tabs[t.table];
   const SeqArgs a = args[t.args];
   switch (T.p) {
-    case 1: sequential_body<1, R, COARSE, false>(T, a.N, (const R*)a.g, (const R*)a.u0, (R*)a.out, a.store_all, buf, smem_raw); break;
-    case 3: sequential_body<3, R, COARSE, false>(T, a.N, (const R*)a.g, (const R*)a.u0, (R*)a.out, a.store_all, buf, smem_raw); break;
-    default: sequential_body<5, R, COARSE, false>(T, a.N, (const R*)a.g, (const R*)a.u0, (R*)a.out, a.store_all, buf, smem_raw); break;
+    case 1: sequential_body<1, R, COARSE, false, kSliceThreads>(T, a.N, (const R*)a.g, (const R*)a.u0, (R*)a.out, a.store_all, buf, smem_raw); break;
+    case 3: sequential_body<3, R, COARSE, false, kSliceThreads>(T, a.N, (const R*)a.g, (const R*)a.u0, (R*)a.out, a.store_all, buf, smem_raw); break;
+    default: sequential_body<5, R, COARSE, false, kSliceThreads>(T, a.N, (const R*)a.g, (const R*)a.u0, (R*)a.out, a.store_all, buf, smem_raw); break;
   }
 }
 
 template <int P, typename R, bool COARSE, bool TRANS>
-__global__ void __launch_bounds__(kSliceThreads) k_apply_1d(LevelTables T, int n0, const R* in, R* out, int buf) {
+__global__ void __launch_bounds__(slice_threads<P, R, COARSE>()) k_apply_1d(LevelTables T, int n0, const R* in,
+                                                                            R* out, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
@@ -866,7 +896,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_apply_1d(LevelTables T, int n
   __syncthreads();
   GatherRegs<P, R> gr;
   load_gather<P, R>(gr, T, n0 + c);
-  if (!full_step<P, R, COARSE, TRANS>(gr, src, dst, T, n0 + c, stg, -1)) return;
+  if (!full_step<P, R, COARSE, TRANS, slice_threads<P, R, COARSE>()>(gr, src, dst, T, n0 + c, stg, -1)) return;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) out[(size_t)c * nx + i] = dst[i];
 }
 
@@ -898,7 +928,7 @@ cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_
     auto kern = k_relax_1d<PP, R, COARSE, TR>;                                                                 \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
     if (e != cudaSuccess) return e;                                                                        \
-    kern<<<grid, kSliceThreads, sm, st>>>(T, a, buf);                                                      \
+    kern<<<grid, slice_threads<PP, R, COARSE>(), sm, st>>>(T, a, buf);                                                      \
     return cudaGetLastError();                                                                             \
   }
   if (T.p == 1) MGRIT_LAUNCH_RELAX(1)
@@ -917,7 +947,7 @@ cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, cons
     auto kern = k_sequential_1d<PP, R, COARSE, TR>;                                                            \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
     if (e != cudaSuccess) return e;                                                                        \
-    kern<<<1, kSliceThreads, sm, st>>>(T, N, (const R*)g, (const R*)u0, (R*)u, store_all, buf);            \
+    kern<<<1, slice_threads<PP, R, COARSE>(), sm, st>>>(T, N, (const R*)g, (const R*)u0, (R*)u, store_all, buf);            \
     return cudaGetLastError();                                                                             \
   }
   if (T.p == 1) MGRIT_LAUNCH_SEQ(1)
@@ -935,7 +965,7 @@ cudaError_t apply_dispatch(const LevelTables& T, int n0, int count, const void* 
     auto kern = k_apply_1d<PP, R, COARSE, TR>;                                                                 \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
     if (e != cudaSuccess) return e;                                                                        \
-    kern<<<count, kSliceThreads, sm, st>>>(T, n0, (const R*)in, (R*)out, buf);                             \
+    kern<<<count, slice_threads<PP, R, COARSE>(), sm, st>>>(T, n0, (const R*)in, (R*)out, buf);                             \
     return cudaGetLastError();                                                                             \
   }
   if (T.p == 1) MGRIT_LAUNCH_APPLY(1)

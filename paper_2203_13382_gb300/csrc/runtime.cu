@@ -60,6 +60,65 @@ struct Level {
   int* bperm = nullptr;
 };
 
+// Device workspace comes from a stream-ordered memory pool per device owned by the library: blocks a
+// destroyed handle returns stay cached for the next setup (no cudaMalloc / cudaFree device
+// synchronisation per solve).  An allocation that fails trims the pool and is retried once.
+cudaMemPool_t workspace_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+// Small pinned host blocks (norm read-back) reused across handles.
+std::mutex& pinned_mu() {
+  static std::mutex* mu = new std::mutex;
+  return *mu;
+}
+std::vector<double*>& pinned_free() {
+  static std::vector<double*>* v = new std::vector<double*>;
+  return *v;
+}
+double* pinned_take() {
+  {
+    std::lock_guard<std::mutex> lk(pinned_mu());
+    if (!pinned_free().empty()) {
+      double* p = pinned_free().back();
+      pinned_free().pop_back();
+      return p;
+    }
+  }
+  double* p = nullptr;
+  if (cudaMallocHost((void**)&p, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void pinned_give(double* p) {
+  std::lock_guard<std::mutex> lk(pinned_mu());
+  pinned_free().push_back(p);
+}
+
 double now_ms() {
   using namespace std::chrono;
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
@@ -76,6 +135,7 @@ struct mgrit_handle {
   int npts = 0;
   std::vector<Level> levels;
   std::vector<void*> allocs;
+  std::vector<char> pooled;  // allocs[i] came from the workspace pool
   int64_t bytes = 0;
   // level-0 C-point state and scratch
   double* X = nullptr;
@@ -102,8 +162,11 @@ struct mgrit_handle {
   size_t ev_next = 0;
 
   ~mgrit_handle() {
-    for (void* p : allocs) cudaFree(p);
-    if (norm_host) cudaFreeHost(norm_host);
+    for (size_t i = 0; i < allocs.size(); ++i) {
+      if (pooled[i]) cudaFreeAsync(allocs[i], stream);
+      else cudaFree(allocs[i]);
+    }
+    if (norm_host) pinned_give(norm_host);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
 
@@ -149,12 +212,26 @@ struct mgrit_handle {
     *p = nullptr;
     if (count == 0) return MGRIT_OK;
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    const size_t nb = count * sizeof(T);
+    cudaMemPool_t pool = workspace_pool();
+    cudaError_t e = cudaErrorMemoryAllocation;
+    if (pool) {
+      e = cudaMallocFromPoolAsync(&q, nb, pool, stream);
+      if (e != cudaSuccess) {  // give cached blocks back to the device and retry once
+        cudaGetLastError();
+        cudaStreamSynchronize(stream);
+        cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocFromPoolAsync(&q, nb, pool, stream);
+      }
+    } else {
+      e = cudaMalloc(&q, nb);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(MGRIT_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+      return fail(MGRIT_ENOMEM, "device allocation of " + std::to_string(nb) + " bytes failed");
     }
     allocs.push_back(q);
+    pooled.push_back(pool ? 1 : 0);
     bytes += (int64_t)(count * sizeof(T));
     *p = (T*)q;
     return MGRIT_OK;
@@ -452,8 +529,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   if ((st = h->alloc(&h->norm_dev, 2)) != MGRIT_OK) return cleanup_fail(st);
   if ((st = h->alloc(&h->flag_dev, 1)) != MGRIT_OK) return cleanup_fail(st);
   if ((st = h->alloc(&h->err_dev, 1)) != MGRIT_OK) return cleanup_fail(st);
-  if (cudaMallocHost((void**)&h->norm_host, 4 * sizeof(double)) != cudaSuccess)
-    return cleanup_fail(fail(MGRIT_ENOMEM, "pinned host allocation failed"));
+  if (!(h->norm_host = pinned_take())) return cleanup_fail(fail(MGRIT_ENOMEM, "pinned host allocation failed"));
 
   cudaStream_t s = h->stream;
   WaveParams wp{wave->kind, wave->a, wave->k, wave->a2};
@@ -612,14 +688,10 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
       a.cin = h->X;
       a.c_stride = np;
       a.rout = h->r64;
+      a.rout32 = h->EC;  // C-relaxation of the error equation from a zero guess gives e_C = r (FP32)
       a.r_stride = np;
       MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_RES));
-      // C-relaxation of the error equation from a zero guess gives e_C = r; F-relax + residual in FP32
-      {
-        const int ev = h->phase_begin();
-        launch_axpy_convert(1, h->r64, h->EC, nullptr, (long long)(J + 1) * np, s);
-        h->phase_end(MGRIT_PHASE_MISC, ev, 1);
-      }
+      // F-relaxation + residual of the error equation in FP32
       a = args0();
       a.m = m1;
       a.J = J;
@@ -1087,6 +1159,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     a = args0();
     a.m = m1; a.J = J; a.nsteps = m1; a.mode = MODE_RES;
     a.start = h->X; a.start_stride = np; a.cin = h->X; a.c_stride = np; a.rout = h->r64; a.r_stride = np;
+    a.rout32 = h->EC;  // e_C = r in FP32
     nt = J;
     return true;
   }));
@@ -1235,14 +1308,13 @@ mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, cons
       mgrit_handle* h = b->hs[q];
       const long long n = active[q] ? (long long)(h->J1() + 1) * h->npts : 0;
       maxn = std::max(maxn, n);
-      seg[q] = Segment{h->r64, h->EC, nullptr, n};
+      seg[q] = Segment{nullptr, nullptr, nullptr, 0};
       seg[nprob + q] = Segment{h->r64, h->X, h->levels[1].E, n};
       seg[2 * nprob + q] = Segment{h->norm_partial, b->d_norms + q, nullptr, active[q] ? (long long)h->J1() : 0};
     }
     MG_CUDA(cudaMemcpyAsync(b->d_active, active.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
     MG_CUDA(cudaMemcpyAsync(b->d_seg, seg.data(), seg.size() * sizeof(Segment), cudaMemcpyHostToDevice, s));
-    MG_TRY(run(b->down[0]));                                  // FP64 residual of every iterate
-    launch_axpy_batched(1, b->d_seg, nprob, maxn, s);         // e_C = r (FP32)
+    MG_TRY(run(b->down[0]));                                  // FP64 residual of every iterate, e_C = r
     for (size_t ph = 1; ph < b->down.size(); ++ph) MG_TRY(run(b->down[ph]));
     for (auto& ph : b->up) MG_TRY(run(ph));
     launch_axpy_batched(5, b->d_seg + nprob, nprob, maxn, s); // u_C += r + E_1
