@@ -16,6 +16,15 @@ namespace {
 
 constexpr int kThreads2d = 256;
 
+// Coefficient of the centred stencil (delta^2)^B at offset o: (-1)^{B+o} C(2B, B+o) (compile time).
+template <int B>
+constexpr int dstencil_int(int o) {
+  int c = 1;
+  for (int t = 1; t <= B + o; ++t) c = c * (2 * B - (B + o) + t) / t;
+  return ((B + o) & 1) ? -c : c;
+}
+constexpr int kThreadsGmres = 1024;  // one CTA per system: more loads in flight per SM
+
 // Weights of one axis for element pt of step row n.  FP32: from the stored eps; FP64: from the offset.
 template <int P, typename R>
 __device__ __forceinline__ void axis_weights(const LevelTables& T, int comp, int n, long long pt, R (&w)[P + 1]) {
@@ -116,10 +125,7 @@ __device__ __forceinline__ R apply_M(const R* x, const double* sx, const double*
   R dxv = (R)0, dyv = (R)0;
 #pragma unroll
   for (int o = -B; o <= B; ++o) {
-    // centred binomial stencil (-1)^{B+o} C(2B, B+o)
-    double c = 1.0;
-    for (int t = 1; t <= B + o; ++t) c = c * (2 * B - (B + o) + t) / t;
-    const R d = (R)(((B + o) & 1) ? -c : c);
+    const R d = (R)dstencil_int<B>(o);
     dxv += d * row[wrap_pow2(i + o, nx)];
     dyv += d * x[(size_t)wrap_pow2(jj + o, nx) * nx + i];
   }
@@ -133,9 +139,7 @@ __device__ __forceinline__ R apply_MT(const R* x, const double* sx, const double
   R dxv = (R)0, dyv = (R)0;
 #pragma unroll
   for (int o = -B; o <= B; ++o) {
-    double c = 1.0;
-    for (int t = 1; t <= B + o; ++t) c = c * (2 * B - (B + o) + t) / t;
-    const R d = (R)(((B + o) & 1) ? -c : c);
+    const R d = (R)dstencil_int<B>(o);
     const long long px = (long long)jj * nx + wrap_pow2(i + o, nx);
     const long long py = (long long)wrap_pow2(jj + o, nx) * nx + i;
     dxv += d * (R)sx[px] * x[px];
@@ -144,11 +148,13 @@ __device__ __forceinline__ R apply_MT(const R* x, const double* sx, const double
   return x[pt] - dxv - dyv;
 }
 
+// CTA-wide dot product; each thread accumulates its strided share in R (FP32 systems stay off the
+// narrow FP64 pipe), the per-thread partial sums are reduced in FP64.
 template <typename R>
 __device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, double* red) {
-  double s = 0.0;
-  for (long long q = threadIdx.x; q < N; q += blockDim.x) s += (double)a[q] * (double)b[q];
-  double t = block_sum(s, red);
+  R s = (R)0;
+  for (long long q = threadIdx.x; q < N; q += blockDim.x) s += a[q] * b[q];
+  double t = block_sum((double)s, red);
   __syncthreads();
   if (threadIdx.x == 0) red[32] = t;
   __syncthreads();
@@ -161,7 +167,7 @@ __device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, d
 // (row nt_rev - 1 - n(j) when nt_rev > 0; TRANS solves with M^T).  basis: [J][kmax + 1][N] scratch.  GMRES (Arnoldi with modified Gram-Schmidt, Givens rotations), zero
 // initial guess, stop when the least-squares residual <= rtol ||b|| or after kmax iterations.
 template <int B, typename R, bool TRANS>
-__global__ void __launch_bounds__(kThreads2d) k_gmres2d(const double* __restrict__ sigma_x,
+__global__ void __launch_bounds__(kThreadsGmres) k_gmres2d(const double* __restrict__ sigma_x,
                                                         const double* __restrict__ sigma_y, int nx, int n0, int m,
                                                         int nt_rev, R* __restrict__ bx_all, R* __restrict__ basis,
                                                         int kmax, double rtol) {
@@ -177,7 +183,8 @@ __global__ void __launch_bounds__(kThreads2d) k_gmres2d(const double* __restrict
   R* V = basis + (size_t)j * (kmax + 1) * N;
   const double beta = sqrt(cta_dot<R>(b, b, N, red));
   if (beta == 0.0) return;  // x = 0
-  for (long long q = threadIdx.x; q < N; q += blockDim.x) V[q] = (R)(b[q] / beta);
+  const R ib = (R)(1.0 / beta);
+  for (long long q = threadIdx.x; q < N; q += blockDim.x) V[q] = b[q] * ib;
   if (threadIdx.x == 0) {
     gv[0] = beta;
     for (int t = 1; t <= kmax; ++t) gv[t] = 0.0;
@@ -218,7 +225,8 @@ __global__ void __launch_bounds__(kThreads2d) k_gmres2d(const double* __restrict
     __syncthreads();
     kused = kk + 1;
     if (red[36] <= rtol * beta || !(hn > 0.0)) break;
-    for (long long q = threadIdx.x; q < N; q += blockDim.x) w[q] = (R)(w[q] / hn);
+    const R ihn = (R)(1.0 / hn);
+    for (long long q = threadIdx.x; q < N; q += blockDim.x) w[q] = w[q] * ihn;
     __syncthreads();
   }
   if (threadIdx.x == 0) {  // back substitution R y = g
@@ -229,10 +237,12 @@ __global__ void __launch_bounds__(kThreads2d) k_gmres2d(const double* __restrict
     }
   }
   __syncthreads();
+  R yr[10];
+  for (int t = 0; t < kused; ++t) yr[t] = (R)yv[t];
   for (long long q = threadIdx.x; q < N; q += blockDim.x) {
-    double x = 0.0;
-    for (int t = 0; t < kused; ++t) x += yv[t] * (double)V[(size_t)t * N + q];
-    b[q] = (R)x;
+    R x = (R)0;
+    for (int t = 0; t < kused; ++t) x += yr[t] * V[(size_t)t * N + q];
+    b[q] = x;
   }
 }
 
@@ -313,7 +323,7 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
         const double* sig = (const double*)T.solver;
         const int B = (T.p + 1) / 2, ntr = T.reverse ? T.nt : 0;
 #define MGRIT_GMT(BB)                                                                                        \
-  k_gmres2d<BB, double, true><<<J, kThreads2d, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, ntr, src, \
+  k_gmres2d<BB, double, true><<<J, kThreadsGmres, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, ntr, src, \
                                                         (double*)S.basis, S.kmax, S.rtol)
         if (B == 1) MGRIT_GMT(1);
         else if (B == 2) MGRIT_GMT(2);
@@ -337,7 +347,7 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
     const double* sig = (const double*)T.solver;  // sigma_x block then sigma_y block, [nt][N] each
     const int B = (T.p + 1) / 2;
 #define MGRIT_GM(BB)                                                                                      \
-  k_gmres2d<BB, R, false><<<J, kThreads2d, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, 0, dst, \
+  k_gmres2d<BB, R, false><<<J, kThreadsGmres, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, 0, dst, \
                                                     (R*)S.basis, S.kmax, S.rtol)
     if (B == 1) MGRIT_GM(1);
     else if (B == 2) MGRIT_GM(2);
