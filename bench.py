@@ -130,10 +130,18 @@ class ClockSampler:
 # roofline of the dominant kernel
 # ------------------------------------------------------------------------------------------------
 
-def phase_work(phase: str, wl: dict, levels: list[tuple[int, int]], launches: int) -> dict | None:
-    """Algorithmic bytes and flops per launch of a level-0 pass (one launch = one sweep of nt steps)."""
-    nx, nt, p = wl["nx"], wl["nt"], wl["order"]
-    J = nt // wl["m"]
+def level_steps(wl: dict) -> list[int]:
+    """Steps per level under the coarsening rule of the library (m on every level, stop at <= max_coarsest)."""
+    out = [wl["nt"]]
+    while out[-1] > wl["max_coarsest"] and out[-1] % wl["m"] == 0:
+        out.append(out[-1] // wl["m"])
+    return out
+
+
+def phase_work(phase: str, wl: dict, launches: int, iterations: int) -> dict | None:
+    """Algorithmic bytes and flops per launch of a phase (averaged over the launches of one solve)."""
+    nx, nt, p, m = wl["nx"], wl["nt"], wl["order"], wl["m"]
+    J = nt // m
     pts = nx * nt
     if phase in ("fine64_res", "fine64_fc", "fine64_post"):
         # per point-step: 2 B shift + (p+1) FP64 weights; per interval: start slice, C value in, C value out
@@ -146,26 +154,36 @@ def phase_work(phase: str, wl: dict, levels: list[tuple[int, int]], launches: in
         byts = pts * (2 + 4) + 2 * J * nx * 4
         flops = pts * (2 * (p + 1) + 3 * (p + 1))
         return {"bytes": byts, "flops": flops, "fp": 32}
+    if phase == "coarse":
+        # relaxation levels 1 .. L-2, passes FC, RES, POST per cycle; per coarse point-step the staged
+        # tables (eps 4 B, shift 2 B, sigma 4 B) and the right-hand side row (4 B), POST also stores
+        # every F-point (4 B); per interval the start slice and one C-point row in / out (4 B each)
+        nts = level_steps(wl)
+        per_cycle = 0
+        for l in range(1, len(nts) - 1):
+            ntl, Jl = nts[l], nts[l] // m
+            per_cycle += ntl * nx * 14 + 2 * Jl * nx * 4          # FC
+            per_cycle += ntl * nx * 14 + 3 * Jl * nx * 4          # RES
+            per_cycle += (ntl - Jl) * nx * 18 + 2 * Jl * nx * 4   # POST
+        return {"bytes": per_cycle * iterations / max(launches, 1), "flops": 0, "fp": 32}
     return None
 
 
-def roofline(stats: dict, wl: dict, hbm_peak: float, hbm_src: str, steps: int, traffic: dict | None) -> dict:
+def roofline_of(phase: str, stats: dict, wl: dict, hbm_peak: float, hbm_src: str, iterations: int,
+                traffic: dict | None) -> dict | None:
     ms, nl = stats["phase_ms"], stats["phase_launches"]
-    ranked = sorted(((ms[k], k) for k in ms if nl[k] > 0 and k not in ("sequential",)), reverse=True)
-    dom = None
-    for _, k in ranked:
-        if phase_work(k, wl, [], nl[k]) is not None:
-            dom = k
-            break
-    top = ranked[0][1] if ranked else None
-    if dom is None:
-        return {"bound": None, "kernel": top}
-    w = phase_work(dom, wl, [], nl[dom])
-    avg_s = ms[dom] / nl[dom] / 1e3
+    if nl.get(phase, 0) == 0:
+        return None
+    w = phase_work(phase, wl, nl[phase], iterations)
+    if w is None:
+        return None
+    avg_s = ms[phase] / nl[phase] / 1e3
     t_hbm = w["bytes"] / (hbm_peak * 1e9)
     t_alu = w["flops"] / (FP64_PEAK_TFLOPS * 1e12) if w["fp"] == 64 else 0.0
-    out = {"kernel": f"k_relax_1d ({dom})", "phase_share": ms[dom] / max(sum(ms.values()), 1e-30),
-           "top_phase": top, "avg_launch_ms": avg_s * 1e3}
+    kern = {"coarse": "k_relax_1d<p, float, coarse> (coarse levels)", "fine32_res": "k_relax_1d<p, float> (level 0)",
+            "fine64_res": "k_relax_1d<p, double> (level 0 residual)"}.get(phase, f"k_relax_1d ({phase})")
+    out = {"kernel": kern, "phase": phase, "phase_share": ms[phase] / max(sum(ms.values()), 1e-30),
+           "avg_launch_ms": avg_s * 1e3}
     if t_alu > t_hbm:
         out.update({"bound": "alu", "achieved": w["flops"] / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"})
@@ -175,8 +193,21 @@ def roofline(stats: dict, wl: dict, hbm_peak: float, hbm_src: str, steps: int, t
     out["frac"] = out["achieved"] / out["peak"]
     out["algorithmic_bytes"] = w["bytes"]
     out["algorithmic_flops"] = w["flops"]
-    out["traffic"] = (traffic or {}).get(dom)
+    out["traffic"] = (traffic or {}).get(phase)
     return out
+
+
+def roofline(stats: dict, wl: dict, hbm_peak: float, hbm_src: str, iterations: int,
+             traffic: dict | None) -> tuple[dict, list]:
+    """The dominant kernel (largest phase share among the relaxation kernels) and the others."""
+    ms = stats["phase_ms"]
+    cands = [k for k in ("coarse", "fine64_res", "fine32_res") if stats["phase_launches"].get(k, 0)]
+    cands.sort(key=lambda k: -ms[k])
+    lines = [roofline_of(k, stats, wl, hbm_peak, hbm_src, iterations, traffic) for k in cands]
+    lines = [x for x in lines if x]
+    if not lines:
+        return {"bound": None}, []
+    return lines[0], lines[1:]
 
 
 # ------------------------------------------------------------------------------------------------
@@ -309,7 +340,8 @@ def run_ours(args) -> None:
     if os.path.exists(os.path.join(ROOT, "profiles", "traffic.json")):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             traffic = json.load(f).get(args.precision)
-    roof = roofline({"phase_ms": agg_ms, "phase_launches": agg_nl}, wl, hbm, hbm_src, args.steps, traffic)
+    roof, roof_others = roofline({"phase_ms": agg_ms, "phase_launches": agg_nl}, wl, hbm, hbm_src,
+                                 sum(s["iterations"] for s in stats), traffic)
 
     seq_ms, seq_best, seq_full_ms, fixed_point, e2e = {}, None, None, None, None
     if not args.no_comparator:
@@ -381,13 +413,192 @@ def run_ours(args) -> None:
                                                   "(one thread-block cluster per slice)",
                            "mgrit_over_sequential": (dof / (ms / 1e3)) / (dof / (seq_full_ms / 1e3)),
                            "fixed_point_rel_diff_final_slice": fixed_point},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "roofline": roof, "roofline_others": roof_others, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
             "phases_ms_per_step": {k: v / args.steps for k, v in agg_ms.items() if agg_nl[k]},
             "phase_launches_per_step": {k: v // args.steps for k, v in agg_nl.items() if v},
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+
+# ------------------------------------------------------------------------------------------------
+# further workloads (--workload): the 2D solve, the batched problems and the 2D adjoint gradient
+# ------------------------------------------------------------------------------------------------
+
+WORKLOAD_2D = {"workload": "advection2d_alpha_1+0.5sin2piy_cos2pit_1+0.5cos2pix_sin2pit_512x512_nt2048_p5_m4",
+               "nx": 512, "nt": 2048, "order": 5, "m": 4, "wave": "sin_cos2", "a": 0.5, "cfl": 0.85,
+               "u0": "5 gaussian bumps, seed 20260002", "rtol": 1e-10, "precision": "fp32bulk",
+               "coarse_solve": "GMRES from zero, rtol 1e-2 or 10 iterations"}
+WORKLOAD_ADJ = {"workload": "adjoint2d_alpha_sin_cos2_a0.5_256x256_nt1024_p3_m4",
+                "nx": 256, "nt": 1024, "order": 3, "m": 4, "wave": "sin_cos2", "a": 0.5, "cfl": 0.85,
+                "u0": "5 gaussian bumps, seed 20260005",
+                "u_target": "sequential solution at a = 0.4 from 5 bumps, seed 20260006", "rtol": 1e-10,
+                "precision": "fp64"}
+WORKLOAD_BATCH = {"workload": "batched1d_256_problems_seed20260004", "problems": 256, "precision": "fp32bulk",
+                  "rtol": 1e-10, "u0": "sin^4(pi x)",
+                  "draws": "nx in 256..4096, nt in 1024..16384 (powers of two), p in {1,3,5}, a in [0.1,0.7], "
+                           "k in {1,2,3}, m in {4,8}"}
+
+
+def _timed(fn, steps: int, warmup: int):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    outs = [fn() for _ in range(steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, outs
+
+
+def _line(args, metric: str, value: float, unit: str, ms: float, cfg: dict, **extra) -> None:
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if cfg.get("precision") == "fp32bulk" else "f64", "data": "synthetic", "config": cfg}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_2d(args) -> None:
+    import torch
+
+    import paper_2203_13382_gb300 as mg
+
+    wl = WORKLOAD_2D
+    nx, nt, p, m = wl["nx"], wl["nt"], wl["order"], wl["m"]
+    npts = nx * nx
+    u0 = torch.from_numpy(W.u0_bumps_2d(nx, W.SEED_C3_BUMPS, 5).ravel().copy()).cuda()
+    U0 = torch.zeros(nt + 1, npts, dtype=torch.float64, device="cuda")
+    rows = np.arange(m, nt + 1, m)  # the solve reads the initial iterate at the C-points only
+    U0[rows] = torch.from_numpy(W.initial_iterate(nt, npts, rows=rows)).cuda()
+    out = torch.empty(nt + 1, npts, dtype=torch.float64, device="cuda")
+
+    def step(profile=0):
+        h = mg.mgrit_setup(nx, nt, p, m, wave=wl["wave"], a=wl["a"], a2=wl["a"], dim=2, precision=1, profile=profile)
+        _, st = h.solve(u0, U0, out)
+        h.destroy()
+        return st
+
+    sampler = ClockSampler("0")
+    sampler.start()
+    ms, stats = _timed(step, args.steps, args.warmup)
+    clocks = sampler.stop()
+    prof = step(1)
+    h = mg.mgrit_setup(nx, nt, p, m, wave=wl["wave"], a=wl["a"], a2=wl["a"], dim=2, precision=1, profile=1)
+    seq_ms, _ = _timed(lambda: h.sequential(u0, store_all=False), 3, 1)
+    last = h.sequential(u0, store_all=False)
+    fixed = float((last - out[-1]).norm() / last.norm())
+    h.destroy()
+    dof = npts * nt
+    ph = prof["phase_ms"]
+    seq_full = seq_ms + ph["departure"] + ph["tables"] * nt / sum(nt // m ** l for l in range(prof["levels"]))
+    _line(args, METRIC, dof / (ms / 1e3), "DOF/s", ms, wl, iterations=stats[0]["iterations"],
+          comparator={"sequential_ms": seq_full, "sequential_steps_only_ms": seq_ms,
+                      "sequential_dof_per_s": dof / (seq_full / 1e3),
+                      "mgrit_over_sequential": seq_full / ms, "fixed_point_rel_diff_final_slice": fixed},
+          phases_ms_per_step={k: v for k, v in ph.items() if v}, clocks=clocks,
+          gpu_launches=int(stats[0]["kernel_launches"]), device_bytes=int(stats[0]["device_bytes"]))
+
+
+def run_batched(args) -> None:
+    import torch
+
+    import paper_2203_13382_gb300 as mg
+
+    wl = WORKLOAD_BATCH
+    probs = W.batched_problems(wl["problems"])
+    specs = [dict(nx=q.nx, nt=q.nt, order=q.order, m=q.m, a=q.a, k=float(q.k)) for q in probs]
+    u0s, inits, outs = [], [], []
+    for q in probs:
+        u0s.append(torch.from_numpy(W.u0_sin4(q.nx)).cuda())
+        U = torch.empty(q.nt + 1, q.nx, dtype=torch.float64, device="cuda")
+        rows = np.arange(q.m, q.nt + 1, q.m)  # read at the C-points only
+        U[rows] = torch.from_numpy(W.initial_iterate(q.nt, q.nx, rows=rows)).cuda()
+        inits.append(U)
+        outs.append(torch.empty(q.nt + 1, q.nx, dtype=torch.float64, device="cuda"))
+    dof = sum(q.nx * q.nt for q in probs)
+
+    def step():
+        b = mg.mgrit_setup_batched(specs)
+        _, st = b.solve(u0s, inits, outs)
+        b.destroy()
+        return st
+
+    sampler = ClockSampler("0")
+    sampler.start()
+    ms, stats = _timed(step, args.steps, args.warmup)
+    clocks = sampler.stop()
+    iters = [st["iterations"] for st in stats[0]]
+    conv = all(st["converged"] for st in stats[0])
+    # comparator: every problem stepped sequentially (one thread-block cluster each) on 16 streams at once,
+    # plus the departure points and tables of every problem
+    streams = [torch.cuda.Stream() for _ in range(16)]
+    hs = [mg.mgrit_setup(q.nx, q.nt, q.order, q.m, wave="sin_kx_cos_t", a=q.a, k=float(q.k), precision=1,
+                         stream=streams[i % 16].cuda_stream, profile=1) for i, q in enumerate(probs)]
+    torch.cuda.synchronize()
+
+    def seq_all():
+        return [h.sequential(u0s[i], store_all=False) for i, h in enumerate(hs)]
+
+    seq_ms, _ = _timed(seq_all, 2, 1)
+    for h in hs:
+        h.destroy()
+    _line(args, METRIC, dof / (ms / 1e3), "DOF/s", ms, {**wl, "dof": dof},
+          iterations_min_max=[min(iters), max(iters)], converged=conv,
+          comparator={"sequential_steps_only_ms": seq_ms, "sequential_dof_per_s_steps_only": dof / (seq_ms / 1e3),
+                      "mgrit_over_sequential_steps_only": seq_ms / ms,
+                      "sequential_includes": "nt SL steps of every problem, 16 streams (setup not included)"},
+          clocks=clocks)
+
+
+def run_adjoint2d(args) -> None:
+    import torch
+
+    import paper_2203_13382_gb300 as mg
+
+    wl = WORKLOAD_ADJ
+    nx, nt, p, m = wl["nx"], wl["nt"], wl["order"], wl["m"]
+    npts = nx * nx
+    u0 = torch.from_numpy(W.u0_bumps_2d(nx, W.SEED_C5_BUMPS, 5).ravel().copy()).cuda()
+    ht = mg.mgrit_setup(nx, nt, p, m, wave="sin_cos2", a=0.4, dim=2)
+    ut = ht.sequential(torch.from_numpy(W.u0_bumps_2d(nx, W.SEED_C5_TARGET, 5).ravel().copy()).cuda(),
+                       store_all=False).clone()
+    ht.destroy()
+    U0 = torch.zeros(nt + 1, npts, dtype=torch.float64, device="cuda")
+    rows = np.arange(m, nt + 1, m)
+    U0[rows] = torch.from_numpy(W.initial_iterate(nt, npts, rows=rows)).cuda()
+    out = torch.empty(nt + 1, npts, dtype=torch.float64, device="cuda")
+    times = {}
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        h = mg.mgrit_setup(nx, nt, p, m, wave=wl["wave"], a=wl["a"], dim=2, precision=0)
+        _, st = h.solve(u0, U0, out)
+        e[1].record()
+        g_u0, g_a, ast = h.adjoint(ut, out[::m].contiguous())
+        e[2].record()
+        h.destroy()
+        torch.cuda.synchronize()
+        times.setdefault("fwd", []).append(e[0].elapsed_time(e[1]))
+        times.setdefault("adj", []).append(e[1].elapsed_time(e[2]))
+        return st, ast, g_a
+
+    sampler = ClockSampler("0")
+    sampler.start()
+    ms, res = _timed(step, args.steps, args.warmup)
+    clocks = sampler.stop()
+    st, ast, g_a = res[0]
+    dof = npts * nt
+    k = args.steps
+    _line(args, "space-time DOF/s of the gradient (MGRIT forward + adjoint MGRIT) to 1e-10", dof / (ms / 1e3),
+          "DOF/s", ms, wl, forward_ms=float(np.mean(times["fwd"][-k:])), adjoint_ms=float(np.mean(times["adj"][-k:])),
+          iterations_forward=st["iterations"], iterations_adjoint=ast["iterations"], dJ_da=g_a, clocks=clocks)
 
 
 def main():
@@ -400,6 +611,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the sequential comparator and e2e runs")
     ap.add_argument("--nt", type=int, default=0, help="override nt (small profiling cases only)")
+    ap.add_argument("--workload", choices=["advection1d", "advection2d", "batched", "adjoint2d"],
+                    default="advection1d", help="advection1d is the benchmark; the others measure further rows")
     ap.add_argument("--no-phase-events", action="store_true",
                     help="time the steps without per-phase events (phase table from one extra step)")
     args = ap.parse_args()
@@ -407,6 +620,12 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "advection2d":
+        run_2d(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "adjoint2d":
+        run_adjoint2d(args)
     else:
         run_ours(args)
 

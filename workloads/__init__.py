@@ -114,10 +114,13 @@ def initial_iterate(nt: int, npts: int, seed: int = SEED_INITIAL_ITERATE, rows: 
         u = np.zeros((nt + 1, npts))
         u[1:] = uniform01(seed, nt * npts).reshape(nt, npts)
         return u
+    rows = np.asarray(rows, dtype=np.int64)
     res = np.zeros((len(rows), npts))
-    for k, n in enumerate(rows):
-        if n >= 1:
-            res[k] = uniform01(seed, npts, start=(int(n) - 1) * npts)
+    live = rows >= 1
+    if live.any():
+        counters = ((rows[live] - 1) * npts)[:, None] + np.arange(npts, dtype=np.int64)[None, :]
+        draws = splitmix64(seed, counters.ravel().astype(np.uint64)) >> np.uint64(11)
+        res[live] = (draws.astype(np.float64) * (1.0 / 9007199254740992.0)).reshape(-1, npts)
     return res
 
 
