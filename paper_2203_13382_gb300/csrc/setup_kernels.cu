@@ -112,19 +112,85 @@ __global__ void __launch_bounds__(256) k_departure_1d(WaveParams w, int nx, int 
   }
 }
 
-__global__ void k_departure_2d(WaveParams w, Tableau T, int nx, int nt, double xmin, double h, double dt,
-                               double* __restrict__ sx, double* __restrict__ sy) {
+// 2D: arrival node (i, j) of the steps n0 .. n0 + kDepSteps - 1 (blockIdx.y).  The node's sin / cos of
+// the spatial phases are formed once; at a stage point (x - dx, y - dy) they follow by angle addition with
+// a small-angle series, and the time factors of the stages are shared by the block.
+template <int R>
+__global__ void __launch_bounds__(256) k_departure_2d(WaveParams w, int nx, int log2nx, int nt, double xmin, double h,
+                                                      double dt, double* __restrict__ sx, double* __restrict__ sy) {
+  using Tb = ErkTab<R>;
+  constexpr int S = Tb::S;
+  __shared__ double tc[kDepSteps][S], ts[kDepSteps][S];
+  const int n0 = blockIdx.y * kDepSteps;
+  for (int q = threadIdx.x; q < kDepSteps * S; q += blockDim.x) {
+    const int nb = q / S, st = q % S;
+    const double t = (n0 + nb + 1) * dt - Tb::c(st) * dt;
+    const double ph = w.kind == 11 ? kTwoPi * t / 3.4 : kTwoPi * t;
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    tc[nb][st] = cs;
+    ts[nb][st] = sn;
+  }
+  __syncthreads();
   const long long npts = (long long)nx * nx;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= npts * nt) return;
-  const int n = (int)(idx / npts);
-  const long long pt = idx % npts;
-  const int j = (int)(pt / nx), i = (int)(pt % nx);
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npts) return;
+  const int i = (int)(pt & (nx - 1)), j = (int)(pt >> log2nx);
   const double x = xmin + h * i, y = xmin + h * j;
-  double dx, dy;
-  erk_displacement_2d(w, T, x, y, (n + 1) * dt, dt, dx, dy);
-  sx[idx] = dx / h;
-  sy[idx] = dy / h;
+  // spatial wavenumber: 2 pi (kind 12) or pi (kind 11, sin^2 / cos^2 of pi x)
+  const double kw = w.kind == 11 ? kPi : kTwoPi;
+  double Sx = 0.0, Cx = 1.0, Sy = 0.0, Cy = 1.0;
+  if (w.kind != 10) {
+    sincos(kw * x, &Sx, &Cx);
+    sincos(kw * y, &Sy, &Cy);
+  }
+  const double inv_h = 1.0 / h;
+  const int nend = min(kDepSteps, nt - n0);
+  for (int nb = 0; nb < nend; ++nb) {
+    double kx[S], ky[S];
+#pragma unroll
+    for (int st = 0; st < S; ++st) {
+      double dx = 0.0, dy = 0.0;  // (x, y) - (stage point)
+#pragma unroll
+      for (int q = 0; q < st; ++q)
+        if (Tb::a(st, q) != 0.0) {
+          dx = dx + dt * Tb::a(st, q) * kx[q];
+          dy = dy + dt * Tb::a(st, q) * ky[q];
+        }
+      double vx, vy;
+      if (w.kind == 10) {
+        vx = w.a;
+        vy = w.a2;
+      } else {
+        double sdx = 0.0, cdx = 1.0, sdy = 0.0, cdy = 1.0;
+        if (st > 0) {
+          small_sincos(kw * dx, sdx, cdx);
+          small_sincos(kw * dy, sdy, cdy);
+        }
+        const double sys = Sy * cdy - Cy * sdy;  // sin(kw (y - dy))
+        const double cxs = Cx * cdx + Sx * sdx;  // cos(kw (x - dx))
+        if (w.kind == 11) {
+          vx = sys * sys * tc[nb][st];
+          vy = -cxs * cxs * tc[nb][st];
+        } else {
+          vx = 1.0 + w.a * sys * tc[nb][st];
+          vy = 1.0 + w.a * cxs * ts[nb][st];
+        }
+      }
+      kx[st] = vx;
+      ky[st] = vy;
+    }
+    double ax = 0.0, ay = 0.0;
+#pragma unroll
+    for (int st = 0; st < S; ++st)
+      if (Tb::b(st) != 0.0) {
+        ax = ax + Tb::b(st) * kx[st];
+        ay = ay + Tb::b(st) * ky[st];
+      }
+    const size_t o = (size_t)(n0 + nb) * npts + pt;
+    sx[o] = dt * ax * inv_h;
+    sy[o] = dt * ay * inv_h;
+  }
 }
 
 void launch_departure_1d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* s,
@@ -138,9 +204,14 @@ void launch_departure_1d(const WaveParams& w, int r, int nx, int nt, double xmin
 
 void launch_departure_2d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* sx,
                          double* sy, cudaStream_t st) {
-  const long long tot = (long long)nx * nx * nt;
+  const long long npts = (long long)nx * nx;
   const int bs = 256;
-  k_departure_2d<<<(unsigned)((tot + bs - 1) / bs), bs, 0, st>>>(w, make_tableau(r), nx, nt, xmin, h, dt, sx, sy);
+  int l2 = 0;
+  while ((1 << l2) < nx) ++l2;
+  dim3 grid((unsigned)((npts + bs - 1) / bs), (unsigned)((nt + kDepSteps - 1) / kDepSteps));
+  if (r == 1) k_departure_2d<1><<<grid, bs, 0, st>>>(w, nx, l2, nt, xmin, h, dt, sx, sy);
+  else if (r == 3) k_departure_2d<3><<<grid, bs, 0, st>>>(w, nx, l2, nt, xmin, h, dt, sx, sy);
+  else k_departure_2d<5><<<grid, bs, 0, st>>>(w, nx, l2, nt, xmin, h, dt, sx, sy);
 }
 
 // Per step: range [min, max] of floor(s) over the arrival points (window of the transposed gather).
@@ -297,15 +368,6 @@ MGRIT_D double frac_eps(double s) {
   return e;
 }
 
-// f_{p+1}(z) = prod_{q=-(p+1)/2}^{(p-1)/2} (q + z) / (p+1)!  (eq. (fpoly_def)).
-MGRIT_D double f_poly(double z, int p) {
-  const int L = (p + 1) / 2;
-  double out = 1.0, fact = 1.0;
-  for (int q = -L; q <= L - 1; ++q) out = out * (q + z);
-  for (int b = 2; b <= p + 1; ++b) fact *= b;
-  return out / fact;
-}
-
 // prod_{q=-(p+1)/2}^{(p-1)/2} (q + z) = (p+1)! f_{p+1}(z)  (eq. (fpoly_def) without its constant factor).
 template <int P>
 MGRIT_D double f_prod(double z) {
@@ -372,48 +434,52 @@ MGRIT_D double p2d(double x, double y, double xE, double yN, double rNE, double 
   return (pN - pS) * (y - yN) + pN;
 }
 
+template <int P>
 __global__ void k_backtrack_2d(const double* __restrict__ sx_prev, const double* __restrict__ sy_prev,
-                               const double* __restrict__ gx_prev, const double* __restrict__ gy_prev, int m, int ntc,
-                               int nx, int p, double* __restrict__ sx_out, double* __restrict__ sy_out,
+                               const double* __restrict__ gx_prev, const double* __restrict__ gy_prev, int m, int nx,
+                               int log2nx, double* __restrict__ sx_out, double* __restrict__ sy_out,
                                double* __restrict__ gx_out, double* __restrict__ gy_out) {
   const long long npts = (long long)nx * nx;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)ntc * npts) return;
-  const int n = (int)(idx / npts);
-  const long long pt = idx % npts;
-  const int j = (int)(pt / nx), i = (int)(pt % nx);
-  const long long base = (long long)m * n * npts;
-  double c = -sx_prev[base + (long long)(m - 1) * npts + pt];
-  double d = -sy_prev[base + (long long)(m - 1) * npts + pt];
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npts) return;
+  const int n = blockIdx.y;
+  const int i = (int)(pt & (nx - 1)), j = (int)(pt >> log2nx);
+  const size_t base = (size_t)m * n * npts;
+  double c = -sx_prev[base + (size_t)(m - 1) * npts + pt];
+  double d = -sy_prev[base + (size_t)(m - 1) * npts + pt];
   for (int k = m - 2; k >= 0; --k) {
-    const double* kx = sx_prev + base + (long long)k * npts;
-    const double* ky = sy_prev + base + (long long)k * npts;
+    const double* kx = sx_prev + base + (size_t)k * npts;
+    const double* ky = sy_prev + base + (size_t)k * npts;
     const double xE = ceil(c), yN = ceil(d);
     const int E = wrap_pow2(i + (int)xE, nx), W = wrap_pow2(i + (int)xE - 1, nx);
     const int N = wrap_pow2(j + (int)yN, nx), S = wrap_pow2(j + (int)yN - 1, nx);
     const double xW = xE - 1.0, yS = yN - 1.0;
-    const long long NE = (long long)N * nx + E, NW = (long long)N * nx + W;
-    const long long SE = (long long)S * nx + E, SW = (long long)S * nx + W;
+    const size_t NE = ((size_t)N << log2nx) + E, NW = ((size_t)N << log2nx) + W;
+    const size_t SE = ((size_t)S << log2nx) + E, SW = ((size_t)S << log2nx) + W;
     const double cx = p2d(c, d, xE, yN, xE - kx[NE], xW - kx[NW], xE - kx[SE], xW - kx[SW]);
     const double cy = p2d(c, d, xE, yN, yN - ky[NE], yN - ky[NW], yS - ky[SE], yS - ky[SW]);
     c = cx;
     d = cy;
   }
+  const size_t idx = (size_t)n * npts + pt;
   sx_out[idx] = -c;
   sy_out[idx] = -d;
   double fx = 0.0, fy = 0.0, sgx = 0.0, sgy = 0.0;
   for (int k = 0; k < m; ++k) {
-    const long long q = base + (long long)k * npts + pt;
-    fx += f_poly(frac_eps(sx_prev[q]), p);
-    fy += f_poly(frac_eps(sy_prev[q]), p);
+    const size_t q = base + (size_t)k * npts + pt;
+    fx += f_prod<P>(frac_eps(sx_prev[q]));
+    fy += f_prod<P>(frac_eps(sy_prev[q]));
     if (gx_prev) {
       sgx += gx_prev[q];
       sgy += gy_prev[q];
     }
   }
-  const double sgn = ((p + 1) & 1) ? -1.0 : 1.0;
-  const double phx = sgn * (f_poly(frac_eps(-c), p) - fx);
-  const double phy = sgn * (f_poly(frac_eps(-d), p) - fy);
+  double inv_fact = 1.0;
+#pragma unroll
+  for (int b = 2; b <= P + 1; ++b) inv_fact /= b;
+  const double sgn = ((P + 1) & 1) ? -1.0 : 1.0;
+  const double phx = sgn * (f_prod<P>(frac_eps(-c)) - fx) * inv_fact;
+  const double phy = sgn * (f_prod<P>(frac_eps(-d)) - fy) * inv_fact;
   gx_out[idx] = gx_prev ? sgx + phx : phx;
   gy_out[idx] = gy_prev ? sgy + phy : phy;
 }
@@ -421,10 +487,17 @@ __global__ void k_backtrack_2d(const double* __restrict__ sx_prev, const double*
 void launch_backtrack_2d(const double* sx_prev, const double* sy_prev, const double* gx_prev, const double* gy_prev,
                          int m, int ntc, int nx, int p, double* sx_out, double* sy_out, double* gx_out, double* gy_out,
                          cudaStream_t st) {
-  const long long tot = (long long)nx * nx * ntc;
+  const long long npts = (long long)nx * nx;
   const int bs = 256;
-  k_backtrack_2d<<<(unsigned)((tot + bs - 1) / bs), bs, 0, st>>>(sx_prev, sy_prev, gx_prev, gy_prev, m, ntc, nx, p,
-                                                                  sx_out, sy_out, gx_out, gy_out);
+  int l2 = 0;
+  while ((1 << l2) < nx) ++l2;
+  dim3 g((unsigned)((npts + bs - 1) / bs), (unsigned)ntc);
+  if (p == 1)
+    k_backtrack_2d<1><<<g, bs, 0, st>>>(sx_prev, sy_prev, gx_prev, gy_prev, m, nx, l2, sx_out, sy_out, gx_out, gy_out);
+  else if (p == 3)
+    k_backtrack_2d<3><<<g, bs, 0, st>>>(sx_prev, sy_prev, gx_prev, gy_prev, m, nx, l2, sx_out, sy_out, gx_out, gy_out);
+  else
+    k_backtrack_2d<5><<<g, bs, 0, st>>>(sx_prev, sy_prev, gx_prev, gy_prev, m, nx, l2, sx_out, sy_out, gx_out, gy_out);
 }
 
 // ------------------------------------------------------------------------------------------------
