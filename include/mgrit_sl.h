@@ -92,7 +92,9 @@ typedef struct {
                        (the aggressive coarsening of Sec. 5) */
   int coarse_fp64;  /* precision == 1 only: 1 = coarse levels and correction solves in FP64,
                        0 (default) = FP32 like the rest of the error cycle */
-  int use_graph;    /* reserved (must be 0 or 1) */
+  int use_graph;    /* 1 (default): each MGRIT cycle's launches are captured once per mgrit_solve call as
+                       a CUDA graph and replayed (one host launch per cycle); 0: launched one by one.
+                       Results are identical either way. */
   int profile;      /* 1: time each phase with CUDA events on the handle's stream (mgrit_stats.phase_ms) */
   int gmres_maxit;  /* 2D coarse correction solves: GMRES from a zero guess with at most this many
                        iterations (default 10, at most 10) ... */

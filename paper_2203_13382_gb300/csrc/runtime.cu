@@ -389,18 +389,96 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   return MGRIT_OK;
 }
 
-mgrit_status read_norm(mgrit_handle* h, int J, double* out) {
+// Enqueues the residual norm's reduction and its read-back (norm and error flag) into pinned memory.
+mgrit_status enqueue_norm(mgrit_handle* h, int J) {
   const int ev = h->phase_begin();
   launch_sum(h->norm_partial, J, h->norm_dev, h->stream);
   h->phase_end(MGRIT_PHASE_MISC, ev, 1);
   MG_CUDA(cudaMemcpyAsync(h->norm_host, h->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   MG_CUDA(cudaMemcpyAsync(h->norm_host + 1, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  return MGRIT_OK;
+}
+
+// Waits for the stream and returns the norm read back by enqueue_norm.
+mgrit_status finish_norm(mgrit_handle* h, double* out) {
   MG_CUDA(cudaStreamSynchronize(h->stream));
   int err = 0;
   std::memcpy(&err, h->norm_host + 1, sizeof(int));
   if (err) return fail(MGRIT_ETIMEOUT, "a bounded device wait gave up (TMA staging did not complete)");
   *out = std::sqrt(h->norm_host[0]);
   return MGRIT_OK;
+}
+
+mgrit_status read_norm(mgrit_handle* h, int J, double* out) {
+  MG_TRY(enqueue_norm(h, J));
+  return finish_norm(h, out);
+}
+
+// One captured cycle: the executable graph, the phase events it records and the launches it issues.
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<std::pair<int, int>> ev;
+  int launches[MGRIT_NUM_PHASES] = {};
+  int64_t total = 0;
+  ~CycleGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+// Runs `body` (which enqueues one cycle on the handle's stream) as a CUDA graph: captured on first use,
+// replayed afterwards.  If the capture fails the body runs directly (same kernels) and *graph_ok is
+// cleared so later cycles do too.
+template <class F>
+mgrit_status run_cycle(mgrit_handle* h, CycleGraph& G, bool* graph_ok, F&& body) {
+  if (!*graph_ok) return body();
+  if (!G.exec) {
+    const size_t ev0 = h->ev_used.size();
+    int pl0[MGRIT_NUM_PHASES];
+    std::memcpy(pl0, h->phase_launches, sizeof(pl0));
+    const int64_t cl0 = h->call_launches;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      *graph_ok = false;
+      return body();
+    }
+    const mgrit_status st = body();
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    cudaError_t ei = cudaErrorUnknown;
+    if (st == MGRIT_OK && e == cudaSuccess && g) ei = cudaGraphInstantiate(&G.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    // the capture executed nothing: undo its bookkeeping, keep it for the replays
+    G.ev.assign(h->ev_used.begin() + ev0, h->ev_used.end());
+    h->ev_used.resize(ev0);
+    for (int i = 0; i < MGRIT_NUM_PHASES; ++i) {
+      G.launches[i] = h->phase_launches[i] - pl0[i];
+      h->phase_launches[i] = pl0[i];
+    }
+    G.total = h->call_launches - cl0;
+    h->call_launches = cl0;
+    if (st != MGRIT_OK) return st;
+    if (e != cudaSuccess || ei != cudaSuccess) {
+      cudaGetLastError();
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+      G.ev.clear();
+      *graph_ok = false;
+      return body();
+    }
+  }
+  MG_CUDA(cudaGraphLaunch(G.exec, h->stream));
+  for (int i = 0; i < MGRIT_NUM_PHASES; ++i) h->phase_launches[i] += G.launches[i];
+  h->call_launches += G.total;
+  return MGRIT_OK;
+}
+
+// After the stream synchronised: add the replayed graph's phase times.
+void collect_graph_times(mgrit_handle* h, const CycleGraph& G) {
+  for (auto& pr : G.ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[pr.second], h->ev_pool[pr.second + 1]) == cudaSuccess)
+      h->phase_ms[pr.first] += ms;
+  }
 }
 
 }  // namespace
@@ -418,7 +496,7 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->max_coarsest = 1;
   opt->m_first = 0;
   opt->coarse_fp64 = 0;
-  opt->use_graph = 0;
+  opt->use_graph = 1;
   opt->profile = 0;
   opt->gmres_maxit = 10;
   opt->gmres_rtol = 1e-2;
@@ -646,7 +724,8 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
   int iters = 0;
   bool converged = false;
   mgrit_status status = MGRIT_OK;
-  for (int k = 0; k < h->opt.max_iter; ++k) {
+  // one cycle's device work (FP64: reads X, writes Y; the caller swaps the pointers afterwards)
+  auto cycle = [&](int k) -> mgrit_status {
     if (!fp32) {
       // FCF relaxation on level 0; the correction of the previous cycle is fused into the first pass
       RelaxArgs a = args0();
@@ -675,7 +754,6 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
       a.norm_partial = h->norm_partial;
       MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_RES));
       MG_TRY(coarse_cycle(h, 1));
-      std::swap(h->X, h->Y);
     } else {
       // FP64 residual of the current iterate (F-relaxation + C-point residual)
       RelaxArgs a = args0();
@@ -711,7 +789,19 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
         h->phase_end(MGRIT_PHASE_MISC, ev, 1);
       }
     }
-    MG_TRY(read_norm(h, J, &rk));
+    return enqueue_norm(h, J);
+  };
+  // CUDA graphs (use_graph): FP32-bulk cycles are identical; FP64 cycles k >= 1 alternate X / Y
+  CycleGraph graphs[2];
+  bool graph_ok = h->opt.use_graph != 0;
+  for (int k = 0; k < h->opt.max_iter; ++k) {
+    const bool graphed = graph_ok && (fp32 || k >= 1);
+    CycleGraph& G = graphs[fp32 ? 0 : (k & 1)];
+    if (graphed) MG_TRY(run_cycle(h, G, &graph_ok, [&] { return cycle(k); }));
+    else MG_TRY(cycle(k));
+    MG_TRY(finish_norm(h, &rk));
+    if (graphed && graph_ok) collect_graph_times(h, G);
+    if (!fp32) std::swap(h->X, h->Y);
     hist.push_back(rk);
     iters = k + 1;
     if (k == 0) r0 = rk;

@@ -157,3 +157,22 @@ def test_setup_rejects_bad_arguments_on_gpu():
         mg.mgrit_setup(64, 100, 3, 8, levels=3)  # 100 not divisible
     with pytest.raises(mg.MgritError):
         mg.mgrit_setup(64, 64, 4, 4)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_matches_direct_launches(precision):
+    """use_graph = 1 (cycles captured once and replayed) and 0 (launched one by one) give identical
+    solutions and residual histories."""
+    case = CASES[2]
+    nx, nt = case[0], case[1]
+    u0 = torch.from_numpy(W.u0_bumps_1d(nx, W.SEED_C2_BUMPS, 3)).cuda()
+    U0 = torch.from_numpy(W.initial_iterate(nt, nx)).cuda()
+    res = []
+    for g in (0, 1):
+        h = gpu_handle(*case, precision=precision, use_graph=g, profile=1)
+        out, st = h.solve(u0, U0)
+        res.append((out.cpu(), st))
+    assert torch.equal(res[0][0], res[1][0])
+    assert res[0][1]["iterations"] == res[1][1]["iterations"]
+    assert res[0][1]["history"] == res[1][1]["history"]
+    assert res[0][1]["kernel_launches"] == res[1][1]["kernel_launches"]

@@ -105,3 +105,16 @@ def test_mgrit_2d(case, precision):
     tol = 1e-9 if precision == 0 else 1e-5
     assert rel(out.cpu().numpy(), seq) < tol
     assert rel(ref.U.reshape(nt + 1, -1), seq) < 1e-9
+
+
+def test_graph_replay_matches_direct_launches_2d():
+    case = CASES[1]
+    nx, nt = case[0], case[1]
+    u0 = torch.from_numpy(W.u0_bumps_2d(nx, W.SEED_C3_BUMPS, 5).ravel().copy()).cuda()
+    U0 = torch.from_numpy(W.initial_iterate(nt, nx * nx)).cuda()
+    outs = []
+    for g in (0, 1):
+        h = gpu(*case, precision=1, use_graph=g)
+        out, st = h.solve(u0, U0)
+        outs.append((out.cpu(), st["iterations"]))
+    assert torch.equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
