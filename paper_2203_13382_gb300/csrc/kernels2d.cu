@@ -5,6 +5,8 @@
 //
 // A 2D slice (nx * nx values) does not fit in shared memory, so a relaxation pass is a sequence of
 // launches, one per step index k of the intervals, each updating every interval's slice in global memory.
+#include <cooperative_groups.h>
+
 #include <type_traits>
 
 #include "common.cuh"
@@ -246,6 +248,149 @@ __global__ void __launch_bounds__(kThreadsGmres) k_gmres2d(const double* __restr
   }
 }
 
+// The same GMRES with one system spread over a thread-block cluster of C CTAs (C = gridDim / J): CTA
+// rank r owns the rows [r N / C, (r + 1) N / C) of every vector.  Dot products are reduced across the
+// cluster through distributed shared memory; every CTA adds the C partial sums in rank order, so all
+// of them hold the same value and take the same Givens rotations and stopping decision.  A cluster
+// barrier orders the writes of each new basis vector before M reads neighbouring rows of it.
+template <int B, typename R, bool TRANS>
+__global__ void __launch_bounds__(kThreadsGmres) k_gmres2d_cluster(const double* __restrict__ sigma_x,
+                                                                   const double* __restrict__ sigma_y, int nx, int n0,
+                                                                   int m, int nt_rev, R* __restrict__ bx_all,
+                                                                   R* __restrict__ basis, int kmax, double rtol) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double red[40];
+  __shared__ double part[2];
+  __shared__ double H[11][10];
+  __shared__ double cs[10], sn[10], gv[11], yv[10];
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const long long N = (long long)nx * nx;
+  const long long lo = N * rank / C, hi = N * (rank + 1) / C;
+  const int j = blockIdx.x / C;
+  const int n = nt_rev > 0 ? nt_rev - 1 - (n0 + j * m) : n0 + j * m;
+  const double* sx = sigma_x + (size_t)n * N;
+  const double* sy = sigma_y + (size_t)n * N;
+  R* b = bx_all + (size_t)j * N;
+  R* V = basis + (size_t)j * (kmax + 1) * N;
+  int slot = 0;
+  // cluster-wide dot product of rows [lo, hi)
+  auto dot = [&](const R* x, const R* y) -> double {
+    R sacc = (R)0;
+    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) sacc += x[q] * y[q];
+    const double t = block_sum((double)sacc, red);
+    if (threadIdx.x == 0) part[slot] = t;
+    cl.sync();
+    double tot = 0.0;
+    for (int r = 0; r < C; ++r) tot += *cl.map_shared_rank(&part[slot], (unsigned)r);
+    slot ^= 1;
+    return tot;
+  };
+  const double beta = sqrt(dot(b, b));
+  if (beta == 0.0) {  // the same decision in every CTA; wait until no CTA reads this one's partials
+    cl.sync();
+    return;
+  }
+  const R ib = (R)(1.0 / beta);
+  for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) V[q] = b[q] * ib;
+  if (threadIdx.x == 0) {
+    gv[0] = beta;
+    for (int t = 1; t <= kmax; ++t) gv[t] = 0.0;
+  }
+  int kused = 0;
+  for (int kk = 0; kk < kmax; ++kk) {
+    R* vk = V + (size_t)kk * N;
+    R* w = V + (size_t)(kk + 1) * N;
+    cl.sync();  // v_k complete in every CTA before M reads its neighbouring rows
+    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x)
+      w[q] = TRANS ? apply_MT<B, R>(vk, sx, sy, q, nx) : apply_M<B, R>(vk, sx, sy, q, nx);
+    __syncthreads();
+    for (int t = 0; t <= kk; ++t) {  // modified Gram-Schmidt
+      const R* vt = V + (size_t)t * N;
+      const double h = dot(vt, w);
+      for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) w[q] -= (R)h * vt[q];
+      if (threadIdx.x == 0) H[t][kk] = h;
+      __syncthreads();
+    }
+    const double hn = sqrt(dot(w, w));
+    if (threadIdx.x == 0) {
+      H[kk + 1][kk] = hn;
+      for (int t = 0; t < kk; ++t) {
+        const double a = H[t][kk], c = H[t + 1][kk];
+        H[t][kk] = cs[t] * a + sn[t] * c;
+        H[t + 1][kk] = -sn[t] * a + cs[t] * c;
+      }
+      const double a = H[kk][kk], c = H[kk + 1][kk];
+      const double r = sqrt(a * a + c * c);
+      cs[kk] = r > 0.0 ? a / r : 1.0;
+      sn[kk] = r > 0.0 ? c / r : 0.0;
+      H[kk][kk] = r;
+      H[kk + 1][kk] = 0.0;
+      gv[kk + 1] = -sn[kk] * gv[kk];
+      gv[kk] = cs[kk] * gv[kk];
+      red[36] = fabs(gv[kk + 1]);
+    }
+    __syncthreads();
+    kused = kk + 1;
+    if (red[36] <= rtol * beta || !(hn > 0.0)) break;
+    const R ihn = (R)(1.0 / hn);
+    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) w[q] = w[q] * ihn;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int t = kused - 1; t >= 0; --t) {
+      double v = gv[t];
+      for (int c = t + 1; c < kused; ++c) v -= H[t][c] * yv[c];
+      yv[t] = v / H[t][t];
+    }
+  }
+  __syncthreads();
+  R yr[10];
+  for (int t = 0; t < kused; ++t) yr[t] = (R)yv[t];
+  for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
+    R x = (R)0;
+    for (int t = 0; t < kused; ++t) x += yr[t] * V[(size_t)t * N + q];
+    b[q] = x;
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// J systems of step index n0 (+ j m): one CTA each, or, when J leaves SMs idle, a cluster of CTAs each.
+template <int B, typename R, bool TRANS>
+cudaError_t launch_gmres(const double* sig, long long N, int nt, int nx, int n0, int m, int ntr, R* b, R* basis,
+                         int kmax, double rtol, int J, cudaStream_t st) {
+  int C = 1;
+  while (C < 16 && J * C * 2 <= 152) C *= 2;
+  if (C > 1) {
+    auto kern = k_gmres2d_cluster<B, R, TRANS>;
+    cudaError_t e = C > 8 ? cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)
+                          : cudaSuccess;
+    for (; C > 1 && e == cudaSuccess; C /= 2) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(J * C));
+      cfg.blockDim = dim3(kThreadsGmres);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        continue;  // try a smaller cluster
+      }
+      return cudaLaunchKernelEx(&cfg, kern, sig, sig + (size_t)nt * N, nx, n0, m, ntr, b, basis, kmax, rtol);
+    }
+    cudaGetLastError();
+  }
+  k_gmres2d<B, R, TRANS><<<J, kThreadsGmres, 0, st>>>(sig, sig + (size_t)nt * N, nx, n0, m, ntr, b, basis, kmax,
+                                                        rtol);
+  return cudaGetLastError();
+}
+
 template <typename R>
 __global__ void k_add_rows(R* __restrict__ dst, const R* __restrict__ g, int m, int k, int n0, long long N,
                            R* __restrict__ fstore) {
@@ -322,13 +467,17 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
       if (coarse) {
         const double* sig = (const double*)T.solver;
         const int B = (T.p + 1) / 2, ntr = T.reverse ? T.nt : 0;
-#define MGRIT_GMT(BB)                                                                                        \
-  k_gmres2d<BB, double, true><<<J, kThreadsGmres, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, ntr, src, \
-                                                        (double*)S.basis, S.kmax, S.rtol)
-        if (B == 1) MGRIT_GMT(1);
-        else if (B == 2) MGRIT_GMT(2);
-        else MGRIT_GMT(3);
-#undef MGRIT_GMT
+        cudaError_t e;
+        if (B == 1)
+          e = launch_gmres<1, double, true>(sig, N, T.nt, T.nx, n_first, m, ntr, src, (double*)S.basis, S.kmax, S.rtol,
+                                            J, st);
+        else if (B == 2)
+          e = launch_gmres<2, double, true>(sig, N, T.nt, T.nx, n_first, m, ntr, src, (double*)S.basis, S.kmax, S.rtol,
+                                            J, st);
+        else
+          e = launch_gmres<3, double, true>(sig, N, T.nt, T.nx, n_first, m, ntr, src, (double*)S.basis, S.kmax, S.rtol,
+                                            J, st);
+        if (e != cudaSuccess) return e;
       }
       if (T.p == 1) k_step2d_T<1><<<grid, kThreads2d, 0, st>>>(T, src, dst, m, k, n0, g, fstore);
       else if (T.p == 3) k_step2d_T<3><<<grid, kThreads2d, 0, st>>>(T, src, dst, m, k, n0, g, fstore);
@@ -346,13 +495,11 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
   if (coarse) {
     const double* sig = (const double*)T.solver;  // sigma_x block then sigma_y block, [nt][N] each
     const int B = (T.p + 1) / 2;
-#define MGRIT_GM(BB)                                                                                      \
-  k_gmres2d<BB, R, false><<<J, kThreadsGmres, 0, st>>>(sig, sig + (size_t)T.nt * N, T.nx, n_first, m, 0, dst, \
-                                                    (R*)S.basis, S.kmax, S.rtol)
-    if (B == 1) MGRIT_GM(1);
-    else if (B == 2) MGRIT_GM(2);
-    else MGRIT_GM(3);
-#undef MGRIT_GM
+    cudaError_t e;
+    if (B == 1) e = launch_gmres<1, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
+    else if (B == 2) e = launch_gmres<2, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
+    else e = launch_gmres<3, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
+    if (e != cudaSuccess) return e;
     k_add_rows<R><<<grid, kThreads2d, 0, st>>>(dst, g, m, k, n0, N, fstore);
   }
   return cudaGetLastError();

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -1149,6 +1150,7 @@ struct mgrit_batch {
     int buf;
     size_t smem;
     size_t region;  // coarse shared region (on-the-fly solve) after the slice buffers
+    int order;      // tile order chosen by the tuner (0: as built, 1: longest first)
   };
   std::vector<Phase> down, up;
   Phase final_post{};
@@ -1164,9 +1166,16 @@ struct mgrit_batch {
   Segment* d_seg = nullptr;
   double* d_norms = nullptr;
   double* h_norms = nullptr;
+  int* h_active = nullptr;    // pinned: uploaded before every cycle
+  Segment* h_seg = nullptr;   // pinned: 3 * nprob segments
+  long long maxn_all = 0;     // largest C-point array of any problem (launch size of the batched axpy)
+  cudaGraphExec_t graph = nullptr;  // one cycle, captured on the first solve (use_graph)
   int final_args_off = 0;
 
   ~mgrit_batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (h_active) cudaFreeHost(h_active);
+    if (h_seg) cudaFreeHost(h_seg);
     for (mgrit_handle* h : hs) delete h;
     cudaFree(d_tabs);
     cudaFree(d_args);
@@ -1181,6 +1190,100 @@ struct mgrit_batch {
 
 namespace {
 
+// Tile order of each relaxation phase, chosen by measurement.  The tiles of one phase carry different
+// work (nx * steps varies 16-fold across a batch); the GPU starts CTAs in launch order, so the order
+// decides the tail.  Candidates: as built (problem by problem) and longest first.  Each is timed on the
+// phase itself (CUDA events, best of two runs after one warm-up; the cycle state is rebuilt by every
+// solve, so these runs leave nothing behind); the faster order is kept.  Choices are cached per
+// batch signature (problem shapes and options), so only the first setup of a batch pays.
+std::mutex& tune_mu() {
+  static std::mutex* m = new std::mutex;
+  return *m;
+}
+std::map<std::string, std::vector<char>>& tune_cache() {
+  static auto* c = new std::map<std::string, std::vector<char>>;
+  return *c;
+}
+
+mgrit_status tune_tile_order(mgrit_batch* b, const mgrit_grid* grids, const mgrit_wavespeed* waves,
+                             const int* orders, const int* ms) {
+  const int nprob = (int)b->hs.size();
+  std::string key;
+  for (int q = 0; q < nprob; ++q) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "%d,%d,%d,%d,%d,%.17g,%.17g,%.17g,%.17g;", grids[q].nx, grids[q].nt, orders[q],
+                  ms[q], waves[q].kind, waves[q].a, waves[q].k, waves[q].a2, grids[q].cfl);
+    key += buf;
+  }
+  key += std::to_string(b->opt.max_coarsest) + "," + std::to_string(b->opt.m_first);
+  std::vector<mgrit_batch::Phase*> phases;
+  for (auto& ph : b->down)
+    if (ph.kind == 0 && ph.ntiles > 1) phases.push_back(&ph);
+  for (auto& ph : b->up)
+    if (ph.kind == 0 && ph.ntiles > 1) phases.push_back(&ph);
+  auto longest_first = [&](const mgrit_batch::Phase& ph) {
+    std::vector<BatchTile> t(b->tiles.begin() + ph.tile_off, b->tiles.begin() + ph.tile_off + ph.ntiles);
+    std::stable_sort(t.begin(), t.end(), [&](const BatchTile& x, const BatchTile& y) {
+      const long long wx = (long long)b->tabs[x.table].nx * b->args[x.args].nsteps;
+      const long long wy = (long long)b->tabs[y.table].nx * b->args[y.args].nsteps;
+      return wx > wy;
+    });
+    return t;
+  };
+  std::vector<char> choice;
+  {
+    std::lock_guard<std::mutex> lk(tune_mu());
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end() && it->second.size() == phases.size()) choice = it->second;
+  }
+  cudaStream_t s = b->stream;
+  if (choice.empty()) {
+    for (int q = 0; q < nprob; ++q) b->h_active[q] = 1;
+    MG_CUDA(cudaMemcpyAsync(b->d_active, b->h_active, nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    MG_CUDA(cudaEventCreate(&e0));
+    MG_CUDA(cudaEventCreate(&e1));
+    for (mgrit_batch::Phase* ph : phases) {
+      const std::vector<BatchTile> built(b->tiles.begin() + ph->tile_off, b->tiles.begin() + ph->tile_off + ph->ntiles);
+      const std::vector<BatchTile> sorted = longest_first(*ph);
+      float best[2] = {0.f, 0.f};
+      for (int c = 0; c < 2; ++c) {
+        const std::vector<BatchTile>& t = c == 0 ? built : sorted;
+        MG_CUDA(cudaMemcpyAsync(b->d_tiles + ph->tile_off, t.data(), t.size() * sizeof(BatchTile),
+                                cudaMemcpyHostToDevice, s));
+        float bt = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          MG_CUDA(cudaEventRecord(e0, s));
+          MG_CUDA(launch_relax_batched(b->d_tabs, b->d_args, b->d_tiles + ph->tile_off, ph->ntiles, b->d_active,
+                                       ph->is_double, ph->coarse, ph->buf, ph->smem, s));
+          MG_CUDA(cudaEventRecord(e1, s));
+          MG_CUDA(cudaEventSynchronize(e1));
+          float ms_ = 0.f;
+          MG_CUDA(cudaEventElapsedTime(&ms_, e0, e1));
+          if (rep > 0) bt = std::min(bt, ms_);
+        }
+        best[c] = bt;
+      }
+      choice.push_back(best[1] < best[0] ? 1 : 0);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(tune_mu());
+    tune_cache()[key] = choice;
+  }
+  for (size_t i = 0; i < phases.size(); ++i) {
+    mgrit_batch::Phase* ph = phases[i];
+    if (choice[i]) {
+      const std::vector<BatchTile> t = longest_first(*ph);
+      std::copy(t.begin(), t.end(), b->tiles.begin() + ph->tile_off);
+    }
+    ph->order = choice[i];
+  }
+  MG_CUDA(cudaMemcpyAsync(b->d_tiles, b->tiles.data(), b->tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  return MGRIT_OK;
+}
+
 size_t batched_smem(int buf, int is_double, size_t region) {
   size_t b = 2 * (size_t)buf * (is_double ? 8 : 4) + 64 * sizeof(double);
   if (region) b = ((b + 127) & ~(size_t)127) + region;
@@ -1191,7 +1294,7 @@ size_t batched_smem(int buf, int is_double, size_t region) {
 // args[args_of(q)].
 template <class F>
 mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F per_problem) {
-  mgrit_batch::Phase ph{0, is_double, coarse, (int)b->tiles.size(), 0, 0, 0, 0};
+  mgrit_batch::Phase ph{0, is_double, coarse, (int)b->tiles.size(), 0, 0, 0, 0, 0};
   for (int q = 0; q < (int)b->hs.size(); ++q) {
     LevelTables T;
     RelaxArgs a;
@@ -1286,7 +1389,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
         return true;
       }));
     // coarsest levels reached at this depth: sequential solves
-    mgrit_batch::Phase ph{1, 0, 1, (int)b->tiles.size(), 0, 0, 0, 0};
+    mgrit_batch::Phase ph{1, 0, 1, (int)b->tiles.size(), 0, 0, 0, 0, 0};
     for (int q = 0; q < nprob; ++q) {
       mgrit_handle* h = b->hs[q];
       if ((int)h->levels.size() - 1 != d) continue;
@@ -1346,9 +1449,19 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
        cudaMalloc((void**)&b->d_seg, 3 * (size_t)nprob * sizeof(Segment)) == cudaSuccess &&
        cudaMalloc((void**)&b->d_norms, nprob * sizeof(double)) == cudaSuccess &&
        cudaMallocHost((void**)&b->h_norms, nprob * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&b->h_active, nprob * sizeof(int)) == cudaSuccess &&
+       cudaMallocHost((void**)&b->h_seg, 3 * (size_t)nprob * sizeof(Segment)) == cudaSuccess;
   if (!ok || cudaStreamSynchronize(b->stream) != cudaSuccess) {
     delete b;
     return fail(MGRIT_ENOMEM, "batched workspace allocation failed");
+  }
+  for (mgrit_handle* h : b->hs) b->maxn_all = std::max(b->maxn_all, (long long)(h->J1() + 1) * h->npts);
+  {
+    const mgrit_status st = tune_tile_order(b, grids, waves, orders, ms);
+    if (st != MGRIT_OK) {
+      delete b;
+      return st;
+    }
   }
   (void)t0;
   *out = b;
@@ -1380,7 +1493,6 @@ mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, cons
   std::vector<int> active(nprob, 1), iters(nprob, 0), conv(nprob, 0);
   std::vector<double> r0(nprob, 0.0), rk(nprob, 0.0);
   std::vector<std::vector<double>> hist(nprob);
-  std::vector<Segment> seg(3 * (size_t)nprob);
   auto run = [&](const mgrit_batch::Phase& ph) -> mgrit_status {
     if (ph.ntiles == 0) return MGRIT_OK;
     cudaError_t e = ph.kind == 0
@@ -1391,25 +1503,46 @@ mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, cons
     if (e != cudaSuccess) return fail(MGRIT_ECUDA, std::string("batched phase: ") + cudaGetErrorString(e));
     return MGRIT_OK;
   };
+  // one cycle of every active problem; the active mask and the segment table are read from device memory
+  // (uploaded before each cycle), so the cycle is the same launch sequence every time
+  auto cycle = [&]() -> mgrit_status {
+    for (auto& ph : b->down) MG_TRY(run(ph));  // down[0]: FP64 residual of every iterate, e_C = r
+    for (auto& ph : b->up) MG_TRY(run(ph));
+    launch_axpy_batched(5, b->d_seg + nprob, nprob, b->maxn_all, s);  // u_C += r + E_1
+    launch_sum_batched(b->d_seg + 2 * nprob, nprob, s);
+    MG_CUDA(cudaMemcpyAsync(b->h_norms, b->d_norms, nprob * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return MGRIT_OK;
+  };
+  bool graph_ok = b->opt.use_graph != 0;
   int n_active = nprob;
   for (int k = 0; k < b->opt.max_iter && n_active > 0; ++k) {
-    long long maxn = 0;
     for (int q = 0; q < nprob; ++q) {
       mgrit_handle* h = b->hs[q];
       const long long n = active[q] ? (long long)(h->J1() + 1) * h->npts : 0;
-      maxn = std::max(maxn, n);
-      seg[q] = Segment{nullptr, nullptr, nullptr, 0};
-      seg[nprob + q] = Segment{h->r64, h->X, h->levels[1].E, n};
-      seg[2 * nprob + q] = Segment{h->norm_partial, b->d_norms + q, nullptr, active[q] ? (long long)h->J1() : 0};
+      b->h_active[q] = active[q];
+      b->h_seg[q] = Segment{nullptr, nullptr, nullptr, 0};
+      b->h_seg[nprob + q] = Segment{h->r64, h->X, h->levels[1].E, n};
+      b->h_seg[2 * nprob + q] = Segment{h->norm_partial, b->d_norms + q, nullptr, active[q] ? (long long)h->J1() : 0};
     }
-    MG_CUDA(cudaMemcpyAsync(b->d_active, active.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
-    MG_CUDA(cudaMemcpyAsync(b->d_seg, seg.data(), seg.size() * sizeof(Segment), cudaMemcpyHostToDevice, s));
-    MG_TRY(run(b->down[0]));                                  // FP64 residual of every iterate, e_C = r
-    for (size_t ph = 1; ph < b->down.size(); ++ph) MG_TRY(run(b->down[ph]));
-    for (auto& ph : b->up) MG_TRY(run(ph));
-    launch_axpy_batched(5, b->d_seg + nprob, nprob, maxn, s); // u_C += r + E_1
-    launch_sum_batched(b->d_seg + 2 * nprob, nprob, s);
-    MG_CUDA(cudaMemcpyAsync(b->h_norms, b->d_norms, nprob * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaMemcpyAsync(b->d_active, b->h_active, nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+    MG_CUDA(cudaMemcpyAsync(b->d_seg, b->h_seg, 3 * (size_t)nprob * sizeof(Segment), cudaMemcpyHostToDevice, s));
+    if (graph_ok && !b->graph) {  // capture the cycle once
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const mgrit_status st = cycle();
+        const cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st != MGRIT_OK) {
+          if (g) cudaGraphDestroy(g);
+          return st;
+        }
+        if (e != cudaSuccess || !g || cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) b->graph = nullptr;
+        if (g) cudaGraphDestroy(g);
+      }
+      cudaGetLastError();
+      if (!b->graph) graph_ok = false;
+    }
+    if (graph_ok) MG_CUDA(cudaGraphLaunch(b->graph, s));
+    else MG_TRY(cycle());
     MG_CUDA(cudaStreamSynchronize(s));
     for (int q = 0; q < nprob; ++q) {
       if (!active[q]) continue;
@@ -1429,8 +1562,8 @@ mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, cons
     }
   }
   // every problem: post F-relaxation into its output
-  std::vector<int> all(nprob, 1);
-  MG_CUDA(cudaMemcpyAsync(b->d_active, all.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+  for (int q = 0; q < nprob; ++q) b->h_active[q] = 1;
+  MG_CUDA(cudaMemcpyAsync(b->d_active, b->h_active, nprob * sizeof(int), cudaMemcpyHostToDevice, s));
   MG_TRY(run(b->final_post));
   MG_CUDA(cudaStreamSynchronize(s));
   bool all_conv = true;
