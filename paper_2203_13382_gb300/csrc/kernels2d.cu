@@ -27,12 +27,17 @@ constexpr int dstencil_int(int o) {
 }
 constexpr int kThreadsGmres = 1024;  // one CTA per system: more loads in flight per SM
 
-// Weights of one axis for element pt of step row n.  FP32: from the stored eps; FP64: from the offset.
+// Weights of one axis for element pt of step row n.  FP32: from the stored eps; FP64: the weight table
+// (or, without one, from the offset).
 template <int P, typename R>
 __device__ __forceinline__ void axis_weights(const LevelTables& T, int comp, int n, long long pt, R (&w)[P + 1]) {
   const long long off = ((long long)comp * T.nt + n) * T.npts + pt;
   if constexpr (std::is_same<R, float>::value) {
     lagrange_weights<P, float>(__ldg(T.eps32 + off), w);
+  } else if (T.w64) {  // table [comp][n][a][pt]
+    const double* wr = T.w64 + ((size_t)comp * T.nt + n) * (P + 1) * T.npts + pt;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) w[a] = __ldg(wr + (size_t)a * T.npts);
   } else {
     const double s = __ldg(T.s64 + off);
     double e = s - floor(s);
@@ -94,6 +99,9 @@ __global__ void __launch_bounds__(kThreads2d) k_step2d_T(LevelTables T, const do
   const int* bp = T.bperm + (size_t)row * N;
   const double* sx = T.s64 + (size_t)row * N;
   const double* sy = T.s64 + ((size_t)T.nt + row) * N;
+  // weight tables of the two axes ([comp][n][a][pt]); without them the weights follow from the offsets
+  const double* wx = T.w64 ? T.w64 + (size_t)row * (P + 1) * N : nullptr;
+  const double* wy = T.w64 ? T.w64 + ((size_t)T.nt + row) * (P + 1) * N : nullptr;
   const double* s = src + (size_t)j * N;
   double acc = 0.0;
 #pragma unroll
@@ -105,12 +113,20 @@ __global__ void __launch_bounds__(kThreads2d) k_step2d_T(LevelTables T, const do
       const int q1 = __ldg(bs + key + 1);
       for (int q = __ldg(bs + key); q < q1; ++q) {
         const int i = __ldg(bp + q);
-        double ex = __ldg(sx + i), ey = __ldg(sy + i);
-        ex -= floor(ex);
-        if (ex >= 1.0) ex -= 1.0;
-        ey -= floor(ey);
-        if (ey >= 1.0) ey -= 1.0;
-        acc += lagrange_basis<P>(ex, a) * lagrange_basis<P>(ey, b) * __ldg(s + i);
+        double wa, wb;
+        if (wx) {
+          wa = __ldg(wx + (size_t)a * N + i);
+          wb = __ldg(wy + (size_t)b * N + i);
+        } else {
+          double ex = __ldg(sx + i), ey = __ldg(sy + i);
+          ex -= floor(ex);
+          if (ex >= 1.0) ex -= 1.0;
+          ey -= floor(ey);
+          if (ey >= 1.0) ey -= 1.0;
+          wa = lagrange_basis<P>(ex, a);
+          wb = lagrange_basis<P>(ey, b);
+        }
+        acc += wa * wb * __ldg(s + i);
       }
     }
   }

@@ -560,7 +560,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     L.is_double = fp32 ? 0 : 1;
     if ((st = h->alloc(&L.s64, rows)) != MGRIT_OK) return cleanup_fail(st);
     if ((st = h->alloc(&L.shift, rows)) != MGRIT_OK) return cleanup_fail(st);
-    const bool need64 = (!fp32 || l == 0) && dim == 1;  // 2D FP64 weights are formed on the fly
+    const bool need64 = !fp32 || l == 0;  // FP64 levels read precomputed weights (2D: per axis)
     const bool need32 = fp32;
     if (need64 && (st = h->alloc(&L.w64, rows * (p + 1))) != MGRIT_OK) return cleanup_fail(st);
     if (need32 && (st = h->alloc(&L.eps32, rows)) != MGRIT_OK) return cleanup_fail(st);
@@ -654,8 +654,9 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     {
       const int ev = h->phase_begin();
       for (int c = 0; c < dim; ++c)
-        launch_build_tables(L.s64 + c * blk, L.nt, nx, np, p, L.shift + c * blk, L.w64,
-                            L.eps32 ? L.eps32 + c * blk : nullptr, s);
+        launch_build_tables(L.s64 + c * blk, L.nt, nx, np, p, L.shift + c * blk,
+                            L.w64 ? L.w64 + (size_t)c * blk * (p + 1) : nullptr, L.eps32 ? L.eps32 + c * blk : nullptr,
+                            s);
       h->phase_end(MGRIT_PHASE_TABLES, ev, dim);
     }
     if (l > 0 && L.solver) {
