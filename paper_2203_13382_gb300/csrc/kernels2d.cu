@@ -27,6 +27,12 @@ constexpr int dstencil_int(int o) {
 }
 constexpr int kThreadsGmres = 1024;  // one CTA per system: more loads in flight per SM
 
+// FP64 systems keep ten FP64 projection sums a thread: 512 threads (128 registers) instead of 1024.
+template <typename R>
+constexpr int gmres_threads() {
+  return std::is_same<R, double>::value ? 512 : kThreadsGmres;
+}
+
 // Weights of one axis for element pt of step row n.  FP32: from the stored eps; FP64: the weight table
 // (or, without one, from the offset).
 template <int P, typename R>
@@ -181,17 +187,69 @@ __device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, d
   return t;
 }
 
+// Classical Gram-Schmidt projections h_t = <v_t, w>, t = 0..kk (kk < 10), of the rows [lo, hi) in one
+// pass over w; per-thread sums in R, reduced over the CTA in FP64 into hsum[0..kk] (all threads see them).
+template <typename R>
+__device__ __forceinline__ void cta_multi_dot(const R* V, long long N, const R* w, int kk, long long lo, long long hi,
+                                              double (*wpart)[11], double* hsum) {
+  R acc[10];
+#pragma unroll
+  for (int t = 0; t < 10; ++t) acc[t] = (R)0;
+  for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
+    const R wq = w[q];
+#pragma unroll
+    for (int t = 0; t < 10; ++t)
+      if (t <= kk) acc[t] += V[(size_t)t * N + q] * wq;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < 10; ++t) {
+    if (t > kk) break;
+    double v = (double)acc[t];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wpart[warp][t] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x <= kk) {
+    double v = 0.0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < nw; ++k) v += wpart[k][threadIdx.x];
+    hsum[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
+// w -= sum_t h_t v_t over the rows [lo, hi).
+template <typename R>
+__device__ __forceinline__ void cta_subtract_projections(const R* V, long long N, R* w, int kk, long long lo,
+                                                         long long hi, const double* h) {
+  R hr[10];
+#pragma unroll
+  for (int t = 0; t < 10; ++t) hr[t] = t <= kk ? (R)h[t] : (R)0;
+  for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
+    R v = w[q];
+#pragma unroll
+    for (int t = 0; t < 10; ++t)
+      if (t <= kk) v -= hr[t] * V[(size_t)t * N + q];
+    w[q] = v;
+  }
+}
+
 // One CTA per interval j: b (= rhs, in place -> solution) of the system of step n(j) = n0 + j*m
-// (row nt_rev - 1 - n(j) when nt_rev > 0; TRANS solves with M^T).  basis: [J][kmax + 1][N] scratch.  GMRES (Arnoldi with modified Gram-Schmidt, Givens rotations), zero
-// initial guess, stop when the least-squares residual <= rtol ||b|| or after kmax iterations.
+// (row nt_rev - 1 - n(j) when nt_rev > 0; TRANS solves with M^T).  basis: [J][kmax + 1][N] scratch.
+// GMRES (Arnoldi with classical Gram-Schmidt: the projections on all basis vectors in one pass over w,
+// then one update pass; Givens rotations), zero initial guess, stop when the least-squares residual
+// <= rtol ||b|| or after kmax iterations.
 template <int B, typename R, bool TRANS>
-__global__ void __launch_bounds__(kThreadsGmres) k_gmres2d(const double* __restrict__ sigma_x,
+__global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const double* __restrict__ sigma_x,
                                                         const double* __restrict__ sigma_y, int nx, int n0, int m,
                                                         int nt_rev, R* __restrict__ bx_all, R* __restrict__ basis,
                                                         int kmax, double rtol) {
   __shared__ double red[40];
   __shared__ double H[11][10];
   __shared__ double cs[10], sn[10], gv[11], yv[10];
+  __shared__ double wpart[32][11];
+  __shared__ double hsum[11];
   const long long N = (long long)nx * nx;
   const int j = blockIdx.x;
   const int n = nt_rev > 0 ? nt_rev - 1 - (n0 + j * m) : n0 + j * m;
@@ -215,13 +273,11 @@ __global__ void __launch_bounds__(kThreadsGmres) k_gmres2d(const double* __restr
     for (long long q = threadIdx.x; q < N; q += blockDim.x)
       w[q] = TRANS ? apply_MT<B, R>(vk, sx, sy, q, nx) : apply_M<B, R>(vk, sx, sy, q, nx);
     __syncthreads();
-    for (int t = 0; t <= kk; ++t) {  // modified Gram-Schmidt
-      const R* vt = V + (size_t)t * N;
-      const double h = cta_dot<R>(vt, w, N, red);
-      for (long long q = threadIdx.x; q < N; q += blockDim.x) w[q] -= (R)h * vt[q];
-      if (threadIdx.x == 0) H[t][kk] = h;
-      __syncthreads();
-    }
+    // classical Gram-Schmidt: all projections in one pass, then one update pass
+    cta_multi_dot<R>(V, N, w, kk, 0, N, wpart, hsum);
+    cta_subtract_projections<R>(V, N, w, kk, 0, N, hsum);
+    if ((int)threadIdx.x <= kk) H[threadIdx.x][kk] = hsum[threadIdx.x];
+    __syncthreads();
     const double hn = sqrt(cta_dot<R>(w, w, N, red));
     if (threadIdx.x == 0) {
       H[kk + 1][kk] = hn;
@@ -270,7 +326,7 @@ __global__ void __launch_bounds__(kThreadsGmres) k_gmres2d(const double* __restr
 // of them hold the same value and take the same Givens rotations and stopping decision.  A cluster
 // barrier orders the writes of each new basis vector before M reads neighbouring rows of it.
 template <int B, typename R, bool TRANS>
-__global__ void __launch_bounds__(kThreadsGmres) k_gmres2d_cluster(const double* __restrict__ sigma_x,
+__global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const double* __restrict__ sigma_x,
                                                                    const double* __restrict__ sigma_y, int nx, int n0,
                                                                    int m, int nt_rev, R* __restrict__ bx_all,
                                                                    R* __restrict__ basis, int kmax, double rtol) {
@@ -278,8 +334,11 @@ __global__ void __launch_bounds__(kThreadsGmres) k_gmres2d_cluster(const double*
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double red[40];
   __shared__ double part[2];
+  __shared__ double mpart[2][11];
   __shared__ double H[11][10];
   __shared__ double cs[10], sn[10], gv[11], yv[10];
+  __shared__ double wpart[32][11];
+  __shared__ double hsum[11];
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const long long N = (long long)nx * nx;
   const long long lo = N * rank / C, hi = N * (rank + 1) / C;
@@ -321,13 +380,20 @@ __global__ void __launch_bounds__(kThreadsGmres) k_gmres2d_cluster(const double*
     for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x)
       w[q] = TRANS ? apply_MT<B, R>(vk, sx, sy, q, nx) : apply_M<B, R>(vk, sx, sy, q, nx);
     __syncthreads();
-    for (int t = 0; t <= kk; ++t) {  // modified Gram-Schmidt
-      const R* vt = V + (size_t)t * N;
-      const double h = dot(vt, w);
-      for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) w[q] -= (R)h * vt[q];
-      if (threadIdx.x == 0) H[t][kk] = h;
-      __syncthreads();
+    // classical Gram-Schmidt: all projections of this CTA's rows in one pass, one cluster reduction
+    cta_multi_dot<R>(V, N, w, kk, lo, hi, wpart, hsum);
+    if ((int)threadIdx.x <= kk) mpart[slot][threadIdx.x] = hsum[threadIdx.x];
+    cl.sync();
+    if ((int)threadIdx.x <= kk) {
+      double v = 0.0;
+      for (int r = 0; r < C; ++r) v += cl.map_shared_rank(&mpart[slot][0], (unsigned)r)[threadIdx.x];
+      hsum[threadIdx.x] = v;
+      H[threadIdx.x][kk] = v;
     }
+    slot ^= 1;
+    __syncthreads();
+    cta_subtract_projections<R>(V, N, w, kk, lo, hi, hsum);
+    __syncthreads();
     const double hn = sqrt(dot(w, w));
     if (threadIdx.x == 0) {
       H[kk + 1][kk] = hn;
@@ -384,7 +450,7 @@ cudaError_t launch_gmres(const double* sig, long long N, int nt, int nx, int n0,
     for (; C > 1 && e == cudaSuccess; C /= 2) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)(J * C));
-      cfg.blockDim = dim3(kThreadsGmres);
+      cfg.blockDim = dim3(gmres_threads<R>());
       cfg.stream = st;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -402,8 +468,8 @@ cudaError_t launch_gmres(const double* sig, long long N, int nt, int nx, int n0,
     }
     cudaGetLastError();
   }
-  k_gmres2d<B, R, TRANS><<<J, kThreadsGmres, 0, st>>>(sig, sig + (size_t)nt * N, nx, n0, m, ntr, b, basis, kmax,
-                                                        rtol);
+  k_gmres2d<B, R, TRANS><<<J, gmres_threads<R>(), 0, st>>>(sig, sig + (size_t)nt * N, nx, n0, m, ntr, b, basis,
+                                                             kmax, rtol);
   return cudaGetLastError();
 }
 
