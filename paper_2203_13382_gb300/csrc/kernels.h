@@ -32,6 +32,11 @@ void launch_backtrack_2d(const double* sx_prev, const double* sy_prev, const dou
 void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, uint16_t* shift, double* w64,
                          float* eps32, cudaStream_t st);
 
+// Block-PCR coefficients of the on-the-fly FP32 correction solve (p <= 3): per step, from the FP32 sigma
+// rows [nt][nx], record_floats(nx, p) floats into out [nt][record].
+unsigned pcr_record_size(int nx, int p);
+cudaError_t launch_pcr_coef(const float* sig32, int nt, int nx, int p, float* out, cudaStream_t st);
+
 // Factorisation of M = I - diag(sigma) D_{p+1} (periodic, half-bandwidth b = (p+1)/2) for each of nt
 // steps (layout: solver_layout.cuh).  Output per step: solver_reals(nx, p) values of type double
 // (is_double = 1) or float.  flag (device int) is set to 1 if a pivot is too small.  Returns the number
@@ -80,6 +85,10 @@ struct LevelTables {
   int gather_stage;
   int otf;
   int* err;
+  // otf levels with p <= 3: the block-PCR coefficients of every step (relax_kernels.cu
+  // pcr_record_floats floats a step, FP32), staged per step into shared memory; NULL: formed on the fly
+  const float* pcr;
+  unsigned pcr_floats;
   // adjoint: trans = 1 applies Phi^T (coarse: (M^{-1} S)^T = S^T M^{-T}, `solver` then holds the
   // factorisation of M^T); reverse = 1 maps step n to table row nt - 1 - n; frange[row] = floor range.
   int trans;

@@ -523,6 +523,351 @@ __device__ __forceinline__ void corr_solve_otf(float* __restrict__ x, const floa
   __syncthreads();
 }
 
+// ---- precomputed reduction coefficients of the on-the-fly solve (FP32 coarse levels, B <= 2) --------
+//
+// Only the right-hand side of the block PCR changes between applications of M^{-1}: the coefficients
+// alpha_t = -L_k D_{k-d}^{-1}, gamma_t = -U_k D_{k+d}^{-1} of every level t and the final (L+D+U)^{-1}
+// depend on sigma alone.  They are formed once per step (the same FP32 arithmetic as corr_solve_otf)
+// and stored as [t][alpha | gamma][B*B][P] then fin [B*B][P], partition fastest, padded to 16 bytes;
+// the solve stages the record of each step into shared memory by TMA and runs the PCR on g only.
+
+MGRIT_HD unsigned pcr_record_floats(int nx, int p) {
+  const int B = (p + 1) / 2, PR = B <= 2 ? 16 : 8, P = nx / PR;
+  int T = 0;
+  while ((1 << T) < P) ++T;
+  const unsigned n = (unsigned)((2 * T + 1) * B * B * P);
+  return (n + 3u) & ~3u;
+}
+
+// One CTA per step row (P threads): the matrix part of corr_solve_otf, storing the coefficients.
+template <int B, int PR>
+__global__ void __launch_bounds__(512) k_pcr_coef(const float* __restrict__ sig_all, int nx, float* __restrict__ out_all,
+                                                  unsigned stride) {
+  constexpr int Q = PR - B, BB = B * B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* X = reinterpret_cast<float*>(smem_raw);
+  const int P = nx / PR;
+  int T = 0;
+  while ((1 << T) < P) ++T;
+  const int k = threadIdx.x;
+  const bool act = k < P;
+  const int g0 = k * PR;
+  const float* sig = sig_all + (size_t)blockIdx.x * nx;
+  float* out = out_all + (size_t)blockIdx.x * stride;
+  float sg[PR];
+  float V[Q][B], W[Q][B];
+  float Lk[BB], Dk[BB], Uk[BB];
+  auto M = [&](int rr, int o) -> float { return (o == 0 ? 1.f : 0.f) - sg[rr] * dcoef<B>(o); };
+  if (act) {
+#pragma unroll
+    for (int c = 0; c < PR / kPartRows; ++c)
+      load_part<float>(sig + g0 + c * kPartRows, *reinterpret_cast<float(*)[kPartRows]>(sg + c * kPartRows));
+    float l[Q][B], U[Q][B + 1], piv[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      float a[2 * B + 1];
+#pragma unroll
+      for (int c = -B; c <= B; ++c) a[c + B] = (r + c >= 0 && r + c < Q) ? M(B + r, c) : 0.f;
+#pragma unroll
+      for (int t = B; t >= 1; --t) {
+        if (r - t < 0) continue;
+        const float lt = a[B - t] * piv[r - t];
+        l[r][t - 1] = lt;
+#pragma unroll
+        for (int c = 1; c <= B; ++c)
+          if (-t + c <= B) a[-t + c + B] -= lt * U[r - t][c];
+      }
+      piv[r] = 1.f / a[B];
+#pragma unroll
+      for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
+    }
+    auto solve = [&](float (&v)[Q]) {
+#pragma unroll
+      for (int r = 0; r < Q; ++r)
+#pragma unroll
+        for (int t = 1; t <= B; ++t)
+          if (r - t >= 0) v[r] -= l[r][t - 1] * v[r - t];
+#pragma unroll
+      for (int r = Q - 1; r >= 0; --r) {
+#pragma unroll
+        for (int t = 1; t <= B; ++t)
+          if (r + t < Q) v[r] -= U[r][t] * v[r + t];
+        v[r] *= piv[r];
+      }
+    };
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      float v[Q], w[Q];
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        const int ov = c - B - r, ow = Q - r + c;
+        v[r] = ov >= -B ? M(B + r, ov) : 0.f;
+        w[r] = ow <= B ? M(B + r, ow) : 0.f;
+      }
+      solve(v);
+      solve(w);
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        V[r][c] = v[r];
+        W[r][c] = w[r];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < B; ++a)
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        X[(size_t)(a * B + c) * P + k] = V[Q - B + a][c];
+        X[(size_t)(BB + a * B + c) * P + k] = W[Q - B + a][c];
+      }
+  }
+  __syncthreads();
+  if (act) {
+    const int km = (k + P - 1) & (P - 1);
+    float Vt[BB], Wt[BB];
+#pragma unroll
+    for (int e = 0; e < BB; ++e) {
+      Vt[e] = X[(size_t)e * P + km];
+      Wt[e] = X[(size_t)(BB + e) * P + km];
+    }
+#pragma unroll
+    for (int a = 0; a < B; ++a)
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        float lv = 0.f, dv = M(a, c - a), uv = 0.f;
+#pragma unroll
+        for (int c2 = 0; c2 < B; ++c2) {
+          const float ct = c2 >= a ? M(a, c2 - B - a) : 0.f;
+          const float ch = c2 <= a ? M(a, B + c2 - a) : 0.f;
+          lv -= ct * Vt[c2 * B + c];
+          dv -= ct * Wt[c2 * B + c] + ch * V[c2][c];
+          uv -= ch * W[c2][c];
+        }
+        Lk[a * B + c] = lv;
+        Dk[a * B + c] = dv;
+        Uk[a * B + c] = uv;
+      }
+  }
+  __syncthreads();
+  for (int t = 0; t < T; ++t) {
+    const int d = 1 << t;
+    if (act) {
+      float Di[BB];
+      inv_small<B>(Dk, Di);
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        X[(size_t)e * P + k] = Di[e];
+        X[(size_t)(BB + e) * P + k] = Lk[e];
+        X[(size_t)(2 * BB + e) * P + k] = Uk[e];
+      }
+    }
+    __syncthreads();
+    if (act) {
+      const int km = (k - d) & (P - 1), kp = (k + d) & (P - 1);
+      float Dm[BB], Dp[BB], al[BB], ga[BB], tmp[BB], tmp2[BB], n1[BB], n2[BB];
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        Dm[e] = X[(size_t)e * P + km];
+        Dp[e] = X[(size_t)e * P + kp];
+      }
+      mm_small<B>(Lk, Dm, al);
+      mm_small<B>(Uk, Dp, ga);
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        al[e] = -al[e];
+        ga[e] = -ga[e];
+        out[((size_t)(2 * t) * BB + e) * P + k] = al[e];
+        out[((size_t)(2 * t + 1) * BB + e) * P + k] = ga[e];
+      }
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        tmp[e] = X[(size_t)(2 * BB + e) * P + km];  // U_{k-d}
+        tmp2[e] = X[(size_t)(BB + e) * P + kp];     // L_{k+d}
+      }
+      mm_small<B>(al, tmp, n1);
+      mm_small<B>(ga, tmp2, n2);
+#pragma unroll
+      for (int e = 0; e < BB; ++e) Dk[e] += n1[e] + n2[e];
+#pragma unroll
+      for (int e = 0; e < BB; ++e) {
+        tmp[e] = X[(size_t)(BB + e) * P + km];       // L_{k-d}
+        tmp2[e] = X[(size_t)(2 * BB + e) * P + kp];  // U_{k+d}
+      }
+      mm_small<B>(al, tmp, Lk);
+      mm_small<B>(ga, tmp2, Uk);
+    }
+    __syncthreads();
+  }
+  if (act) {
+    float F[BB], Fi[BB];
+#pragma unroll
+    for (int e = 0; e < BB; ++e) F[e] = Lk[e] + Dk[e] + Uk[e];
+    inv_small<B>(F, Fi);
+#pragma unroll
+    for (int e = 0; e < BB; ++e) out[((size_t)(2 * T) * BB + e) * P + k] = Fi[e];
+  }
+}
+
+// The solve with the stored coefficients `cf` (in shared memory): x <- M^{-1} x.  The interior LU, y,
+// the spikes and the separator right-hand side are formed from sigma as in corr_solve_otf; the PCR
+// updates g only.  X: exchange area of at least 2 B P floats.
+template <int B, int PR>
+__device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const float* __restrict__ sig,
+                                                const float* __restrict__ cf, float* __restrict__ X, int nx) {
+  constexpr int Q = PR - B, BB = B * B;
+  const int P = nx / PR;
+  int T = 0;
+  while ((1 << T) < P) ++T;
+  const int k = threadIdx.x;
+  const bool act = k < P;
+  const int g0 = k * PR;
+  float xp[PR], sg[PR];
+  float y[Q], V[Q][B], W[Q][B];
+  float gk[B];
+  auto M = [&](int rr, int o) -> float { return (o == 0 ? 1.f : 0.f) - sg[rr] * dcoef<B>(o); };
+  if (act) {
+#pragma unroll
+    for (int c = 0; c < PR / kPartRows; ++c) {
+      load_part<float>(x + g0 + c * kPartRows, *reinterpret_cast<float(*)[kPartRows]>(xp + c * kPartRows));
+      load_part<float>(sig + g0 + c * kPartRows, *reinterpret_cast<float(*)[kPartRows]>(sg + c * kPartRows));
+    }
+    float l[Q][B], U[Q][B + 1], piv[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      float a[2 * B + 1];
+#pragma unroll
+      for (int c = -B; c <= B; ++c) a[c + B] = (r + c >= 0 && r + c < Q) ? M(B + r, c) : 0.f;
+#pragma unroll
+      for (int t = B; t >= 1; --t) {
+        if (r - t < 0) continue;
+        const float lt = a[B - t] * piv[r - t];
+        l[r][t - 1] = lt;
+#pragma unroll
+        for (int c = 1; c <= B; ++c)
+          if (-t + c <= B) a[-t + c + B] -= lt * U[r - t][c];
+      }
+      piv[r] = 1.f / a[B];
+#pragma unroll
+      for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
+    }
+    auto solve = [&](float (&v)[Q]) {
+#pragma unroll
+      for (int r = 0; r < Q; ++r)
+#pragma unroll
+        for (int t = 1; t <= B; ++t)
+          if (r - t >= 0) v[r] -= l[r][t - 1] * v[r - t];
+#pragma unroll
+      for (int r = Q - 1; r >= 0; --r) {
+#pragma unroll
+        for (int t = 1; t <= B; ++t)
+          if (r + t < Q) v[r] -= U[r][t] * v[r + t];
+        v[r] *= piv[r];
+      }
+    };
+#pragma unroll
+    for (int r = 0; r < Q; ++r) y[r] = xp[B + r];
+    solve(y);
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      float v[Q], w[Q];
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        const int ov = c - B - r, ow = Q - r + c;
+        v[r] = ov >= -B ? M(B + r, ov) : 0.f;
+        w[r] = ow <= B ? M(B + r, ow) : 0.f;
+      }
+      solve(v);
+      solve(w);
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        V[r][c] = v[r];
+        W[r][c] = w[r];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < B; ++a) X[(size_t)a * P + k] = y[Q - B + a];
+  }
+  __syncthreads();
+  if (act) {
+    const int km = (k + P - 1) & (P - 1);
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      float g = xp[a];
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const float ct = c >= a ? M(a, c - B - a) : 0.f;
+        const float ch = c <= a ? M(a, B + c - a) : 0.f;
+        g -= ct * X[(size_t)c * P + km] + ch * y[c];
+      }
+      gk[a] = g;
+    }
+  }
+  // block PCR on g with the stored alpha / gamma (double-buffered exchange: one barrier a level)
+  for (int t = 0; t < T; ++t) {
+    float* gb = X + (size_t)(((t & 1) + 1) * B) * P;
+    if (act) {
+#pragma unroll
+      for (int a = 0; a < B; ++a) gb[(size_t)a * P + k] = gk[a];
+    }
+    __syncthreads();
+    if (act) {
+      const int d = 1 << t;
+      const int km = (k - d) & (P - 1), kp = (k + d) & (P - 1);
+      float gm[B], gp[B];
+#pragma unroll
+      for (int a = 0; a < B; ++a) {
+        gm[a] = gb[(size_t)a * P + km];
+        gp[a] = gb[(size_t)a * P + kp];
+      }
+      const float* al = cf + (size_t)(2 * t) * BB * P + k;
+      const float* ga = cf + (size_t)(2 * t + 1) * BB * P + k;
+#pragma unroll
+      for (int a = 0; a < B; ++a) {
+        float v = gk[a];
+#pragma unroll
+        for (int c = 0; c < B; ++c) v += al[(size_t)(a * B + c) * P] * gm[c] + ga[(size_t)(a * B + c) * P] * gp[c];
+        gk[a] = v;
+      }
+    }
+  }
+  float xs[B];
+  if (act) {
+    const float* fi = cf + (size_t)(2 * T) * BB * P + k;
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      float v = 0.f;
+#pragma unroll
+      for (int c = 0; c < B; ++c) v += fi[(size_t)(a * B + c) * P] * gk[c];
+      xs[a] = v;
+    }
+  }
+  __syncthreads();  // every thread is done with the exchange area
+  if (act) {
+#pragma unroll
+    for (int a = 0; a < B; ++a) X[(size_t)a * P + k] = xs[a];
+  }
+  __syncthreads();
+  if (act) {
+    const int kp = (k + 1) & (P - 1);
+    float xn[B];
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      xn[a] = X[(size_t)a * P + kp];
+      xp[a] = xs[a];
+    }
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      float v = y[r];
+#pragma unroll
+      for (int c = 0; c < B; ++c) v -= V[r][c] * xs[c] + W[r][c] * xn[c];
+      xp[B + r] = v;
+    }
+#pragma unroll
+    for (int c = 0; c < PR / kPartRows; ++c)
+      store_part<float>(x + g0 + c * kPartRows, *reinterpret_cast<const float(*)[kPartRows]>(xp + c * kPartRows));
+  }
+  __syncthreads();
+}
+
 // Rows per partition of the on-the-fly solve: 16 for B <= 2 (half the partitions of the stored layout,
 // so one PCR level less and half the reduction work), 8 for B = 3 (register budget).
 template <int B>
@@ -560,14 +905,15 @@ __device__ __forceinline__ void apply_gather_T(const LevelTables& T, int row, co
 // Byte offsets from the 128-aligned start of the region: buffer b starts at b * per_buf with eps at
 // +0, shift at +e, sigma at +e+h; the two barriers at `bars`.
 struct StageLayout {
-  unsigned e, h, per_buf, bars, xch, total, tx;  // tx: bytes copied per step
+  unsigned e, h, per_buf, cf, bars, xch, total, tx;  // tx: table bytes copied per step
 };
-MGRIT_HD StageLayout stage_layout(int nx, int p, int otf) {
+MGRIT_HD StageLayout stage_layout(int nx, int p, int otf, unsigned cf_floats) {
   StageLayout o;
   o.e = ((unsigned)nx * 4u + 127u) & ~127u;
   o.h = ((unsigned)nx * 2u + 127u) & ~127u;
   o.per_buf = o.e + o.h + (otf ? o.e : 0u);
-  o.bars = 2 * o.per_buf;
+  o.cf = 2 * o.per_buf;  // one buffer of block-PCR coefficients (otf levels with stored coefficients)
+  o.bars = o.cf + ((cf_floats * 4u + 127u) & ~127u);
   o.xch = o.bars + 128;
   const int B = (p + 1) / 2, P = nx / (B <= 2 ? 16 : 8);  // partitions of the on-the-fly solve
   o.total = o.xch + (otf ? (unsigned)((3 * B * B + B) * P * 4) : 0u);
@@ -582,13 +928,15 @@ struct Stage {
   StageLayout lay;
   uint32_t phase;
   int cur;
-  int pending;  // step row whose copy into buffer `cur` is in flight (-1: none)
+  int pending;     // step row whose copy into buffer `cur` is in flight (-1: none)
+  int cf_pending;  // step row whose coefficient record is in flight (-1: none)
   MGRIT_D uint64_t* bar(int b) const { return reinterpret_cast<uint64_t*>(base + lay.bars) + b; }
   MGRIT_D unsigned char* buf(int b) const { return base + (size_t)b * lay.per_buf; }
   MGRIT_D const float* eps(int b) const { return reinterpret_cast<const float*>(buf(b)); }
   MGRIT_D const uint16_t* sh(int b) const { return reinterpret_cast<const uint16_t*>(buf(b) + lay.e); }
   MGRIT_D const float* sig(int b) const { return reinterpret_cast<const float*>(buf(b) + lay.e + lay.h); }
   MGRIT_D float* xch() const { return reinterpret_cast<float*>(base + lay.xch); }
+  MGRIT_D float* cf() const { return reinterpret_cast<float*>(base + lay.cf); }
 };
 
 // Carves the region out of dynamic shared memory after `used` bytes and initialises the barriers
@@ -599,12 +947,14 @@ __device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, co
   s.phase = 0;
   s.cur = 0;
   s.pending = -1;
+  s.cf_pending = -1;
   if (!T.gather_stage) return s;
-  s.lay = stage_layout(T.nx, T.p, coarse && T.otf);
+  s.lay = stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u);
   s.base = smem + ((used + 127) & ~(size_t)127);
   if (threadIdx.x == 0) {
     mbar_init(s.bar(0), 1);
     mbar_init(s.bar(1), 1);
+    mbar_init(s.bar(2), 1);
   }
   __syncthreads();
   return s;
@@ -620,6 +970,14 @@ __device__ __forceinline__ void stage_issue(const Stage& s, const LevelTables& T
   bulk_copy_g2s(d + s.lay.e, T.shift + (size_t)row * T.table_stride, nx * 2u, s.bar(b));
   if (otf)
     bulk_copy_g2s(d + s.lay.e + s.lay.h, (const float*)T.solver + (size_t)row * T.solver_stride, nx * 4u, s.bar(b));
+}
+
+// Thread 0: bulk copy of the block-PCR coefficient record of step `row` (completes on bar(2)).
+__device__ __forceinline__ void stage_issue_cf(const Stage& s, const LevelTables& T, int row) {
+  const unsigned bytes = T.pcr_floats * 4u;
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(s.bar(2), bytes);
+  bulk_copy_g2s(s.cf(), T.pcr + (size_t)row * T.pcr_floats, bytes, s.bar(2));
 }
 
 // Issues the next step's copies (and this step's if it was not prefetched), then waits for buffer
@@ -666,11 +1024,37 @@ __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R*
     return true;
   }
   if constexpr (std::is_same<R, float>::value) {  // tables staged by TMA; coarse: factorised on the fly
-    if (!stage_acquire(stg, T, n, next_n, COARSE)) return false;
+    // p <= 3: the stored block-PCR coefficients (every FP32 coarse level has them); p = 5: on the fly
+    constexpr bool coef = COARSE && B <= 2;
+    if (coef && threadIdx.x == 0 && stg.cf_pending != n) stage_issue_cf(stg, T, n);
+    if (!stage_acquire(stg, T, n, next_n, COARSE)) {
+      if (coef && threadIdx.x == 0) mbar_wait_bounded(stg.bar(2), (stg.phase >> 2) & 1u, kWaitLimitCycles);
+      return false;
+    }
     const int b = stg.cur;
     apply_gather_staged<P, NT>(stg.eps(b), stg.sh(b), (const float*)src, (float*)dst, T.nx);
     __syncthreads();
-    if constexpr (COARSE) corr_solve_otf<B, otf_rows<B>()>((float*)dst, stg.sig(b), stg.xch(), T.nx);
+    if constexpr (COARSE) {
+      if constexpr (coef) {
+        const uint32_t par = (stg.phase >> 2) & 1u;
+        const bool ok = mbar_wait_bounded(stg.bar(2), par, kWaitLimitCycles);
+        stg.phase ^= 4u;
+        if (__syncthreads_or(!ok)) {
+          if (threadIdx.x == 0) {
+            atomicExch(T.err, 1);
+            mbar_wait_bounded(stg.bar(2), par, kWaitLimitCycles);
+            if (next_n >= 0) mbar_wait_bounded(stg.bar(b ^ 1), (stg.phase >> (b ^ 1)) & 1u, kWaitLimitCycles);
+          }
+          return false;
+        }
+        corr_solve_coef<B, otf_rows<B>()>((float*)dst, stg.sig(b), stg.cf(), stg.xch(), T.nx);
+        // the solve ends with a barrier: the record buffer is free for the next step's copy
+        if (threadIdx.x == 0 && next_n >= 0) stage_issue_cf(stg, T, next_n);
+        stg.cf_pending = next_n;
+      } else {
+        corr_solve_otf<B, otf_rows<B>()>((float*)dst, stg.sig(b), stg.xch(), T.nx);
+      }
+    }
     stg.cur ^= 1;
     stg.pending = next_n;
     (void)gr;
@@ -913,7 +1297,9 @@ int buffer_elems(const LevelTables& T, bool coarse) {
 template <typename R>
 size_t smem_bytes(int buf, const LevelTables& T, bool coarse) {
   size_t b = 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double);
-  if (T.gather_stage) b = ((b + 127) & ~(size_t)127) + stage_layout(T.nx, T.p, coarse && T.otf).total;
+  if (T.gather_stage)
+    b = ((b + 127) & ~(size_t)127) +
+        stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u).total;
   return b;
 }
 
@@ -1114,7 +1500,9 @@ void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem
   const int b = buffer_elems(T, coarse);
   *buf = b;
   *smem = is_double ? smem_bytes<double>(b, T, coarse) : smem_bytes<float>(b, T, coarse);
-  *region = T.gather_stage ? stage_layout(T.nx, T.p, coarse && T.otf).total : 0;
+  *region = T.gather_stage
+                ? stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u).total
+                : 0;
 }
 
 cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles,
@@ -1188,6 +1576,20 @@ cudaError_t launch_gradient_a_1d(const LevelTables& T, const double* s64, const 
   if (T.p == 3) MGRIT_LAUNCH_GRAD(3)
   MGRIT_LAUNCH_GRAD(5)
 #undef MGRIT_LAUNCH_GRAD
+}
+
+unsigned pcr_record_size(int nx, int p) { return pcr_record_floats(nx, p); }
+
+cudaError_t launch_pcr_coef(const float* sig32, int nt, int nx, int p, float* out, cudaStream_t st) {
+  const int B = (p + 1) / 2;
+  if (B > 2) return cudaErrorInvalidValue;
+  const int P = nx / 16;
+  const unsigned stride = pcr_record_floats(nx, p);
+  const size_t smem = (size_t)3 * B * B * P * sizeof(float);
+  const int threads = ((P + 31) / 32) * 32;
+  if (B == 1) k_pcr_coef<1, 16><<<nt, threads, smem, st>>>(sig32, nx, out, stride);
+  else k_pcr_coef<2, 16><<<nt, threads, smem, st>>>(sig32, nx, out, stride);
+  return cudaGetLastError();
 }
 
 void launch_axpy_convert(int kind, const void* x, void* y, const void* z, long long n, cudaStream_t st) {

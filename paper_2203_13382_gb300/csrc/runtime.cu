@@ -48,6 +48,8 @@ struct Level {
   float* eps32 = nullptr;
   void* solver = nullptr;   // stored factorisation (FP64 coarse levels)
   float* sig32 = nullptr;   // sigma as FP32 rows (FP32 coarse levels, factorised on the fly)
+  float* pcr32 = nullptr;   // FP32 coarse levels, p <= 3: block-PCR coefficients of every step
+  unsigned pcr_floats = 0;
   size_t solver_stride = 0;
   int P = 0;
   int is_double = 1;  // arithmetic of this level's cycle
@@ -257,6 +259,8 @@ struct mgrit_handle {
     T.err = err_dev;
     T.otf = 0;
     T.gather_stage = 0;
+    T.pcr = nullptr;
+    T.pcr_floats = 0;
     T.trans = 0;
     T.reverse = 0;
     T.frange = L.frange;
@@ -274,6 +278,8 @@ struct mgrit_handle {
         T.otf = 1;
         T.solver = L.sig32;
         T.solver_stride = (size_t)grid.nx;
+        T.pcr = L.pcr32;  // p <= 3: the block-PCR coefficients precomputed in setup
+        T.pcr_floats = L.pcr_floats;
       }
     }
     return T;
@@ -576,8 +582,12 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
           L.solver_stride = solver_reals(nx, p);
           const size_t tot = L.solver_stride * L.nt * sizeof(double);
           if ((st = h->alloc((char**)&L.solver, tot)) != MGRIT_OK) return cleanup_fail(st);
-        } else if ((st = h->alloc(&L.sig32, (size_t)L.nt * nx)) != MGRIT_OK) {
-          return cleanup_fail(st);
+        } else {
+          if ((st = h->alloc(&L.sig32, (size_t)L.nt * nx)) != MGRIT_OK) return cleanup_fail(st);
+          if (p <= 3) {
+            L.pcr_floats = pcr_record_size(nx, p);
+            if ((st = h->alloc(&L.pcr32, (size_t)L.nt * L.pcr_floats)) != MGRIT_OK) return cleanup_fail(st);
+          }
         }
       }
     }
@@ -667,7 +677,8 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     if (l > 0 && L.sig32) {
       const int ev = h->phase_begin();
       launch_axpy_convert(1, L.sigma, L.sig32, nullptr, (long long)L.nt * nx, s);
-      h->phase_end(MGRIT_PHASE_FACTOR, ev, 1);
+      if (L.pcr32) launch_pcr_coef(L.sig32, L.nt, nx, p, L.pcr32, s);
+      h->phase_end(MGRIT_PHASE_FACTOR, ev, L.pcr32 ? 2 : 1);
     }
     if ((st = cuda_fail("setup")) != MGRIT_OK) return st;
   }
