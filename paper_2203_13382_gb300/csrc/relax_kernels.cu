@@ -707,9 +707,11 @@ __global__ void __launch_bounds__(512) k_pcr_coef(const float* __restrict__ sig_
   }
 }
 
-// The solve with the stored coefficients `cf` (in shared memory): x <- M^{-1} x.  The interior LU, y,
-// the spikes and the separator right-hand side are formed from sigma as in corr_solve_otf; the PCR
-// updates g only.  X: exchange area of at least 2 B P floats.
+// The solve with the stored coefficients `cf` (in shared memory): x <- M^{-1} x.  The interior rows are
+// solved twice with the banded LU formed from sigma: first with their own right-hand side (y, which
+// gives the separator right-hand side g), then, once the separators are known, with the separator
+// couplings moved to the right-hand side (the spikes of the stored factorisation are not needed).
+// The PCR updates g only.  X: exchange area of at least 3 B P floats.
 template <int B, int PR>
 __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const float* __restrict__ sig,
                                                 const float* __restrict__ cf, float* __restrict__ X, int nx) {
@@ -721,15 +723,10 @@ __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const flo
   const bool act = k < P;
   const int g0 = k * PR;
   float xp[PR], sg[PR];
-  float y[Q], V[Q][B], W[Q][B];
   float gk[B];
   auto M = [&](int rr, int o) -> float { return (o == 0 ? 1.f : 0.f) - sg[rr] * dcoef<B>(o); };
-  if (act) {
-#pragma unroll
-    for (int c = 0; c < PR / kPartRows; ++c) {
-      load_part<float>(x + g0 + c * kPartRows, *reinterpret_cast<float(*)[kPartRows]>(xp + c * kPartRows));
-      load_part<float>(sig + g0 + c * kPartRows, *reinterpret_cast<float(*)[kPartRows]>(sg + c * kPartRows));
-    }
+  // v <- A^{-1} v for the interior block A (banded LU without pivoting, formed from sigma)
+  auto interior_solve = [&](float (&v)[Q]) {
     float l[Q][B], U[Q][B + 1], piv[Q];
 #pragma unroll
     for (int r = 0; r < Q; ++r) {
@@ -748,58 +745,52 @@ __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const flo
       piv[r] = 1.f / a[B];
 #pragma unroll
       for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
+      // forward substitution of this row as soon as it is eliminated
+#pragma unroll
+      for (int t = 1; t <= B; ++t)
+        if (r - t >= 0) v[r] -= l[r][t - 1] * v[r - t];
     }
-    auto solve = [&](float (&v)[Q]) {
 #pragma unroll
-      for (int r = 0; r < Q; ++r)
+    for (int r = Q - 1; r >= 0; --r) {
 #pragma unroll
-        for (int t = 1; t <= B; ++t)
-          if (r - t >= 0) v[r] -= l[r][t - 1] * v[r - t];
+      for (int t = 1; t <= B; ++t)
+        if (r + t < Q) v[r] -= U[r][t] * v[r + t];
+      v[r] *= piv[r];
+    }
+  };
+  if (act) {
 #pragma unroll
-      for (int r = Q - 1; r >= 0; --r) {
-#pragma unroll
-        for (int t = 1; t <= B; ++t)
-          if (r + t < Q) v[r] -= U[r][t] * v[r + t];
-        v[r] *= piv[r];
-      }
-    };
+    for (int c = 0; c < PR / kPartRows; ++c) {
+      load_part<float>(x + g0 + c * kPartRows, *reinterpret_cast<float(*)[kPartRows]>(xp + c * kPartRows));
+      load_part<float>(sig + g0 + c * kPartRows, *reinterpret_cast<float(*)[kPartRows]>(sg + c * kPartRows));
+    }
+    float y[Q];
 #pragma unroll
     for (int r = 0; r < Q; ++r) y[r] = xp[B + r];
-    solve(y);
+    interior_solve(y);
 #pragma unroll
-    for (int c = 0; c < B; ++c) {
-      float v[Q], w[Q];
-#pragma unroll
-      for (int r = 0; r < Q; ++r) {
-        const int ov = c - B - r, ow = Q - r + c;
-        v[r] = ov >= -B ? M(B + r, ov) : 0.f;
-        w[r] = ow <= B ? M(B + r, ow) : 0.f;
-      }
-      solve(v);
-      solve(w);
-#pragma unroll
-      for (int r = 0; r < Q; ++r) {
-        V[r][c] = v[r];
-        W[r][c] = w[r];
-      }
+    for (int a = 0; a < B; ++a) {
+      X[(size_t)a * P + k] = y[Q - B + a];
+      gk[a] = y[a];  // head of y, used below
     }
-#pragma unroll
-    for (int a = 0; a < B; ++a) X[(size_t)a * P + k] = y[Q - B + a];
   }
   __syncthreads();
   if (act) {
     const int km = (k + P - 1) & (P - 1);
+    float g[B];
 #pragma unroll
     for (int a = 0; a < B; ++a) {
-      float g = xp[a];
+      float v = xp[a];
 #pragma unroll
       for (int c = 0; c < B; ++c) {
         const float ct = c >= a ? M(a, c - B - a) : 0.f;
         const float ch = c <= a ? M(a, B + c - a) : 0.f;
-        g -= ct * X[(size_t)c * P + km] + ch * y[c];
+        v -= ct * X[(size_t)c * P + km] + ch * gk[c];
       }
-      gk[a] = g;
+      g[a] = v;
     }
+#pragma unroll
+    for (int a = 0; a < B; ++a) gk[a] = g[a];
   }
   // block PCR on g with the stored alpha / gamma (double-buffered exchange: one barrier a level)
   for (int t = 0; t < T; ++t) {
@@ -850,17 +841,25 @@ __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const flo
     const int kp = (k + 1) & (P - 1);
     float xn[B];
 #pragma unroll
-    for (int a = 0; a < B; ++a) {
-      xn[a] = X[(size_t)a * P + kp];
-      xp[a] = xs[a];
-    }
+    for (int a = 0; a < B; ++a) xn[a] = X[(size_t)a * P + kp];
+    // interior: A x_I = b_I - M[I, S_k] x_S(k) - M[I, S_{k+1}] x_S(k+1)
+    float v[Q];
 #pragma unroll
     for (int r = 0; r < Q; ++r) {
-      float v = y[r];
+      float w = xp[B + r];
 #pragma unroll
-      for (int c = 0; c < B; ++c) v -= V[r][c] * xs[c] + W[r][c] * xn[c];
-      xp[B + r] = v;
+      for (int c = 0; c < B; ++c) {
+        const int ov = c - B - r, ow = Q - r + c;
+        if (ov >= -B) w -= M(B + r, ov) * xs[c];
+        if (ow <= B) w -= M(B + r, ow) * xn[c];
+      }
+      v[r] = w;
     }
+    interior_solve(v);
+#pragma unroll
+    for (int a = 0; a < B; ++a) xp[a] = xs[a];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) xp[B + r] = v[r];
 #pragma unroll
     for (int c = 0; c < PR / kPartRows; ++c)
       store_part<float>(x + g0 + c * kPartRows, *reinterpret_cast<const float(*)[kPartRows]>(xp + c * kPartRows));
