@@ -480,7 +480,10 @@ def run_2d(args) -> None:
 
     import paper_2203_13382_gb300 as mg
 
-    wl = WORKLOAD_2D
+    wl = dict(WORKLOAD_2D)
+    if args.nx or args.nt:  # smaller grids (profiling captures only)
+        wl["nx"], wl["nt"] = args.nx or wl["nx"], args.nt or wl["nt"]
+        wl["workload"] += f"_override_{wl['nx']}x{wl['nx']}_nt{wl['nt']}"
     nx, nt, p, m = wl["nx"], wl["nt"], wl["order"], wl["m"]
     npts = nx * nx
     u0 = torch.from_numpy(W.u0_bumps_2d(nx, W.SEED_C3_BUMPS, 5).ravel().copy()).cuda()
@@ -622,6 +625,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the sequential comparator and e2e runs")
     ap.add_argument("--nt", type=int, default=0, help="override nt (small profiling cases only)")
+    ap.add_argument("--nx", type=int, default=0, help="override nx of the 2D workload (small profiling cases only)")
     ap.add_argument("--workload", choices=["advection1d", "advection2d", "batched", "adjoint2d"],
                     default="advection1d", help="advection1d is the benchmark; the others measure further rows")
     ap.add_argument("--no-phase-events", action="store_true",

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads2d) k_step2d_T(LevelTables T, const do
 
 // y = M x with M = I - diag(sx) (I (x) D) - diag(sy) (D (x) I), D = (delta^2)^B (periodic).
 template <int B, typename R>
-__device__ __forceinline__ R apply_M(const R* x, const double* sx, const double* sy, long long pt, int nx) {
+__device__ __forceinline__ R apply_M(const R* x, const R* sx, const R* sy, long long pt, int nx) {
   const int i = (int)(pt % nx), jj = (int)(pt / nx);
   const R* row = x + (size_t)jj * nx;
   R dxv = (R)0, dyv = (R)0;
@@ -153,12 +153,12 @@ __device__ __forceinline__ R apply_M(const R* x, const double* sx, const double*
     dxv += d * row[wrap_pow2(i + o, nx)];
     dyv += d * x[(size_t)wrap_pow2(jj + o, nx) * nx + i];
   }
-  return x[pt] - (R)sx[pt] * dxv - (R)sy[pt] * dyv;
+  return x[pt] - sx[pt] * dxv - sy[pt] * dyv;
 }
 
 // y = M^T x = x - (I (x) D) diag(sx) x - (D (x) I) diag(sy) x (D is symmetric).
 template <int B, typename R>
-__device__ __forceinline__ R apply_MT(const R* x, const double* sx, const double* sy, long long pt, int nx) {
+__device__ __forceinline__ R apply_MT(const R* x, const R* sx, const R* sy, long long pt, int nx) {
   const int i = (int)(pt % nx), jj = (int)(pt / nx);
   R dxv = (R)0, dyv = (R)0;
 #pragma unroll
@@ -166,8 +166,8 @@ __device__ __forceinline__ R apply_MT(const R* x, const double* sx, const double
     const R d = (R)dstencil_int<B>(o);
     const long long px = (long long)jj * nx + wrap_pow2(i + o, nx);
     const long long py = (long long)wrap_pow2(jj + o, nx) * nx + i;
-    dxv += d * (R)sx[px] * x[px];
-    dyv += d * (R)sy[py] * x[py];
+    dxv += d * sx[px] * x[px];
+    dyv += d * sy[py] * x[py];
   }
   return x[pt] - dxv - dyv;
 }
@@ -241,8 +241,8 @@ __device__ __forceinline__ void cta_subtract_projections(const R* V, long long N
 // then one update pass; Givens rotations), zero initial guess, stop when the least-squares residual
 // <= rtol ||b|| or after kmax iterations.
 template <int B, typename R, bool TRANS>
-__global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const double* __restrict__ sigma_x,
-                                                        const double* __restrict__ sigma_y, int nx, int n0, int m,
+__global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restrict__ sigma_x,
+                                                        const R* __restrict__ sigma_y, int nx, int n0, int m,
                                                         int nt_rev, R* __restrict__ bx_all, R* __restrict__ basis,
                                                         int kmax, double rtol) {
   __shared__ double red[40];
@@ -253,8 +253,8 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const double* __
   const long long N = (long long)nx * nx;
   const int j = blockIdx.x;
   const int n = nt_rev > 0 ? nt_rev - 1 - (n0 + j * m) : n0 + j * m;
-  const double* sx = sigma_x + (size_t)n * N;
-  const double* sy = sigma_y + (size_t)n * N;
+  const R* sx = sigma_x + (size_t)n * N;
+  const R* sy = sigma_y + (size_t)n * N;
   R* b = bx_all + (size_t)j * N;
   R* V = basis + (size_t)j * (kmax + 1) * N;
   const double beta = sqrt(cta_dot<R>(b, b, N, red));
@@ -326,8 +326,8 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const double* __
 // of them hold the same value and take the same Givens rotations and stopping decision.  A cluster
 // barrier orders the writes of each new basis vector before M reads neighbouring rows of it.
 template <int B, typename R, bool TRANS>
-__global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const double* __restrict__ sigma_x,
-                                                                   const double* __restrict__ sigma_y, int nx, int n0,
+__global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const R* __restrict__ sigma_x,
+                                                                   const R* __restrict__ sigma_y, int nx, int n0,
                                                                    int m, int nt_rev, R* __restrict__ bx_all,
                                                                    R* __restrict__ basis, int kmax, double rtol) {
   namespace cg = cooperative_groups;
@@ -344,8 +344,8 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const do
   const long long lo = N * rank / C, hi = N * (rank + 1) / C;
   const int j = blockIdx.x / C;
   const int n = nt_rev > 0 ? nt_rev - 1 - (n0 + j * m) : n0 + j * m;
-  const double* sx = sigma_x + (size_t)n * N;
-  const double* sy = sigma_y + (size_t)n * N;
+  const R* sx = sigma_x + (size_t)n * N;
+  const R* sy = sigma_y + (size_t)n * N;
   R* b = bx_all + (size_t)j * N;
   R* V = basis + (size_t)j * (kmax + 1) * N;
   int slot = 0;
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const do
 
 // J systems of step index n0 (+ j m): one CTA each, or, when J leaves SMs idle, a cluster of CTAs each.
 template <int B, typename R, bool TRANS>
-cudaError_t launch_gmres(const double* sig, long long N, int nt, int nx, int n0, int m, int ntr, R* b, R* basis,
+cudaError_t launch_gmres(const R* sig, long long N, int nt, int nx, int n0, int m, int ntr, R* b, R* basis,
                          int kmax, double rtol, int J, cudaStream_t st) {
   int C = 1;
   while (C < 16 && J * C * 2 <= 152) C *= 2;
@@ -547,7 +547,7 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
   if (T.trans) {  // Phi^T = S^T M^{-T}: the correction solve (in place on src), then the transposed step
     if constexpr (std::is_same<R, double>::value) {
       if (coarse) {
-        const double* sig = (const double*)T.solver;
+        const double* sig = (const double*)T.solver;  // FP64 (the adjoint is FP64)
         const int B = (T.p + 1) / 2, ntr = T.reverse ? T.nt : 0;
         cudaError_t e;
         if (B == 1)
@@ -575,7 +575,8 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
   else MGRIT_STEP2D(5);
 #undef MGRIT_STEP2D
   if (coarse) {
-    const double* sig = (const double*)T.solver;  // sigma_x block then sigma_y block, [nt][N] each
+    // sigma_x block then sigma_y block, [nt][N] each, in the level's precision
+    const R* sig = (const R*)T.solver;
     const int B = (T.p + 1) / 2;
     cudaError_t e;
     if (B == 1) e = launch_gmres<1, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);

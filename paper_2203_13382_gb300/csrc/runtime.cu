@@ -253,7 +253,10 @@ struct mgrit_handle {
     T.eps32 = L.eps32;
     T.table_stride = npts;
     T.nt = L.nt;
-    T.solver = (l > 0 && opt.coarse_op == 0) ? (grid.dim == 2 ? (const void*)L.sigma : L.solver) : nullptr;
+    // 2D: sigma for the GMRES correction solves, FP32 copy on FP32 levels
+    T.solver = (l > 0 && opt.coarse_op == 0)
+                   ? (grid.dim == 2 ? (!is_double && L.sig32 ? (const void*)L.sig32 : (const void*)L.sigma) : L.solver)
+                   : nullptr;
     T.solver_stride = L.solver_stride;
     T.s64 = L.s64;
     T.err = err_dev;
@@ -576,6 +579,9 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
       const size_t esz = L.is_double ? sizeof(double) : sizeof(float);
       if ((st = h->alloc((char**)&L.E, full * esz)) != MGRIT_OK) return cleanup_fail(st);
       if ((st = h->alloc((char**)&L.G, full * esz)) != MGRIT_OK) return cleanup_fail(st);
+      if (opt.coarse_op == 0 && dim == 2 && !L.is_double &&
+          (st = h->alloc(&L.sig32, rows)) != MGRIT_OK)  // FP32 sigma of the FP32 GMRES solves
+        return cleanup_fail(st);
       if (opt.coarse_op == 0 && dim == 1) {
         L.P = nx / 8;
         if (L.is_double) {
@@ -676,7 +682,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     }
     if (l > 0 && L.sig32) {
       const int ev = h->phase_begin();
-      launch_axpy_convert(1, L.sigma, L.sig32, nullptr, (long long)L.nt * nx, s);
+      launch_axpy_convert(1, L.sigma, L.sig32, nullptr, (long long)L.nt * np * dim, s);
       if (L.pcr32) launch_pcr_coef(L.sig32, L.nt, nx, p, L.pcr32, s);
       h->phase_end(MGRIT_PHASE_FACTOR, ev, L.pcr32 ? 2 : 1);
     }
