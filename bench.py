@@ -615,6 +615,72 @@ def run_adjoint2d(args) -> None:
           iterations_forward=st["iterations"], iterations_adjoint=ast["iterations"], dJ_da=g_a, clocks=clocks)
 
 
+def run_twolevel(args) -> None:
+    """The two-level constant-speed case (nx = nt = 256, alpha = 1, p = 1, m = 4, FP64): GPU MGRIT and
+    sequential stepping, and the oracle's MGRIT and sequential stepping on one core (the whole case)."""
+    import torch
+
+    import paper_2203_13382_gb300 as mg
+    from oracle import mgrit as omg
+    from oracle import semi_lagrangian as osl
+
+    nx, nt = 256, 256
+    u0 = torch.from_numpy(W.u0_sin4(nx)).cuda()
+    U0 = torch.from_numpy(W.initial_iterate(nt, nx)).cuda()
+
+    def step():
+        h = mg.mgrit_setup(nx, nt, 1, 4, wave="const", a=1.0, levels=2)
+        _, st = h.solve(u0, U0)
+        h.destroy()
+        return st
+
+    ms, stats = _timed(step, max(args.steps, 10), args.warmup)
+    h = mg.mgrit_setup(nx, nt, 1, 4, wave="const", a=1.0, levels=2)
+    seq_ms, _ = _timed(lambda: h.sequential(u0, store_all=False), 10, 2)
+    h.destroy()
+    t0 = time.perf_counter()
+    H = omg.build_hierarchy(osl.Grid(nx, nt), osl.WaveSpeed("const", a=1.0), 1, 4, levels=2)
+    R = omg.mgrit_solve(H, W.u0_sin4(nx), W.initial_iterate(nt, nx))
+    t_or = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    omg.sequential_solve(omg.Hierarchy(osl.Grid(nx, nt), osl.WaveSpeed("const", a=1.0), 1, []), W.u0_sin4(nx))
+    t_seq = time.perf_counter() - t0
+    dof = nx * nt
+    _line(args, METRIC, dof / (ms / 1e3), "DOF/s", ms,
+          {"workload": "advection1d_const_alpha1_nx256_nt256_p1_m4_two_levels", "precision": "fp64"},
+          iterations=stats[0]["iterations"], iterations_oracle=R.iterations,
+          comparator={"sequential_ms": seq_ms, "sequential_dof_per_s": dof / (seq_ms / 1e3)},
+          cpu_baseline={"value": dof / t_or, "unit": "DOF/s", "cores": cores_used(), "kind": "oracle",
+                        "sample": "the whole case (oracle MGRIT, setup included)"},
+          cpu_sequential={"value": dof / t_seq, "unit": "DOF/s", "cores": cores_used(), "kind": "oracle"})
+
+
+def run_cpu(args) -> None:
+    """The oracle's sequential stepping and MGRIT on bounded samples of the 1D workload (one core)."""
+    from oracle import mgrit as omg
+    from oracle import semi_lagrangian as osl
+
+    wl = WORKLOAD
+    nx = wl["nx"]
+    out = {}
+    for name, nts in (("sequential", 2048), ("mgrit", CPU_SAMPLE_NT)):
+        g = osl.Grid(nx, nts, cfl=wl["cfl"])
+        ws = osl.WaveSpeed(wl["wave"], a=wl["a"], k=wl["k"])
+        u0 = W.u0_bumps_1d(nx, W.SEED_C2_BUMPS, 3)
+        t0 = time.perf_counter()
+        if name == "sequential":
+            omg.sequential_solve(omg.Hierarchy(g, ws, wl["order"], []), u0)
+            its = None
+        else:
+            H = omg.build_hierarchy(g, ws, wl["order"], wl["m"], max_coarsest=wl["max_coarsest"])
+            its = omg.mgrit_solve(H, u0, W.initial_iterate(nts, nx), rtol=wl["rtol"]).iterations
+        el = time.perf_counter() - t0
+        out[name] = {"value": nx * nts / el, "unit": "DOF/s", "cores": cores_used(), "kind": "oracle",
+                     "sample": f"first {nts} of {wl['nt']} steps, nx = {nx}, departure points included",
+                     "seconds": el, "iterations": its}
+    print(json.dumps({"impl": "oracle", "workload": wl["workload"], **out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -626,7 +692,7 @@ def main():
     ap.add_argument("--no-comparator", action="store_true", help="skip the sequential comparator and e2e runs")
     ap.add_argument("--nt", type=int, default=0, help="override nt (small profiling cases only)")
     ap.add_argument("--nx", type=int, default=0, help="override nx of the 2D workload (small profiling cases only)")
-    ap.add_argument("--workload", choices=["advection1d", "advection2d", "batched", "adjoint2d"],
+    ap.add_argument("--workload", choices=["advection1d", "advection2d", "batched", "adjoint2d", "twolevel", "cpu"],
                     default="advection1d", help="advection1d is the benchmark; the others measure further rows")
     ap.add_argument("--no-phase-events", action="store_true",
                     help="skip the second, instrumented timed region (phase table from one solve)")
@@ -641,6 +707,10 @@ def main():
         run_batched(args)
     elif args.workload == "adjoint2d":
         run_adjoint2d(args)
+    elif args.workload == "twolevel":
+        run_twolevel(args)
+    elif args.workload == "cpu":
+        run_cpu(args)
     else:
         run_ours(args)
 
