@@ -979,6 +979,19 @@ __device__ __forceinline__ void stage_issue_cf(const Stage& s, const LevelTables
   bulk_copy_g2s(s.cf(), T.pcr + (size_t)row * T.pcr_floats, bytes, s.bar(2));
 }
 
+// Thread 0 issues the copies of a CTA's first step n right after stage_init, so that they overlap the
+// load of the start slice (FP32 levels; coarse levels with stored coefficients also the record).
+template <int P, bool COARSE>
+__device__ __forceinline__ void stage_prefetch_first(Stage& s, const LevelTables& T, int n) {
+  if (!s.base || n < 0) return;
+  if (threadIdx.x == 0) {
+    stage_issue(s, T, n, s.cur, COARSE);
+    if (COARSE && (P + 1) / 2 <= 2) stage_issue_cf(s, T, n);
+  }
+  s.pending = n;
+  if (COARSE && (P + 1) / 2 <= 2) s.cf_pending = n;
+}
+
 // Issues the next step's copies (and this step's if it was not prefetched), then waits for buffer
 // `cur`; false if the bounded wait gave up (T.err set; thread 0 lets the copies in flight land first).
 __device__ __forceinline__ bool stage_acquire(Stage& s, const LevelTables& T, int n, int next_n, bool otf) {
@@ -1083,6 +1096,8 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
   double* red = reinterpret_cast<double*>(dst + buf);
   const int nx = T.nx;
   Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), T, COARSE);
+  if constexpr (std::is_same<R, float>::value)
+    stage_prefetch_first<P, COARSE>(stg, T, (j < a.J && a.nsteps > 0) ? j * a.m : -1);
   {
     const R* st = a.start ? (const R*)a.start + (size_t)j * a.start_stride : nullptr;
     const R* co = a.corr ? (const R*)a.corr + (size_t)j * a.corr_stride : nullptr;
@@ -1190,6 +1205,7 @@ __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, con
   R* dst = src + buf;
   const int nx = T.nx;
   Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), T, COARSE);
+  if constexpr (std::is_same<R, float>::value) stage_prefetch_first<P, COARSE>(stg, T, N > 0 ? 0 : -1);
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const R v = u0 ? u0[i] : (R)0;
     src[i] = v;
