@@ -1250,7 +1250,8 @@ __global__ void __launch_bounds__(slice_threads<P, R, COARSE>()) k_sequential_1d
 // ---- batched problems: one launch per cycle phase over (problem, interval) tiles --------------------
 
 template <typename R, bool COARSE>
-__global__ void __launch_bounds__(kSliceThreads, 1) k_relax_batched(const LevelTables* __restrict__ tabs,
+__global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : (std::is_same<R, float>::value ? 2 : 3))
+    k_relax_batched(const LevelTables* __restrict__ tabs,
                                                                     const RelaxArgs* __restrict__ args,
                                                                     const BatchTile* __restrict__ tiles,
                                                                     const int* __restrict__ active, int buf) {
