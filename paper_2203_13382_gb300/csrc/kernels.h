@@ -38,12 +38,12 @@ unsigned pcr_record_size(int nx, int p);
 cudaError_t launch_pcr_coef(const float* sig32, int nt, int nx, int p, float* out, cudaStream_t st);
 
 // Factorisation of M = I - diag(sigma) D_{p+1} (periodic, half-bandwidth b = (p+1)/2) for each of nt
-// steps (layout: solver_layout.cuh).  Output per step: solver_reals(nx, p) values of type double
-// (is_double = 1) or float.  flag (device int) is set to 1 if a pivot is too small.  Returns the number
-// of kernel launches issued.
+// steps (layout: solver_layout.cuh), FP64, solver_reals(nx, p) values per step (FP64 coarse levels and
+// the adjoint's M^T; FP32 levels use launch_pcr_coef).  flag (device int) is set to 1 if a pivot is too
+// small.  Returns the number of kernel launches issued.
 size_t solver_reals(int nx, int p);
-int launch_factor_1d(const double* sigma, int nt, int nx, int p, void* out, int is_double, int* flag,
-                     cudaStream_t st, int transpose = 0);
+int launch_factor_1d(const double* sigma, int nt, int nx, int p, double* out, int* flag, cudaStream_t st,
+                     int transpose = 0);
 
 // Adjoint support: per step the range of floor(s) (window of the transposed gather), and d s / d a by
 // the tangent-linear ERK step.

@@ -677,7 +677,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     }
     if (l > 0 && L.solver) {
       const int ev = h->phase_begin();
-      const int nl = launch_factor_1d(L.sigma, L.nt, nx, p, L.solver, L.is_double, h->flag_dev, s);
+      const int nl = launch_factor_1d(L.sigma, L.nt, nx, p, (double*)L.solver, h->flag_dev, s);
       h->phase_end(MGRIT_PHASE_FACTOR, ev, nl);
     }
     if (l > 0 && L.sig32) {
@@ -974,7 +974,7 @@ mgrit_status ensure_adjoint(mgrit_handle* h) {
     launch_floor_range(L.s64, L.nt, nx, L.frange, s);
     if (l > 0 && L.solver) {
       MG_TRY(h->alloc((char**)&L.solverT, L.solver_stride * L.nt * sizeof(double)));
-      launch_factor_1d(L.sigma, L.nt, nx, p, L.solverT, 1, h->flag_dev, s, 1);
+      launch_factor_1d(L.sigma, L.nt, nx, p, (double*)L.solverT, h->flag_dev, s, 1);
     }
   }
   Level& L0 = h->levels[0];

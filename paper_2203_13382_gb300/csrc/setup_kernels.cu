@@ -804,8 +804,8 @@ __global__ void __launch_bounds__(512) k_factor_1d(const double* __restrict__ si
   }
 }
 
-int launch_factor_1d(const double* sigma, int nt, int nx, int p, void* out, int is_double, int* flag,
-                     cudaStream_t st, int transpose) {
+int launch_factor_1d(const double* sigma, int nt, int nx, int p, double* out, int* flag, cudaStream_t st,
+                     int transpose) {
   const SolverGeom G = solver_geom(nx, p);
   const int threads = ((G.P + 31) / 32) * 32;
   const size_t smem = (size_t)G.P * 3 * G.B * G.B * sizeof(double);
@@ -813,13 +813,10 @@ int launch_factor_1d(const double* sigma, int nt, int nx, int p, void* out, int 
 #define MGRIT_FACTOR(BB)                                                                                         \
   if (transpose) {                                                                                               \
     cudaFuncSetAttribute(k_factor_1d<BB, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-    k_factor_1d<BB, double, true><<<nt, threads, smem, st>>>(sigma, nx, (double*)out, stride, flag);             \
-  } else if (is_double) {                                                                                        \
-    cudaFuncSetAttribute(k_factor_1d<BB, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    k_factor_1d<BB, double, false><<<nt, threads, smem, st>>>(sigma, nx, (double*)out, stride, flag);            \
+    k_factor_1d<BB, double, true><<<nt, threads, smem, st>>>(sigma, nx, out, stride, flag);                      \
   } else {                                                                                                       \
-    cudaFuncSetAttribute(k_factor_1d<BB, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-    k_factor_1d<BB, float, false><<<nt, threads, smem, st>>>(sigma, nx, (float*)out, stride, flag);             \
+    cudaFuncSetAttribute(k_factor_1d<BB, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    k_factor_1d<BB, double, false><<<nt, threads, smem, st>>>(sigma, nx, out, stride, flag);                     \
   }
   if (G.B == 1) {
     MGRIT_FACTOR(1)
