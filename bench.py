@@ -69,6 +69,22 @@ def peaks():
     return hbm, src
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of every rank's value (the replicas' step time is the slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(dof_per_rank: int, world: int, ms: float) -> float:
+    """DOF/s of all ranks together: every rank solves its own replica of the workload."""
+    return world * dof_per_rank / (ms / 1e3)
+
+
 def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -332,11 +348,8 @@ def run_ours(args) -> None:
     ms_events = f0.elapsed_time(f1) / args.steps if pstats else None
     if not pstats:  # phase table from one solve outside the timed regions
         pstats = [one_step(1)]
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * dof / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_value(dof, world, ms)
 
     # phase sums over the instrumented timed steps
     agg_ms = {k: sum(s["phase_ms"][k] for s in pstats) for k in pstats[0]["phase_ms"]}
