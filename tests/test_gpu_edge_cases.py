@@ -86,3 +86,32 @@ def test_argument_errors():
         mg.mgrit_setup(64, 64, 2, 4)        # even order
     with pytest.raises(mg.MgritError):
         mg.mgrit_setup(64, 63, 3, 4, levels=2)  # nt not divisible by m for the requested levels
+
+
+@pytest.mark.parametrize("p", [1, 3, 5])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_variable_coarsening_first_level(p, precision):
+    """Sec. 5's coarsening: factor 16 on the first level, 4 below (option m_first)."""
+    nx, nt = 128, 1024
+    H = omg.build_hierarchy(osl.Grid(nx, nt), osl.WaveSpeed("sin_kx_cos_t", a=0.4, k=1.0), p, [16, 4])
+    u0 = W.u0_bumps_1d(nx, W.SEED_C2_BUMPS, 3)
+    U0 = W.initial_iterate(nt, nx)
+    ref = omg.mgrit_solve(H, u0, U0)
+    h = mg.mgrit_setup(nx, nt, p, 4, wave="sin_kx_cos_t", a=0.4, k=1.0, m_first=16, precision=precision)
+    assert [h.level_info(l)[0] for l in range(h.nlevels)] == [lv.nt for lv in H.levels]
+    out, st = h.solve(torch.from_numpy(u0).cuda(), torch.from_numpy(U0).cuda())
+    assert st["iterations"] == ref.iterations
+    assert rel(out.cpu().numpy(), ref.U) < (1e-12 if precision == 0 else 1e-5)
+
+
+def test_rediscretised_coarse_operator():
+    """coarse_op = 1: the plain coarse SL step (no correction), as the oracle's coarse = "sl"."""
+    nx, nt, p, m = 64, 256, 3, 4
+    H = omg.build_hierarchy(osl.Grid(nx, nt, cfl=1.0), osl.WaveSpeed("const", a=1.0), p, m, coarse="sl")
+    u0 = W.u0_sin4(nx)
+    U0 = W.initial_iterate(nt, nx)
+    ref = omg.mgrit_solve(H, u0, U0)
+    h = mg.mgrit_setup(nx, nt, p, m, wave="const", a=1.0, cfl=1.0, coarse_op=1)
+    out, st = h.solve(torch.from_numpy(u0).cuda(), torch.from_numpy(U0).cuda())
+    assert st["iterations"] == ref.iterations
+    assert rel(out.cpu().numpy(), ref.U) < 1e-12
