@@ -206,19 +206,29 @@ def c_residual(H: Hierarchy, l: int, U: np.ndarray, g: np.ndarray, m: int) -> np
     return gc
 
 
-def vcycle(H: Hierarchy, l: int, U: np.ndarray, g: np.ndarray) -> None:
-    """One V-cycle on level l: FCF, coarse residual by injection, recursive coarse solve, correction, F."""
+def relax(H: Hierarchy, l: int, U: np.ndarray, g: np.ndarray, m: int, mode: str) -> None:
+    """The pre-relaxation of a cycle (Sec. 2.2): "FCF" (F, then C, then F) or "F" (F-relaxation only,
+    the Parareal form)."""
+    f_relax(H, l, U, g, m)
+    if mode == "FCF":
+        c_relax(H, l, U, g, m)
+        f_relax(H, l, U, g, m)
+    elif mode != "F":
+        raise ValueError(mode)
+
+
+def vcycle(H: Hierarchy, l: int, U: np.ndarray, g: np.ndarray, mode: str = "FCF") -> None:
+    """One V-cycle on level l: relaxation, coarse residual by injection, recursive coarse solve,
+    correction, F-relaxation."""
     if l == H.nlevels - 1:
         for n in range(1, U.shape[0]):
             U[n] = H.step(l, n - 1, U[n - 1]) + g[n]
         return
     m = H.levels[l + 1].m
-    f_relax(H, l, U, g, m)
-    c_relax(H, l, U, g, m)
-    f_relax(H, l, U, g, m)
+    relax(H, l, U, g, m, mode)
     gc = c_residual(H, l, U, g, m)
     Ec = np.zeros_like(gc)
-    vcycle(H, l + 1, Ec, gc)
+    vcycle(H, l + 1, Ec, gc, mode)
     N = U.shape[0] - 1
     for j in range(1, N // m + 1):
         U[j * m] += Ec[j]
@@ -234,7 +244,7 @@ class SolveResult:
 
 
 def mgrit_solve(H: Hierarchy, u0: np.ndarray, U_init: np.ndarray, rtol: float = 1e-10, max_iter: int = 200,
-                norm_mode: int = 1) -> SolveResult:
+                norm_mode: int = 1, mode: str = "FCF") -> SolveResult:
     """Iterate MGRIT V-cycles from U_init until the space-time residual drops by rtol (Sec. 2.2).
 
     norm_mode 0: r_0 is the 2-norm of the residual of the initial iterate over
@@ -247,6 +257,7 @@ def mgrit_solve(H: Hierarchy, u0: np.ndarray, U_init: np.ndarray, rtol: float = 
       F-relaxation; after cycle k the solve stops if k >= 1 and
       r_k < rtol r_0, and reports k + 1 cycles.  (With exact coarse solves this
       reproduces the constant-wave-speed columns of Table 2 exactly.)
+    mode: "FCF" (the paper's relaxation) or "F" (F-relaxation only, every level).
     """
     if H.nlevels < 2:
         raise ValueError("MGRIT needs at least two levels")
@@ -258,7 +269,7 @@ def mgrit_solve(H: Hierarchy, u0: np.ndarray, U_init: np.ndarray, rtol: float = 
         r0 = float(np.linalg.norm(residual(H, 0, U, g)))
         hist.append(r0)
         for it in range(1, max_iter + 1):
-            vcycle(H, 0, U, g)
+            vcycle(H, 0, U, g, mode)
             rk = float(np.linalg.norm(residual(H, 0, U, g)))
             hist.append(rk)
             if rk < rtol * r0:
@@ -267,14 +278,12 @@ def mgrit_solve(H: Hierarchy, u0: np.ndarray, U_init: np.ndarray, rtol: float = 
     m = H.levels[1].m
     N = U.shape[0] - 1
     for k in range(0, max_iter):
-        f_relax(H, 0, U, g, m)
-        c_relax(H, 0, U, g, m)
-        f_relax(H, 0, U, g, m)
+        relax(H, 0, U, g, m, mode)
         gc = c_residual(H, 0, U, g, m)
         rk = float(np.linalg.norm(gc))
         hist.append(rk)
         Ec = np.zeros_like(gc)
-        vcycle(H, 1, Ec, gc)
+        vcycle(H, 1, Ec, gc, mode)
         for j in range(1, N // m + 1):
             U[j * m] += Ec[j]
         f_relax(H, 0, U, g, m)

@@ -125,3 +125,48 @@ def test_table1_two_level_iterations(a, p, m, expect):
 @pytest.mark.parametrize("a,p,m,expect", read_table("table1_two_level_iters.txt"))
 def test_table1_two_level_iterations_all(a, p, m, expect):
     _table_case("table1", a, p, m, expect, levels=2)
+
+
+# ---------------------------------------------------------------------------
+# F-relaxation only (the Parareal form of Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+
+def _f_problem(nt=64, m=4, levels=2):
+    g = sl.Grid(48, nt)
+    ws = sl.WaveSpeed("sin_kx_cos_t", a=0.5, k=1.0)
+    return mg.build_hierarchy(g, ws, 3, m, levels=levels)
+
+
+def test_f_relaxation_two_level_is_exact_on_the_first_k_intervals_after_k_cycles():
+    """Two-level MGRIT with F-relaxation is Parareal: after k cycles the C-points j m, j <= k, equal
+    sequential stepping (and j = k + 1 does not yet)."""
+    H = _f_problem()
+    u0 = W.u0_bumps_1d(48, W.SEED_C2_BUMPS, 3)
+    seq = mg.sequential_solve(H, u0)
+    U0 = W.initial_iterate(64, 48)
+    for k in (1, 2, 3):
+        R = mg.mgrit_solve(H, u0, U0, max_iter=k, mode="F")
+        for j in range(1, k + 1):
+            assert np.max(np.abs(R.U[4 * j] - seq[4 * j])) < 1e-12
+        assert np.max(np.abs(R.U[4 * (k + 1)] - seq[4 * (k + 1)])) > 1e-8
+
+
+def test_f_relaxation_with_the_ideal_coarse_operator_converges_in_one_cycle():
+    g = sl.Grid(48, 64)
+    H = mg.build_hierarchy(g, sl.WaveSpeed("sin_kx_cos_t", a=0.5, k=1.0), 3, 4, levels=2, coarse="ideal")
+    u0 = W.u0_bumps_1d(48, W.SEED_C2_BUMPS, 3)
+    R = mg.mgrit_solve(H, u0, W.initial_iterate(64, 48), max_iter=1, mode="F")
+    seq = mg.sequential_solve(H, u0)
+    assert np.max(np.abs(R.U - seq)) < 1e-12
+
+
+def test_f_and_fcf_relaxation_reach_the_same_fixed_point():
+    H = _f_problem(nt=128, levels=0)
+    u0 = W.u0_bumps_1d(48, W.SEED_C2_BUMPS, 3)
+    U0 = W.initial_iterate(128, 48)
+    a = mg.mgrit_solve(H, u0, U0, mode="F")
+    b = mg.mgrit_solve(H, u0, U0, mode="FCF")
+    seq = mg.sequential_solve(H, u0)
+    assert a.converged and b.converged and a.iterations >= b.iterations
+    assert np.linalg.norm(a.U - seq) / np.linalg.norm(seq) < 1e-9
