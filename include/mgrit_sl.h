@@ -100,6 +100,10 @@ typedef struct {
                        iterations (default 10, at most 10) ... */
   double gmres_rtol;/* ... stopped at this relative residual (default 1e-2): the paper's setting for
                        multilevel and 2D runs (Sec. 3.4, 4.3).  1D correction solves are exact. */
+  int relax;        /* 0 (default): FCF relaxation on every level (Sec. 2.2, the paper's runs);
+                       1: F-relaxation only on every level -- with two levels this is Parareal
+                       (Sec. 2.2), which after k cycles reproduces the first k coarse intervals of
+                       sequential stepping exactly.  Single-problem solves only. */
 } mgrit_options;
 
 /* Phases timed when mgrit_options.profile = 1 (indices into mgrit_stats.phase_ms / phase_launches). */

@@ -121,6 +121,7 @@ struct RelaxArgs {
   void* fstore;        // optional F-point store, full level array [(N+1)][npts]
   void* cout;          // MODE_FC output (stride c_stride)
   const void* cin;     // MODE_RES: current C value (stride c_stride)
+  const void* cin_corr;  // MODE_RES: optional correction added to cin (stride corr_stride)
   void* rout;          // MODE_RES: residual output (stride r_stride)
   float* rout32;       // MODE_RES, FP64 passes: optional FP32 copy of the residual (stride r_stride)
   long long c_stride;

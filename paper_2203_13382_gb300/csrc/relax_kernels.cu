@@ -1164,6 +1164,7 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
       }
     } else {  // MODE_RES
       const R* ci = a.cin ? (const R*)a.cin + (size_t)(j + 1) * a.c_stride : nullptr;
+      const R* cc = a.cin_corr ? (const R*)a.cin_corr + (size_t)(j + 1) * a.corr_stride : nullptr;
       R* ro = (R*)a.rout + (size_t)(j + 1) * a.r_stride;
       float* ro32 = a.rout32 ? a.rout32 + (size_t)(j + 1) * a.r_stride : nullptr;
       R sqt = (R)0;  // FP32 levels accumulate their (FP32) residual in FP32 per thread
@@ -1171,6 +1172,7 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
         R v = dst[i];
         if (gr && a.g_at_c) v += gr[i];
         if (ci) v -= ci[i];
+        if (cc) v -= cc[i];
         ro[i] = v;
         if (ro32) ro32[i] = (float)v;
         if (a.norm_partial) sqt += v * v;

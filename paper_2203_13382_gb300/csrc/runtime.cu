@@ -354,27 +354,32 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   }
   Level& Lc = h->levels[l + 1];
   const int m = Lc.m, J = L.nt / m;
-  // F- then C-relaxation from a zero initial guess
-  RelaxArgs a = args0();
-  a.m = m;
-  a.J = J;
-  a.nsteps = m;
-  a.mode = MODE_FC;
-  a.g = L.G;
-  a.cout = L.E;
-  a.c_stride = (long long)m * np;
-  MG_TRY(relax(h, l, dbl, a, MGRIT_PHASE_COARSE));
-  // F-relaxation and the C-point residual -> right-hand side of level l+1
+  const bool fcf = h->opt.relax == 0;
+  RelaxArgs a;
+  if (fcf) {
+    // F- then C-relaxation from a zero initial guess
+    a = args0();
+    a.m = m;
+    a.J = J;
+    a.nsteps = m;
+    a.mode = MODE_FC;
+    a.g = L.G;
+    a.cout = L.E;
+    a.c_stride = (long long)m * np;
+    MG_TRY(relax(h, l, dbl, a, MGRIT_PHASE_COARSE));
+  }
+  // F-relaxation and the C-point residual -> right-hand side of level l+1 (F-relaxation only: from the
+  // zero initial guess, whose C-points stay zero)
   a = args0();
   a.m = m;
   a.J = J;
   a.nsteps = m;
   a.mode = MODE_RES;
-  a.start = L.E;
+  a.start = fcf ? L.E : nullptr;
   a.start_stride = (long long)m * np;
   a.g = L.G;
   a.g_at_c = 1;
-  a.cin = L.E;
+  a.cin = fcf ? L.E : nullptr;
   a.c_stride = (long long)m * np;
   a.rout = Lc.G;
   a.r_stride = np;
@@ -386,7 +391,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   a.J = J;
   a.nsteps = m - 1;
   a.mode = MODE_POST;
-  a.start = L.E;
+  a.start = fcf ? L.E : nullptr;
   a.start_stride = (long long)m * np;
   a.corr = Lc.E;
   a.corr_stride = np;
@@ -510,6 +515,7 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->profile = 0;
   opt->gmres_maxit = 10;
   opt->gmres_rtol = 1e-2;
+  opt->relax = 0;
   return MGRIT_OK;
 }
 
@@ -531,6 +537,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   if (opt.coarse_fp64 != 0) return fail(MGRIT_EUNSUPPORTED, "coarse_fp64 is not implemented");
   if (opt.gmres_maxit < 1 || opt.gmres_maxit > 10) return fail(MGRIT_EINVAL, "gmres_maxit must be in 1..10");
   if (!(opt.gmres_rtol >= 0.0 && opt.gmres_rtol < 1.0)) return fail(MGRIT_EINVAL, "gmres_rtol must be in [0, 1)");
+  if (opt.relax != 0 && opt.relax != 1) return fail(MGRIT_EINVAL, "relax must be 0 (FCF) or 1 (F)");
   if (levels < 0 || levels == 1) return fail(MGRIT_EINVAL, "levels must be 0 or >= 2");
   std::vector<int> fac = factors(grid->nt, m, opt.m_first, levels, opt.max_coarsest);
   if (fac.empty()) return fail(MGRIT_EINVAL, "nt does not allow a coarse level with this m");
@@ -744,8 +751,32 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
   bool converged = false;
   mgrit_status status = MGRIT_OK;
   // one cycle's device work (FP64: reads X, writes Y; the caller swaps the pointers afterwards)
+  const bool fcf = h->opt.relax == 0;
   auto cycle = [&](int k) -> mgrit_status {
-    if (!fp32) {
+    if (!fp32 && !fcf) {
+      // F-relaxation only: one pass from the corrected C-points X + E_1 (written to Y for the next
+      // cycle), F-relaxation and the C-point residual against the corrected C-points
+      RelaxArgs a = args0();
+      a.m = m1;
+      a.J = J;
+      a.nsteps = m1;
+      a.mode = MODE_RES;
+      a.start = h->X;
+      a.start_stride = np;
+      a.corr = k > 0 ? L1.E : nullptr;
+      a.corr_stride = np;
+      a.start_wb = h->Y;
+      a.wb_stride = np;
+      a.extra_cta = 1;
+      a.cin = h->X;
+      a.cin_corr = k > 0 ? L1.E : nullptr;
+      a.c_stride = np;
+      a.rout = L1.G;
+      a.r_stride = np;
+      a.norm_partial = h->norm_partial;
+      MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_RES));
+      MG_TRY(coarse_cycle(h, 1));
+    } else if (!fp32) {
       // FCF relaxation on level 0; the correction of the previous cycle is fused into the first pass
       RelaxArgs a = args0();
       a.m = m1;
@@ -785,8 +816,20 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
       a.cin = h->X;
       a.c_stride = np;
       a.rout = h->r64;
-      a.rout32 = h->EC;  // C-relaxation of the error equation from a zero guess gives e_C = r (FP32)
       a.r_stride = np;
+      if (!fcf) {
+        // F-relaxation only: on the error equation from a zero guess the F-points stay zero and the
+        // C-point residual is r itself, the right-hand side of level 1; then u_C += E_1
+        a.rout32 = (float*)L1.G;
+        a.norm_partial = h->norm_partial;
+        MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_RES));
+        MG_TRY(coarse_cycle(h, 1));
+        const int ev = h->phase_begin();
+        launch_axpy_convert(2, L1.E, h->X, nullptr, (long long)(J + 1) * np, s);
+        h->phase_end(MGRIT_PHASE_MISC, ev, 1);
+        return enqueue_norm(h, J);
+      }
+      a.rout32 = h->EC;  // C-relaxation of the error equation from a zero guess gives e_C = r (FP32)
       MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_RES));
       // F-relaxation + residual of the error equation in FP32
       a = args0();
@@ -1346,6 +1389,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
   if (opt_in) opt = *opt_in;
   else mgrit_default_options(&opt);
   if (opt.precision != 1) return fail(MGRIT_EUNSUPPORTED, "batched solves run the FP32-bulk mode (precision 1)");
+  if (opt.relax != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves run FCF relaxation (relax 0)");
   if (opt.coarse_op != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves use the corrected coarse operator");
   for (int q = 0; q < nprob; ++q)
     if (grids[q].dim != 1) return fail(MGRIT_EUNSUPPORTED, "batched solves are 1D");
