@@ -170,6 +170,25 @@ def phase_work(phase: str, wl: dict, launches: int, iterations: int) -> dict | N
         byts = pts * (2 + 4) + 2 * J * nx * 4
         flops = pts * (2 * (p + 1) + 3 * (p + 1))
         return {"bytes": byts, "flops": flops, "fp": 32}
+    if phase == "coarse" and wl.get("coarse_levels_fp64"):
+        # FP64 coarse levels: per point-step the shift (2 B), p+1 FP64 weights, the stored factorisation
+        # of M (solver reals per row, FP64) and the right-hand side row (8 B); each stored factor value
+        # enters one FMA, plus the gather's p+1 FMAs
+        nts = level_steps(wl)
+        B, P = (p + 1) // 2, nx // 8
+        T = P.bit_length() - 1
+        q = 8 - B
+        reals = (q * (2 * B + 1) + 2 * q * B + 2 * B * B) * P + T * 2 * B * B * P + B * B * P
+        per_pt_b = 2 + 8 * (p + 1) + 8 * reals / nx + 8
+        per_pt_f = 2 * (p + 1) + 2 * reals / nx
+        byts = flops = 0.0
+        for l in range(1, len(nts) - 1):
+            ntl, Jl = nts[l], nts[l] // m
+            steps = 2 * ntl * nx + (ntl - Jl) * nx  # FC, RES (m steps an interval), POST (m - 1)
+            byts += steps * per_pt_b + 7 * Jl * nx * 8 + (ntl - Jl) * nx * 8
+            flops += steps * per_pt_f
+        return {"bytes": byts * iterations / max(launches, 1), "flops": flops * iterations / max(launches, 1),
+                "fp": 64}
     if phase == "coarse":
         # relaxation levels 1 .. L-2, passes FC, RES, POST per cycle; per coarse point-step the staged
         # tables (eps 4 B, shift 2 B, sigma 4 B) and the right-hand side row (4 B), POST also stores
@@ -196,7 +215,7 @@ def roofline_of(phase: str, stats: dict, wl: dict, hbm_peak: float, hbm_src: str
     avg_s = ms[phase] / nl[phase] / 1e3
     t_hbm = w["bytes"] / (hbm_peak * 1e9)
     t_alu = w["flops"] / (FP64_PEAK_TFLOPS * 1e12) if w["fp"] == 64 else 0.0
-    kern = {"coarse": "k_relax_1d<p, float, coarse> (coarse levels)", "fine32_res": "k_relax_1d<p, float> (level 0)",
+    kern = {"coarse": "k_relax_1d<p, %s, coarse> (coarse levels)" % ("double" if wl.get("coarse_levels_fp64") else "float"), "fine32_res": "k_relax_1d<p, float> (level 0)",
             "fine64_res": "k_relax_1d<p, double> (level 0 residual)"}.get(phase, f"k_relax_1d ({phase})")
     out = {"kernel": kern, "phase": phase, "phase_share": ms[phase] / max(sum(ms.values()), 1e-30),
            "avg_launch_ms": avg_s * 1e3}
@@ -295,7 +314,10 @@ def run_ours(args) -> None:
         wl["workload"] = WORKLOAD["workload"].replace(f"nt{WORKLOAD['nt']}", f"nt{args.nt}")
     nx, nt = wl["nx"], wl["nt"]
     dof = nx * nt
-    prec = 1 if args.precision == "fp32bulk" else 0
+    prec = 0 if args.precision == "fp64" else 1
+    cf64 = 1 if args.precision == "fp32bulk_coarse64" else 0
+    wl["precision"] = args.precision
+    wl["coarse_levels_fp64"] = 1 if (prec == 0 or cf64) else 0
     u0_h = W.u0_bumps_1d(nx, W.SEED_C2_BUMPS, 3)
     U_h = W.initial_iterate(nt, nx)
     u0 = torch.from_numpy(u0_h).cuda()
@@ -305,7 +327,8 @@ def run_ours(args) -> None:
 
     def one_step(profile: int):
         h = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
-                           max_coarsest=wl["max_coarsest"], precision=prec, rtol=wl["rtol"], profile=profile)
+                           max_coarsest=wl["max_coarsest"], precision=prec, coarse_fp64=cf64, rtol=wl["rtol"],
+                           profile=profile)
         _, st = h.solve(u0, U0, u_out)
         h.destroy()
         return st
@@ -402,7 +425,7 @@ def run_ours(args) -> None:
         t0 = time.perf_counter()
         for _ in range(ne2e):
             he = mg.mgrit_setup(nx, nt, wl["order"], wl["m"], wave=wl["wave"], a=wl["a"], k=wl["k"], cfl=wl["cfl"],
-                                max_coarsest=wl["max_coarsest"], precision=prec, rtol=wl["rtol"])
+                                max_coarsest=wl["max_coarsest"], precision=prec, coarse_fp64=cf64, rtol=wl["rtol"])
             he.solve_host(u0_pin.numpy(), U_pin.numpy(), out_pin.numpy())
             he.destroy()
         torch.cuda.synchronize()
@@ -700,7 +723,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32bulk", "fp64"], default="fp32bulk")
+    ap.add_argument("--precision", choices=["fp32bulk", "fp64", "fp32bulk_coarse64"], default="fp32bulk",
+                    help="fp32bulk_coarse64: FP32 error relaxation on level 0, FP64 coarse cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the sequential comparator and e2e runs")
     ap.add_argument("--nt", type=int, default=0, help="override nt (small profiling cases only)")

@@ -90,8 +90,10 @@ typedef struct {
                        the paper's rule: coarsen until fewer than two time points would remain) */
   int m_first;      /* 0 (default): factor m on every level; > 0: this factor on level 1 and m below
                        (the aggressive coarsening of Sec. 5) */
-  int coarse_fp64;  /* precision == 1 only: 1 = coarse levels and correction solves in FP64,
-                       0 (default) = FP32 like the rest of the error cycle */
+  int coarse_fp64;  /* precision == 1 only: 1 = the coarse cycle (levels >= 1: relaxation, coarse
+                       residuals, correction solves, coarsest solve) in FP64 with only level 0's
+                       error relaxation in FP32; 0 (default) = FP32 like the rest of the error
+                       cycle.  Single-problem solves only. */
   int use_graph;    /* 1 (default): each MGRIT cycle's launches are captured once per mgrit_solve call as
                        a CUDA graph and replayed (one host launch per cycle); 0: launched one by one.
                        Results are identical either way. */
@@ -104,6 +106,12 @@ typedef struct {
                        1: F-relaxation only on every level -- with two levels this is Parareal
                        (Sec. 2.2), which after k cycles reproduces the first k coarse intervals of
                        sequential stepping exactly.  Single-problem solves only. */
+  int cluster_coarse; /* 1 (default): on 1D FP64 coarse levels with few intervals (and the FP64
+                       coarsest solve) each interval's slice is split over a thread-block cluster of
+                       up to 16 CTAs, so more SMs share its FP64 steps, sized so that the level's
+                       clusters are resident at once; 2, 4, 8, 16: that cluster size on every FP64
+                       coarse pass (where the slice allows it); 0: one CTA per interval.  Results
+                       are identical either way. */
 } mgrit_options;
 
 /* Phases timed when mgrit_options.profile = 1 (indices into mgrit_stats.phase_ms / phase_launches). */

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_NAME = "libmgrit_sl.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
-SOURCES = ["setup_kernels.cu", "relax_kernels.cu", "kernels2d.cu", "seq_cluster.cu", "runtime.cu"]
+SOURCES = ["setup_kernels.cu", "relax_kernels.cu", "kernels2d.cu", "seq_cluster.cu", "coarse_cluster.cu",
+           "runtime.cu"]
 HEADERS = ["common.cuh", "physics.cuh", "kernels.h", "solver_layout.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -101,6 +101,10 @@ struct LevelTables {
   // bperm[row][bstart[row][key] .. bstart[row][key+1]) lists them in increasing order.
   const int* bstart;  // [nt][npts + 1]
   const int* bperm;   // [nt][npts]
+  // 1D FP64 coarse levels: 0 = one CTA per interval; 1 = passes over few intervals split each interval
+  // over a thread-block cluster sized automatically; 2..16 = that cluster size (coarse_cluster.cu;
+  // identical results)
+  int cluster;
 };
 
 
@@ -124,6 +128,7 @@ struct RelaxArgs {
   const void* cin_corr;  // MODE_RES: optional correction added to cin (stride corr_stride)
   void* rout;          // MODE_RES: residual output (stride r_stride)
   float* rout32;       // MODE_RES, FP64 passes: optional FP32 copy of the residual (stride r_stride)
+  int rout_f64;        // MODE_RES, FP32 passes: rout holds doubles (an FP64 coarse level's right-hand side)
   long long c_stride;
   long long r_stride;
   int g_at_c;          // MODE_RES: add g at the C-point
@@ -132,6 +137,12 @@ struct RelaxArgs {
 
 // is_double selects FP64 (tables w64) or FP32 (tables eps32) arithmetic and storage.
 cudaError_t launch_relax_1d(const LevelTables& T, const RelaxArgs& a, int is_double, cudaStream_t st);
+
+// FP64 coarse passes split over a cluster of C CTAs per interval (coarse_cluster.cu).  cluster_relax_size
+// returns the cluster size for this pass (1: use the one-CTA-per-interval kernel); the launch returns
+// cudaErrorNotSupported when no cluster of that size (or a smaller power of two) can be formed.
+int cluster_relax_size(const LevelTables& T, const RelaxArgs& a);
+cudaError_t launch_relax_cluster_1d(const LevelTables& T, const RelaxArgs& a, int C, cudaStream_t st);
 
 // Sequential stepping over all steps of a level: u[n+1] = Phi_n u[n] + g[n+1], n = 0..N-1 (coarsest
 // level solve, and the fine-level comparator), from u0 ([npts]; NULL = zero).  store_all = 1: out is
@@ -193,7 +204,7 @@ void launch_sum_batched(const Segment* d_seg, int nseg, cudaStream_t st);
 // Deterministic sum of `count` doubles (fixed order): out[0] = sum.
 void launch_sum(const double* v, int count, double* out, cudaStream_t st);
 // Elementwise update with type conversion: kind 0: y = x (d); 1: y(f) = x(d); 2: y(d) += x(f);
-// 3: y(d) = x(f); 4: y(d) += x(d); 5: y(d) += x(d) + z(f); 6: y(d) = x(d) - z(d).
+// 3: y(d) = x(f); 4: y(d) += x(d); 5: y(d) += x(d) + z(f); 6: y(d) = x(d) - z(d); 7: y(d) += x(d) + z(d).
 void launch_axpy_convert(int kind, const void* x, void* y, const void* z, long long n, cudaStream_t st);
 // zero fill
 void launch_fill_zero(void* y, long long bytes, cudaStream_t st);

@@ -1165,7 +1165,8 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
     } else {  // MODE_RES
       const R* ci = a.cin ? (const R*)a.cin + (size_t)(j + 1) * a.c_stride : nullptr;
       const R* cc = a.cin_corr ? (const R*)a.cin_corr + (size_t)(j + 1) * a.corr_stride : nullptr;
-      R* ro = (R*)a.rout + (size_t)(j + 1) * a.r_stride;
+      R* ro = a.rout_f64 ? nullptr : (R*)a.rout + (size_t)(j + 1) * a.r_stride;
+      double* ro64 = a.rout_f64 ? (double*)a.rout + (size_t)(j + 1) * a.r_stride : nullptr;
       float* ro32 = a.rout32 ? a.rout32 + (size_t)(j + 1) * a.r_stride : nullptr;
       R sqt = (R)0;  // FP32 levels accumulate their (FP32) residual in FP32 per thread
       for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -1173,7 +1174,8 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
         if (gr && a.g_at_c) v += gr[i];
         if (ci) v -= ci[i];
         if (cc) v -= cc[i];
-        ro[i] = v;
+        if (ro64) ro64[i] = (double)v;
+        else ro[i] = v;
         if (ro32) ro32[i] = (float)v;
         if (a.norm_partial) sqt += v * v;
       }
@@ -1439,6 +1441,7 @@ __global__ void k_axpy_convert(int kind, const void* __restrict__ x, void* __res
     case 3: ((double*)y)[i] = (double)((const float*)x)[i]; break;
     case 4: ((double*)y)[i] += ((const double*)x)[i]; break;
     case 5: ((double*)y)[i] += ((const double*)x)[i] + (double)((const float*)z)[i]; break;
+    case 7: ((double*)y)[i] += ((const double*)x)[i] + ((const double*)z)[i]; break;
     default: ((double*)y)[i] = ((const double*)x)[i] - ((const double*)z)[i]; break;
   }
 }
@@ -1450,6 +1453,14 @@ cudaError_t launch_relax_1d(const LevelTables& T, const RelaxArgs& a, int is_dou
   if (T.trans) {
     if (!is_double) return cudaErrorInvalidValue;
     return coarse ? relax_dispatch<double, true, true>(T, a, st) : relax_dispatch<double, false, true>(T, a, st);
+  }
+  if (is_double && coarse && T.cluster) {
+    const int C = cluster_relax_size(T, a);
+    if (C > 1) {
+      const cudaError_t e = launch_relax_cluster_1d(T, a, C, st);
+      if (e != cudaErrorNotSupported) return e;
+      cudaGetLastError();
+    }
   }
   if (is_double)
     return coarse ? relax_dispatch<double, true, false>(T, a, st) : relax_dispatch<double, false, false>(T, a, st);

@@ -269,6 +269,7 @@ struct mgrit_handle {
     T.frange = L.frange;
     T.bstart = L.bstart;
     T.bperm = L.bperm;
+    T.cluster = opt.cluster_coarse;
     if (trans_mode) {
       T.trans = 1;
       T.reverse = 1;
@@ -345,6 +346,21 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   const int np = h->npts;
   const int dbl = L.is_double;
   if (l == (int)h->levels.size() - 1) {  // coarsest: sequential stepping (Sec. 2.2)
+    if (h->grid.dim == 1 && dbl && h->opt.cluster_coarse && h->opt.coarse_op == 0 && !h->trans_mode) {
+      // FP64: one interval of nt steps through the relaxation pass (FC: F-points stored, the last step
+      // is the C-point), which splits the slice over a thread-block cluster
+      RelaxArgs a = args0();
+      a.m = L.nt;
+      a.J = 1;
+      a.nsteps = L.nt;
+      a.mode = MODE_FC;
+      a.start_wb = L.E;
+      a.g = L.G;
+      a.fstore = L.E;
+      a.cout = L.E;
+      a.c_stride = (long long)L.nt * np;
+      return relax(h, l, dbl, a, MGRIT_PHASE_COARSEST);
+    }
     LevelTables T = h->tables(l, dbl);
     const int ev = h->phase_begin();
     if (h->grid.dim == 2) MG_CUDA(launch_sequential_2d(T, L.nt, L.G, nullptr, L.E, 1, h->s2d, dbl, h->stream));
@@ -516,6 +532,7 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->gmres_maxit = 10;
   opt->gmres_rtol = 1e-2;
   opt->relax = 0;
+  opt->cluster_coarse = 1;
   return MGRIT_OK;
 }
 
@@ -534,10 +551,13 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   if (!(opt.rtol > 0.0 && opt.rtol < 1.0)) return fail(MGRIT_EINVAL, "rtol must be in (0, 1)");
   if (opt.max_coarsest < 1) return fail(MGRIT_EINVAL, "max_coarsest must be >= 1");
   if (opt.m_first < 0 || opt.m_first == 1) return fail(MGRIT_EINVAL, "m_first must be 0 or >= 2");
-  if (opt.coarse_fp64 != 0) return fail(MGRIT_EUNSUPPORTED, "coarse_fp64 is not implemented");
+  if (opt.coarse_fp64 != 0 && opt.coarse_fp64 != 1) return fail(MGRIT_EINVAL, "coarse_fp64 must be 0 or 1");
+  if (opt.coarse_fp64 && opt.precision != 1) return fail(MGRIT_EINVAL, "coarse_fp64 applies to precision 1 only");
   if (opt.gmres_maxit < 1 || opt.gmres_maxit > 10) return fail(MGRIT_EINVAL, "gmres_maxit must be in 1..10");
   if (!(opt.gmres_rtol >= 0.0 && opt.gmres_rtol < 1.0)) return fail(MGRIT_EINVAL, "gmres_rtol must be in [0, 1)");
   if (opt.relax != 0 && opt.relax != 1) return fail(MGRIT_EINVAL, "relax must be 0 (FCF) or 1 (F)");
+  if (opt.cluster_coarse < 0 || opt.cluster_coarse > 16 || (opt.cluster_coarse & (opt.cluster_coarse - 1)) != 0)
+    return fail(MGRIT_EINVAL, "cluster_coarse must be 0, 1, 2, 4, 8 or 16");
   if (levels < 0 || levels == 1) return fail(MGRIT_EINVAL, "levels must be 0 or >= 2");
   std::vector<int> fac = factors(grid->nt, m, opt.m_first, levels, opt.max_coarsest);
   if (fac.empty()) return fail(MGRIT_EINVAL, "nt does not allow a coarse level with this m");
@@ -556,6 +576,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   const double hgrid = (grid->xmax - grid->xmin) / nx;
   const double dt = grid->cfl * hgrid;
   const int fp32 = opt.precision == 1;
+  const int cf64 = fp32 && opt.coarse_fp64;  // FP32 bulk on level 0 only, FP64 coarse cycle
 
   auto cleanup_fail = [&](mgrit_status s) {
     delete h;
@@ -573,11 +594,11 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
   for (size_t l = 0; l < h->levels.size(); ++l) {
     Level& L = h->levels[l];
     const size_t rows = (size_t)L.nt * np * dim;  // 2D: x block then y block
-    L.is_double = fp32 ? 0 : 1;
+    L.is_double = (fp32 && !(cf64 && l > 0)) ? 0 : 1;
     if ((st = h->alloc(&L.s64, rows)) != MGRIT_OK) return cleanup_fail(st);
     if ((st = h->alloc(&L.shift, rows)) != MGRIT_OK) return cleanup_fail(st);
-    const bool need64 = !fp32 || l == 0;  // FP64 levels read precomputed weights (2D: per axis)
-    const bool need32 = fp32;
+    const bool need64 = L.is_double || l == 0;  // FP64 levels read precomputed weights (2D: per axis)
+    const bool need32 = !L.is_double;
     if (need64 && (st = h->alloc(&L.w64, rows * (p + 1))) != MGRIT_OK) return cleanup_fail(st);
     if (need32 && (st = h->alloc(&L.eps32, rows)) != MGRIT_OK) return cleanup_fail(st);
     if (l > 0) {
@@ -611,7 +632,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     for (size_t l = 1; l + 1 < h->levels.size(); ++l)
       jc = std::max(jc, (size_t)(h->levels[l].nt / h->levels[l + 1].m));
     jmax = std::max(jmax, jc);
-    const size_t rsz = fp32 ? sizeof(float) : sizeof(double);
+    const size_t rsz = (fp32 && !cf64) ? sizeof(float) : sizeof(double);  // coarse GMRES basis
     h->s2d.kmax = opt.gmres_maxit;
     h->s2d.rtol = opt.gmres_rtol;
     if ((st = h->alloc((char**)&h->s2d.cur, jmax * np * sizeof(double))) != MGRIT_OK) return cleanup_fail(st);
@@ -820,12 +841,13 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
       if (!fcf) {
         // F-relaxation only: on the error equation from a zero guess the F-points stay zero and the
         // C-point residual is r itself, the right-hand side of level 1; then u_C += E_1
-        a.rout32 = (float*)L1.G;
+        if (L1.is_double) a.rout = L1.G;  // FP64 coarse cycle: r is its right-hand side as it is
+        else a.rout32 = (float*)L1.G;
         a.norm_partial = h->norm_partial;
         MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_RES));
         MG_TRY(coarse_cycle(h, 1));
         const int ev = h->phase_begin();
-        launch_axpy_convert(2, L1.E, h->X, nullptr, (long long)(J + 1) * np, s);
+        launch_axpy_convert(L1.is_double ? 4 : 2, L1.E, h->X, nullptr, (long long)(J + 1) * np, s);
         h->phase_end(MGRIT_PHASE_MISC, ev, 1);
         return enqueue_norm(h, J);
       }
@@ -840,6 +862,7 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
       a.start = h->EC;
       a.start_stride = np;
       a.rout = L1.G;
+      a.rout_f64 = L1.is_double;
       a.r_stride = np;
       a.norm_partial = h->norm_partial;
       MG_TRY(relax(h, 0, 0, a, MGRIT_PHASE_FINE32_RES));
@@ -847,7 +870,7 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
       // u_C += r + E_1
       {
         const int ev = h->phase_begin();
-        launch_axpy_convert(5, h->r64, h->X, L1.E, (long long)(J + 1) * np, s);
+        launch_axpy_convert(L1.is_double ? 7 : 5, h->r64, h->X, L1.E, (long long)(J + 1) * np, s);
         h->phase_end(MGRIT_PHASE_MISC, ev, 1);
       }
     }
@@ -1390,6 +1413,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
   else mgrit_default_options(&opt);
   if (opt.precision != 1) return fail(MGRIT_EUNSUPPORTED, "batched solves run the FP32-bulk mode (precision 1)");
   if (opt.relax != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves run FCF relaxation (relax 0)");
+  if (opt.coarse_fp64 != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves run FP32 coarse levels (coarse_fp64 0)");
   if (opt.coarse_op != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves use the corrected coarse operator");
   for (int q = 0; q < nprob; ++q)
     if (grids[q].dim != 1) return fail(MGRIT_EUNSUPPORTED, "batched solves are 1D");
