@@ -13,9 +13,16 @@ namespace mgrit {
 // K1: fine departure offsets (Sec. 2.1 eq. (depart_ODE); Sec. 4.1 eq. (SL2D_char1-2))
 // ------------------------------------------------------------------------------------------------
 
-// sin and cos of a small angle: Taylor polynomials (truncation below 3e-19 for |t| < 1/8), else sincos.
+// sin and cos of a small angle: Taylor polynomials, else sincos.  |t| < 2^-7 (the stage offsets of the
+// fine steps): sin to t^5, cos to t^6, truncation below 5e-17 relative; |t| < 1/8: sin to t^9, cos to
+// t^10, truncation below 3e-19.
 MGRIT_D void small_sincos(double t, double& st, double& ct) {
-  if (fabs(t) < 0.125) {
+  const double at = fabs(t);
+  if (at < 0.0078125) {
+    const double t2 = t * t;
+    st = t * (1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120)));
+    ct = 1.0 + t2 * (-0.5 + t2 * (1.0 / 24 + t2 * (-1.0 / 720)));
+  } else if (at < 0.125) {
     const double t2 = t * t;
     st = t * (1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040 + t2 * (1.0 / 362880)))));
     ct = 1.0 + t2 * (-0.5 + t2 * (1.0 / 24 + t2 * (-1.0 / 720 + t2 * (1.0 / 40320 + t2 * (-1.0 / 3628800)))));
@@ -369,12 +376,29 @@ MGRIT_D double frac_eps(double s) {
 }
 
 // prod_{q=-(p+1)/2}^{(p-1)/2} (q + z) = (p+1)! f_{p+1}(z)  (eq. (fpoly_def) without its constant factor).
+// prod_{q=-L}^{L-1} (q + z), L = (P+1)/2, evaluated as its monic polynomial in z by Horner's rule
+// (integer coefficients, exact; P + 1 multiply-adds instead of P + 1 adds and P multiplies).
+template <int P>
+struct FProdCoef {
+  double c[P + 2];  // c[d]: coefficient of z^d
+  constexpr FProdCoef() : c{} {
+    constexpr int L = (P + 1) / 2;
+    c[0] = 1.0;
+    int deg = 0;
+    for (int q = -L; q <= L - 1; ++q) {  // multiply by (z + q)
+      for (int d = deg + 1; d >= 1; --d) c[d] = c[d - 1] + q * c[d];
+      c[0] = q * c[0];
+      ++deg;
+    }
+  }
+};
+
 template <int P>
 MGRIT_D double f_prod(double z) {
-  constexpr int L = (P + 1) / 2;
+  constexpr FProdCoef<P> k{};
   double out = 1.0;
 #pragma unroll
-  for (int q = -L; q <= L - 1; ++q) out = out * (q + z);
+  for (int d = P; d >= 0; --d) out = out * z + k.c[d];
   return out;
 }
 
