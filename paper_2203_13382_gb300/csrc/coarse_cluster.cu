@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(kClusterRelaxThreads, P <= 3 ? 2 : 1) k_relax_
       for (int q = threadIdx.x; q < chunk; q += kClusterRelaxThreads) {
         double v = dst[q];
         if (gr && a.g_at_c) v += gr[q];
-        if (ci) v -= ci[q];
-        if (cc) v -= cc[q];
+        if (cc) v -= (ci ? ci[q] : 0.0) + cc[q];
+        else if (ci) v -= ci[q];
         ro[q] = v;
         if (ro32) ro32[q] = (float)v;
       }

@@ -31,23 +31,46 @@ MGRIT_HD double lagrange_denominator_inv(int a) {
   return (((P - a) & 1) ? -1.0 : 1.0) / (f * g);
 }
 
+// Monomial coefficients of the Lagrange basis polynomials of lagrange_weights: c[a][d] is the
+// coefficient of eps^d in w_a(eps) = prod_{b != a} (-eps - j_b) / prod_{b != a} (j_a - j_b), j_b = b - L.
+// Formed at compile time in FP64 (the products have integer coefficients; one rounding by the
+// denominator).
+template <int P>
+struct LagrangeCoef {
+  double c[P + 1][P + 1];
+  constexpr LagrangeCoef() : c{} {
+    constexpr int L = (P + 1) / 2;
+    for (int a = 0; a <= P; ++a) {
+      double poly[P + 1] = {};
+      poly[0] = 1.0;
+      int deg = 0;
+      for (int b = 0; b <= P; ++b) {
+        if (b == a) continue;
+        const double q = -(double)(b - L);  // factor (q - eps)
+        for (int d = deg + 1; d >= 1; --d) poly[d] = q * poly[d] - poly[d - 1];
+        poly[0] = q * poly[0];
+        ++deg;
+      }
+      double den = 1.0;  // prod_{b != a} (a - b) = (-1)^{P-a} a! (P-a)!
+      for (int b = 0; b <= P; ++b)
+        if (b != a) den *= (double)(a - b);
+      for (int d = 0; d <= P; ++d) c[a][d] = poly[d] / den;
+    }
+  }
+};
+
 // Lagrange weights w_a(eps), a = 0..P, for interpolation at the point -eps relative to the east
-// node, with nodes j = a - (P+1)/2 (Sec. 2.1).  Prefix/suffix products of the factors (-eps - j).
+// node, with nodes j = a - (P+1)/2 (Sec. 2.1), each by Horner's rule on its monomial coefficients
+// (P multiply-adds a weight).
 template <int P, typename R>
 MGRIT_D void lagrange_weights(R eps, R (&w)[P + 1]) {
-  constexpr int L = (P + 1) / 2;
-  R f[P + 1];
+  constexpr LagrangeCoef<P> k{};
 #pragma unroll
-  for (int a = 0; a <= P; ++a) f[a] = -eps - (R)(a - L);
-  R pre[P + 1];
-  pre[0] = (R)1;
+  for (int a = 0; a <= P; ++a) {
+    R v = (R)k.c[a][P];
 #pragma unroll
-  for (int a = 1; a <= P; ++a) pre[a] = pre[a - 1] * f[a - 1];
-  R suf = (R)1;
-#pragma unroll
-  for (int a = P; a >= 0; --a) {
-    w[a] = pre[a] * suf * (R)lagrange_denominator_inv<P>(a);
-    suf *= f[a];
+    for (int d = P - 1; d >= 0; --d) v = v * eps + (R)k.c[a][d];
+    w[a] = v;
   }
 }
 

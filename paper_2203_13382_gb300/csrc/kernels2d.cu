@@ -516,8 +516,9 @@ __global__ void __launch_bounds__(kThreads2d) k_finish2d(const R* __restrict__ c
       ((R*)a.cout)[(size_t)(j + 1) * a.c_stride + pt] = v;
     } else {
       if (gr && a.g_at_c) v += gr[pt];
-      if (a.cin) v -= ((const R*)a.cin)[(size_t)(j + 1) * a.c_stride + pt];
-      if (a.cin_corr) v -= ((const R*)a.cin_corr)[(size_t)(j + 1) * a.corr_stride + pt];
+      const R ci = a.cin ? ((const R*)a.cin)[(size_t)(j + 1) * a.c_stride + pt] : (R)0;
+      if (a.cin_corr) v -= ci + ((const R*)a.cin_corr)[(size_t)(j + 1) * a.corr_stride + pt];
+      else if (a.cin) v -= ci;
       if (a.rout_f64) ((double*)a.rout)[(size_t)(j + 1) * a.r_stride + pt] = (double)v;
       else ((R*)a.rout)[(size_t)(j + 1) * a.r_stride + pt] = v;
       if (a.rout32) a.rout32[(size_t)(j + 1) * a.r_stride + pt] = (float)v;

@@ -264,16 +264,16 @@ constexpr float dcoef(int o) {
 template <int B>
 __device__ __forceinline__ void inv_small(const float (&A)[B * B], float (&R)[B * B]) {
   if constexpr (B == 1) {
-    R[0] = 1.f / A[0];
+    R[0] = __frcp_rn(A[0]);
   } else if constexpr (B == 2) {
-    const float id = 1.f / (A[0] * A[3] - A[1] * A[2]);
+    const float id = __frcp_rn(A[0] * A[3] - A[1] * A[2]);
     R[0] = A[3] * id;
     R[1] = -A[1] * id;
     R[2] = -A[2] * id;
     R[3] = A[0] * id;
   } else {  // adjugate / determinant
     const float c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
-    const float id = 1.f / (A[0] * c00 + A[1] * c01 + A[2] * c02);
+    const float id = __frcp_rn(A[0] * c00 + A[1] * c01 + A[2] * c02);
     R[0] = c00 * id;
     R[1] = (A[2] * A[7] - A[1] * A[8]) * id;
     R[2] = (A[1] * A[5] - A[2] * A[4]) * id;
@@ -337,7 +337,7 @@ __device__ __forceinline__ void corr_solve_otf(float* __restrict__ x, const floa
         for (int c = 1; c <= B; ++c)
           if (-t + c <= B) a[-t + c + B] -= lt * U[r - t][c];
       }
-      piv[r] = 1.f / a[B];
+      piv[r] = __frcp_rn(a[B]);
 #pragma unroll
       for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
     }
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(512) k_pcr_coef(const float* __restrict__ sig_
         for (int c = 1; c <= B; ++c)
           if (-t + c <= B) a[-t + c + B] -= lt * U[r - t][c];
       }
-      piv[r] = 1.f / a[B];
+      piv[r] = __frcp_rn(a[B]);
 #pragma unroll
       for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
     }
@@ -742,7 +742,7 @@ __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const flo
         for (int c = 1; c <= B; ++c)
           if (-t + c <= B) a[-t + c + B] -= lt * U[r - t][c];
       }
-      piv[r] = 1.f / a[B];
+      piv[r] = __frcp_rn(a[B]);
 #pragma unroll
       for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
       // forward substitution of this row as soon as it is eliminated
@@ -1172,8 +1172,8 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
       for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         R v = dst[i];
         if (gr && a.g_at_c) v += gr[i];
-        if (ci) v -= ci[i];
-        if (cc) v -= cc[i];
+        if (cc) v -= (ci ? ci[i] : (R)0) + cc[i];  // the corrected C value, rounded as it is stored
+        else if (ci) v -= ci[i];
         if (ro64) ro64[i] = (double)v;
         else ro[i] = v;
         if (ro32) ro32[i] = (float)v;

@@ -103,9 +103,12 @@ __global__ void __launch_bounds__(256) k_departure_1d(WaveParams w, int nx, int 
         a = w.a;
       } else if (w.kind == 1) {
         a = tf[nb][st];
+      } else if (st == 0) {  // the first stage point is the arrival node itself
+        if (w.kind == 2) a = tf[nb][0] * Cx;
+        else a = 1.0 + w.a * Sx * tf[nb][0];
       } else {
-        double sth = 0.0, cth = 1.0;
-        if (st > 0) small_sincos(kw * d, sth, cth);
+        double sth, cth;
+        small_sincos(kw * d, sth, cth);
         if (w.kind == 2) a = tf[nb][st] * (Cx * cth + Sx * sth);  // cos(2 pi t) cos(2 pi (x - d))
         else a = 1.0 + w.a * (Sx * cth - Cx * sth) * tf[nb][st];  // 1 + a sin(2 pi k (x - d)) cos(2 pi t)
       }
