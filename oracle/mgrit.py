@@ -241,10 +241,12 @@ class SolveResult:
     iterations: int
     history: list[float]
     converged: bool
+    final_errors: list[float] | None = None
 
 
 def mgrit_solve(H: Hierarchy, u0: np.ndarray, U_init: np.ndarray, rtol: float = 1e-10, max_iter: int = 200,
-                norm_mode: int = 1, mode: str = "FCF") -> SolveResult:
+                norm_mode: int = 1, mode: str = "FCF", u_final_ref: np.ndarray | None = None,
+                final_tol: float = 0.0) -> SolveResult:
     """Iterate MGRIT V-cycles from U_init until the space-time residual drops by rtol (Sec. 2.2).
 
     norm_mode 0: r_0 is the 2-norm of the residual of the initial iterate over
@@ -258,6 +260,11 @@ def mgrit_solve(H: Hierarchy, u0: np.ndarray, U_init: np.ndarray, rtol: float = 
       r_k < rtol r_0, and reports k + 1 cycles.  (With exact coarse solves this
       reproduces the constant-wave-speed columns of Table 2 exactly.)
     mode: "FCF" (the paper's relaxation) or "F" (F-relaxation only, every level).
+    u_final_ref (norm_mode 1): the alternative stopping rule of Sec. SM4 -- after the correction and
+      post F-relaxation of cycle k, e_k = (h^d sum (u(T) - u_final_ref)^2)^(1/2) (the discrete l2
+      norm of the final time slice's distance to the reference, e.g. the exact PDE solution); the
+      solve stops at the first e_k <= final_tol and reports k + 1 cycles (the residual test is not
+      applied).  The e_k are returned in final_errors.
     """
     if H.nlevels < 2:
         raise ValueError("MGRIT needs at least two levels")
@@ -277,6 +284,8 @@ def mgrit_solve(H: Hierarchy, u0: np.ndarray, U_init: np.ndarray, rtol: float = 
         return SolveResult(U, max_iter, hist, False)
     m = H.levels[1].m
     N = U.shape[0] - 1
+    errs: list[float] | None = None if u_final_ref is None else []
+    wgt = None if u_final_ref is None else H.grid.h ** H.grid.dim
     for k in range(0, max_iter):
         relax(H, 0, U, g, m, mode)
         gc = c_residual(H, 0, U, g, m)
@@ -287,6 +296,11 @@ def mgrit_solve(H: Hierarchy, u0: np.ndarray, U_init: np.ndarray, rtol: float = 
         for j in range(1, N // m + 1):
             U[j * m] += Ec[j]
         f_relax(H, 0, U, g, m)
-        if k >= 1 and rk < rtol * hist[0]:
+        if errs is not None:
+            ek = float(np.sqrt(wgt * np.sum((U[N] - u_final_ref) ** 2)))
+            errs.append(ek)
+            if ek <= final_tol:
+                return SolveResult(U, k + 1, hist, True, errs)
+        elif k >= 1 and rk < rtol * hist[0]:
             return SolveResult(U, k + 1, hist, True)
-    return SolveResult(U, max_iter, hist, False)
+    return SolveResult(U, max_iter, hist, False, errs)

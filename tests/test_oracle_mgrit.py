@@ -170,3 +170,56 @@ def test_f_and_fcf_relaxation_reach_the_same_fixed_point():
     seq = mg.sequential_solve(H, u0)
     assert a.converged and b.converged and a.iterations >= b.iterations
     assert np.linalg.norm(a.U - seq) / np.linalg.norm(seq) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Stopping at discretisation accuracy (Sec. SM4)
+# ---------------------------------------------------------------------------
+
+
+def _cos_t_exact_final(grid, u0_fn):
+    """alpha = cos(2 pi t): characteristics x(t) = x0 + sin(2 pi t) / (2 pi), so u(x, T) = u0(x - sin(2 pi T)/(2 pi))."""
+    T = grid.nt * grid.dt
+    x = grid.xmin + grid.h * np.arange(grid.nx)
+    return u0_fn(x - np.sin(2 * np.pi * T) / (2 * np.pi))
+
+
+def _sin4(x):
+    return np.sin(np.pi * x) ** 4
+
+
+def test_sl_discretisation_error_against_the_closed_form_flow_falls_with_order():
+    """The sequential SL solution's error at T against the exact flow of alpha = cos(2 pi t) shrinks with p
+    (Sec. SM4 reports the same ordering for its test problem)."""
+    g = sl.Grid(128, 256)
+    ws = sl.WaveSpeed("cos_t")
+    u0 = _sin4(g.xmin + g.h * np.arange(g.nx))
+    ref = _cos_t_exact_final(g, _sin4)
+    errs = []
+    for p in (1, 3, 5):
+        seq = mg.sequential_solve(mg.Hierarchy(g, ws, p, []), u0)
+        errs.append(float(np.sqrt(g.h * np.sum((seq[-1] - ref) ** 2))))
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10, errs
+
+
+def test_stopping_at_discretisation_accuracy():
+    """With u_final_ref = the exact final state and the tolerance just above the sequential solution's own
+    error, MGRIT stops once u(T) is that accurate: the recorded final errors are the distances of the
+    returned iterates, the last is within the tolerance and the one before is not, and (as in Sec. SM4 for
+    p = 1, 3) fewer cycles are needed than for the 1e-10 residual reduction."""
+    g = sl.Grid(128, 256)
+    ws = sl.WaveSpeed("cos_t")
+    u0 = _sin4(g.xmin + g.h * np.arange(g.nx))
+    ref = _cos_t_exact_final(g, _sin4)
+    for p in (1, 3):
+        H = mg.build_hierarchy(g, ws, p, 4)
+        seq = mg.sequential_solve(H, u0)
+        disc = float(np.sqrt(g.h * np.sum((seq[-1] - ref) ** 2)))
+        tol = 1.01 * disc
+        U0 = W.initial_iterate(g.nt, g.nx)
+        R = mg.mgrit_solve(H, u0, U0, u_final_ref=ref, final_tol=tol)
+        full = mg.mgrit_solve(H, u0, U0)
+        assert R.converged and R.iterations == len(R.final_errors)
+        assert abs(R.final_errors[-1] - np.sqrt(g.h * np.sum((R.U[-1] - ref) ** 2))) < 1e-15
+        assert R.final_errors[-1] <= tol and (R.iterations == 1 or R.final_errors[-2] > tol)
+        assert R.iterations < full.iterations
