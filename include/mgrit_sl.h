@@ -145,6 +145,7 @@ typedef struct {
   int64_t kernel_launches;  /* kernels launched by this handle: mgrit_setup plus this call */
   double phase_ms[12];      /* profile = 1: summed event time per phase (setup phases from mgrit_setup) */
   int phase_launches[12];   /* kernels per phase (setup phases from mgrit_setup, others from this call) */
+  double final_error;       /* mgrit_solve_to_reference: the last distance of u(T) to the reference */
 } mgrit_stats;
 
 typedef struct mgrit_handle mgrit_handle;
@@ -185,6 +186,18 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
  */
 mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_init, double* d_u_out,
                          mgrit_stats* stats);
+
+/*
+ * mgrit_solve with the alternative stopping rule of the paper's strong-scaling supplement (Sec. SM4):
+ * instead of the residual reduction, iterate until the final time slice of the iterate, u(T) after a
+ * cycle's correction, is within tol of d_u_final_ref (N values, e.g. the exact PDE solution at T) in
+ * the discrete l2 norm e = (h^d sum_i (u_i(T) - ref_i)^2)^(1/2), i.e. to discretisation accuracy.
+ * The residual norms are still recorded; stats->final_error holds the last e and stats->converged
+ * is 1 when e <= tol.  opt.max_iter bounds the cycles (then MGRIT_ENOTCONVERGED).  Other arguments,
+ * results and errors as mgrit_solve; tol < 0 gives MGRIT_EINVAL.
+ */
+mgrit_status mgrit_solve_to_reference(mgrit_handle* h, const double* d_u0, const double* d_u_init, double* d_u_out,
+                                      const double* d_u_final_ref, double tol, mgrit_stats* stats);
 
 /*
  * Sequential SL time stepping (eq. (one-step) with g = 0), the comparator of MGRIT:

@@ -63,7 +63,7 @@ class MgritStats(ctypes.Structure):
                 ("residual_history", ctypes.c_double * 256), ("setup_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("phase_ms", ctypes.c_double * 12),
-                ("phase_launches", ctypes.c_int * 12)]
+                ("phase_launches", ctypes.c_int * 12), ("final_error", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {
@@ -79,6 +79,7 @@ class MgritStats(ctypes.Structure):
             "kernel_launches": self.kernel_launches,
             "phase_ms": {PHASES[i]: self.phase_ms[i] for i in range(12)},
             "phase_launches": {PHASES[i]: self.phase_launches[i] for i in range(12)},
+            "final_error": self.final_error,
         }
 
 
@@ -92,6 +93,8 @@ _SIGNATURES = {
     "mgrit_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(MgritStats)]),
     "sl_step_sequential": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     "mgrit_solve_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(MgritStats)]),
+    "mgrit_solve_to_reference": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double,
+                                                ctypes.POINTER(MgritStats)]),
     "mgrit_adjoint_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(MgritStats)]),
     "mgrit_level_info": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -244,6 +247,18 @@ class Handle:
         allow = (4,) if allow_not_converged else ()
         _check(load_library().mgrit_solve(self._h(), _ptr(u0), _ptr(u_init), _ptr(u_out), ctypes.byref(st)),
                "mgrit_solve", allow)
+        return u_out, st.as_dict()
+
+    def solve_to_reference(self, u0, u_final_ref, tol: float, u_init=None, u_out=None,
+                           allow_not_converged: bool = False):
+        """MGRIT until the final slice is within tol of u_final_ref (discrete l2 norm; Sec. SM4)."""
+        if u_out is None:
+            u_out = self._empty(self.grid.nt + 1, self.npts)
+        st = MgritStats()
+        allow = (4,) if allow_not_converged else ()
+        _check(load_library().mgrit_solve_to_reference(self._h(), _ptr(u0), _ptr(u_init), _ptr(u_out),
+                                                       _ptr(u_final_ref), float(tol), ctypes.byref(st)),
+               "mgrit_solve_to_reference", allow)
         return u_out, st.as_dict()
 
     def solve_host(self, u0, u_init=None, u_out=None):

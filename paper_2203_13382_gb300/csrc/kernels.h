@@ -203,6 +203,8 @@ void launch_sum_batched(const Segment* d_seg, int nseg, cudaStream_t st);
 
 // Deterministic sum of `count` doubles (fixed order): out[0] = sum.
 void launch_sum(const double* v, int count, double* out, cudaStream_t st);
+// out[0] = sum_i (a[i] + b[i] - ref[i])^2 over n values (b may be NULL), fixed order.
+void launch_dist2(const double* a, const double* b, const double* ref, long long n, double* out, cudaStream_t st);
 // Elementwise update with type conversion: kind 0: y = x (d); 1: y(f) = x(d); 2: y(d) += x(f);
 // 3: y(d) = x(f); 4: y(d) += x(d); 5: y(d) += x(d) + z(f); 6: y(d) = x(d) - z(d); 7: y(d) += x(d) + z(d).
 void launch_axpy_convert(int kind, const void* x, void* y, const void* z, long long n, cudaStream_t st);

@@ -1502,6 +1502,27 @@ void launch_sum(const double* v, int count, double* out, cudaStream_t st) { k_su
 
 namespace {
 
+// out = sum_i (a[i] + b[i] - ref[i])^2 (b optional), one CTA, fixed summation order.
+__global__ void k_dist2(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ ref,
+                        long long n, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double e = (b ? a[i] + b[i] : a[i]) - ref[i];
+    s += e * e;
+  }
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) out[0] = t;
+}
+
+}  // namespace
+
+void launch_dist2(const double* a, const double* b, const double* ref, long long n, double* out, cudaStream_t st) {
+  k_dist2<<<1, 1024, 0, st>>>(a, b, ref, n, out);
+}
+
+namespace {
+
 __global__ void k_axpy_batched(int kind, const Segment* __restrict__ seg) {
   const Segment sg = seg[blockIdx.y];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < sg.n; i += (long long)gridDim.x * blockDim.x) {

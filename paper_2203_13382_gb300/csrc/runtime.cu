@@ -748,8 +748,10 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
 namespace {
 
 // The MGRIT iteration.  u0 / u_init may be host or device pointers (kinds given); u_out is on the device.
+// d_final_ref != NULL: the final-slice stopping rule (mgrit_solve_to_reference) with tolerance final_tol.
 mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_kind, const double* d_u_init,
-                        cudaMemcpyKind init_kind, double* d_u_out, mgrit_stats* stats) {
+                        cudaMemcpyKind init_kind, double* d_u_out, mgrit_stats* stats,
+                        const double* d_final_ref = nullptr, double final_tol = 0.0) {
   const double t0 = now_ms();
   cudaStream_t s = h->stream;
   const int np = h->npts;
@@ -773,7 +775,7 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
   mgrit_status status = MGRIT_OK;
   // one cycle's device work (FP64: reads X, writes Y; the caller swaps the pointers afterwards)
   const bool fcf = h->opt.relax == 0;
-  auto cycle = [&](int k) -> mgrit_status {
+  auto cycle_body = [&](int k) -> mgrit_status {
     if (!fp32 && !fcf) {
       // F-relaxation only: one pass from the corrected C-points X + E_1 (written to Y for the next
       // cycle), F-relaxation and the C-point residual against the corrected C-points
@@ -876,6 +878,22 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
     }
     return enqueue_norm(h, J);
   };
+  // with a final-slice reference: the squared distance of u(T) after this cycle's correction (FP64:
+  // the relaxed C-points in Y plus E_1, applied by the next pass; FP32 bulk: X, already corrected)
+  auto cycle = [&](int k) -> mgrit_status {
+    MG_TRY(cycle_body(k));
+    if (d_final_ref) {
+      const size_t last = (size_t)J * np;
+      const int ev = h->phase_begin();
+      launch_dist2(fp32 ? h->X + last : h->Y + last, fp32 ? nullptr : (const double*)L1.E + last, d_final_ref, np,
+                   h->norm_dev + 1, s);
+      h->phase_end(MGRIT_PHASE_MISC, ev, 1);
+      MG_CUDA(cudaMemcpyAsync(h->norm_host + 2, h->norm_dev + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    return MGRIT_OK;
+  };
+  const double wgt = std::pow((h->grid.xmax - h->grid.xmin) / h->grid.nx, (double)h->grid.dim);
+  double ek = 0.0;
   // CUDA graphs (use_graph): FP32-bulk cycles are identical; FP64 cycles k >= 1 alternate X / Y
   CycleGraph graphs[2];
   bool graph_ok = h->opt.use_graph != 0;
@@ -894,7 +912,13 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
       status = fail(MGRIT_EDIVERGED, "residual norm diverged");
       break;
     }
-    if (k >= 1 && rk < h->opt.rtol * r0) {
+    if (d_final_ref) {
+      ek = std::sqrt(wgt * h->norm_host[2]);
+      if (ek <= final_tol) {
+        converged = true;
+        break;
+      }
+    } else if (k >= 1 && rk < h->opt.rtol * r0) {
       converged = true;
       break;
     }
@@ -926,6 +950,7 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
     stats->levels = (int)h->levels.size();
     stats->r0 = r0;
     stats->r_final = rk;
+    stats->final_error = ek;
     const int nh = (int)hist.size() < 256 ? (int)hist.size() : 256;
     stats->history_len = nh;
     for (int i = 0; i < nh; ++i) stats->residual_history[i] = hist[i];
@@ -949,6 +974,15 @@ mgrit_status mgrit_solve(mgrit_handle* h, const double* d_u0, const double* d_u_
                          mgrit_stats* stats) {
   if (!h || !d_u0 || !d_u_out) return fail(MGRIT_EINVAL, "handle, u0 and u_out must not be NULL");
   return solve_impl(h, d_u0, cudaMemcpyDeviceToDevice, d_u_init, cudaMemcpyDeviceToDevice, d_u_out, stats);
+}
+
+mgrit_status mgrit_solve_to_reference(mgrit_handle* h, const double* d_u0, const double* d_u_init, double* d_u_out,
+                                      const double* d_u_final_ref, double tol, mgrit_stats* stats) {
+  if (!h || !d_u0 || !d_u_out || !d_u_final_ref)
+    return fail(MGRIT_EINVAL, "handle, u0, u_out and u_final_ref must not be NULL");
+  if (!(tol >= 0.0)) return fail(MGRIT_EINVAL, "tol must be >= 0");
+  return solve_impl(h, d_u0, cudaMemcpyDeviceToDevice, d_u_init, cudaMemcpyDeviceToDevice, d_u_out, stats,
+                    d_u_final_ref, tol);
 }
 
 mgrit_status mgrit_solve_host(mgrit_handle* h, const double* h_u0, const double* h_u_init, double* h_u_out,

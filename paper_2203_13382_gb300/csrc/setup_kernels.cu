@@ -75,11 +75,13 @@ __global__ void __launch_bounds__(256) k_departure_1d(WaveParams w, int nx, int 
                                                       double dt, double* __restrict__ s) {
   using Tb = ErkTab<R>;
   constexpr int S = Tb::S;
+  // tf[nb][st]: the time factor of stage st of step n0 + nb (kind 3: a cos(2 pi t), else cos(2 pi t))
   __shared__ double tf[kDepSteps][S];
   const int n0 = blockIdx.y * kDepSteps;
   for (int q = threadIdx.x; q < kDepSteps * S; q += blockDim.x) {
     const int nb = q / S, st = q % S;
-    tf[nb][st] = cos(kTwoPi * ((n0 + nb + 1) * dt - Tb::c(st) * dt));
+    const double c = cos(kTwoPi * ((n0 + nb + 1) * dt - Tb::c(st) * dt));
+    tf[nb][st] = w.kind == 3 ? w.a * c : c;
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -88,16 +90,20 @@ __global__ void __launch_bounds__(256) k_departure_1d(WaveParams w, int nx, int 
   const double kw = (w.kind == 3) ? kTwoPi * w.k : kTwoPi;  // spatial wavenumber
   double Sx = 0.0, Cx = 1.0;
   if (w.kind >= 2) sincos(kw * x, &Sx, &Cx);
-  const double inv_h = 1.0 / h;
+  // stage offsets in units of the phase: kw (x - stage point) = sum_j pa[st][j] k_j; the offset in
+  // grid units s = sum_st pb[st] k_st
+  double pa[S][S], pb[S];
+#pragma unroll
+  for (int st = 0; st < S; ++st) {
+#pragma unroll
+    for (int j = 0; j < S; ++j) pa[st][j] = kw * dt * Tb::a(st, j);
+    pb[st] = Tb::b(st) * dt / h;
+  }
   const int nend = min(kDepSteps, nt - n0);
   for (int nb = 0; nb < nend; ++nb) {
     double k[S];
 #pragma unroll
     for (int st = 0; st < S; ++st) {
-      double d = 0.0;  // x - (stage point)
-#pragma unroll
-      for (int j = 0; j < st; ++j)
-        if (Tb::a(st, j) != 0.0) d = d + dt * Tb::a(st, j) * k[j];
       double a;
       if (w.kind == 0) {
         a = w.a;
@@ -105,20 +111,24 @@ __global__ void __launch_bounds__(256) k_departure_1d(WaveParams w, int nx, int 
         a = tf[nb][st];
       } else if (st == 0) {  // the first stage point is the arrival node itself
         if (w.kind == 2) a = tf[nb][0] * Cx;
-        else a = 1.0 + w.a * Sx * tf[nb][0];
+        else a = 1.0 + tf[nb][0] * Sx;
       } else {
+        double ph = 0.0;  // kw (x - stage point)
+#pragma unroll
+        for (int j = 0; j < st; ++j)
+          if (Tb::a(st, j) != 0.0) ph = ph + pa[st][j] * k[j];
         double sth, cth;
-        small_sincos(kw * d, sth, cth);
+        small_sincos(ph, sth, cth);
         if (w.kind == 2) a = tf[nb][st] * (Cx * cth + Sx * sth);  // cos(2 pi t) cos(2 pi (x - d))
-        else a = 1.0 + w.a * (Sx * cth - Cx * sth) * tf[nb][st];  // 1 + a sin(2 pi k (x - d)) cos(2 pi t)
+        else a = 1.0 + tf[nb][st] * (Sx * cth - Cx * sth);  // 1 + a sin(2 pi k (x - d)) cos(2 pi t)
       }
       k[st] = a;
     }
-    double dsum = 0.0;
+    double sv = 0.0;
 #pragma unroll
     for (int st = 0; st < S; ++st)
-      if (Tb::b(st) != 0.0) dsum = dsum + Tb::b(st) * k[st];
-    s[(size_t)(n0 + nb) * nx + i] = dt * dsum * inv_h;
+      if (Tb::b(st) != 0.0) sv = sv + pb[st] * k[st];
+    s[(size_t)(n0 + nb) * nx + i] = sv;
   }
 }
 
