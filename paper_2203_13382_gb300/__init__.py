@@ -244,7 +244,7 @@ class Handle:
         if u_out is None:
             u_out = self._empty(self.grid.nt + 1, self.npts)
         st = MgritStats()
-        allow = (4,) if allow_not_converged else ()
+        allow = (4, 5) if allow_not_converged else ()  # not converged / diverged: stats still filled
         _check(load_library().mgrit_solve(self._h(), _ptr(u0), _ptr(u_init), _ptr(u_out), ctypes.byref(st)),
                "mgrit_solve", allow)
         return u_out, st.as_dict()
