@@ -267,6 +267,25 @@ def cores_used() -> int:
     return int(os.environ.get("OMP_NUM_THREADS", "1"))
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def run_reference(args) -> None:
     rank, _, world = rank_info()
     if rank != 0:
@@ -440,6 +459,7 @@ def run_ours(args) -> None:
     if rank == 0 and not args.no_cpu_baseline:
         secs, cpu_its = oracle_sample(CPU_SAMPLE_NT)
         cpu = {"value": nx * CPU_SAMPLE_NT / secs, "unit": "DOF/s", "cores": cores_used(), "kind": "oracle",
+               "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
                "sample": f"oracle MGRIT solve to 1e-10 of the first {CPU_SAMPLE_NT} of {nt} time steps "
                          f"(nx={nx}; {cpu_its} iterations, {secs:.1f} s)"}
     if rank == 0:
@@ -450,6 +470,9 @@ def run_ours(args) -> None:
             "config": {**wl, "precision": args.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2: per-step gather tables alone exceed 2 GB"},
             "iterations": iters[0], "iterations_all_steps": sorted(set(iters)),
+            "setup_ms_per_step": float(np.median([st["setup_ms"] for st in stats])),
+            "solve_only_ms_per_step": float(np.median([st["solve_ms"] for st in stats])),
+            "solve_only_value": dof / (float(np.median([st["solve_ms"] for st in stats])) / 1e3),
             "comparator": None if args.no_comparator else {"sequential_dof_per_s": dof / (seq_full_ms / 1e3),
                            "sequential_ms": seq_full_ms, "sequential_precision": seq_best,
                            "sequential_steps_only_ms": seq_ms,
