@@ -101,6 +101,14 @@ std::vector<double*>& pinned_free() {
   static std::vector<double*>* v = new std::vector<double*>;
   return *v;
 }
+// Stream-ordered scratch from the library's pool (kept between calls), else the device's default pool.
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool = workspace_pool();
+  if (pool && cudaMallocFromPoolAsync(p, bytes, pool, st) == cudaSuccess) return cudaSuccess;
+  cudaGetLastError();
+  return cudaMallocAsync(p, bytes, st);
+}
+
 double* pinned_take() {
   {
     std::lock_guard<std::mutex> lk(pinned_mu());
@@ -991,7 +999,7 @@ mgrit_status mgrit_solve_host(mgrit_handle* h, const double* h_u0, const double*
   const size_t np = h->npts, nt = h->grid.nt;
   double* d_out = nullptr;
   cudaStream_t s = h->stream;
-  MG_CUDA(cudaMallocAsync((void**)&d_out, (nt + 1) * np * sizeof(double), s));
+  MG_CUDA(scratch_alloc((void**)&d_out, (nt + 1) * np * sizeof(double), s));
   // the initial iterate is read only at the C-points, straight from host memory
   mgrit_status st = solve_impl(h, h_u0, cudaMemcpyHostToDevice, h_u_init, cudaMemcpyHostToDevice, d_out, stats);
   cudaMemcpyAsync(h_u_out, d_out, (nt + 1) * np * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1025,8 +1033,8 @@ mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u
   } else {
     const size_t rows = store_all ? (size_t)(nt + 1) : 1;
     float *u0f = nullptr, *outf = nullptr;
-    MG_CUDA(cudaMallocAsync((void**)&u0f, np * sizeof(float), s));
-    MG_CUDA(cudaMallocAsync((void**)&outf, rows * np * sizeof(float), s));
+    MG_CUDA(scratch_alloc((void**)&u0f, np * sizeof(float), s));
+    MG_CUDA(scratch_alloc((void**)&outf, rows * np * sizeof(float), s));
     launch_axpy_convert(1, d_u0, u0f, nullptr, np, s);
     if (h->grid.dim == 2) MG_CUDA(launch_sequential_2d(T, nt, nullptr, u0f, outf, store_all, h->s2d, 0, s));
     else MG_CUDA(seq1d(u0f, outf, 0));
@@ -1101,8 +1109,8 @@ mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, cons
   cudaStream_t s = h->stream;
   const int np = h->npts, nt = h->grid.nt, m1 = h->levels[1].m, J = h->J1();
   double *mu0 = nullptr, *mu = nullptr;
-  MG_CUDA(cudaMallocAsync((void**)&mu0, (size_t)np * sizeof(double), s));
-  MG_CUDA(cudaMallocAsync((void**)&mu, (size_t)(nt + 1) * np * sizeof(double), s));
+  MG_CUDA(scratch_alloc((void**)&mu0, (size_t)np * sizeof(double), s));
+  MG_CUDA(scratch_alloc((void**)&mu, (size_t)(nt + 1) * np * sizeof(double), s));
   // mu_0 = lambda_nt = u_nt - u_target; u_nt is the last checkpoint (nt is a C-point)
   launch_axpy_convert(6, d_C_checkpoints + (size_t)J * np, mu0, d_u_target, np, s);
   // the reversed problem mu_{k+1} = Phi_{nt-1-k}^T mu_k by MGRIT from a zero initial iterate
@@ -1174,8 +1182,8 @@ mgrit_status mgrit_apply_step(mgrit_handle* h, int level, int n0, int count, con
     else MG_CUDA(launch_apply_steps_1d(T, n0, count, d_in, d_out, 1, s));
   } else {
     float *fi = nullptr, *fo = nullptr;
-    MG_CUDA(cudaMallocAsync((void**)&fi, (size_t)count * np * sizeof(float), s));
-    MG_CUDA(cudaMallocAsync((void**)&fo, (size_t)count * np * sizeof(float), s));
+    MG_CUDA(scratch_alloc((void**)&fi, (size_t)count * np * sizeof(float), s));
+    MG_CUDA(scratch_alloc((void**)&fo, (size_t)count * np * sizeof(float), s));
     launch_axpy_convert(1, d_in, fi, nullptr, (long long)count * np, s);
     if (h->grid.dim == 2) MG_CUDA(launch_apply_steps_2d(T, n0, count, fi, fo, h->s2d, 0, s));
     else MG_CUDA(launch_apply_steps_1d(T, n0, count, fi, fo, 0, s));
