@@ -123,6 +123,23 @@ MGRIT_D double block_sum(double v, double* smem_scratch) {
   return t;  // valid in thread 0
 }
 
+// Deterministic block sum of one R per thread: the warp sums in R (FP32 values stay off the FP64 pipe,
+// which GB300 runs at 2 operations a clock per SM), the warp partials in FP64 (result in thread 0).
+template <typename R>
+MGRIT_D double block_sum_r(R v, double* smem_scratch) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) smem_scratch[warp] = (double)v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < nw; ++k) t += smem_scratch[k];
+  }
+  return t;  // valid in thread 0
+}
+
 // ---- TMA bulk copies into shared memory, completed on an mbarrier (sm_90+ PTX) ---------------------
 
 MGRIT_D uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }

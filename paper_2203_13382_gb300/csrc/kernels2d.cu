@@ -172,13 +172,13 @@ __device__ __forceinline__ R apply_MT(const R* x, const R* sx, const R* sy, long
   return x[pt] - dxv - dyv;
 }
 
-// CTA-wide dot product; each thread accumulates its strided share in R (FP32 systems stay off the
-// narrow FP64 pipe), the per-thread partial sums are reduced in FP64.
+// CTA-wide dot product; each thread accumulates its strided share in R and the warps reduce in R (FP32
+// systems stay off the narrow FP64 pipe), the warp partials are summed in FP64.
 template <typename R>
 __device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, double* red) {
   R s = (R)0;
   for (long long q = threadIdx.x; q < N; q += blockDim.x) s += a[q] * b[q];
-  double t = block_sum((double)s, red);
+  double t = block_sum_r<R>(s, red);
   __syncthreads();
   if (threadIdx.x == 0) red[32] = t;
   __syncthreads();
@@ -188,7 +188,8 @@ __device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, d
 }
 
 // Classical Gram-Schmidt projections h_t = <v_t, w>, t = 0..kk (kk < 10), of the rows [lo, hi) in one
-// pass over w; per-thread sums in R, reduced over the CTA in FP64 into hsum[0..kk] (all threads see them).
+// pass over w; per-thread and per-warp sums in R, the warp partials summed in FP64 into hsum[0..kk] (all
+// threads see them).
 template <typename R>
 __device__ __forceinline__ void cta_multi_dot(const R* V, long long N, const R* w, int kk, long long lo, long long hi,
                                               double (*wpart)[11], double* hsum) {
@@ -205,9 +206,9 @@ __device__ __forceinline__ void cta_multi_dot(const R* V, long long N, const R* 
 #pragma unroll
   for (int t = 0; t < 10; ++t) {
     if (t > kk) break;
-    double v = (double)acc[t];
+    R v = acc[t];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) wpart[warp][t] = v;
+    if (lane == 0) wpart[warp][t] = (double)v;
   }
   __syncthreads();
   if ((int)threadIdx.x <= kk) {
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const R*
   auto dot = [&](const R* x, const R* y) -> double {
     R sacc = (R)0;
     for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) sacc += x[q] * y[q];
-    const double t = block_sum((double)sacc, red);
+    const double t = block_sum_r<R>(sacc, red);
     if (threadIdx.x == 0) part[slot] = t;
     cl.sync();
     double tot = 0.0;
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(kThreads2d) k_finish2d(const R* __restrict__ c
                                                          double* __restrict__ partial, int chunks) {
   __shared__ double red[33];
   const int j = blockIdx.y;
-  double sq = 0.0;
+  R sq = (R)0;  // FP32 levels: the per-thread and per-warp sums in FP32
   const int nC = (j + 1) * a.m;
   const R* gr = a.g ? (const R*)a.g + (size_t)nC * N : nullptr;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < N; pt += (long long)gridDim.x * blockDim.x) {
@@ -522,11 +523,11 @@ __global__ void __launch_bounds__(kThreads2d) k_finish2d(const R* __restrict__ c
       if (a.rout_f64) ((double*)a.rout)[(size_t)(j + 1) * a.r_stride + pt] = (double)v;
       else ((R*)a.rout)[(size_t)(j + 1) * a.r_stride + pt] = v;
       if (a.rout32) a.rout32[(size_t)(j + 1) * a.r_stride + pt] = (float)v;
-      sq += (double)v * (double)v;
+      sq += v * v;
     }
   }
   if (a.mode == MODE_RES && partial) {
-    const double t = block_sum(sq, red);
+    const double t = block_sum_r<R>(sq, red);
     if (threadIdx.x == 0) partial[(size_t)j * chunks + blockIdx.x] = t;
   }
 }
