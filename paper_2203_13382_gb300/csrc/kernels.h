@@ -190,9 +190,11 @@ struct Segment {
 // region placed (128-aligned) after the slice buffers; a launch over several tiles takes the largest
 // buffer and the largest region.
 void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem, size_t* region);
+// threads: CTA size of FP32 launches (32 .. 512, every tile's slice at most 8 * threads points); FP64
+// launches use 512.
 cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles,
                                  int ntiles, const int* d_active, int is_double, int coarse, int buf, size_t smem,
-                                 cudaStream_t st);
+                                 int threads, cudaStream_t st);
 cudaError_t launch_sequential_batched(const LevelTables* d_tabs, const SeqArgs* d_args, const BatchTile* d_tiles,
                                       int ntiles, const int* d_active, int is_double, int coarse, int buf,
                                       size_t smem, cudaStream_t st);

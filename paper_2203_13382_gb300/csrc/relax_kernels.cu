@@ -16,8 +16,7 @@ namespace mgrit {
 namespace {
 
 // ---- gather tables of one step, loaded into registers ahead of use (software pipelining) ----------
-constexpr int kPts = 8;  // points per thread: nx <= kPts * kSliceThreads = 4096
-constexpr int kMaxNx = kPts * kSliceThreads;
+constexpr int kPts = 8;  // points per thread: nx <= kPts * threads (4096 for 512-thread CTAs)
 
 // Threads of the slice-resident kernels (one CTA per interval).  Measured on the 4096-point coarse
 // levels: 512 threads at one CTA per SM beat 256 threads at two (longer per-thread gathers and
@@ -73,7 +72,7 @@ template <int P, int NT>
 __device__ __forceinline__ void apply_gather_staged(const float* __restrict__ eps, const uint16_t* __restrict__ sh,
                                                     const float* __restrict__ src, float* __restrict__ dst, int nx) {
 #pragma unroll 2
-  for (int q = 0; q < kMaxNx / NT; ++q) {
+  for (int q = 0; q < kPts; ++q) {
     const int i = threadIdx.x + q * NT;
     if (i < nx) {
       float w[P + 1];
@@ -1090,7 +1089,7 @@ __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R*
 template <int P, typename R, bool COARSE, bool TRANS, int NT>
 __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs& a, int j, int buf,
                                            unsigned char* smem_raw) {
-  constexpr int kP = kMaxNx / NT;  // points per thread
+  constexpr int kP = kPts;  // points per thread (nx <= kPts * NT)
   R* src = reinterpret_cast<R*>(smem_raw);
   R* dst = src + buf;
   double* red = reinterpret_cast<double*>(dst + buf);
@@ -1253,21 +1252,22 @@ __global__ void __launch_bounds__(slice_threads<P, R, COARSE>()) k_sequential_1d
 
 // ---- batched problems: one launch per cycle phase over (problem, interval) tiles --------------------
 
-template <typename R, bool COARSE>
-__global__ void __launch_bounds__(kSliceThreads, COARSE ? 1 : (std::is_same<R, float>::value ? 2 : 3))
-    k_relax_batched(const LevelTables* __restrict__ tabs,
-                                                                    const RelaxArgs* __restrict__ args,
-                                                                    const BatchTile* __restrict__ tiles,
-                                                                    const int* __restrict__ active, int buf) {
+// NT threads a CTA (FP32 tiles of slices up to kPts * NT points; FP64 tiles use 512): a smaller CTA for
+// the problems with shorter slices, so that more of their intervals are resident on an SM at once.  The
+// minimum CTAs per SM scale with 512 / NT, keeping the register budget a thread of the 512-thread kernel.
+template <typename R, bool COARSE, int NT>
+__global__ void __launch_bounds__(NT, (COARSE ? 1 : (std::is_same<R, float>::value ? 2 : 3)) * (kSliceThreads / NT))
+    k_relax_batched(const LevelTables* __restrict__ tabs, const RelaxArgs* __restrict__ args,
+                    const BatchTile* __restrict__ tiles, const int* __restrict__ active, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BatchTile t = tiles[blockIdx.x];
   if (active && !active[t.problem]) return;
   const LevelTables T = tabs[t.table];
   const RelaxArgs a = args[t.args];
   switch (T.p) {
-    case 1: relax_body<1, R, COARSE, false, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
-    case 3: relax_body<3, R, COARSE, false, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
-    default: relax_body<5, R, COARSE, false, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
+    case 1: relax_body<1, R, COARSE, false, NT>(T, a, t.j, buf, smem_raw); break;
+    case 3: relax_body<3, R, COARSE, false, NT>(T, a, t.j, buf, smem_raw); break;
+    default: relax_body<5, R, COARSE, false, NT>(T, a, t.j, buf, smem_raw); break;
   }
 }
 
@@ -1555,25 +1555,42 @@ void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem
                 : 0;
 }
 
+namespace {
+
+template <typename R, bool CC, int NT>
+cudaError_t launch_batched_nt(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles, int ntiles,
+                              const int* d_active, int buf, size_t smem, cudaStream_t st) {
+  auto kern = k_relax_batched<R, CC, NT>;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<ntiles, NT, smem, st>>>(d_tabs, d_args, d_tiles, d_active, buf);
+  return cudaGetLastError();
+}
+
+template <bool CC>
+cudaError_t launch_batched_f32(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles, int ntiles,
+                               const int* d_active, int buf, size_t smem, int threads, cudaStream_t st) {
+  switch (threads) {
+    case 32: return launch_batched_nt<float, CC, 32>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+    case 64: return launch_batched_nt<float, CC, 64>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+    case 128: return launch_batched_nt<float, CC, 128>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+    case 256: return launch_batched_nt<float, CC, 256>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+    default: return launch_batched_nt<float, CC, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+  }
+}
+
+}  // namespace
+
 cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles,
                                  int ntiles, const int* d_active, int is_double, int coarse, int buf, size_t smem,
-                                 cudaStream_t st) {
+                                 int threads, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-#define MGRIT_BATCH(RR, CC)                                                                                   \
-  {                                                                                                           \
-    cudaError_t e = cudaFuncSetAttribute(k_relax_batched<RR, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                         (int)smem);                                                          \
-    if (e != cudaSuccess) return e;                                                                           \
-    k_relax_batched<RR, CC><<<ntiles, kSliceThreads, smem, st>>>(d_tabs, d_args, d_tiles, d_active, buf);      \
-    return cudaGetLastError();                                                                                \
-  }
   if (is_double) {
-    if (coarse) MGRIT_BATCH(double, true)
-    MGRIT_BATCH(double, false)
+    if (coarse) return launch_batched_nt<double, true, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+    return launch_batched_nt<double, false, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
   }
-  if (coarse) MGRIT_BATCH(float, true)
-  MGRIT_BATCH(float, false)
-#undef MGRIT_BATCH
+  if (coarse) return launch_batched_f32<true>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, threads, st);
+  return launch_batched_f32<false>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, threads, st);
 }
 
 cudaError_t launch_sequential_batched(const LevelTables* d_tabs, const SeqArgs* d_args, const BatchTile* d_tiles,

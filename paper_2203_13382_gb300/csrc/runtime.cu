@@ -1277,6 +1277,7 @@ struct mgrit_batch {
     size_t smem;
     size_t region;  // coarse shared region (on-the-fly solve) after the slice buffers
     int order;      // tile order chosen by the tuner (0: as built, 1: longest first)
+    int threads;    // CTA size of an FP32 relaxation phase (its tiles' slices hold at most 8 * threads points)
   };
   std::vector<Phase> down, up;
   Phase final_post{};
@@ -1316,12 +1317,13 @@ struct mgrit_batch {
 
 namespace {
 
-// Tile order of each relaxation phase, chosen by measurement.  The tiles of one phase carry different
-// work (nx * steps varies 16-fold across a batch); the GPU starts CTAs in launch order, so the order
-// decides the tail.  Candidates: as built (problem by problem) and longest first.  Each is timed on the
-// phase itself (CUDA events, best of two runs after one warm-up; the cycle state is rebuilt by every
-// solve, so these runs leave nothing behind); the faster order is kept.  Choices are cached per
-// batch signature (problem shapes and options), so only the first setup of a batch pays.
+// Tile order and CTA size of each relaxation phase, chosen by measurement.  The tiles of one phase carry
+// different work (nx * steps varies 16-fold across a batch); the GPU starts CTAs in launch order, so the
+// order decides the tail.  Order candidates: as built (problem by problem) and longest first; CTA sizes
+// (FP32 phases): the size of the phase's slice class (cta_threads) and up to two doublings.  Each
+// candidate is timed on the phase itself (CUDA events, best of two runs after one warm-up; the cycle
+// state is rebuilt by every solve, so these runs leave nothing behind); the fastest is kept.  Choices
+// are cached per batch signature (problem shapes and options), so only the first setup of a batch pays.
 std::mutex& tune_mu() {
   static std::mutex* m = new std::mutex;
   return *m;
@@ -1372,25 +1374,33 @@ mgrit_status tune_tile_order(mgrit_batch* b, const mgrit_grid* grids, const mgri
     for (mgrit_batch::Phase* ph : phases) {
       const std::vector<BatchTile> built(b->tiles.begin() + ph->tile_off, b->tiles.begin() + ph->tile_off + ph->ntiles);
       const std::vector<BatchTile> sorted = longest_first(*ph);
-      float best[2] = {0.f, 0.f};
+      // candidates: tile order x CTA size (FP32 phases: the class size and up to two doublings, <= 512)
+      const int max_shift = ph->is_double ? 0 : (ph->threads <= 128 ? 2 : (ph->threads <= 256 ? 1 : 0));
+      float best_t = 1e30f;
+      int best_code = 0;
       for (int c = 0; c < 2; ++c) {
         const std::vector<BatchTile>& t = c == 0 ? built : sorted;
         MG_CUDA(cudaMemcpyAsync(b->d_tiles + ph->tile_off, t.data(), t.size() * sizeof(BatchTile),
                                 cudaMemcpyHostToDevice, s));
-        float bt = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-          MG_CUDA(cudaEventRecord(e0, s));
-          MG_CUDA(launch_relax_batched(b->d_tabs, b->d_args, b->d_tiles + ph->tile_off, ph->ntiles, b->d_active,
-                                       ph->is_double, ph->coarse, ph->buf, ph->smem, s));
-          MG_CUDA(cudaEventRecord(e1, s));
-          MG_CUDA(cudaEventSynchronize(e1));
-          float ms_ = 0.f;
-          MG_CUDA(cudaEventElapsedTime(&ms_, e0, e1));
-          if (rep > 0) bt = std::min(bt, ms_);
+        for (int sh = 0; sh <= max_shift; ++sh) {
+          float bt = 1e30f;
+          for (int rep = 0; rep < 3; ++rep) {
+            MG_CUDA(cudaEventRecord(e0, s));
+            MG_CUDA(launch_relax_batched(b->d_tabs, b->d_args, b->d_tiles + ph->tile_off, ph->ntiles, b->d_active,
+                                         ph->is_double, ph->coarse, ph->buf, ph->smem, ph->threads << sh, s));
+            MG_CUDA(cudaEventRecord(e1, s));
+            MG_CUDA(cudaEventSynchronize(e1));
+            float ms_ = 0.f;
+            MG_CUDA(cudaEventElapsedTime(&ms_, e0, e1));
+            if (rep > 0) bt = std::min(bt, ms_);
+          }
+          if (bt < best_t) {
+            best_t = bt;
+            best_code = c | (sh << 1);
+          }
         }
-        best[c] = bt;
       }
-      choice.push_back(best[1] < best[0] ? 1 : 0);
+      choice.push_back((char)best_code);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1399,11 +1409,13 @@ mgrit_status tune_tile_order(mgrit_batch* b, const mgrit_grid* grids, const mgri
   }
   for (size_t i = 0; i < phases.size(); ++i) {
     mgrit_batch::Phase* ph = phases[i];
-    if (choice[i]) {
+    const int order = choice[i] & 1, sh = choice[i] >> 1;
+    if (order) {
       const std::vector<BatchTile> t = longest_first(*ph);
       std::copy(t.begin(), t.end(), b->tiles.begin() + ph->tile_off);
     }
-    ph->order = choice[i];
+    ph->order = order;
+    ph->threads <<= sh;
   }
   MG_CUDA(cudaMemcpyAsync(b->d_tiles, b->tiles.data(), b->tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s));
   MG_CUDA(cudaStreamSynchronize(s));
@@ -1418,10 +1430,18 @@ size_t batched_smem(int buf, int is_double, size_t region) {
 
 // Appends a phase of relax tiles; per problem q: J tiles (plus one if extra) using tabs[tab_of(q)] and
 // args[args_of(q)].
+// CTA size for the FP32 tiles of a problem: one thread per 8 slice points, between 32 and 512.  Problems
+// with short slices then keep several intervals resident on an SM instead of one 512-thread CTA each.
+int cta_threads(int nx) {
+  const int t = nx / 8;
+  return t < 32 ? 32 : (t > 512 ? 512 : t);
+}
+
 template <class F>
-mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F per_problem) {
-  mgrit_batch::Phase ph{0, is_double, coarse, (int)b->tiles.size(), 0, 0, 0, 0, 0};
+mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F per_problem, int threads = 0) {
+  mgrit_batch::Phase ph{0, is_double, coarse, (int)b->tiles.size(), 0, 0, 0, 0, 0, threads ? threads : 512};
   for (int q = 0; q < (int)b->hs.size(); ++q) {
+    if (threads && cta_threads(b->hs[q]->grid.nx) != threads) continue;
     LevelTables T;
     RelaxArgs a;
     int ntile = 0;
@@ -1440,6 +1460,20 @@ mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F 
   // a common buffer length for every tile, then the largest coarse region after it
   ph.smem = batched_smem(ph.buf, is_double, ph.region);
   return ph;
+}
+
+// The phases of one relaxation pass: FP64 passes in one launch of 512-thread CTAs, FP32 passes in one
+// launch per CTA size (cta_threads), each over the problems of that size.
+template <class F>
+void add_relax_phases(mgrit_batch* b, int is_double, int coarse, F per_problem, std::vector<mgrit_batch::Phase>& list) {
+  if (is_double) {
+    list.push_back(add_relax_phase(b, is_double, coarse, per_problem));
+    return;
+  }
+  for (int t : {512, 256, 128, 64, 32}) {
+    mgrit_batch::Phase ph = add_relax_phase(b, is_double, coarse, per_problem, t);
+    if (ph.ntiles) list.push_back(ph);
+  }
 }
 
 }  // namespace
@@ -1484,7 +1518,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     nt = J;
     return true;
   }));
-  b->down.push_back(add_relax_phase(b, 0, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+  add_relax_phases(b, 0, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
     mgrit_handle* h = b->hs[q];
     const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
     T = h->tables(0, 0);
@@ -1493,12 +1527,12 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     a.start = h->EC; a.start_stride = np; a.rout = h->levels[1].G; a.r_stride = np; a.norm_partial = h->norm_partial;
     nt = J;
     return true;
-  }));
+  }, b->down);
   int maxL = 0;
   for (mgrit_handle* h : b->hs) maxL = std::max(maxL, (int)h->levels.size());
   for (int d = 1; d < maxL; ++d) {
     for (int pass = 0; pass < 2; ++pass)
-      b->down.push_back(add_relax_phase(b, 0, 1, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+      add_relax_phases(b, 0, 1, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
         mgrit_handle* h = b->hs[q];
         if ((int)h->levels.size() - 1 <= d) return false;
         Level& L = h->levels[d];
@@ -1515,9 +1549,9 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
         }
         nt = J;
         return true;
-      }));
+      }, b->down);
     // coarsest levels reached at this depth: sequential solves
-    mgrit_batch::Phase ph{1, 0, 1, (int)b->tiles.size(), 0, 0, 0, 0, 0};
+    mgrit_batch::Phase ph{1, 0, 1, (int)b->tiles.size(), 0, 0, 0, 0, 0, 512};
     for (int q = 0; q < nprob; ++q) {
       mgrit_handle* h = b->hs[q];
       if ((int)h->levels.size() - 1 != d) continue;
@@ -1539,7 +1573,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     if (ph.ntiles) b->down.push_back(ph);
   }
   for (int d = maxL - 2; d >= 1; --d)
-    b->up.push_back(add_relax_phase(b, 0, 1, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+    add_relax_phases(b, 0, 1, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
       mgrit_handle* h = b->hs[q];
       if ((int)h->levels.size() - 1 <= d) return false;
       Level& L = h->levels[d];
@@ -1552,7 +1586,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
       a.g = L.G; a.fstore = L.E;
       nt = J + 1;
       return true;
-    }));
+    }, b->up);
   b->final_args_off = (int)b->args.size();
   b->final_post = add_relax_phase(b, 1, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
     mgrit_handle* h = b->hs[q];
@@ -1625,7 +1659,7 @@ mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, cons
     if (ph.ntiles == 0) return MGRIT_OK;
     cudaError_t e = ph.kind == 0
                         ? launch_relax_batched(b->d_tabs, b->d_args, b->d_tiles + ph.tile_off, ph.ntiles, b->d_active,
-                                               ph.is_double, ph.coarse, ph.buf, ph.smem, s)
+                                               ph.is_double, ph.coarse, ph.buf, ph.smem, ph.threads, s)
                         : launch_sequential_batched(b->d_tabs, b->d_seq, b->d_tiles + ph.tile_off, ph.ntiles,
                                                     b->d_active, ph.is_double, ph.coarse, ph.buf, ph.smem, s);
     if (e != cudaSuccess) return fail(MGRIT_ECUDA, std::string("batched phase: ") + cudaGetErrorString(e));
