@@ -162,6 +162,7 @@ struct mgrit_handle {
   Scratch2d s2d{};         // 2D work buffers (allocated in mgrit_setup)
   bool adjoint_ready = false;
   double setup_ms = 0.0;
+  double setup_t0 = 0.0;
   // launch accounting and optional per-phase event timing
   int64_t setup_launches = 0, call_launches = 0;
   int setup_phase_launches[MGRIT_NUM_PHASES] = {};
@@ -544,8 +545,38 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   return MGRIT_OK;
 }
 
-mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, int order, int m, int levels,
-                         const mgrit_options* opt_in, void* stream, mgrit_handle** out) {
+// Completes a setup enqueued by setup_impl: waits for the handle's stream, checks for execution errors
+// and singular correction matrices (the handle is destroyed and *out cleared on failure), records times.
+static mgrit_status setup_finish(mgrit_handle** out) {
+  mgrit_handle* h = *out;
+  const cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    *out = nullptr;
+    return fail(MGRIT_ECUDA, std::string("setup: ") + cudaGetErrorString(e));
+  }
+  int flag = 0;
+  std::memcpy(&flag, h->norm_host + 3, sizeof(int));
+  if (flag) {
+    delete h;
+    *out = nullptr;
+    return fail(MGRIT_ESINGULAR, "a correction matrix has a (near) zero pivot");
+  }
+  h->collect_phase_times();
+  h->setup_launches = h->call_launches;
+  for (int i = 0; i < MGRIT_NUM_PHASES; ++i) {
+    h->setup_phase_launches[i] = h->phase_launches[i];
+    h->setup_phase_ms[i] = h->phase_ms[i];
+  }
+  h->reset_call_counters();
+  h->setup_ms = now_ms() - h->setup_t0;
+  return MGRIT_OK;
+}
+
+// The work of mgrit_setup enqueued on the handle's stream; defer = true returns before the stream is
+// synchronised (setup_finish completes it), so several problems' setups can overlap.
+static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wave, int order, int m, int levels,
+                               const mgrit_options* opt_in, void* stream, mgrit_handle** out, bool defer) {
   if (!out) return fail(MGRIT_EINVAL, "out is NULL");
   *out = nullptr;
   MG_TRY(check_grid(grid, wave, order, m));
@@ -664,9 +695,8 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
 
   cudaStream_t s = h->stream;
   WaveParams wp{wave->kind, wave->a, wave->k, wave->a2};
-  auto cuda_fail = [&](const char* what) {
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  auto launch_fail = [&](const char* what) {  // launch errors; execution errors surface in setup_finish
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cleanup_fail(fail(MGRIT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)));
     return MGRIT_OK;
   };
@@ -722,7 +752,7 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
       if (L.pcr32) launch_pcr_coef(L.sig32, L.nt, nx, p, L.pcr32, s);
       h->phase_end(MGRIT_PHASE_FACTOR, ev, L.pcr32 ? 2 : 1);
     }
-    if ((st = cuda_fail("setup")) != MGRIT_OK) return st;
+    if ((st = launch_fail("setup")) != MGRIT_OK) return st;
   }
   // zero rows that are read but never written: E_l[0], G_l[0], r64[0], EC[0]
   for (size_t l = 1; l < h->levels.size(); ++l) {
@@ -735,20 +765,18 @@ mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, in
     cudaMemsetAsync(h->r64, 0, (size_t)(J1 + 1) * np * sizeof(double), s);
     cudaMemsetAsync(h->EC, 0, (size_t)(J1 + 1) * np * sizeof(float), s);
   }
-  int flag = 0;
-  cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if ((st = cuda_fail("setup")) != MGRIT_OK) return st;
-  if (flag) return cleanup_fail(fail(MGRIT_ESINGULAR, "a correction matrix has a (near) zero pivot"));
-  h->collect_phase_times();
-  h->setup_launches = h->call_launches;
-  for (int i = 0; i < MGRIT_NUM_PHASES; ++i) {
-    h->setup_phase_launches[i] = h->phase_launches[i];
-    h->setup_phase_ms[i] = h->phase_ms[i];
-  }
-  h->reset_call_counters();
-  h->setup_ms = now_ms() - t0;
+  // the pivot flag travels with the stream; setup_finish reads it after the synchronisation
+  cudaMemcpyAsync(h->norm_host + 3, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if ((st = launch_fail("setup")) != MGRIT_OK) return st;
+  h->setup_t0 = t0;
   *out = h;
-  return MGRIT_OK;
+  if (defer) return MGRIT_OK;
+  return setup_finish(out);
+}
+
+mgrit_status mgrit_setup(const mgrit_grid* grid, const mgrit_wavespeed* wave, int order, int m, int levels,
+                         const mgrit_options* opt_in, void* stream, mgrit_handle** out) {
+  return setup_impl(grid, wave, order, m, levels, opt_in, stream, out, false);
 }
 
 }  // extern "C"
@@ -1497,14 +1525,43 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
   mgrit_batch* b = new mgrit_batch();
   b->stream = (cudaStream_t)stream;
   b->opt = opt;
-  for (int q = 0; q < nprob; ++q) {
-    mgrit_handle* h = nullptr;
-    mgrit_status st = mgrit_setup(&grids[q], &waves[q], orders[q], ms[q], 0, &opt, stream, &h);
-    if (st != MGRIT_OK) {
-      delete b;
-      return fail(st, "problem " + std::to_string(q) + ": " + g_last_error);
+  // the problems' setups are enqueued on a few streams of their own so that they overlap, then completed
+  // one by one; afterwards every handle works on the batch's stream
+  {
+    std::vector<cudaStream_t> ss((size_t)std::min(nprob, 8), nullptr);
+    for (cudaStream_t& x : ss)
+      if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        x = (cudaStream_t)stream;
+      }
+    if (stream) cudaStreamSynchronize((cudaStream_t)stream);  // work the caller queued before the setups
+    mgrit_status st = MGRIT_OK;
+    std::string err;
+    for (int q = 0; q < nprob && st == MGRIT_OK; ++q) {
+      mgrit_handle* h = nullptr;
+      st = setup_impl(&grids[q], &waves[q], orders[q], ms[q], 0, &opt, (void*)ss[q % ss.size()], &h, true);
+      if (st == MGRIT_OK) b->hs.push_back(h);
+      else err = "problem " + std::to_string(q) + ": " + g_last_error;
     }
-    b->hs.push_back(h);
+    for (size_t q = 0; q < b->hs.size(); ++q) {
+      const mgrit_status fs = setup_finish(&b->hs[q]);
+      if (fs != MGRIT_OK && st == MGRIT_OK) {
+        st = fs;
+        err = "problem " + std::to_string(q) + ": " + g_last_error;
+      }
+    }
+    for (mgrit_handle* h : b->hs)
+      if (h) h->stream = (cudaStream_t)stream;
+    for (cudaStream_t x : ss)
+      if (x && x != (cudaStream_t)stream) cudaStreamDestroy(x);
+    if (st != MGRIT_OK) {
+      std::vector<mgrit_handle*> keep;
+      for (mgrit_handle* h : b->hs)
+        if (h) keep.push_back(h);
+      b->hs = keep;
+      delete b;
+      return fail(st, err);
+    }
   }
   // phases of one cycle
   b->down.push_back(add_relax_phase(b, 1, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
