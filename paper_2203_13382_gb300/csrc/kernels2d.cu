@@ -187,17 +187,20 @@ __device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, d
   return t;
 }
 
-// Classical Gram-Schmidt projections h_t = <v_t, w>, t = 0..kk (kk < 10), of the rows [lo, hi) in one
-// pass over w; per-thread and per-warp sums in R, the warp partials summed in FP64 into hsum[0..kk] (all
-// threads see them).
-template <typename R>
-__device__ __forceinline__ void cta_multi_dot(const R* V, long long N, const R* w, int kk, long long lo, long long hi,
-                                              double (*wpart)[11], double* hsum) {
+// Arnoldi step with an unnormalised basis: the stored vectors are u_t with v_t = s_t u_t.  Pass A forms
+// w = s_k M u_k row by row (M^T for TRANS), stores it, and accumulates the raw projections <u_t, w>,
+// t = 0..k, in R per thread and warp, the warp partials summed in FP64 into hsum[0..k] (all threads see
+// them).  Rows [lo, hi).
+template <int B, typename R, bool TRANS>
+__device__ __forceinline__ void cta_apply_project(const R* uk, const R* sx, const R* sy, int nx, const R* V, long long N,
+                                                  R* w, int kk, long long lo, long long hi, R sk,
+                                                  double (*wpart)[11], double* hsum) {
   R acc[10];
 #pragma unroll
   for (int t = 0; t < 10; ++t) acc[t] = (R)0;
   for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
-    const R wq = w[q];
+    const R wq = sk * (TRANS ? apply_MT<B, R>(uk, sx, sy, q, nx) : apply_M<B, R>(uk, sx, sy, q, nx));
+    w[q] = wq;
 #pragma unroll
     for (int t = 0; t < 10; ++t)
       if (t <= kk) acc[t] += V[(size_t)t * N + q] * wq;
@@ -220,20 +223,24 @@ __device__ __forceinline__ void cta_multi_dot(const R* V, long long N, const R* 
   __syncthreads();
 }
 
-// w -= sum_t h_t v_t over the rows [lo, hi).
+// Pass B: w -= sum_t c_t u_t over the rows [lo, hi) and the sum of squares of the result (this CTA's
+// rows, valid in thread 0).
 template <typename R>
-__device__ __forceinline__ void cta_subtract_projections(const R* V, long long N, R* w, int kk, long long lo,
-                                                         long long hi, const double* h) {
-  R hr[10];
+__device__ __forceinline__ double cta_subtract_sumsq(const R* V, long long N, R* w, int kk, long long lo, long long hi,
+                                                     const double* c, double* red) {
+  R cr[10];
 #pragma unroll
-  for (int t = 0; t < 10; ++t) hr[t] = t <= kk ? (R)h[t] : (R)0;
+  for (int t = 0; t < 10; ++t) cr[t] = t <= kk ? (R)c[t] : (R)0;
+  R nn = (R)0;
   for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
     R v = w[q];
 #pragma unroll
     for (int t = 0; t < 10; ++t)
-      if (t <= kk) v -= hr[t] * V[(size_t)t * N + q];
+      if (t <= kk) v -= cr[t] * V[(size_t)t * N + q];
     w[q] = v;
+    nn += v * v;
   }
+  return block_sum_r<R>(nn, red);
 }
 
 // One CTA per interval j: b (= rhs, in place -> solution) of the system of step n(j) = n0 + j*m
@@ -260,26 +267,31 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restr
   R* V = basis + (size_t)j * (kmax + 1) * N;
   const double beta = sqrt(cta_dot<R>(b, b, N, red));
   if (beta == 0.0) return;  // x = 0
-  const R ib = (R)(1.0 / beta);
-  for (long long q = threadIdx.x; q < N; q += blockDim.x) V[q] = b[q] * ib;
+  __shared__ double sc[11], cf[10];  // v_t = sc[t] u_t; projection coefficients of the update pass
+  for (long long q = threadIdx.x; q < N; q += blockDim.x) V[q] = b[q];  // u_0 = b, v_0 = b / beta
   if (threadIdx.x == 0) {
     gv[0] = beta;
     for (int t = 1; t <= kmax; ++t) gv[t] = 0.0;
+    sc[0] = 1.0 / beta;
   }
   __syncthreads();
   int kused = 0;
   for (int kk = 0; kk < kmax; ++kk) {
-    R* vk = V + (size_t)kk * N;
+    R* uk = V + (size_t)kk * N;
     R* w = V + (size_t)(kk + 1) * N;
-    for (long long q = threadIdx.x; q < N; q += blockDim.x)
-      w[q] = TRANS ? apply_MT<B, R>(vk, sx, sy, q, nx) : apply_M<B, R>(vk, sx, sy, q, nx);
+    // classical Gram-Schmidt in two passes: w = M v_k with the projections on all basis vectors, then
+    // the update with the norm of the result
+    cta_apply_project<B, R, TRANS>(uk, sx, sy, nx, V, N, w, kk, 0, N, (R)sc[kk], wpart, hsum);
+    if ((int)threadIdx.x <= kk) {
+      const double h = sc[threadIdx.x] * hsum[threadIdx.x];
+      H[threadIdx.x][kk] = h;
+      cf[threadIdx.x] = h * sc[threadIdx.x];
+    }
     __syncthreads();
-    // classical Gram-Schmidt: all projections in one pass, then one update pass
-    cta_multi_dot<R>(V, N, w, kk, 0, N, wpart, hsum);
-    cta_subtract_projections<R>(V, N, w, kk, 0, N, hsum);
-    if ((int)threadIdx.x <= kk) H[threadIdx.x][kk] = hsum[threadIdx.x];
+    double nn = cta_subtract_sumsq<R>(V, N, w, kk, 0, N, cf, red);
+    if (threadIdx.x == 0) red[33] = nn;
     __syncthreads();
-    const double hn = sqrt(cta_dot<R>(w, w, N, red));
+    const double hn = sqrt(red[33]);
     if (threadIdx.x == 0) {
       H[kk + 1][kk] = hn;
       for (int t = 0; t < kk; ++t) {  // previous rotations
@@ -296,13 +308,11 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restr
       gv[kk + 1] = -sn[kk] * gv[kk];
       gv[kk] = cs[kk] * gv[kk];
       red[36] = fabs(gv[kk + 1]);
+      sc[kk + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
     }
     __syncthreads();
     kused = kk + 1;
     if (red[36] <= rtol * beta || !(hn > 0.0)) break;
-    const R ihn = (R)(1.0 / hn);
-    for (long long q = threadIdx.x; q < N; q += blockDim.x) w[q] = w[q] * ihn;
-    __syncthreads();
   }
   if (threadIdx.x == 0) {  // back substitution R y = g
     for (int t = kused - 1; t >= 0; --t) {
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restr
   }
   __syncthreads();
   R yr[10];
-  for (int t = 0; t < kused; ++t) yr[t] = (R)yv[t];
+  for (int t = 0; t < kused; ++t) yr[t] = (R)(yv[t] * sc[t]);
   for (long long q = threadIdx.x; q < N; q += blockDim.x) {
     R x = (R)0;
     for (int t = 0; t < kused; ++t) x += yr[t] * V[(size_t)t * N + q];
@@ -367,35 +377,39 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const R*
     cl.sync();
     return;
   }
-  const R ib = (R)(1.0 / beta);
-  for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) V[q] = b[q] * ib;
+  __shared__ double sc[11], cf[10];  // v_t = sc[t] u_t; projection coefficients of the update pass
+  for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) V[q] = b[q];  // u_0 = b, v_0 = b / beta
   if (threadIdx.x == 0) {
     gv[0] = beta;
     for (int t = 1; t <= kmax; ++t) gv[t] = 0.0;
+    sc[0] = 1.0 / beta;
   }
   int kused = 0;
   for (int kk = 0; kk < kmax; ++kk) {
-    R* vk = V + (size_t)kk * N;
+    R* uk = V + (size_t)kk * N;
     R* w = V + (size_t)(kk + 1) * N;
-    cl.sync();  // v_k complete in every CTA before M reads its neighbouring rows
-    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x)
-      w[q] = TRANS ? apply_MT<B, R>(vk, sx, sy, q, nx) : apply_M<B, R>(vk, sx, sy, q, nx);
-    __syncthreads();
-    // classical Gram-Schmidt: all projections of this CTA's rows in one pass, one cluster reduction
-    cta_multi_dot<R>(V, N, w, kk, lo, hi, wpart, hsum);
+    cl.sync();  // u_k complete in every CTA before M reads its neighbouring rows
+    // classical Gram-Schmidt in two passes: w = M v_k with this CTA's raw projections on all basis
+    // vectors (one cluster reduction), then the update with the sum of squares (one cluster reduction)
+    cta_apply_project<B, R, TRANS>(uk, sx, sy, nx, V, N, w, kk, lo, hi, (R)sc[kk], wpart, hsum);
     if ((int)threadIdx.x <= kk) mpart[slot][threadIdx.x] = hsum[threadIdx.x];
     cl.sync();
     if ((int)threadIdx.x <= kk) {
       double v = 0.0;
       for (int r = 0; r < C; ++r) v += cl.map_shared_rank(&mpart[slot][0], (unsigned)r)[threadIdx.x];
-      hsum[threadIdx.x] = v;
-      H[threadIdx.x][kk] = v;
+      const double h = sc[threadIdx.x] * v;
+      H[threadIdx.x][kk] = h;
+      cf[threadIdx.x] = h * sc[threadIdx.x];
     }
     slot ^= 1;
     __syncthreads();
-    cta_subtract_projections<R>(V, N, w, kk, lo, hi, hsum);
-    __syncthreads();
-    const double hn = sqrt(dot(w, w));
+    const double nn = cta_subtract_sumsq<R>(V, N, w, kk, lo, hi, cf, red);
+    if (threadIdx.x == 0) part[slot] = nn;
+    cl.sync();
+    double tot = 0.0;
+    for (int r = 0; r < C; ++r) tot += *cl.map_shared_rank(&part[slot], (unsigned)r);
+    slot ^= 1;
+    const double hn = sqrt(tot);
     if (threadIdx.x == 0) {
       H[kk + 1][kk] = hn;
       for (int t = 0; t < kk; ++t) {
@@ -412,13 +426,11 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const R*
       gv[kk + 1] = -sn[kk] * gv[kk];
       gv[kk] = cs[kk] * gv[kk];
       red[36] = fabs(gv[kk + 1]);
+      sc[kk + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
     }
     __syncthreads();
     kused = kk + 1;
     if (red[36] <= rtol * beta || !(hn > 0.0)) break;
-    const R ihn = (R)(1.0 / hn);
-    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) w[q] = w[q] * ihn;
-    __syncthreads();
   }
   if (threadIdx.x == 0) {
     for (int t = kused - 1; t >= 0; --t) {
@@ -429,7 +441,7 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const R*
   }
   __syncthreads();
   R yr[10];
-  for (int t = 0; t < kused; ++t) yr[t] = (R)yv[t];
+  for (int t = 0; t < kused; ++t) yr[t] = (R)(yv[t] * sc[t]);
   for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
     R x = (R)0;
     for (int t = 0; t < kused; ++t) x += yr[t] * V[(size_t)t * N + q];
