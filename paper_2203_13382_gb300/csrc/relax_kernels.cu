@@ -309,7 +309,7 @@ __device__ __forceinline__ void corr_solve_otf(float* __restrict__ x, const floa
   const int k = threadIdx.x;
   const bool act = k < P;
   const int g0 = k * PR;
-  float xp[PR], sg[PR];
+  float xp[PR], sg[PR] = {};  // sg is read only by the partition threads, after their loads
   float y[Q], V[Q][B], W[Q][B];
   float Lk[BB], Dk[BB], Uk[BB], gk[B];
   // M[g0 + rr, g0 + rr + o] for |o| <= B
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(512) k_pcr_coef(const float* __restrict__ sig_
   const int g0 = k * PR;
   const float* sig = sig_all + (size_t)blockIdx.x * nx;
   float* out = out_all + (size_t)blockIdx.x * stride;
-  float sg[PR];
+  float sg[PR] = {};  // read only by the partition threads, after their loads
   float V[Q][B], W[Q][B];
   float Lk[BB], Dk[BB], Uk[BB];
   auto M = [&](int rr, int o) -> float { return (o == 0 ? 1.f : 0.f) - sg[rr] * dcoef<B>(o); };
@@ -721,7 +721,7 @@ __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const flo
   const int k = threadIdx.x;
   const bool act = k < P;
   const int g0 = k * PR;
-  float xp[PR], sg[PR];
+  float xp[PR], sg[PR] = {};  // sg is read only by the partition threads, after their loads
   float gk[B];
   auto M = [&](int rr, int o) -> float { return (o == 0 ? 1.f : 0.f) - sg[rr] * dcoef<B>(o); };
   // v <- A^{-1} v for the interior block A (banded LU without pivoting, formed from sigma)

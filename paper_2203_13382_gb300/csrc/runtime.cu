@@ -449,11 +449,6 @@ mgrit_status finish_norm(mgrit_handle* h, double* out) {
   return MGRIT_OK;
 }
 
-mgrit_status read_norm(mgrit_handle* h, int J, double* out) {
-  MG_TRY(enqueue_norm(h, J));
-  return finish_norm(h, out);
-}
-
 // One captured cycle: the executable graph, the phase events it records and the launches it issues.
 struct CycleGraph {
   cudaGraphExec_t exec = nullptr;
