@@ -1,9 +1,11 @@
-"""The GPU's 1D multilevel MGRIT iteration counts against the paper's printed counts at its larger grids:
-Table 2 (Sec. 3.4) at 2^10 x 2^12 and 2^12 x 2^14 (the oracle reproduces the 2^8 x 2^10 row in the CPU
-suite), and the strong-scaling problem of Sec. 5 / SM4 (2^12 x 2^14, coarsening 16 then 4).
+"""The GPU's 1D MGRIT iteration counts against the paper's printed counts at its larger grids: Table 2
+(multilevel, Sec. 3.4) and Table 1 (two levels, Sec. 3.3) at 2^10 x 2^12 and 2^12 x 2^14 (the oracle
+reproduces their 2^8 x 2^10 rows in the CPU suite), and the strong-scaling problem of Sec. 5 / SM4
+(2^12 x 2^14, coarsening 16 then 4).
 
 The golden values are the paper's printed counts (tests/golden/table2_multilevel_iters_large.txt,
-tests/golden/sm4_strong_scaling_iters.txt), with the paper's settings: FP64, linear MGRIT, FCF, the
+tests/golden/table1_two_level_iters_large.txt, tests/golden/sm4_strong_scaling_iters.txt), with the
+paper's settings (Table 1: two levels; the paper's 10-iteration GMRES correction solves are exact here): FP64, linear MGRIT, FCF, the
 corrected coarse operator with exact 1D correction solves, u0 = sin^4(pi x), a random U[0, 1] initial
 iterate.  The paper's random iterate is not known, so a count may differ from the printed one by a
 cycle; every cell must agree within one and most cells exactly.  Each cell's pair is printed.
@@ -28,18 +30,20 @@ WAVES = {"alpha1": dict(wave="const", a=1.0), "alpha2": dict(wave="cos_t"), "alp
 
 
 def cells():
-    """(log2 nx, log2 nt, alpha, p, m_first, m, printed count) of both golden files."""
+    """(log2 nx, log2 nt, alpha, p, m_first, m, levels, printed count) of the golden files."""
     out = []
-    for name, has_first in (("table2_multilevel_iters_large.txt", False), ("sm4_strong_scaling_iters.txt", True)):
+    for name, kind in (("table2_multilevel_iters_large.txt", "t2"), ("table1_two_level_iters_large.txt", "t1"),
+                       ("sm4_strong_scaling_iters.txt", "sm4")):
         with open(os.path.join(HERE, name)) as f:
             for line in f:
                 if line.startswith("#") or not line.strip():
                     continue
                 v = line.split()
-                if has_first:
-                    out.append((int(v[0]), int(v[1]), v[2], int(v[3]), int(v[4]), int(v[5]), int(v[6])))
+                if kind == "sm4":
+                    out.append((int(v[0]), int(v[1]), v[2], int(v[3]), int(v[4]), int(v[5]), 0, int(v[6])))
                 else:
-                    out.append((int(v[0]), int(v[1]), v[2], int(v[3]), 0, int(v[4]), int(v[5])))
+                    out.append((int(v[0]), int(v[1]), v[2], int(v[3]), 0, int(v[4]), 2 if kind == "t1" else 0,
+                                int(v[5])))
     return out
 
 
@@ -47,9 +51,9 @@ def cells():
 def counts():
     res = {}
     for c in cells():
-        lnx, lnt, a, p, mf, m, _ = c
+        lnx, lnt, a, p, mf, m, lv, _ = c
         nx, nt = 1 << lnx, 1 << lnt
-        h = mg.mgrit_setup(nx, nt, p, m, m_first=mf, **WAVES[a])
+        h = mg.mgrit_setup(nx, nt, p, m, levels=lv, m_first=mf, **WAVES[a])
         u0 = torch.from_numpy(W.u0_sin4(nx)).cuda()
         U0 = torch.from_numpy(W.initial_iterate(nt, nx)).cuda()
         _, st = h.solve(u0, U0)
@@ -59,15 +63,19 @@ def counts():
     return res
 
 
-@pytest.mark.parametrize("cell", cells(), ids=lambda c: f"{c[2]}-p{c[3]}-m{c[4] or c[5]}{'-' + str(c[5]) if c[4] else ''}-2^{c[0]}x2^{c[1]}")
+def cell_id(c):
+    m = f"{c[4]}-{c[5]}" if c[4] else f"{c[5]}"
+    return f"{'two-level' if c[6] == 2 else 'multilevel'}-{c[2]}-p{c[3]}-m{m}-2^{c[0]}x2^{c[1]}"
+
+
+@pytest.mark.parametrize("cell", cells(), ids=cell_id)
 def test_cell_within_one_cycle(counts, cell):
-    got, expect = counts[cell], cell[6]
-    print(f"{cell[2]} p={cell[3]} m={(str(cell[4]) + '/') if cell[4] else ''}{cell[5]} nx=2^{cell[0]} nt=2^{cell[1]}: "
-          f"paper {expect}, GPU {got}")
+    got, expect = counts[cell], cell[7]
+    print(f"{cell_id(cell)}: paper {expect}, GPU {got}")
     assert abs(got - expect) <= 1
 
 
 def test_most_cells_exact(counts):
-    exact = sum(counts[c] == c[6] for c in counts)
+    exact = sum(counts[c] == c[7] for c in counts)
     print(f"{exact} of {len(counts)} cells equal the paper's printed count")
     assert exact >= 0.8 * len(counts)
