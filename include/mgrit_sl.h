@@ -112,6 +112,9 @@ typedef struct {
                        clusters are resident at once; 2, 4, 8, 16: that cluster size on every FP64
                        coarse pass (where the slice allows it); 0: one CTA per interval.  Results
                        are identical either way. */
+  double diverge_ratio; /* MGRIT_EDIVERGED once a residual norm exceeds this multiple of the first
+                       (default 1e3); 0: only a non-finite norm ends the iteration (rediscretised coarse
+                       operators can grow the residual for many cycles before converging) */
 } mgrit_options;
 
 /* Phases timed when mgrit_options.profile = 1 (indices into mgrit_stats.phase_ms / phase_launches). */

@@ -537,6 +537,7 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->gmres_rtol = 1e-2;
   opt->relax = 0;
   opt->cluster_coarse = 1;
+  opt->diverge_ratio = 1e3;
   return MGRIT_OK;
 }
 
@@ -592,6 +593,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
   if (opt.relax != 0 && opt.relax != 1) return fail(MGRIT_EINVAL, "relax must be 0 (FCF) or 1 (F)");
   if (opt.cluster_coarse < 0 || opt.cluster_coarse > 16 || (opt.cluster_coarse & (opt.cluster_coarse - 1)) != 0)
     return fail(MGRIT_EINVAL, "cluster_coarse must be 0, 1, 2, 4, 8 or 16");
+  if (!(opt.diverge_ratio >= 0.0)) return fail(MGRIT_EINVAL, "diverge_ratio must be >= 0");
   if (levels < 0 || levels == 1) return fail(MGRIT_EINVAL, "levels must be 0 or >= 2");
   std::vector<int> fac = factors(grid->nt, m, opt.m_first, levels, opt.max_coarsest);
   if (fac.empty()) return fail(MGRIT_EINVAL, "nt does not allow a coarse level with this m");
@@ -939,7 +941,7 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
     hist.push_back(rk);
     iters = k + 1;
     if (k == 0) r0 = rk;
-    if (!std::isfinite(rk) || rk > 1e3 * r0) {
+    if (!std::isfinite(rk) || (h->opt.diverge_ratio > 0.0 && rk > h->opt.diverge_ratio * r0)) {
       status = fail(MGRIT_EDIVERGED, "residual norm diverged");
       break;
     }
@@ -1765,7 +1767,7 @@ mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, cons
       iters[q] = k + 1;
       rk[q] = r;
       if (k == 0) r0[q] = r;
-      if (!std::isfinite(r) || r > 1e3 * r0[q]) {
+      if (!std::isfinite(r) || (b->opt.diverge_ratio > 0.0 && r > b->opt.diverge_ratio * r0[q])) {
         active[q] = 0;
         --n_active;
       } else if (k >= 1 && r < b->opt.rtol * r0[q]) {
