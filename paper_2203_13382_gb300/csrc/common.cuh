@@ -20,6 +20,12 @@ constexpr int kSliceThreads = 512;
 
 MGRIT_HD int wrap_pow2(int idx, int nx) { return idx & (nx - 1); }
 
+// Column i and row j of element pt of an nx x nx slice, nx a power of two (shifts, not a 64-bit divide).
+MGRIT_D void split_pow2(long long pt, int nx, int& i, int& j) {
+  i = (int)(pt & (nx - 1));
+  j = (int)(pt >> (__ffs(nx) - 1));
+}
+
 // Coefficient 1 / prod_{q != j} (j - q) of the Lagrange basis polynomial of node j = a - (P+1)/2,
 // a = 0..P, on the unit-spaced nodes -(P+1)/2 .. (P-1)/2: equals (-1)^{P-a} / (a! (P-a)!).
 template <int P>

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(kThreads2d) k_step2d(LevelTables T, const R* _
   if (pt >= N) return;
   const int n = m > 0 ? j * m + k : n0;
   const int nx = T.nx;
-  const int i = (int)(pt % nx), jj = (int)(pt / nx);
+  int i, jj;
+  split_pow2(pt, nx, i, jj);
   R wx[P + 1], wy[P + 1];
   axis_weights<P, R>(T, 0, n, pt, wx);
   axis_weights<P, R>(T, 1, n, pt, wy);
@@ -100,7 +101,8 @@ __global__ void __launch_bounds__(kThreads2d) k_step2d_T(LevelTables T, const do
   const int n = m > 0 ? j * m + k : n0;
   const int row = T.reverse ? T.nt - 1 - n : n;
   const int nx = T.nx, mask = nx - 1;
-  const int X = (int)(pt % nx), Y = (int)(pt / nx);
+  int X, Y;
+  split_pow2(pt, nx, X, Y);
   const int* bs = T.bstart + (size_t)row * (N + 1);
   const int* bp = T.bperm + (size_t)row * N;
   const double* sx = T.s64 + (size_t)row * N;
@@ -144,7 +146,8 @@ __global__ void __launch_bounds__(kThreads2d) k_step2d_T(LevelTables T, const do
 // y = M x with M = I - diag(sx) (I (x) D) - diag(sy) (D (x) I), D = (delta^2)^B (periodic).
 template <int B, typename R>
 __device__ __forceinline__ R apply_M(const R* x, const R* sx, const R* sy, long long pt, int nx) {
-  const int i = (int)(pt % nx), jj = (int)(pt / nx);
+  int i, jj;
+  split_pow2(pt, nx, i, jj);
   const R* row = x + (size_t)jj * nx;
   R dxv = (R)0, dyv = (R)0;
 #pragma unroll
@@ -159,7 +162,8 @@ __device__ __forceinline__ R apply_M(const R* x, const R* sx, const R* sy, long 
 // y = M^T x = x - (I (x) D) diag(sx) x - (D (x) I) diag(sy) x (D is symmetric).
 template <int B, typename R>
 __device__ __forceinline__ R apply_MT(const R* x, const R* sx, const R* sy, long long pt, int nx) {
-  const int i = (int)(pt % nx), jj = (int)(pt / nx);
+  int i, jj;
+  split_pow2(pt, nx, i, jj);
   R dxv = (R)0, dyv = (R)0;
 #pragma unroll
   for (int o = -B; o <= B; ++o) {
@@ -659,7 +663,8 @@ cudaError_t sequential2d(const LevelTables& T, int Nst, const R* g, const R* u0,
 __device__ __forceinline__ int base_key(const uint16_t* __restrict__ shift, int nt, int n, long long N, int nx,
                                         long long pt) {
   const int mask = nx - 1;
-  const int i = (int)(pt % nx), jj = (int)(pt / nx);
+  int i, jj;
+  split_pow2(pt, nx, i, jj);
   const int bx = (i + (int)shift[(size_t)n * N + pt]) & mask;
   const int by = (jj + (int)shift[((size_t)nt + n) * N + pt]) & mask;
   return by * nx + bx;
@@ -761,7 +766,8 @@ __global__ void __launch_bounds__(kThreads2d) k_grad2d(LevelTables T, const doub
     lagrange_weights<P, double>(ey, wy);
     lagrange_weights_deps<P>(ex, dwx);
     lagrange_weights_deps<P>(ey, dwy);
-    const int i = (int)(pt % nx), jj = (int)(pt / nx);
+    int i, jj;
+    split_pow2(pt, nx, i, jj);
     const int bx = i + (int)T.shift[ox], by = jj + (int)T.shift[oy];
     const double dsx = ds[ox], dsy = ds[oy];
     double val = 0.0;

@@ -338,7 +338,8 @@ __global__ void k_departure_da_2d(WaveParams w, Tableau T, int nx, int nt, doubl
   const int n = blockIdx.y;
   const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= npts) return;
-  const int j = (int)(pt / nx), i = (int)(pt % nx);
+  int i, j;
+  split_pow2(pt, nx, i, j);
   const double x = xmin + h * i, y = xmin + h * j;
   const double t1 = (n + 1) * dt;
   double kx[6], ky[6], dkx[6], dky[6];
