@@ -304,8 +304,7 @@ __device__ __forceinline__ void corr_solve_otf(float* __restrict__ x, const floa
                                                float* __restrict__ X, int nx) {
   constexpr int Q = PR - B, BB = B * B;
   const int P = nx / PR;
-  int T = 0;
-  while ((1 << T) < P) ++T;
+  const int T = __ffs(P) - 1;  // P is a power of two
   const int k = threadIdx.x;
   const bool act = k < P;
   const int g0 = k * PR;
@@ -546,8 +545,7 @@ __global__ void __launch_bounds__(512) k_pcr_coef(const float* __restrict__ sig_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* X = reinterpret_cast<float*>(smem_raw);
   const int P = nx / PR;
-  int T = 0;
-  while ((1 << T) < P) ++T;
+  const int T = __ffs(P) - 1;  // P is a power of two
   const int k = threadIdx.x;
   const bool act = k < P;
   const int g0 = k * PR;
@@ -716,8 +714,7 @@ __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const flo
                                                 const float* __restrict__ cf, float* __restrict__ X, int nx) {
   constexpr int Q = PR - B, BB = B * B;
   const int P = nx / PR;
-  int T = 0;
-  while ((1 << T) < P) ++T;
+  const int T = __ffs(P) - 1;  // P is a power of two
   const int k = threadIdx.x;
   const bool act = k < P;
   const int g0 = k * PR;
