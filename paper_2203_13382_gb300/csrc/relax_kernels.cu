@@ -709,9 +709,14 @@ __global__ void __launch_bounds__(512) k_pcr_coef(const float* __restrict__ sig_
 // gives the separator right-hand side g), then, once the separators are known, with the separator
 // couplings moved to the right-hand side (the spikes of the stored factorisation are not needed).
 // The PCR updates g only.  X: exchange area of at least 3 B P floats.
-template <int B, int PR>
-__device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const float* __restrict__ sig,
-                                                const float* __restrict__ cf, float* __restrict__ X, int nx) {
+// `cf` is being filled by a bulk copy that completes on cf_bar (phase parity cf_par): the first interior
+// solve needs no coefficient, so the wait comes after it, on the barrier that publishes its tails.  Once
+// every thread has read the last coefficient, thread 0 calls issue_next() (the next step's copy into the
+// same buffer).  Returns false (all threads) if the bounded wait gave up.
+template <int B, int PR, typename IssueNext>
+__device__ __forceinline__ bool corr_solve_coef(float* __restrict__ x, const float* __restrict__ sig,
+                                                const float* __restrict__ cf, float* __restrict__ X, int nx,
+                                                uint64_t* cf_bar, uint32_t cf_par, IssueNext issue_next) {
   constexpr int Q = PR - B, BB = B * B;
   const int P = nx / PR;
   const int T = __ffs(P) - 1;  // P is a power of two
@@ -770,7 +775,8 @@ __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const flo
       gk[a] = y[a];  // head of y, used below
     }
   }
-  __syncthreads();
+  const bool cf_ok = mbar_wait_bounded(cf_bar, cf_par, kWaitLimitCycles);
+  if (__syncthreads_or(!cf_ok)) return false;
   if (act) {
     const int km = (k + P - 1) & (P - 1);
     float g[B];
@@ -827,12 +833,14 @@ __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const flo
       xs[a] = v;
     }
   }
-  __syncthreads();  // every thread is done with the exchange area
+  // the separators go to the area of the y tails, which every thread last read before the first PCR
+  // barrier (P = 1: no PCR level, and the one partition thread reads back its own values)
   if (act) {
 #pragma unroll
     for (int a = 0; a < B; ++a) X[(size_t)a * P + k] = xs[a];
   }
   __syncthreads();
+  if (threadIdx.x == 0) issue_next();  // every coefficient of this step has been read
   if (act) {
     const int kp = (k + 1) & (P - 1);
     float xn[B];
@@ -861,6 +869,7 @@ __device__ __forceinline__ void corr_solve_coef(float* __restrict__ x, const flo
       store_part<float>(x + g0 + c * kPartRows, *reinterpret_cast<const float(*)[kPartRows]>(xp + c * kPartRows));
   }
   __syncthreads();
+  return true;
 }
 
 // Rows per partition of the on-the-fly solve: 16 for B <= 2 (half the partitions of the stored layout,
@@ -1045,9 +1054,12 @@ __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R*
     if constexpr (COARSE) {
       if constexpr (coef) {
         const uint32_t par = (stg.phase >> 2) & 1u;
-        const bool ok = mbar_wait_bounded(stg.bar(2), par, kWaitLimitCycles);
         stg.phase ^= 4u;
-        if (__syncthreads_or(!ok)) {
+        const bool ok = corr_solve_coef<B, otf_rows<B>()>((float*)dst, stg.sig(b), stg.cf(), stg.xch(), T.nx, stg.bar(2),
+                                                          par, [&]() {
+                                                            if (next_n >= 0) stage_issue_cf(stg, T, next_n);
+                                                          });
+        if (!ok) {  // nothing of the next step's record was issued; the current one may still land
           if (threadIdx.x == 0) {
             atomicExch(T.err, 1);
             mbar_wait_bounded(stg.bar(2), par, kWaitLimitCycles);
@@ -1055,9 +1067,6 @@ __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R*
           }
           return false;
         }
-        corr_solve_coef<B, otf_rows<B>()>((float*)dst, stg.sig(b), stg.cf(), stg.xch(), T.nx);
-        // the solve ends with a barrier: the record buffer is free for the next step's copy
-        if (threadIdx.x == 0 && next_n >= 0) stage_issue_cf(stg, T, next_n);
         stg.cf_pending = next_n;
       } else {
         corr_solve_otf<B, otf_rows<B>()>((float*)dst, stg.sig(b), stg.xch(), T.nx);
