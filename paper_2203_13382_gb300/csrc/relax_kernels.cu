@@ -67,7 +67,8 @@ __device__ __forceinline__ void apply_gather(const GatherRegs<P, double>& g, con
 }
 
 // The same gather in FP32 with the step's eps / shift rows in shared memory; the weights are formed
-// from eps in registers.
+// from eps in registers.  src carries the periodic halo src[nx + t] = src[t], t < kMaxOrder, so a
+// stencil is P + 1 consecutive elements from its wrapped first node.
 template <int P, int NT>
 __device__ __forceinline__ void apply_gather_staged(const float* __restrict__ eps, const uint16_t* __restrict__ sh,
                                                     const float* __restrict__ src, float* __restrict__ dst, int nx) {
@@ -77,13 +78,19 @@ __device__ __forceinline__ void apply_gather_staged(const float* __restrict__ ep
     if (i < nx) {
       float w[P + 1];
       lagrange_weights<P, float>(eps[i], w);
-      const int b = i + (int)sh[i];
-      float acc = w[0] * src[wrap_pow2(b, nx)];
+      const float* s = src + wrap_pow2(i + (int)sh[i], nx);
+      float acc = w[0] * s[0];
 #pragma unroll
-      for (int a = 1; a <= P; ++a) acc += w[a] * src[wrap_pow2(b + a, nx)];
+      for (int a = 1; a <= P; ++a) acc += w[a] * s[a];
       dst[i] = acc;
     }
   }
+}
+
+// Thread t < kMaxOrder: the periodic halo of slice s (its element t already final and visible to t).
+template <typename R>
+__device__ __forceinline__ void write_halo(R* s, int nx) {
+  if (threadIdx.x < kMaxOrder) s[nx + threadIdx.x] = s[threadIdx.x];
 }
 
 // ---- correction solve x <- M^{-1} x, M = I - diag(sigma) D_{2B} (layout: solver_layout.cuh) ----------
@@ -934,6 +941,7 @@ struct Stage {
   int cur;
   int pending;     // step row whose copy into buffer `cur` is in flight (-1: none)
   int cf_pending;  // step row whose coefficient record is in flight (-1: none)
+  bool ready;      // buffer `cur` has been waited for (stage_wait_ahead)
   MGRIT_D uint64_t* bar(int b) const { return reinterpret_cast<uint64_t*>(base + lay.bars) + b; }
   MGRIT_D unsigned char* buf(int b) const { return base + (size_t)b * lay.per_buf; }
   MGRIT_D const float* eps(int b) const { return reinterpret_cast<const float*>(buf(b)); }
@@ -952,6 +960,7 @@ __device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, co
   s.cur = 0;
   s.pending = -1;
   s.cf_pending = -1;
+  s.ready = false;
   if (!T.gather_stage) return s;
   s.lay = stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u);
   s.base = smem + ((used + 127) & ~(size_t)127);
@@ -998,12 +1007,17 @@ __device__ __forceinline__ void stage_prefetch_first(Stage& s, const LevelTables
 }
 
 // Issues the next step's copies (and this step's if it was not prefetched), then waits for buffer
-// `cur`; false if the bounded wait gave up (T.err set; thread 0 lets the copies in flight land first).
+// `cur` unless stage_wait_ahead already did; false if the bounded wait gave up (T.err set; thread 0 lets
+// the copies in flight land first).
 __device__ __forceinline__ bool stage_acquire(Stage& s, const LevelTables& T, int n, int next_n, bool otf) {
   const int b = s.cur;
   if (threadIdx.x == 0) {
     if (s.pending != n) stage_issue(s, T, n, b, otf);
     if (next_n >= 0) stage_issue(s, T, next_n, b ^ 1, otf);
+  }
+  if (s.ready) {
+    s.ready = false;
+    return true;
   }
   const uint32_t par = (s.phase >> b) & 1u;
   const bool ok = mbar_wait_bounded(s.bar(b), par, kWaitLimitCycles);
@@ -1017,6 +1031,28 @@ __device__ __forceinline__ bool stage_acquire(Stage& s, const LevelTables& T, in
     return false;
   }
   return true;
+}
+
+// At the end of a step: this thread waits for buffer `cur` (the next step's rows, copied since the start
+// of the step), so that the caller's end-of-step barrier also agrees on the outcome; the next
+// stage_acquire then skips its wait.  On false the caller's barrier reports the failure and the CTA
+// stops through stage_abandon.
+__device__ __forceinline__ bool stage_wait_ahead(Stage& s) {
+  const int b = s.cur;
+  const bool ok = mbar_wait_bounded(s.bar(b), (s.phase >> b) & 1u, kWaitLimitCycles);
+  s.phase ^= 1u << b;
+  s.ready = true;
+  return ok;
+}
+
+// After a failed stage_wait_ahead: thread 0 sets T.err and lets the copies still in flight (the next
+// step's rows and, with stored coefficients, its record) land before the CTA returns.
+__device__ __forceinline__ void stage_abandon(const Stage& s, const LevelTables& T, bool record) {
+  if (threadIdx.x != 0) return;
+  atomicExch(T.err, 1);
+  const int b = s.cur;
+  mbar_wait_bounded(s.bar(b), ((s.phase >> b) & 1u) ^ 1u, kWaitLimitCycles);
+  if (record && s.cf_pending >= 0) mbar_wait_bounded(s.bar(2), (s.phase >> 2) & 1u, kWaitLimitCycles);
 }
 
 // One full step src -> dst (Phi, or Psi with the correction solve), given the prefetched gather table.
@@ -1114,6 +1150,7 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
       if (wb) wb[i] = v;
     }
   }
+  if constexpr (std::is_same<R, float>::value) write_halo(src, nx);
   __syncthreads();
   if (j >= a.J) return;  // extra CTA: only the correction of the last C-point
   double sq = 0.0;
@@ -1186,7 +1223,19 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
       }
       sq += (double)sqt;
     }
-    __syncthreads();
+    if constexpr (kPipe) {  // FP32: halo of the next step's source; the wait for its rows joins the barrier
+      bool ahead_ok = true;
+      if (k + 1 < a.nsteps) {
+        write_halo(dst, nx);
+        ahead_ok = stage_wait_ahead(stg);
+      }
+      if (__syncthreads_or(!ahead_ok)) {
+        stage_abandon(stg, T, COARSE && (P + 1) / 2 <= 2);
+        return;
+      }
+    } else {
+      __syncthreads();
+    }
     R* t = src;
     src = dst;
     dst = t;
@@ -1220,6 +1269,7 @@ __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, con
     src[i] = v;
     if (store_all) out_all[i] = v;
   }
+  if constexpr (std::is_same<R, float>::value) write_halo(src, nx);
   __syncthreads();
   constexpr bool kPipe = std::is_same<R, float>::value;
   GatherRegs<P, R> gcur, gnext;
@@ -1240,6 +1290,7 @@ __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, con
       dst[i] = v;
       if (out) out[i] = v;
     }
+    if constexpr (kPipe) write_halo(dst, nx);
     __syncthreads();
     R* t = src;
     src = dst;
@@ -1303,6 +1354,7 @@ __global__ void __launch_bounds__(slice_threads<P, R, COARSE>()) k_apply_1d(Leve
   const int nx = T.nx, c = blockIdx.x;
   Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), T, COARSE);
   for (int i = threadIdx.x; i < nx; i += blockDim.x) src[i] = in[(size_t)c * nx + i];
+  if constexpr (std::is_same<R, float>::value) write_halo(src, nx);
   __syncthreads();
   GatherRegs<P, R> gr;
   load_gather<P, R>(gr, T, n0 + c);
@@ -1311,7 +1363,7 @@ __global__ void __launch_bounds__(slice_threads<P, R, COARSE>()) k_apply_1d(Leve
 }
 
 int buffer_elems(const LevelTables& T, bool coarse) {
-  int e = T.nx;
+  int e = T.nx + kMaxOrder;  // the slice and the periodic halo of the FP32 gather
   if (coarse && !T.otf) {  // the stored-factor solve uses the consumed gather source as exchange area
     const int need = 4 * (T.nx / kPartRows) * ((T.p + 1) / 2);
     if (need > e) e = need;
