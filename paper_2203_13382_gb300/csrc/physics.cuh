@@ -94,21 +94,6 @@ MGRIT_HD Tableau make_tableau(int r) {
   return T;
 }
 
-// Displacement x - xi(t_n) of the backward ERK step from (x, t1 = t_{n+1}) over dt (1D).
-MGRIT_D double erk_displacement_1d(const WaveParams& w, const Tableau& T, double x, double t1, double dt) {
-  double k[6];
-  for (int s = 0; s < T.stages; ++s) {
-    double xs = x;
-    for (int j = 0; j < s; ++j)
-      if (T.A[s][j] != 0.0) xs = xs - dt * T.A[s][j] * k[j];
-    k[s] = alpha_1d(w, xs, t1 - T.c[s] * dt);
-  }
-  double d = 0.0;
-  for (int s = 0; s < T.stages; ++s)
-    if (T.b[s] != 0.0) d = d + T.b[s] * k[s];
-  return dt * d;
-}
-
 // 2D displacement (x - xi, y - eta) of the backward ERK step.
 MGRIT_D void erk_displacement_2d(const WaveParams& w, const Tableau& T, double x, double y, double t1, double dt,
                                  double& dx, double& dy) {
