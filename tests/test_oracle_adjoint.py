@@ -155,6 +155,20 @@ def test_tangent_linear_departure_2d_matches_finite_differences(r, kind):
 
 
 @pytest.mark.parametrize("p", [1, 3, 5])
+def test_dphi_da_1d_is_the_directional_derivative_of_the_step(p):
+    """(dPhi/da) u equals the central difference of sl_apply_1d along ds away from floor switches."""
+    rng = np.random.default_rng(13)
+    nx = 24
+    s = rng.uniform(0.2, 0.8, nx) + rng.integers(-3, 4, nx)
+    ds, u = rng.standard_normal(nx), rng.standard_normal(nx)
+    d = 1e-6
+    fd = (sl.sl_apply_1d(u, s + d * ds, p) - sl.sl_apply_1d(u, s - d * ds, p)) / (2 * d)
+    got = adj.dphi_da_apply_1d(u, s, ds, p)
+    assert np.allclose(got, fd, atol=1e-7)
+    assert np.max(np.abs(got)) > 1e-2
+
+
+@pytest.mark.parametrize("p", [1, 3, 5])
 def test_dphi_da_2d_is_the_directional_derivative_of_the_step(p):
     """(dPhi/da) u equals the central difference of sl_apply_2d along (dsx, dsy) away from floor switches."""
     rng = np.random.default_rng(14)
