@@ -129,6 +129,40 @@ def test_sigma_recursion_sums_over_levels():
     assert np.allclose(s2[1], ph1[4] + ph1[5] + ph1[6] + ph1[7] + ph2[1])
 
 
+@pytest.mark.parametrize("p", [1, 3, 5])
+def test_multilevel_sigma_telescopes_to_the_fine_level(p):
+    """Eq. (nu_p_def) with eq. (varphi_p_multilevel_def) telescopes: on level l, sigma[n][i] equals
+    (-1)^{p+1} (f(eps_l[n][i]) - the sum of f(eps_0[k][i]) over the fine steps k inside coarse step n),
+    with no reference to the levels in between (variable alpha, uneven factors)."""
+    from oracle import mgrit as mg
+
+    H = mg.Hierarchy(sl.Grid(32, 64), sl.WaveSpeed("sin_kx_cos_t", a=0.5, k=1.0), p, [4, 2, 4])
+    f0 = co.f_poly(co.eps_of(H.levels[0].s), p)
+    span = 1
+    for lev in H.levels[1:]:
+        span *= lev.m
+        fine_sum = f0.reshape(lev.nt, span, -1).sum(axis=1)
+        expect = (-1.0) ** (p + 1) * (co.f_poly(co.eps_of(lev.s), p) - fine_sum)
+        assert np.allclose(lev.sigma, expect, atol=1e-12)
+        assert np.std(lev.sigma) > 1e-3  # sigma varies in n and i, so an index slip would show
+
+
+def test_multilevel_sigma_2d_telescopes_to_the_fine_level():
+    """The same telescoping for each axis of the 2D sigma (Sec. 4, eq. (BEOper_2D))."""
+    from oracle import mgrit as mg
+
+    p = 3
+    H = mg.Hierarchy(sl.Grid(8, 16, dim=2), sl.WaveSpeed("sin_cos2", a=0.5, a2=0.5), p, [2, 4])
+    for axis in (0, 1):
+        f0 = co.f_poly(co.eps_of(H.levels[0].s[axis]), p)
+        span = 1
+        for lev in H.levels[1:]:
+            span *= lev.m
+            fine_sum = f0.reshape((lev.nt, span) + f0.shape[1:]).sum(axis=1)
+            expect = co.f_poly(co.eps_of(lev.s[axis]), p) - fine_sum
+            assert np.allclose(lev.sigma[axis], expect, atol=1e-12)
+
+
 def test_correction_solvers():
     rng = np.random.default_rng(6)
     sig = rng.uniform(0.0, 2.0, 48)
