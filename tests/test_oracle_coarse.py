@@ -71,6 +71,32 @@ def test_backtracking_2d_equals_fine_steps_for_uniform_velocity():
     assert np.allclose(cx, 4 * 0.8 * 0.7, atol=1e-12) and np.allclose(cy, 4 * -1.3 * 0.7, atol=1e-12)
 
 
+def test_backtracking_2d_is_exact_for_bilinear_fine_maps():
+    """Sec. SM6 fits each component bilinearly through the four fine characteristics around the current
+    point, so when every fine offset field is bilinear in (x, y) the backtracked coarse departure point is
+    the exact composition of the m fine departure maps.  Distinct x, y and xy coefficients per fine step
+    make a swapped axis, a mixed-up corner or a reversed step order fail.  Nodes are taken away from the
+    periodic seam, where a bilinear field on the torus is not bilinear."""
+    nx, m = 64, 4
+    rng = np.random.default_rng(21)
+    coef = rng.uniform([0.6, 0.004, -0.006, 1e-4], [1.4, 0.012, 0.006, 3e-4], size=(2, m, 4))
+    J, I = np.meshgrid(np.arange(nx, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+
+    def field(axis, k, X, Y):
+        a, b, c, e = coef[axis, k]
+        return a + b * X + c * Y + e * X * Y
+
+    sx = np.stack([field(0, k, I, J) for k in range(m)])
+    sy = np.stack([-field(1, k, I, J) for k in range(m)])
+    cx, cy = co.backtrack_2d(sx, sy, m)
+    X, Y = I.copy(), J.copy()
+    for k in range(m - 1, -1, -1):
+        X, Y = X - field(0, k, X, Y), Y + field(1, k, X, Y)
+    inner = (slice(20, 44), slice(20, 44))
+    assert np.allclose(cx[0][inner], (I - X)[inner], atol=1e-10)
+    assert np.allclose(cy[0][inner], (J - Y)[inner], atol=1e-10)
+
+
 def test_backtracking_follows_a_varying_flow():
     """On eq. (alpha4) the backtracked coarse departure point tracks the exact coarse characteristic
     much better than one coarse ERK step (Sec. 3.3.1, Fig. 4)."""
