@@ -71,6 +71,24 @@ def test_backtracking_2d_equals_fine_steps_for_uniform_velocity():
     assert np.allclose(cx, 4 * 0.8 * 0.7, atol=1e-12) and np.allclose(cy, 4 * -1.3 * 0.7, atol=1e-12)
 
 
+def test_backtracking_1d_is_exact_for_affine_fine_maps():
+    """Eq. (coarse_depart_interp) interpolates linearly between the fine characteristics through the east
+    and west nodes, so affine fine offset fields (a different one per fine step) are followed exactly:
+    the coarse departure point is the composition of the m fine departure maps (nodes away from the
+    periodic seam)."""
+    nx, m = 128, 8
+    rng = np.random.default_rng(22)
+    a = rng.uniform(0.3, 2.7, m)
+    b = rng.uniform(-0.01, 0.01, m)
+    X0 = np.arange(nx, dtype=np.float64)
+    s = np.stack([a[k] + b[k] * X0 for k in range(m)])
+    c = co.backtrack_1d(s, m)[0]
+    X = X0.copy()
+    for k in range(m - 1, -1, -1):
+        X = X - (a[k] + b[k] * X)
+    assert np.allclose(c[40:88], (X0 - X)[40:88], atol=1e-11)
+
+
 def test_backtracking_2d_is_exact_for_bilinear_fine_maps():
     """Sec. SM6 fits each component bilinearly through the four fine characteristics around the current
     point, so when every fine offset field is bilinear in (x, y) the backtracked coarse departure point is
