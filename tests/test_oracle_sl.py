@@ -131,6 +131,39 @@ def test_sequential_global_order(p):
     assert orders[-1] > p - 0.3, (errs, orders)
 
 
+@pytest.mark.parametrize("r", [1, 3, 5])
+def test_departure_2d_local_order_against_an_ode_solver(r):
+    """Eq. (SL2D_char1-2) by one backward ERK step: against scipy's adaptive RK integration of the
+    characteristic ODE of the 2D workload's velocity (written out here), local error O(dt^{r+1}).  A
+    swapped component, a stage time slip or a wrong axis order of the [j][i] arrays changes the order."""
+    integrate = pytest.importorskip("scipy.integrate")
+    a = 0.5
+
+    def rhs(t, z):
+        x, y = z[: len(z) // 2], z[len(z) // 2:]
+        return np.concatenate([1.0 + a * np.sin(TWO_PI * y) * math.cos(TWO_PI * t),
+                               1.0 + a * np.cos(TWO_PI * x) * math.sin(TWO_PI * t)])
+
+    ws = sl.WaveSpeed("sin_cos2", a=a, a2=a)
+    pts = [(1, 2), (5, 3), (7, 12), (10, 6), (14, 9)]  # (i, j) on the 16-point grid
+    errs = []
+    for nx in (16, 32, 64):
+        g = sl.Grid(nx, 4, dim=2)
+        n = 2
+        sx, sy = sl.departure_offsets_2d(g, ws, n, r)
+        q = nx // 16
+        x0 = np.array([g.x[i * q] for i, _ in pts])
+        y0 = np.array([g.x[j * q] for _, j in pts])
+        sol = integrate.solve_ivp(rhs, ((n + 1) * g.dt, n * g.dt), np.concatenate([x0, y0]), method="DOP853",
+                                  rtol=1e-13, atol=1e-14)
+        xe, ye = sol.y[: len(pts), -1], sol.y[len(pts):, -1]
+        xi = np.array([x0[k] - g.h * sx[j * q, i * q] for k, (i, j) in enumerate(pts)])
+        eta = np.array([y0[k] - g.h * sy[j * q, i * q] for k, (i, j) in enumerate(pts)])
+        errs.append(max(np.max(np.abs(xi - xe)), np.max(np.abs(eta - ye))))
+    orders = [math.log(errs[i] / errs[i + 1], 2) for i in range(2)]
+    assert orders[-1] > r + 1 - 0.4 and min(orders) > r - 0.3, (errs, orders)
+
+
 @pytest.mark.parametrize("p", [1, 3, 5])
 def test_sl2d_reproduces_polynomials(p):
     """Tensor-product interpolation is exact on x^a y^b, a, b <= p (Sec. 4.1)."""
