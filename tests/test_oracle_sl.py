@@ -131,20 +131,26 @@ def test_sequential_global_order(p):
     assert orders[-1] > p - 0.3, (errs, orders)
 
 
+@pytest.mark.parametrize("kind", ["sin_cos2", "paper2"])
 @pytest.mark.parametrize("r", [1, 3, 5])
-def test_departure_2d_local_order_against_an_ode_solver(r):
+def test_departure_2d_local_order_against_an_ode_solver(r, kind):
     """Eq. (SL2D_char1-2) by one backward ERK step: against scipy's adaptive RK integration of the
-    characteristic ODE of the 2D workload's velocity (written out here), local error O(dt^{r+1}).  A
-    swapped component, a stage time slip or a wrong axis order of the [j][i] arrays changes the order."""
+    characteristic ODE (velocities written out here: the 2D workload's field and eq. (alpha-var_2D)),
+    local error O(dt^{r+1}).  A swapped component, a stage time slip or a wrong axis order of the
+    [j][i] arrays changes the order."""
     integrate = pytest.importorskip("scipy.integrate")
     a = 0.5
 
-    def rhs(t, z):
-        x, y = z[: len(z) // 2], z[len(z) // 2:]
-        return np.concatenate([1.0 + a * np.sin(TWO_PI * y) * math.cos(TWO_PI * t),
-                               1.0 + a * np.cos(TWO_PI * x) * math.sin(TWO_PI * t)])
+    def velocity(x, y, t):
+        if kind == "sin_cos2":
+            return 1.0 + a * np.sin(TWO_PI * y) * math.cos(TWO_PI * t), 1.0 + a * np.cos(TWO_PI * x) * math.sin(TWO_PI * t)
+        ct = math.cos(TWO_PI * t / 3.4)
+        return np.sin(math.pi * y) ** 2 * ct, -(np.cos(math.pi * x) ** 2) * ct
 
-    ws = sl.WaveSpeed("sin_cos2", a=a, a2=a)
+    def rhs(t, z):
+        return np.concatenate(velocity(z[: len(z) // 2], z[len(z) // 2:], t))
+
+    ws = sl.WaveSpeed(kind, a=a, a2=a)
     pts = [(1, 2), (5, 3), (7, 12), (10, 6), (14, 9)]  # (i, j) on the 16-point grid
     errs = []
     for nx in (16, 32, 64):
@@ -161,7 +167,7 @@ def test_departure_2d_local_order_against_an_ode_solver(r):
         eta = np.array([y0[k] - g.h * sy[j * q, i * q] for k, (i, j) in enumerate(pts)])
         errs.append(max(np.max(np.abs(xi - xe)), np.max(np.abs(eta - ye))))
     orders = [math.log(errs[i] / errs[i + 1], 2) for i in range(2)]
-    assert orders[-1] > r + 1 - 0.4 and min(orders) > r - 0.3, (errs, orders)
+    assert orders[-1] > r + 1 - 0.5 and min(orders) > r - 0.3, (errs, orders)
 
 
 @pytest.mark.parametrize("p", [1, 3, 5])
