@@ -65,6 +65,20 @@ def test_fixed_point_is_sequential_solution(norm_mode):
     assert np.linalg.norm(R.U - Useq) / np.linalg.norm(Useq) < 1e-9
 
 
+@pytest.mark.parametrize("solve_mode", ["exact", "gmres"])
+def test_fixed_point_2d_is_sequential_solution(solve_mode):
+    """2D (Sec. 4): with exact correction solves or the paper's inexact GMRES (rtol 1e-2, 10 iterations)
+    the cycle converges to the solution of the fine one-step system, i.e. sequential stepping."""
+    nx, nt = 8, 64
+    g = sl.Grid(nx, nt, dim=2)
+    H = mg.build_hierarchy(g, sl.WaveSpeed("sin_cos2", a=0.5, a2=0.5), 3, 2, solve_mode=solve_mode)
+    u0 = W.u0_bumps_2d(nx, W.SEED_C5_BUMPS, 5)
+    R = mg.mgrit_solve(H, u0, W.initial_iterate(nt, nx * nx).reshape(nt + 1, nx, nx), norm_mode=1)
+    assert R.converged and R.iterations > 3
+    Useq = mg.sequential_solve(H, u0)
+    assert np.linalg.norm(R.U - Useq) / np.linalg.norm(Useq) < 1e-9
+
+
 def test_residual_history_is_contracting():
     g, H, u0, U0 = _small(kind="cos_t_cos_x", p=1, m=8)
     R = mg.mgrit_solve(H, u0, U0)
