@@ -75,6 +75,51 @@ def test_host_only_calls(lib):
     assert lib.mgrit_setup(ctypes.byref(g3), ctypes.byref(w), 3, 64, 3, None, None, ctypes.byref(h)) == 1
 
 
+@pytest.mark.parametrize("field,value,status,msg", [
+    ("precision", 2, 1, b"precision"),
+    ("coarse_op", 2, 1, b"coarse_op"),
+    ("norm_mode", 0, 7, b"norm_mode"),
+    ("max_iter", 0, 1, b"max_iter"),
+    ("rtol", 1.0, 1, b"rtol"),
+    ("max_coarsest", 0, 1, b"max_coarsest"),
+    ("m_first", 1, 1, b"m_first"),
+    ("coarse_fp64", 1, 1, b"precision 1 only"),  # with the default precision 0
+    ("gmres_maxit", 11, 1, b"gmres_maxit"),
+    ("gmres_rtol", -0.5, 1, b"gmres_rtol"),
+    ("relax", 2, 1, b"relax"),
+    ("cluster_coarse", 3, 1, b"cluster_coarse"),
+    ("diverge_ratio", -1.0, 1, b"diverge_ratio"),
+])
+def test_option_errors_are_reported_before_any_cuda_call(lib, field, value, status, msg):
+    """Every option is range-checked by mgrit_setup before it touches the device (here: no GPU at all)."""
+    import ctypes
+
+    import paper_2203_13382_gb300 as mg
+
+    o = mg.default_options()
+    setattr(o, field, value)
+    g = mg.MgritGrid(1, 64, 64, -1.0, 1.0, 0.85)
+    w = mg.MgritWavespeed(0, 1.0, 1.0, 1.0)
+    h = ctypes.c_void_p()
+    assert lib.mgrit_setup(ctypes.byref(g), ctypes.byref(w), 3, 4, 0, ctypes.byref(o), None, ctypes.byref(h)) == status
+    assert msg in lib.mgrit_last_error() and not h.value
+
+
+def test_level_count_errors(lib):
+    import ctypes
+
+    import paper_2203_13382_gb300 as mg
+
+    w = mg.MgritWavespeed(0, 1.0, 1.0, 1.0)
+    h = ctypes.c_void_p()
+    g = mg.MgritGrid(1, 64, 64, -1.0, 1.0, 0.85)
+    assert lib.mgrit_setup(ctypes.byref(g), ctypes.byref(w), 3, 4, 1, None, None, ctypes.byref(h)) == 1
+    assert b"levels" in lib.mgrit_last_error()
+    g = mg.MgritGrid(1, 64, 24, -1.0, 1.0, 0.85)  # 24 -> 6 -> (not divisible by 4)
+    assert lib.mgrit_setup(ctypes.byref(g), ctypes.byref(w), 3, 4, 4, None, None, ctypes.byref(h)) == 1
+    assert b"divisible" in lib.mgrit_last_error()
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """ctypes mirrors of the C structs have the C sizes and field offsets (compiled with gcc here)."""
     import ctypes
