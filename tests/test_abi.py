@@ -120,6 +120,32 @@ def test_level_count_errors(lib):
     assert b"divisible" in lib.mgrit_last_error()
 
 
+def test_batched_setup_rejects_what_it_does_not_run(lib):
+    """mgrit_setup_batched runs FP32 bulk, FCF, FP32 coarse levels, the corrected operator, 1D only; other
+    requests are refused before any device work (no GPU here)."""
+    import ctypes
+
+    import paper_2203_13382_gb300 as mg
+
+    grids = (mg.MgritGrid * 2)(mg.MgritGrid(1, 64, 64, -1.0, 1.0, 0.85), mg.MgritGrid(1, 128, 64, -1.0, 1.0, 0.85))
+    waves = (mg.MgritWavespeed * 2)(mg.MgritWavespeed(0, 1.0, 1.0, 1.0), mg.MgritWavespeed(0, 1.0, 1.0, 1.0))
+    orders = (ctypes.c_int * 2)(3, 1)
+    ms = (ctypes.c_int * 2)(4, 4)
+    b = ctypes.c_void_p()
+    for field, value in (("precision", 0), ("relax", 1), ("coarse_fp64", 1), ("coarse_op", 1)):
+        o = mg.default_options()
+        o.precision = 1
+        setattr(o, field, value)
+        assert lib.mgrit_setup_batched(2, grids, waves, orders, ms, ctypes.byref(o), None, ctypes.byref(b)) == 7
+        assert not b.value
+    o = mg.default_options()
+    o.precision = 1
+    assert lib.mgrit_setup_batched(0, grids, waves, orders, ms, ctypes.byref(o), None, ctypes.byref(b)) == 1
+    grids[1].dim = 2
+    assert lib.mgrit_setup_batched(2, grids, waves, orders, ms, ctypes.byref(o), None, ctypes.byref(b)) == 7
+    assert b"1D" in lib.mgrit_last_error()
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """ctypes mirrors of the C structs have the C sizes and field offsets (compiled with gcc here)."""
     import ctypes
