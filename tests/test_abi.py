@@ -146,6 +146,34 @@ def test_batched_setup_rejects_what_it_does_not_run(lib):
     assert b"1D" in lib.mgrit_last_error()
 
 
+def test_null_handles_are_argument_errors(lib):
+    """Every call that takes a handle returns MGRIT_EINVAL for a null one; the destroy calls accept it."""
+    import ctypes
+
+    import paper_2203_13382_gb300 as mg
+
+    st = mg.MgritStats()
+    a, b = ctypes.c_int(), ctypes.c_int()
+    calls = [
+        lambda: lib.mgrit_solve(None, None, None, None, ctypes.byref(st)),
+        lambda: lib.sl_step_sequential(None, None, None, 0),
+        lambda: lib.mgrit_solve_host(None, None, None, None, ctypes.byref(st)),
+        lambda: lib.mgrit_solve_to_reference(None, None, None, None, None, 0.0, ctypes.byref(st)),
+        lambda: lib.mgrit_adjoint_solve(None, None, None, None, None, ctypes.byref(st)),
+        lambda: lib.mgrit_level_info(None, 0, ctypes.byref(a), ctypes.byref(b)),
+        lambda: lib.mgrit_copy_offsets(None, 0, None),
+        lambda: lib.mgrit_copy_sigma(None, 0, None),
+        lambda: lib.mgrit_apply_step(None, 0, 0, 1, None, None),
+        lambda: lib.mgrit_apply_step_noalloc(None, 0, 0, 1, None, None),
+        lambda: lib.mgrit_solve_batched(None, None, None, None, None),
+        lambda: lib.mgrit_default_options(None),
+    ]
+    assert [c() for c in calls] == [1] * len(calls)
+    lib.mgrit_destroy(None)
+    lib.mgrit_destroy_batched(None)
+    assert lib.mgrit_status_string(99) == b"unknown status"
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """ctypes mirrors of the C structs have the C sizes and field offsets (compiled with gcc here)."""
     import ctypes
