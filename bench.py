@@ -667,7 +667,7 @@ def run_adjoint2d(args) -> None:
         torch.cuda.synchronize()
         times.setdefault("fwd", []).append(e[0].elapsed_time(e[1]))
         times.setdefault("adj", []).append(e[1].elapsed_time(e[2]))
-        return st, ast, g_a
+        return st, ast, float(g_a)
 
     sampler = ClockSampler("0")
     sampler.start()

@@ -115,6 +115,11 @@ typedef struct {
   double diverge_ratio; /* MGRIT_EDIVERGED once a residual norm exceeds this multiple of the first
                        (default 1e3); 0: only a non-finite norm ends the iteration (rediscretised coarse
                        operators can grow the residual for many cycles before converging) */
+  int test_wait_cycles; /* testing the timeout path only; 0 (default): off.  > 0: in every 1D FP32 pass
+                       whose tables are staged into shared memory by bulk copies, each CTA's first bounded
+                       wait is made on a barrier that nothing completes, with this limit in SM cycles, so
+                       it gives up; the CTA then lets its copies in flight land (normal limit) and stops,
+                       and mgrit_solve returns MGRIT_ETIMEOUT.  The handle stays usable. */
 } mgrit_options;
 
 /* Phases timed when mgrit_options.profile = 1 (indices into mgrit_stats.phase_ms / phase_launches). */
@@ -233,13 +238,14 @@ mgrit_status mgrit_solve_host(mgrit_handle* h, const double* h_u0, const double*
  * others; dPhi/da acts through d s/d a of a tangent-linear ERK step, and u_n is recomputed from the
  * checkpoints.
  * d_C_checkpoints: [(nt/m_1 + 1) x N] the C-point rows u_{j m_1} of a converged forward solve.
- * d_dJ_du0: [N]; h_dJ_da: host scalar.  FP64 handles (precision 0), 1D and 2D.  The first call builds
+ * d_dJ_du0: [N]; d_dJ_dparams: [1] device array receiving dJ/da (both stay on the device, so a caller
+ * can chain further device work on the handle's stream).  FP64 handles (precision 0), 1D and 2D.  The first call builds
  * the transposed data (1D: floor ranges and M^T factors; 2D: buckets, 8 bytes per point and step of
  * every level) and d s/d a (8 bytes per fine point, step and dimension).  Synchronous.
  * stats (optional) describes the adjoint MGRIT solve.
  */
 mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, const double* d_C_checkpoints,
-                                 double* d_dJ_du0, double* h_dJ_da, mgrit_stats* stats);
+                                 double* d_dJ_du0, double* d_dJ_dparams, mgrit_stats* stats);
 
 /* ---- Introspection (for tests): copies of intermediate setup data --------------------------- */
 
@@ -266,10 +272,12 @@ mgrit_status mgrit_apply_step(mgrit_handle* h, int level, int n0, int count, con
  * cudaFree.  Same arguments, layout and result as mgrit_apply_step.  Levels that work in FP32 are
  * staged through an 8 MiB buffer in file-scope device memory that every GPU loading this library
  * holds until the process exits; count * N must not exceed 1048576 (MGRIT_EINVAL otherwise, before
- * any launch).  The first call on a device looks up that buffer's address, so make it before any
- * stream capture.  All calls share the buffer: calls that overlap on the GPU (other streams, other
- * threads, other handles) race; calls issued one after another are safe, as each call overwrites
- * every staged value it reads.  Synchronous; the current device must be the handle's device.
+ * any launch).  Every call looks up that buffer's address on the current device (cudaGetSymbolAddress),
+ * and the current device must be the handle's device (MGRIT_EINVAL otherwise, before any launch).  The
+ * call ends with a stream synchronisation, so it cannot be made while its stream is being captured.
+ * All calls share the buffer: calls that overlap on the GPU (other streams, other threads, other
+ * handles) race; calls issued one after another are safe, as each call overwrites every staged value
+ * it reads.  Synchronous.
  */
 mgrit_status mgrit_apply_step_noalloc(mgrit_handle* h, int level, int n0, int count, const double* d_in,
                                       double* d_out);

@@ -50,7 +50,8 @@ class MgritOptions(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("rtol", ctypes.c_double), ("max_coarsest", ctypes.c_int),
                 ("m_first", ctypes.c_int), ("coarse_fp64", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
-                ("relax", ctypes.c_int), ("cluster_coarse", ctypes.c_int), ("diverge_ratio", ctypes.c_double)]
+                ("relax", ctypes.c_int), ("cluster_coarse", ctypes.c_int), ("diverge_ratio", ctypes.c_double),
+                ("test_wait_cycles", ctypes.c_int)]
 
 
 PHASES = ["departure", "backtrack", "tables", "factor", "fine64_fc", "fine64_res", "fine64_post", "fine32_res",
@@ -95,8 +96,7 @@ _SIGNATURES = {
     "mgrit_solve_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(MgritStats)]),
     "mgrit_solve_to_reference": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double,
                                                 ctypes.POINTER(MgritStats)]),
-    "mgrit_adjoint_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double),
-                                           ctypes.POINTER(MgritStats)]),
+    "mgrit_adjoint_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(MgritStats)]),
     "mgrit_level_info": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
     "mgrit_copy_offsets": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
@@ -224,7 +224,15 @@ class Handle:
         _check(load_library().mgrit_copy_sigma(self._h(), level, _ptr(out)), "mgrit_copy_sigma")
         return out
 
+    def _check_slices(self, slices, out=None) -> None:
+        """The C calls read and write count * npts values: refuse tensors of any other shape."""
+        if slices.ndim != 2 or slices.shape[1] != self.npts:
+            raise ValueError(f"slices must have shape (count, {self.npts}), got {tuple(slices.shape)}")
+        if out is not None and (tuple(out.shape) != tuple(slices.shape) or out.device != slices.device):
+            raise ValueError(f"out must have the shape and device of slices, got {tuple(out.shape)} on {out.device}")
+
     def apply_step(self, level: int, n0: int, slices):
+        self._check_slices(slices)
         out = self._empty(*slices.shape)
         count = slices.shape[0]
         _check(load_library().mgrit_apply_step(self._h(), level, n0, count, _ptr(slices), _ptr(out)),
@@ -234,6 +242,7 @@ class Handle:
     def apply_step_noalloc(self, level: int, n0: int, slices, out=None):
         """apply_step for callers that cannot allocate device memory: the library allocates nothing, and
         `out` (if given) must be preallocated by the caller."""
+        self._check_slices(slices, out)
         if out is None:
             out = self._empty(*slices.shape)
         _check(load_library().mgrit_apply_step_noalloc(self._h(), level, n0, slices.shape[0], _ptr(slices),
@@ -277,13 +286,14 @@ class Handle:
         return u_out, st.as_dict()
 
     def adjoint(self, u_target, checkpoints):
-        """Discrete adjoint (mgrit_adjoint_solve): returns (dJ/du0, dJ/da, stats of the adjoint MGRIT)."""
+        """Discrete adjoint (mgrit_adjoint_solve): returns (dJ/du0, dJ/da, stats of the adjoint MGRIT); both
+        gradients are CUDA tensors (dJ/da of shape [1])."""
         dJdu0 = self._empty(self.npts)
-        dJda = ctypes.c_double()
+        dJda = self._empty(1)
         st = MgritStats()
         _check(load_library().mgrit_adjoint_solve(self._h(), _ptr(u_target), _ptr(checkpoints), _ptr(dJdu0),
-                                                   ctypes.byref(dJda), ctypes.byref(st)), "mgrit_adjoint_solve")
-        return dJdu0, dJda.value, st.as_dict()
+                                                   _ptr(dJda), ctypes.byref(st)), "mgrit_adjoint_solve")
+        return dJdu0, dJda, st.as_dict()
 
     def sequential(self, u0, u_out=None, store_all: bool = True):
         if u_out is None:

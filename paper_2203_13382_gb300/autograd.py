@@ -38,7 +38,7 @@ class AdvectionSolve(torch.autograd.Function):
         u_target = (ctx.u_T - grad_uT.reshape(-1)).contiguous()
         dJdu0, dJda, _ = ctx.h.adjoint(u_target, ctx.checkpoints)
         ctx.h.destroy()
-        return dJdu0.reshape(ctx.shape), torch.tensor(dJda, dtype=ctx.a_dtype, device=grad_uT.device), None
+        return dJdu0.reshape(ctx.shape), dJda.reshape(()).to(dtype=ctx.a_dtype, device=grad_uT.device), None
 
 
 def advection_solve(u0, a, **spec):

@@ -105,6 +105,9 @@ struct LevelTables {
   // over a thread-block cluster sized automatically; 2..16 = that cluster size (coarse_cluster.cu;
   // identical results)
   int cluster;
+  // testing the timeout path only (mgrit_options.test_wait_cycles): > 0 makes the first bounded wait of
+  // every CTA of a staged FP32 pass wait, with this limit in SM cycles, on a barrier nothing completes
+  int test_wait;
 };
 
 

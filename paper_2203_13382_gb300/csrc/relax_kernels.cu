@@ -942,6 +942,7 @@ struct Stage {
   int pending;     // step row whose copy into buffer `cur` is in flight (-1: none)
   int cf_pending;  // step row whose coefficient record is in flight (-1: none)
   bool ready;      // buffer `cur` has been waited for (stage_wait_ahead)
+  int test_wait;   // > 0: the next stage_acquire waits on bar(3), which nothing completes (timeout test)
   MGRIT_D uint64_t* bar(int b) const { return reinterpret_cast<uint64_t*>(base + lay.bars) + b; }
   MGRIT_D unsigned char* buf(int b) const { return base + (size_t)b * lay.per_buf; }
   MGRIT_D const float* eps(int b) const { return reinterpret_cast<const float*>(buf(b)); }
@@ -961,13 +962,16 @@ __device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, co
   s.pending = -1;
   s.cf_pending = -1;
   s.ready = false;
+  s.test_wait = 0;
   if (!T.gather_stage) return s;
+  s.test_wait = T.test_wait;
   s.lay = stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u);
   s.base = smem + ((used + 127) & ~(size_t)127);
   if (threadIdx.x == 0) {
     mbar_init(s.bar(0), 1);
     mbar_init(s.bar(1), 1);
     mbar_init(s.bar(2), 1);
+    mbar_init(s.bar(3), 1);  // never arrived on: the barrier of the timeout test
   }
   __syncthreads();
   return s;
@@ -1020,7 +1024,13 @@ __device__ __forceinline__ bool stage_acquire(Stage& s, const LevelTables& T, in
     return true;
   }
   const uint32_t par = (s.phase >> b) & 1u;
-  const bool ok = mbar_wait_bounded(s.bar(b), par, kWaitLimitCycles);
+  bool ok;
+  if (s.test_wait > 0) {  // timeout test: a wait that runs out; the copies are drained below
+    ok = mbar_wait_bounded(s.bar(3), 0u, s.test_wait);
+    s.test_wait = 0;
+  } else {
+    ok = mbar_wait_bounded(s.bar(b), par, kWaitLimitCycles);
+  }
   s.phase ^= 1u << b;
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) {

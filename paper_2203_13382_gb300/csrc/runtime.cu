@@ -143,6 +143,7 @@ struct mgrit_handle {
   int order = 1;
   mgrit_options opt;
   cudaStream_t stream = nullptr;
+  int device = 0;  // CUDA device current at setup (the handle's workspace lives there)
   int npts = 0;
   std::vector<Level> levels;
   std::vector<void*> allocs;
@@ -279,6 +280,7 @@ struct mgrit_handle {
     T.bstart = L.bstart;
     T.bperm = L.bperm;
     T.cluster = opt.cluster_coarse;
+    T.test_wait = opt.test_wait_cycles;
     if (trans_mode) {
       T.trans = 1;
       T.reverse = 1;
@@ -538,6 +540,7 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->relax = 0;
   opt->cluster_coarse = 1;
   opt->diverge_ratio = 1e3;
+  opt->test_wait_cycles = 0;
   return MGRIT_OK;
 }
 
@@ -594,6 +597,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
   if (opt.cluster_coarse < 0 || opt.cluster_coarse > 16 || (opt.cluster_coarse & (opt.cluster_coarse - 1)) != 0)
     return fail(MGRIT_EINVAL, "cluster_coarse must be 0, 1, 2, 4, 8 or 16");
   if (!(opt.diverge_ratio >= 0.0)) return fail(MGRIT_EINVAL, "diverge_ratio must be >= 0");
+  if (opt.test_wait_cycles < 0) return fail(MGRIT_EINVAL, "test_wait_cycles must be >= 0");
   if (levels < 0 || levels == 1) return fail(MGRIT_EINVAL, "levels must be 0 or >= 2");
   std::vector<int> fac = factors(grid->nt, m, opt.m_first, levels, opt.max_coarsest);
   if (fac.empty()) return fail(MGRIT_EINVAL, "nt does not allow a coarse level with this m");
@@ -607,6 +611,11 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
   h->order = order;
   h->opt = opt;
   h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(MGRIT_ECUDA, "cudaGetDevice failed");
+  }
   h->npts = grid->dim == 2 ? grid->nx * grid->nx : grid->nx;
   const int nx = grid->nx, np = h->npts, dim = grid->dim;
   const double hgrid = (grid->xmax - grid->xmin) / nx;
@@ -791,6 +800,7 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
   const int m1 = h->levels[1].m, J = h->J1();
   const int fp32 = h->opt.precision == 1;
   h->reset_call_counters();
+  MG_CUDA(cudaMemsetAsync(h->err_dev, 0, sizeof(int), s));  // a timeout of an earlier call is not this one's
   // initial iterate at the C-points
   MG_CUDA(cudaMemcpyAsync(h->X, d_u0, np * sizeof(double), u0_kind, s));
   MG_CUDA(cudaMemcpyAsync(h->Y, h->X, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1126,8 +1136,8 @@ mgrit_status ensure_adjoint(mgrit_handle* h) {
 extern "C" {
 
 mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, const double* d_C_checkpoints,
-                                 double* d_dJ_du0, double* h_dJ_da, mgrit_stats* stats) {
-  if (!h || !d_u_target || !d_C_checkpoints || !d_dJ_du0 || !h_dJ_da)
+                                 double* d_dJ_du0, double* d_dJ_dparams, mgrit_stats* stats) {
+  if (!h || !d_u_target || !d_C_checkpoints || !d_dJ_du0 || !d_dJ_dparams)
     return fail(MGRIT_EINVAL, "NULL argument");
   if (h->opt.precision != 0) return fail(MGRIT_EUNSUPPORTED, "the adjoint solve needs an FP64 handle (precision 0)");
   MG_TRY(ensure_adjoint(h));
@@ -1154,7 +1164,7 @@ mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, cons
                         : launch_gradient_a_1d(T0, L0.s64, L0.ds, d_C_checkpoints, mu, nt, m1, h->norm_partial, s);
     if (e != cudaSuccess) st = fail(MGRIT_ECUDA, std::string("gradient kernel: ") + cudaGetErrorString(e));
     launch_sum(h->norm_partial, J, h->norm_dev, s);
-    cudaMemcpyAsync(h_dJ_da, h->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(d_dJ_dparams, h->norm_dev, sizeof(double), cudaMemcpyDeviceToDevice, s);
   }
   cudaFreeAsync(mu0, s);
   cudaFreeAsync(mu, s);
@@ -1226,25 +1236,15 @@ namespace {
 
 // Staging memory of mgrit_apply_step_noalloc: two buffers of kNoAllocMaxElems FP32 values (8 MiB in
 // total) in file-scope device memory.  Every GPU that loads this library holds it until the process
-// exits.  In host code `g_noalloc_stage` only names a host-side stand-in, so its device address is
-// looked up with cudaGetSymbolAddress, once per device, with that device current.
+// exits.  In host code `g_noalloc_stage` only names a host-side stand-in, so its device address on the
+// current device is looked up with cudaGetSymbolAddress on every call (cheap, and never stale).
 constexpr long long kNoAllocMaxElems = 1LL << 20;
 static __device__ __align__(256) float g_noalloc_stage[2 * kNoAllocMaxElems];
 
-std::mutex g_noalloc_mutex;
-std::vector<float*> g_noalloc_addr;  // indexed by device ordinal
-
 mgrit_status noalloc_stage_address(float** out) {
-  int dev = 0;
-  MG_CUDA(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if ((int)g_noalloc_addr.size() <= dev) g_noalloc_addr.resize(dev + 1, nullptr);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    MG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_stage));
-    g_noalloc_addr[dev] = static_cast<float*>(p);
-  }
-  *out = g_noalloc_addr[dev];
+  void* p = nullptr;
+  MG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_stage));
+  *out = static_cast<float*>(p);
   return MGRIT_OK;
 }
 
@@ -1263,6 +1263,11 @@ mgrit_status mgrit_apply_step_noalloc(mgrit_handle* h, int level, int n0, int co
   if (elems > kNoAllocMaxElems)
     return fail(MGRIT_EINVAL, "count * slice size exceeds the no-allocation staging capacity of " +
                                   std::to_string(kNoAllocMaxElems) + " values");
+  int dev = -1;
+  MG_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device)
+    return fail(MGRIT_EINVAL, "the current device (" + std::to_string(dev) + ") is not the handle's device (" +
+                                  std::to_string(h->device) + ")");
   cudaStream_t s = h->stream;
   const int dbl = L.is_double;
   LevelTables T = h->tables(level, dbl);

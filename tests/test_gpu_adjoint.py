@@ -54,7 +54,9 @@ def test_adjoint_matches_oracle(case):
     U, st = h.solve(torch.from_numpy(u0).cuda(), torch.from_numpy(U_init).cuda())
     assert st["iterations"] == fwd.iterations
     m1 = h.level_info(1)[1]
-    dJdu0, ga, ast = h.adjoint(torch.from_numpy(ut).cuda(), U[::m1].contiguous())
+    dJdu0, ga_dev, ast = h.adjoint(torch.from_numpy(ut).cuda(), U[::m1].contiguous())
+    assert ga_dev.is_cuda and ga_dev.shape == (1,)  # dJ/da stays on the device
+    ga = float(ga_dev)
     assert ast["iterations"] == res.iterations
     assert rel(dJdu0.cpu().numpy(), lam[0]) < 1e-11
     assert abs(ga - dJda) <= 1e-11 * max(abs(dJda), 1e-12)
