@@ -1,18 +1,21 @@
 #!/usr/bin/env python
 """Benchmark: space-time DOF/s of MGRIT solves to a 1e-10 relative residual on one GB300.
 
-Workload (the paper's 1D variable-speed setting with the synthetic wave speed and initial data of this
-project): u_t + alpha u_x = 0 on periodic [-1, 1), alpha = 1 + 0.5 sin(2 pi x) cos(2 pi t), nx = 4096,
-nt = 16384, dt = 0.85 h, SL order p = r = 3, coarsening m = 8 on every level until at most 8 coarse
-steps remain (5 levels), u0 = three seeded Gaussian bumps, random U[0,1] initial iterate.
+Default workload (batched): 256 independent 1D problems u_t + alpha u_x = 0 on periodic [-1, 1),
+alpha = 1 + a sin(2 pi k x) cos(2 pi t), drawn with SplitMix64 (seed 20260004): nx in 256 .. 4096 and
+nt in 1024 .. 16384 (powers of two), order p = r in {1, 3, 5}, a in [0.1, 0.7], k in {1, 2, 3}, m in
+{4, 8}; dt = 0.85 h, u0 = sin^4(pi x), random U[0,1] initial iterate; FP32 bulk with FP64 residual;
+all problems' cycles in one launch per phase (mgrit_setup_batched / mgrit_solve_batched).
 
-One step = one complete solve through the library: mgrit_setup (departure points, backtracking,
-sigma, factorisations) + mgrit_solve to 1e-10 + mgrit_destroy, with u0 and the initial iterate
-already resident in HBM.  value = DOF / time per step (DOF = nx * nt), summed over ranks.
+One step = mgrit_setup_batched (departure points, backtracking, sigma, coefficients) + the batched solve
+to 1e-10 + mgrit_destroy_batched, with every u0 and initial iterate already resident in HBM.
+value = sum of nx * nt over the problems / time per step, summed over ranks (replicas).
 
-Also reported: the same-GPU sequential SL stepping comparator, the roofline of the dominant kernel,
-the CPU oracle on a bounded sample of the workload, an end-to-end figure through the host-buffer
-entry point, SM clocks sampled during the timed region, and the number of kernels launched.
+Also reported: the same-GPU sequential SL stepping comparator (every problem in one launch, with the
+setup it needs), the roofline of the dominant kernel, the CPU oracle on a bounded sample of the workload,
+an end-to-end figure through the host-buffer entry point, SM clocks sampled during the timed region and
+the number of kernels launched.  --workload advection1d | advection2d | adjoint2d | twolevel measure the
+single-problem rows (advection1d: the 4096 x 16384 variable-speed problem, p = 3, m = 8).
 
 `--impl reference` times the CPU oracle (the method restated in numpy from the paper) on a bounded
 sample of the same workload and prints the same JSON line with "impl": "reference".
@@ -585,55 +588,313 @@ def run_2d(args) -> None:
           gpu_launches=int(stats[0]["kernel_launches"]), device_bytes=int(stats[0]["device_bytes"]))
 
 
+# ---- the batched workload (the default benchmark line) -----------------------------------------------
+
+BATCH_CPU_SAMPLE = (8, 256)   # cpu_baseline: the first 8 problems, each on its first 256 time steps
+BATCH_REF_SAMPLE = (2, 256)   # --impl reference: one step = the first 2 problems on their first 256 steps
+
+
+def batch_levels(q, max_coarsest: int = 1) -> list[int]:
+    """Steps per level of one batched problem under the library's rule (factor m until <= max_coarsest)."""
+    out = [q.nt]
+    while out[-1] > max_coarsest and out[-1] % q.m == 0:
+        out.append(out[-1] // q.m)
+    return out
+
+
+def batch_phase_work(phase: str, probs, iters: list[int]) -> dict | None:
+    """Algorithmic bytes and flops of one phase over a whole batched solve (problem q takes part in
+    iters[q] cycles; the per-pass figures are those of phase_work for one problem)."""
+    byts = flops = 0.0
+    fp = 32
+    for q, it in zip(probs, iters):
+        nx, p, m = q.nx, q.order, q.m
+        nts = batch_levels(q)
+        J = q.nt // m
+        pts = nx * q.nt
+        if phase == "fine64_res":
+            # per point-step: 2 B shift + (p+1) FP64 weights; per interval: start slice and C value in (8 B each),
+            # residual out in FP64 and FP32
+            byts += it * (pts * (2 + 8 * (p + 1)) + J * nx * (8 + 8 + 8 + 4))
+            flops += it * pts * 2 * (p + 1)
+            fp = 64
+        elif phase == "fine32_res":
+            byts += it * (pts * 6 + J * nx * (4 + 4))
+            flops += it * pts * 2 * (p + 1)
+        elif phase == "coarse":
+            per_cycle = 0
+            for l in range(1, len(nts) - 1):
+                ntl, Jl = nts[l], nts[l] // m
+                per_cycle += ntl * nx * 14 + 2 * Jl * nx * 4          # FC
+                per_cycle += ntl * nx * 14 + 3 * Jl * nx * 4          # RES
+                per_cycle += (ntl - Jl) * nx * 18 + 2 * Jl * nx * 4   # POST
+            byts += it * per_cycle
+        elif phase == "coarsest":
+            byts += it * nts[-1] * nx * 14
+        else:
+            return None
+    return {"bytes": byts, "flops": flops, "fp": fp}
+
+
+BATCH_KERNELS = {"fine64_res": "k_relax_batched<double, false, 512> (level-0 FP64 residual, every problem)",
+                 "fine32_res": "k_relax_batched<float, false, NT> (level-0 FP32 error pass, per CTA size)",
+                 "coarse": "k_relax_batched<float, true, NT> (coarse levels FC/RES/POST)",
+                 "coarsest": "k_sequential_batched<float, true> (coarsest levels)"}
+
+
+def batch_roofline(phase_ms: dict, phase_n: dict, probs, iters, hbm_peak: float, hbm_src: str,
+                   traffic: dict | None) -> tuple[dict, list]:
+    """Roofline of every relaxation phase of the batched solve; the first is the one with the largest share."""
+    total = max(sum(phase_ms.values()), 1e-30)
+    lines = []
+    for ph in ("fine64_res", "fine32_res", "coarse", "coarsest"):
+        n = phase_n.get(ph, 0)
+        if not n:
+            continue
+        w = batch_phase_work(ph, probs, iters)
+        t = phase_ms[ph] / 1e3  # seconds over the solve
+        t_hbm = w["bytes"] / (hbm_peak * 1e9)
+        t_alu = w["flops"] / (FP64_PEAK_TFLOPS * 1e12) if w["fp"] == 64 else 0.0
+        out = {"kernel": BATCH_KERNELS[ph], "phase": ph, "phase_share": phase_ms[ph] / total, "launches": n,
+               "avg_launch_ms": phase_ms[ph] / n}
+        if t_alu > t_hbm:
+            out.update({"bound": "alu", "achieved": w["flops"] / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"})
+        else:
+            out.update({"bound": "hbm", "achieved": w["bytes"] / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "peak_source": f"{hbm_src} hbm_gbs"})
+        out["frac"] = out["achieved"] / out["peak"]
+        out["algorithmic_bytes_per_launch"] = w["bytes"] / n
+        out["algorithmic_flops_per_launch"] = w["flops"] / n
+        out["traffic"] = (traffic or {}).get(ph)
+        lines.append(out)
+    lines.sort(key=lambda x: -x["phase_share"])
+    if not lines:
+        return {"bound": None}, []
+    return lines[0], lines[1:]
+
+
+def batch_inputs(probs):
+    """u0 = sin^4(pi x) and the random initial iterate (read at the C-points only) of every problem."""
+    u0s = [W.u0_sin4(q.nx) for q in probs]
+    rows = [np.arange(0, q.nt + 1, q.m) for q in probs]
+    inits_c = [W.initial_iterate(q.nt, q.nx, rows=r) for q, r in zip(probs, rows)]  # row 0 is zero (ignored)
+    return u0s, rows, inits_c
+
+
+def oracle_batch_sample(nprob: int, nt_s: int) -> tuple[float, int, list[int]]:
+    """Oracle MGRIT solves of the first nprob batched problems, each on its first nt_s steps (same nx, p, m,
+    alpha, u0, initial iterate); returns (seconds, DOF, iterations)."""
+    from oracle import mgrit as omg
+    from oracle import semi_lagrangian as osl
+
+    probs = W.batched_problems(WORKLOAD_BATCH["problems"])[:nprob]
+    t0 = time.perf_counter()
+    its = []
+    for q in probs:
+        H = omg.build_hierarchy(osl.Grid(q.nx, nt_s), osl.WaveSpeed("sin_kx_cos_t", a=q.a, k=float(q.k)), q.order, q.m)
+        its.append(omg.mgrit_solve(H, W.u0_sin4(q.nx), W.initial_iterate(nt_s, q.nx), rtol=WORKLOAD_BATCH["rtol"]).iterations)
+    return time.perf_counter() - t0, sum(q.nx * nt_s for q in probs), its
+
+
+def run_reference_batched(args) -> None:
+    rank, _, _ = rank_info()
+    if rank != 0:
+        return
+    nprob, nt_s = BATCH_REF_SAMPLE
+    for _ in range(args.warmup):
+        oracle_batch_sample(nprob, nt_s)
+    el, dof, its = 0.0, 0, []
+    for _ in range(args.steps):
+        t, dof, its = oracle_batch_sample(nprob, nt_s)
+        el += t
+    value = dof * args.steps / el
+    sample = (f"oracle MGRIT solves to 1e-10 of the first {nprob} of {WORKLOAD_BATCH['problems']} batched problems, "
+              f"each on its first {nt_s} time steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**WORKLOAD_BATCH, "sample_problems": nprob, "sample_nt": nt_s}, "iterations": its,
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores_used(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args) -> None:
     import torch
 
     import paper_2203_13382_gb300 as mg
 
-    wl = WORKLOAD_BATCH
+    rank, local_rank, world = rank_info()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    wl = dict(WORKLOAD_BATCH)
     probs = W.batched_problems(wl["problems"])
     specs = [dict(nx=q.nx, nt=q.nt, order=q.order, m=q.m, a=q.a, k=float(q.k)) for q in probs]
-    u0s, inits, outs = [], [], []
-    for q in probs:
-        u0s.append(torch.from_numpy(W.u0_sin4(q.nx)).cuda())
-        U = torch.empty(q.nt + 1, q.nx, dtype=torch.float64, device="cuda")
-        rows = np.arange(q.m, q.nt + 1, q.m)  # read at the C-points only
-        U[rows] = torch.from_numpy(W.initial_iterate(q.nt, q.nx, rows=rows)).cuda()
+    u0_h, rows, inits_c = batch_inputs(probs)
+    u0s = [torch.from_numpy(u).cuda() for u in u0_h]
+    inits, outs = [], []
+    for q, r, ic in zip(probs, rows, inits_c):
+        U = torch.zeros(q.nt + 1, q.nx, dtype=torch.float64, device="cuda")
+        U[torch.from_numpy(r).cuda()] = torch.from_numpy(ic).cuda()
         inits.append(U)
         outs.append(torch.empty(q.nt + 1, q.nx, dtype=torch.float64, device="cuda"))
     dof = sum(q.nx * q.nt for q in probs)
+    stream = torch.cuda.current_stream()
 
-    def step():
-        b = mg.mgrit_setup_batched(specs)
+    def one_step(profile: int):
+        b = mg.mgrit_setup_batched(specs, rtol=wl["rtol"], profile=profile)
         _, st = b.solve(u0s, inits, outs)
         b.destroy()
         return st
 
-    sampler = ClockSampler("0")
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):  # the first setup also runs the tuner (its choices are cached per batch)
+        one_step(0)
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(_gpu_id(torch, local_rank))
     sampler.start()
-    ms, stats = _timed(step, args.steps, args.warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [one_step(0) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    # kernel durations: a few more steps with CUDA events around every launch on its stream
+    nprof = max(1, min(3, args.steps))
+    pstats = [one_step(1) for _ in range(nprof)]
+    torch.cuda.synchronize()
     clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    value = whole_job_value(dof, world, ms)
     iters = [st["iterations"] for st in stats[0]]
     conv = all(st["converged"] for st in stats[0])
-    # comparator: every problem stepped sequentially (one thread-block cluster each) on 16 streams at once,
-    # plus the departure points and tables of every problem
-    streams = [torch.cuda.Stream() for _ in range(16)]
-    hs = [mg.mgrit_setup(q.nx, q.nt, q.order, q.m, wave="sin_kx_cos_t", a=q.a, k=float(q.k), precision=1,
-                         stream=streams[i % 16].cuda_stream, profile=1) for i, q in enumerate(probs)]
-    torch.cuda.synchronize()
+    launches = int(sum(st[0]["kernel_launches"] for st in stats))
+    # phase table per step: setup phases summed over the problems, cycle phases from the batch totals
+    setup_ph = ("departure", "backtrack", "tables", "factor")
+    ph_ms = {k: 0.0 for k in pstats[0][0]["phase_ms"]}
+    ph_n = {k: 0 for k in ph_ms}
+    for st in pstats:
+        for k in ph_ms:
+            if k in setup_ph:
+                ph_ms[k] += sum(x["phase_ms"][k] for x in st) / nprof
+                ph_n[k] += sum(x["phase_launches"][k] for x in st) // nprof
+            else:
+                ph_ms[k] += st[0]["phase_ms"][k] / nprof
+                ph_n[k] += st[0]["phase_launches"][k] // nprof
+    hbm, hbm_src = peaks()
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get("batched")
+    roof, roof_others = batch_roofline(ph_ms, ph_n, probs, [x["iterations"] for x in pstats[0]], hbm, hbm_src,
+                                       traffic)
 
-    def seq_all():
-        return [h.sequential(u0s[i], store_all=False) for i, h in enumerate(hs)]
+    comparator, e2e = None, None
+    if not args.no_comparator:
+        # comparator: sequential SL stepping of every problem on the same GPU, all problems in one launch (one CTA
+        # each, FP32), plus what it needs from the setup: the fine departure points and level-0 tables
+        b = mg.mgrit_setup_batched(specs, profile=1)
+        b.sequential(u0s)
+        torch.cuda.synchronize()
+        nseq = max(3, min(args.steps, 10))
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(nseq):
+            last = b.sequential(u0s)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        seq_steps_ms = s0.elapsed_time(s1) / nseq
+        _, sst = b.solve(u0s, inits, outs)
+        b.destroy()
+        dep_ms = sum(x["phase_ms"]["departure"] for x in sst)
+        tab_ms = 0.0
+        for q, x in zip(probs, sst):  # the level-0 share of each problem's tables phase
+            nts = batch_levels(q)
+            tab_ms += x["phase_ms"]["tables"] * nts[0] / sum(nts)
+        seq_ms = seq_steps_ms + dep_ms + tab_ms
+        fixed = max(float((l - o[-1]).norm() / l.norm()) for l, o in zip(last, outs))
+        comparator = {"sequential_dof_per_s": dof / (seq_ms / 1e3), "sequential_ms": seq_ms,
+                      "sequential_steps_only_ms": seq_steps_ms, "sequential_setup_ms": dep_ms + tab_ms,
+                      "sequential_precision": "fp32",
+                      "sequential_includes": "sl_step_sequential_batched (all problems in one launch, one CTA each, "
+                                             "FP32) + every problem's FP64 departure points and level-0 gather tables "
+                                             "(sum of their kernel times)",
+                      "mgrit_over_sequential": seq_ms / ms,
+                      "fp32_sequential_vs_mgrit_final_slice_max_rel_diff": fixed}
+        # end to end through the host-buffer entry point: inputs from pinned host memory, every solution back
+        try:
+            u0_pin = [torch.from_numpy(u).pin_memory() for u in u0_h]
+            ic_pin = [torch.from_numpy(ic).pin_memory() for ic in inits_c]
+            out_pin = [torch.empty(q.nt + 1, q.nx, dtype=torch.float64, pin_memory=True) for q in probs]
+            pinned = True
+        except RuntimeError:
+            u0_pin = [torch.from_numpy(u) for u in u0_h]
+            ic_pin = [torch.from_numpy(ic) for ic in inits_c]
+            out_pin = [torch.empty(q.nt + 1, q.nx, dtype=torch.float64) for q in probs]
+            pinned = False
+        ne2e = 2
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ne2e):
+            be = mg.mgrit_setup_batched(specs, rtol=wl["rtol"])
+            be.solve_host([u.numpy() for u in u0_pin], [x.numpy() for x in ic_pin], [x.numpy() for x in out_pin])
+            be.destroy()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / ne2e
+        e2e = {"value": world * dof / e2e_s, "unit": "DOF/s",
+               "h2d_bytes_per_step": int(sum((q.nx + (q.nt // q.m) * q.nx) * 8 for q in probs)),
+               "d2h_bytes_per_step": int(sum((q.nt + 1) * q.nx * 8 for q in probs)), "pinned": pinned,
+               "path": "mgrit_setup_batched + mgrit_solve_batched_host (host u0, C-point iterate in; every full "
+                       "solution out) + mgrit_destroy_batched, wall clock"}
+        del u0_pin, ic_pin, out_pin
 
-    seq_ms, _ = _timed(seq_all, 2, 1)
-    for h in hs:
-        h.destroy()
-    _line(args, METRIC, dof / (ms / 1e3), "DOF/s", ms, {**wl, "dof": dof},
-          iterations_min_max=[min(iters), max(iters)], converged=conv,
-          comparator={"sequential_steps_only_ms": seq_ms, "sequential_dof_per_s_steps_only": dof / (seq_ms / 1e3),
-                      "mgrit_over_sequential_steps_only": seq_ms / ms,
-                      "sequential_includes": "nt SL steps of every problem, 16 streams (setup not included)"},
-          clocks=clocks)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        nprob, nt_s = BATCH_CPU_SAMPLE
+        secs, sdof, sits = oracle_batch_sample(nprob, nt_s)
+        cpu = {"value": sdof / secs, "unit": "DOF/s", "cores": cores_used(), "kind": "oracle", "cpu_model": cpu_model(),
+               "host_cores": os.cpu_count(),
+               "sample": f"oracle MGRIT solves to 1e-10 of the first {nprob} of {len(probs)} problems, each on its "
+                         f"first {nt_s} time steps (iterations {sits}, {secs:.1f} s)"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {**wl, "dof": dof, "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (per-step gather tables of the batch exceed 10 GB)"},
+            "iterations_min_max": [min(iters), max(iters)], "converged": conv,
+            "setup_ms_per_step": float(np.median([max(x["setup_ms"] for x in st) for st in stats])),
+            "comparator": comparator, "roofline": roof, "roofline_others": roof_others, "cpu_baseline": cpu,
+            "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "phases_ms_per_step": {k: v for k, v in ph_ms.items() if ph_n[k]},
+            "phase_launches_per_step": {k: v for k, v in ph_n.items() if v},
+            "timing": {"value": "K steps (batched setup + solve + destroy) without instrumentation, CUDA events",
+                       "kernels": f"{nprof} further steps with CUDA events around every launch on its stream; setup "
+                                  "phases summed over the problems (their setups overlap on 8 streams)"},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _gpu_id(torch, local_rank: int) -> str:
+    props = torch.cuda.get_device_properties(local_rank)
+    gpu_id = str(getattr(props, "uuid", local_rank))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    return gpu_id
 
 
 def run_adjoint2d(args) -> None:
@@ -759,15 +1020,18 @@ def main():
     ap.add_argument("--no-comparator", action="store_true", help="skip the sequential comparator and e2e runs")
     ap.add_argument("--nt", type=int, default=0, help="override nt (small profiling cases only)")
     ap.add_argument("--nx", type=int, default=0, help="override nx of the 2D workload (small profiling cases only)")
-    ap.add_argument("--workload", choices=["advection1d", "advection2d", "batched", "adjoint2d", "twolevel", "cpu"],
-                    default="advection1d", help="advection1d is the benchmark; the others measure further rows")
+    ap.add_argument("--workload", choices=["batched", "advection1d", "advection2d", "adjoint2d", "twolevel", "cpu"],
+                    default="batched", help="batched (256 problems) is the benchmark; the others measure further rows")
     ap.add_argument("--no-phase-events", action="store_true",
                     help="skip the second, instrumented timed region (phase table from one solve)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload == "batched":
+            run_reference_batched(args)
+        else:
+            run_reference(args)
     elif args.workload == "advection2d":
         run_2d(args)
     elif args.workload == "batched":

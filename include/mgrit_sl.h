@@ -298,6 +298,27 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
                                  const int* ms, const mgrit_options* opt, void* stream, mgrit_batch** out);
 mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, const double* const* d_u_init,
                                  double* const* d_u_out, mgrit_stats* stats);
+/*
+ * With mgrit_options.profile = 1, stats[q].phase_ms / phase_launches hold problem q's own setup phases
+ * (departure .. factor) and, for the cycle phases, the totals of the batch's launches, which serve every
+ * problem at once (the same figures in every stats[q]); stats[0].kernel_launches counts every kernel of
+ * the batch (the problems' setups, the tuner's timed runs, this call), the other entries 0.
+ *
+ * mgrit_solve_batched_host: the same solve from HOST arrays (end-to-end timing): h_u0[q] [N];
+ * h_u_init_c[q] the initial iterate at the C-points only, [(nt/m_1 + 1) x N] with row j the iterate at
+ * time index j m_1 (row 0 ignored), or NULL (zero) -- the solver reads nothing else of the iterate;
+ * h_u_out[q] [(nt + 1) x N] the full solution.  The call copies in, solves, and copies every solution
+ * back before it returns; device staging comes from the library's pool.
+ */
+mgrit_status mgrit_solve_batched_host(mgrit_batch* b, const double* const* h_u0, const double* const* h_u_init_c,
+                                      double* const* h_u_out, mgrit_stats* stats);
+/*
+ * Sequential SL time stepping of every problem of the batch (eq. (one-step) with g = 0), the comparator
+ * of the batched solve: u_{n+1} = S_{p,r}^{(t_n, dt)} u_n on each problem's fine level, FP32 (the batch's
+ * bulk precision), all problems in one launch (one CTA per problem, slice in shared memory).
+ * d_u0[q] [N] FP64 start slices; d_u_out[q] [N] FP64 final slices.  Returns once done.
+ */
+mgrit_status sl_step_sequential_batched(mgrit_batch* b, const double* const* d_u0, double* const* d_u_out);
 void mgrit_destroy_batched(mgrit_batch* b);
 const char* mgrit_status_string(mgrit_status s);
 const char* mgrit_last_error(void);

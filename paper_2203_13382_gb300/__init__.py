@@ -109,6 +109,9 @@ _SIGNATURES = {
                                            ctypes.POINTER(MgritOptions), _VP, ctypes.POINTER(_VP)]),
     "mgrit_solve_batched": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                            ctypes.POINTER(MgritStats)]),
+    "mgrit_solve_batched_host": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                                ctypes.POINTER(MgritStats)]),
+    "sl_step_sequential_batched": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "mgrit_destroy_batched": (None, [_VP]),
     "mgrit_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mgrit_last_error": (ctypes.c_char_p, []),
@@ -351,6 +354,37 @@ class Batch:
         _check(load_library().mgrit_solve_batched(self._ptr, arr(u0_list), init, arr(out_list), st),
                "mgrit_solve_batched")
         return out_list, [s.as_dict() for s in st]
+
+    def solve_host(self, u0_list, u_init_c_list=None, out_list=None):
+        """End-to-end batched solve from host (numpy float64) arrays: u_init_c_list[q] holds the initial iterate
+        at the C-points only ((nt/m_1 + 1) x nx, row 0 ignored); returns the full solutions (host arrays)."""
+        import numpy as np
+
+        n = len(self.grids)
+        c = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+        u0_list = [c(a) for a in u0_list]
+        if u_init_c_list is not None:
+            u_init_c_list = [c(a) for a in u_init_c_list]
+        if out_list is None:
+            out_list = [np.empty((g.nt + 1, g.nx)) for g in self.grids]
+        vp = lambda al: (_VP * n)(*[a.ctypes.data for a in al])  # noqa: E731
+        st = (MgritStats * n)()
+        init = vp(u_init_c_list) if u_init_c_list is not None else None
+        _check(load_library().mgrit_solve_batched_host(self._ptr, vp(u0_list), init, vp(out_list), st),
+               "mgrit_solve_batched_host")
+        return out_list, [s.as_dict() for s in st]
+
+    def sequential(self, u0_list, out_list=None):
+        """sl_step_sequential_batched: the final slice of every problem by sequential SL stepping (FP32)."""
+        import torch
+
+        n = len(self.grids)
+        if out_list is None:
+            out_list = [torch.empty(g.nx, dtype=torch.float64, device="cuda") for g in self.grids]
+        arr = lambda ts: (_VP * n)(*[_ptr(t) for t in ts])  # noqa: E731
+        _check(load_library().sl_step_sequential_batched(self._ptr, arr(u0_list), arr(out_list)),
+               "sl_step_sequential_batched")
+        return out_list
 
 
 def mgrit_setup_batched(problems: list, stream=None, **options) -> Batch:

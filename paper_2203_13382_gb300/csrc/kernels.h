@@ -201,7 +201,8 @@ cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_a
 cudaError_t launch_sequential_batched(const LevelTables* d_tabs, const SeqArgs* d_args, const BatchTile* d_tiles,
                                       int ntiles, const int* d_active, int is_double, int coarse, int buf,
                                       size_t smem, cudaStream_t st);
-// launch_axpy_convert over many segments in one launch; segments of inactive problems have n = 0.
+// launch_axpy_convert over many segments in one launch (kinds 1, 3, 5 and 0 = copy); segments of
+// inactive problems have n = 0.
 void launch_axpy_batched(int kind, const Segment* d_seg, int nseg, long long maxn, cudaStream_t st);
 // out = sum of seg.x[0 .. n) (doubles, fixed order) written to *(double*)seg.y, one CTA per segment.
 void launch_sum_batched(const Segment* d_seg, int nseg, cudaStream_t st);

@@ -1596,6 +1596,7 @@ __global__ void k_axpy_batched(int kind, const Segment* __restrict__ seg) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < sg.n; i += (long long)gridDim.x * blockDim.x) {
     switch (kind) {
       case 1: ((float*)sg.y)[i] = (float)((const double*)sg.x)[i]; break;
+      case 3: ((double*)sg.y)[i] = (double)((const float*)sg.x)[i]; break;
       case 5: ((double*)sg.y)[i] += ((const double*)sg.x)[i] + (double)((const float*)sg.z)[i]; break;
       default: ((double*)sg.y)[i] = ((const double*)sg.x)[i]; break;
     }

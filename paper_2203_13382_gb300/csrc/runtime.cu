@@ -707,7 +707,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
     return MGRIT_OK;
   };
   if (opt.profile) {
-    h->ev_pool.resize(4096);
+    h->ev_pool.resize(defer ? 64 : 4096);  // a batched problem times only its setup phases
     for (auto& e : h->ev_pool)
       if (cudaEventCreate(&e) != cudaSuccess) return cleanup_fail(fail(MGRIT_ECUDA, "cudaEventCreate failed"));
   }
@@ -1328,8 +1328,12 @@ struct mgrit_batch {
   long long maxn_all = 0;     // largest C-point array of any problem (launch size of the batched axpy)
   cudaGraphExec_t graph = nullptr;  // one cycle, captured on the first solve (use_graph)
   int final_args_off = 0;
+  int64_t setup_launches = 0;       // the problems' setup kernels and the tuner's timed runs
+  int* d_err = nullptr;             // bounded-wait flag of every batched launch (LevelTables.err)
+  std::vector<cudaEvent_t> ev;      // profile = 1: a start / end pair per launch of one cycle
 
   ~mgrit_batch() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (graph) cudaGraphExecDestroy(graph);
     if (h_active) cudaFreeHost(h_active);
     if (h_seg) cudaFreeHost(h_seg);
@@ -1341,6 +1345,7 @@ struct mgrit_batch {
     cudaFree(d_active);
     cudaFree(d_seg);
     cudaFree(d_norms);
+    cudaFree(d_err);
     if (h_norms) cudaFreeHost(h_norms);
   }
 };
@@ -1415,6 +1420,7 @@ mgrit_status tune_tile_order(mgrit_batch* b, const mgrit_grid* grids, const mgri
         for (int sh = 0; sh <= max_shift; ++sh) {
           float bt = 1e30f;
           for (int rep = 0; rep < 3; ++rep) {
+            ++b->setup_launches;
             MG_CUDA(cudaEventRecord(e0, s));
             MG_CUDA(launch_relax_batched(b->d_tabs, b->d_args, b->d_tiles + ph->tile_off, ph->ntiles, b->d_active,
                                          ph->is_double, ph->coarse, ph->buf, ph->smem, ph->threads << sh, s));
@@ -1476,6 +1482,7 @@ mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F 
     RelaxArgs a;
     int ntile = 0;
     if (!per_problem(q, T, a, ntile)) continue;
+    T.err = b->d_err;
     const int ti = (int)b->tabs.size(), ai = (int)b->args.size();
     b->tabs.push_back(T);
     b->args.push_back(a);
@@ -1565,6 +1572,11 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
       return fail(st, err);
     }
   }
+  if (cudaMalloc((void**)&b->d_err, sizeof(int)) != cudaSuccess || cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return fail(MGRIT_ENOMEM, "batched workspace allocation failed");
+  }
   // phases of one cycle
   b->down.push_back(add_relax_phase(b, 1, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
     mgrit_handle* h = b->hs[q];
@@ -1616,6 +1628,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
       if ((int)h->levels.size() - 1 != d) continue;
       Level& L = h->levels[d];
       LevelTables T = h->tables(d, 0);
+      T.err = b->d_err;
       SeqArgs sa{L.nt, L.G, nullptr, L.E, 1};
       const int ti = (int)b->tabs.size(), ai = (int)b->seqs.size();
       b->tabs.push_back(T);
@@ -1676,7 +1689,19 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     delete b;
     return fail(MGRIT_ENOMEM, "batched workspace allocation failed");
   }
-  for (mgrit_handle* h : b->hs) b->maxn_all = std::max(b->maxn_all, (long long)(h->J1() + 1) * h->npts);
+  for (mgrit_handle* h : b->hs) {
+    b->maxn_all = std::max(b->maxn_all, (long long)(h->J1() + 1) * h->npts);
+    b->setup_launches += h->setup_launches;
+  }
+  if (opt.profile) {  // two events per launch of one cycle (phases, batched update, sum) and the final pass
+    b->ev.resize(2 * (b->down.size() + b->up.size() + 3));
+    for (auto& e : b->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(MGRIT_ECUDA, "cudaEventCreate failed");
+      }
+  }
   {
     const mgrit_status st = tune_tile_order(b, grids, waves, orders, ms);
     if (st != MGRIT_OK) {
@@ -1689,53 +1714,102 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
   return MGRIT_OK;
 }
 
-mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, const double* const* d_u_init,
-                                 double* const* d_u_out, mgrit_stats* stats) {
-  if (!b || !d_u0 || !d_u_out) return fail(MGRIT_EINVAL, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+// Timing category (MGRIT_PHASE_*) of a batched phase.
+int batch_phase_index(const mgrit_batch::Phase& ph) {
+  if (ph.kind == 1) return MGRIT_PHASE_COARSEST;
+  if (ph.coarse) return MGRIT_PHASE_COARSE;
+  return ph.is_double ? MGRIT_PHASE_FINE64_RES : MGRIT_PHASE_FINE32_RES;
+}
+
+// The batched MGRIT iteration.  u0[q] / init[q] are device (kind DeviceToDevice) or host
+// (HostToDevice) pointers; init_compact: init[q] holds only the C-point rows j = 1 .. J (row 0 first,
+// ignored), else the full (nt + 1) x N iterate.  d_out[q] are device arrays.
+mgrit_status batched_solve_impl(mgrit_batch* b, const double* const* u0, const double* const* init,
+                                cudaMemcpyKind kind, bool init_compact, double* const* d_out, mgrit_stats* stats) {
   const double t0 = now_ms();
   cudaStream_t s = b->stream;
   const int nprob = (int)b->hs.size();
   for (int q = 0; q < nprob; ++q) {
     mgrit_handle* h = b->hs[q];
     const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
-    MG_CUDA(cudaMemcpyAsync(h->X, d_u0[q], np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (d_u_init && d_u_init[q])
-      MG_CUDA(cudaMemcpy2DAsync(h->X + np, np * sizeof(double), d_u_init[q] + (size_t)m1 * np,
-                                (size_t)m1 * np * sizeof(double), np * sizeof(double), J, cudaMemcpyDeviceToDevice, s));
+    MG_CUDA(cudaMemcpyAsync(h->X, u0[q], np * sizeof(double), kind, s));
+    if (init && init[q] && init_compact)
+      MG_CUDA(cudaMemcpyAsync(h->X + np, init[q] + np, (size_t)J * np * sizeof(double), kind, s));
+    else if (init && init[q])
+      MG_CUDA(cudaMemcpy2DAsync(h->X + np, np * sizeof(double), init[q] + (size_t)m1 * np,
+                                (size_t)m1 * np * sizeof(double), np * sizeof(double), J, kind, s));
     else
       MG_CUDA(cudaMemsetAsync(h->X + np, 0, (size_t)J * np * sizeof(double), s));
     // per-call output pointers of the final post F-relaxation
     RelaxArgs& a = b->args[b->final_args_off + q];
-    a.start_wb = d_u_out[q];
-    a.fstore = d_u_out[q];
+    a.start_wb = d_out[q];
+    a.fstore = d_out[q];
   }
   MG_CUDA(cudaMemcpyAsync(b->d_args + b->final_args_off, b->args.data() + b->final_args_off,
                           nprob * sizeof(RelaxArgs), cudaMemcpyHostToDevice, s));
+  MG_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), s));  // a timeout of an earlier call is not this one's
   std::vector<int> active(nprob, 1), iters(nprob, 0), conv(nprob, 0);
   std::vector<double> r0(nprob, 0.0), rk(nprob, 0.0);
   std::vector<std::vector<double>> hist(nprob);
-  auto run = [&](const mgrit_batch::Phase& ph) -> mgrit_status {
+  const bool prof = !b->ev.empty();
+  double phase_ms[MGRIT_NUM_PHASES] = {};
+  int phase_n[MGRIT_NUM_PHASES] = {};
+  std::vector<int> ev_phase;  // phase of each recorded event pair of the current cycle
+  int64_t launches = 0;
+  auto ev_begin = [&]() -> int {
+    if (!prof || 2 * ev_phase.size() + 2 > b->ev.size()) return -1;
+    const int i = (int)ev_phase.size();
+    cudaEventRecord(b->ev[2 * i], s);
+    return i;
+  };
+  auto ev_end = [&](int i, int phase) {
+    ++launches;
+    ++phase_n[phase];
+    if (i < 0) return;
+    cudaEventRecord(b->ev[2 * i + 1], s);
+    ev_phase.push_back(phase);
+  };
+  auto ev_collect = [&]() {
+    for (size_t i = 0; i < ev_phase.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, b->ev[2 * i], b->ev[2 * i + 1]) == cudaSuccess) phase_ms[ev_phase[i]] += ms;
+    }
+    ev_phase.clear();
+  };
+  auto run = [&](const mgrit_batch::Phase& ph, int phase) -> mgrit_status {
     if (ph.ntiles == 0) return MGRIT_OK;
-    cudaError_t e = ph.kind == 0
-                        ? launch_relax_batched(b->d_tabs, b->d_args, b->d_tiles + ph.tile_off, ph.ntiles, b->d_active,
-                                               ph.is_double, ph.coarse, ph.buf, ph.smem, ph.threads, s)
-                        : launch_sequential_batched(b->d_tabs, b->d_seq, b->d_tiles + ph.tile_off, ph.ntiles,
-                                                    b->d_active, ph.is_double, ph.coarse, ph.buf, ph.smem, s);
-    if (e != cudaSuccess) return fail(MGRIT_ECUDA, std::string("batched phase: ") + cudaGetErrorString(e));
+    const int e = ev_begin();
+    cudaError_t err = ph.kind == 0
+                          ? launch_relax_batched(b->d_tabs, b->d_args, b->d_tiles + ph.tile_off, ph.ntiles, b->d_active,
+                                                 ph.is_double, ph.coarse, ph.buf, ph.smem, ph.threads, s)
+                          : launch_sequential_batched(b->d_tabs, b->d_seq, b->d_tiles + ph.tile_off, ph.ntiles,
+                                                      b->d_active, ph.is_double, ph.coarse, ph.buf, ph.smem, s);
+    ev_end(e, phase);
+    if (err != cudaSuccess) return fail(MGRIT_ECUDA, std::string("batched phase: ") + cudaGetErrorString(err));
     return MGRIT_OK;
   };
   // one cycle of every active problem; the active mask and the segment table are read from device memory
   // (uploaded before each cycle), so the cycle is the same launch sequence every time
   auto cycle = [&]() -> mgrit_status {
-    for (auto& ph : b->down) MG_TRY(run(ph));  // down[0]: FP64 residual of every iterate, e_C = r
-    for (auto& ph : b->up) MG_TRY(run(ph));
+    for (auto& ph : b->down) MG_TRY(run(ph, batch_phase_index(ph)));  // down[0]: FP64 residual, e_C = r
+    for (auto& ph : b->up) MG_TRY(run(ph, MGRIT_PHASE_COARSE));
+    int e = ev_begin();
     launch_axpy_batched(5, b->d_seg + nprob, nprob, b->maxn_all, s);  // u_C += r + E_1
+    ev_end(e, MGRIT_PHASE_MISC);
+    e = ev_begin();
     launch_sum_batched(b->d_seg + 2 * nprob, nprob, s);
+    ev_end(e, MGRIT_PHASE_MISC);
     MG_CUDA(cudaMemcpyAsync(b->h_norms, b->d_norms, nprob * sizeof(double), cudaMemcpyDeviceToHost, s));
     return MGRIT_OK;
   };
-  bool graph_ok = b->opt.use_graph != 0;
+  // CUDA graph of one cycle (not while profiling: the events then surround each launch)
+  bool graph_ok = b->opt.use_graph != 0 && !prof;
   int n_active = nprob;
+  int64_t cycle_launches = 0;
   for (int k = 0; k < b->opt.max_iter && n_active > 0; ++k) {
     for (int q = 0; q < nprob; ++q) {
       mgrit_handle* h = b->hs[q];
@@ -1749,6 +1823,9 @@ mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, cons
     MG_CUDA(cudaMemcpyAsync(b->d_seg, b->h_seg, 3 * (size_t)nprob * sizeof(Segment), cudaMemcpyHostToDevice, s));
     if (graph_ok && !b->graph) {  // capture the cycle once
       cudaGraph_t g = nullptr;
+      const int64_t l0 = launches;
+      int n0[MGRIT_NUM_PHASES];
+      std::memcpy(n0, phase_n, sizeof(n0));
       if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         const mgrit_status st = cycle();
         const cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -1760,11 +1837,24 @@ mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, cons
         if (g) cudaGraphDestroy(g);
       }
       cudaGetLastError();
+      cycle_launches = launches - l0;  // the capture executed nothing
+      launches = l0;
+      std::memcpy(phase_n, n0, sizeof(n0));
       if (!b->graph) graph_ok = false;
     }
-    if (graph_ok) MG_CUDA(cudaGraphLaunch(b->graph, s));
-    else MG_TRY(cycle());
+    if (graph_ok) {
+      MG_CUDA(cudaGraphLaunch(b->graph, s));
+      if (!cycle_launches) {  // captured by an earlier solve: count the launches of one cycle
+        for (auto& ph : b->down) cycle_launches += ph.ntiles ? 1 : 0;
+        for (auto& ph : b->up) cycle_launches += ph.ntiles ? 1 : 0;
+        cycle_launches += 2;
+      }
+      launches += cycle_launches;
+    } else {
+      MG_TRY(cycle());
+    }
     MG_CUDA(cudaStreamSynchronize(s));
+    ev_collect();
     for (int q = 0; q < nprob; ++q) {
       if (!active[q]) continue;
       const double r = std::sqrt(b->h_norms[q]);
@@ -1785,27 +1875,142 @@ mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, cons
   // every problem: post F-relaxation into its output
   for (int q = 0; q < nprob; ++q) b->h_active[q] = 1;
   MG_CUDA(cudaMemcpyAsync(b->d_active, b->h_active, nprob * sizeof(int), cudaMemcpyHostToDevice, s));
-  MG_TRY(run(b->final_post));
+  MG_TRY(run(b->final_post, MGRIT_PHASE_FINE64_POST));
   MG_CUDA(cudaStreamSynchronize(s));
+  ev_collect();
+  int timed_out = 0;
+  MG_CUDA(cudaMemcpy(&timed_out, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   bool all_conv = true;
   for (int q = 0; q < nprob; ++q) {
     all_conv = all_conv && conv[q];
     if (stats) {
       mgrit_stats& st = stats[q];
+      mgrit_handle* h = b->hs[q];
       std::memset(&st, 0, sizeof(st));
       st.iterations = iters[q];
       st.converged = conv[q];
-      st.levels = (int)b->hs[q]->levels.size();
+      st.levels = (int)h->levels.size();
       st.r0 = r0[q];
       st.r_final = rk[q];
       st.history_len = std::min<int>(256, (int)hist[q].size());
       for (int i = 0; i < st.history_len; ++i) st.residual_history[i] = hist[q][i];
-      st.setup_ms = b->hs[q]->setup_ms;
+      st.setup_ms = h->setup_ms;
       st.solve_ms = now_ms() - t0;
-      st.device_bytes = b->hs[q]->bytes;
+      st.device_bytes = h->bytes;
+      // setup phases: this problem's kernels; cycle phases: the batch's launches, which serve every problem
+      st.kernel_launches = q == 0 ? b->setup_launches + launches : 0;
+      for (int i = 0; i < MGRIT_NUM_PHASES; ++i) {
+        const bool setup_phase = i <= MGRIT_PHASE_FACTOR;
+        st.phase_ms[i] = setup_phase ? h->setup_phase_ms[i] : phase_ms[i];
+        st.phase_launches[i] = setup_phase ? h->setup_phase_launches[i] : phase_n[i];
+      }
     }
   }
+  if (timed_out) return fail(MGRIT_ETIMEOUT, "a bounded device wait gave up (TMA staging did not complete)");
   return all_conv ? MGRIT_OK : fail(MGRIT_ENOTCONVERGED, "some problems did not converge");
+}
+
+}  // namespace
+
+extern "C" {
+
+mgrit_status mgrit_solve_batched(mgrit_batch* b, const double* const* d_u0, const double* const* d_u_init,
+                                 double* const* d_u_out, mgrit_stats* stats) {
+  if (!b || !d_u0 || !d_u_out) return fail(MGRIT_EINVAL, "NULL argument");
+  for (size_t q = 0; q < b->hs.size(); ++q)
+    if (!d_u0[q] || !d_u_out[q]) return fail(MGRIT_EINVAL, "NULL problem buffer");
+  return batched_solve_impl(b, d_u0, d_u_init, cudaMemcpyDeviceToDevice, false, d_u_out, stats);
+}
+
+mgrit_status mgrit_solve_batched_host(mgrit_batch* b, const double* const* h_u0, const double* const* h_u_init_c,
+                                      double* const* h_u_out, mgrit_stats* stats) {
+  if (!b || !h_u0 || !h_u_out) return fail(MGRIT_EINVAL, "NULL argument");
+  const int nprob = (int)b->hs.size();
+  size_t total = 0;
+  for (int q = 0; q < nprob; ++q) {
+    if (!h_u0[q] || !h_u_out[q]) return fail(MGRIT_EINVAL, "NULL problem buffer");
+    total += (size_t)(b->hs[q]->grid.nt + 1) * b->hs[q]->npts;
+  }
+  cudaStream_t s = b->stream;
+  double* d = nullptr;
+  MG_CUDA(scratch_alloc((void**)&d, total * sizeof(double), s));
+  std::vector<double*> outs(nprob);
+  size_t off = 0;
+  for (int q = 0; q < nprob; ++q) {
+    outs[q] = d + off;
+    off += (size_t)(b->hs[q]->grid.nt + 1) * b->hs[q]->npts;
+  }
+  mgrit_status st = batched_solve_impl(b, h_u0, h_u_init_c, cudaMemcpyHostToDevice, true, outs.data(), stats);
+  for (int q = 0; q < nprob; ++q)
+    cudaMemcpyAsync(h_u_out[q], outs[q], (size_t)(b->hs[q]->grid.nt + 1) * b->hs[q]->npts * sizeof(double),
+                    cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  MG_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+mgrit_status sl_step_sequential_batched(mgrit_batch* b, const double* const* d_u0, double* const* d_u_out) {
+  if (!b || !d_u0 || !d_u_out) return fail(MGRIT_EINVAL, "NULL argument");
+  const int nprob = (int)b->hs.size();
+  for (int q = 0; q < nprob; ++q)
+    if (!d_u0[q] || !d_u_out[q]) return fail(MGRIT_EINVAL, "NULL problem buffer");
+  cudaStream_t s = b->stream;
+  size_t total = 0;
+  for (mgrit_handle* h : b->hs) total += h->npts;
+  float* f = nullptr;  // FP32 start slices, then the final slices
+  MG_CUDA(scratch_alloc((void**)&f, 2 * total * sizeof(float), s));
+  std::vector<LevelTables> tabs(nprob);
+  std::vector<SeqArgs> args(nprob);
+  std::vector<BatchTile> tiles(nprob);
+  std::vector<Segment> seg(2 * nprob);
+  int buf = 0;
+  size_t region = 0;
+  size_t off = 0;
+  long long maxn = 0;
+  for (int q = 0; q < nprob; ++q) {
+    mgrit_handle* h = b->hs[q];
+    tabs[q] = h->tables(0, 0);
+    tabs[q].solver = nullptr;
+    tabs[q].err = b->d_err;
+    args[q] = SeqArgs{h->grid.nt, nullptr, f + off, f + total + off, 0};
+    tiles[q] = BatchTile{q, q, 0, q};
+    seg[q] = Segment{d_u0[q], f + off, nullptr, h->npts};
+    seg[nprob + q] = Segment{f + total + off, d_u_out[q], nullptr, h->npts};
+    off += h->npts;
+    maxn = std::max(maxn, (long long)h->npts);
+    int bq;
+    size_t smq, rq;
+    relax_smem_need(tabs[q], 0, &bq, &smq, &rq);
+    buf = std::max(buf, bq);
+    region = std::max(region, rq);
+  }
+  // one device block for the per-problem launch records (stream-ordered, freed below)
+  const size_t tb = nprob * sizeof(LevelTables), ab = nprob * sizeof(SeqArgs), ib = nprob * sizeof(BatchTile),
+               sb = 2 * nprob * sizeof(Segment);
+  char* rec = nullptr;
+  MG_CUDA(scratch_alloc((void**)&rec, tb + ab + ib + sb, s));
+  std::vector<char> hrec(tb + ab + ib + sb);
+  std::memcpy(hrec.data(), tabs.data(), tb);
+  std::memcpy(hrec.data() + tb, args.data(), ab);
+  std::memcpy(hrec.data() + tb + ab, tiles.data(), ib);
+  std::memcpy(hrec.data() + tb + ab + ib, seg.data(), sb);
+  MG_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), s));
+  MG_CUDA(cudaMemcpyAsync(rec, hrec.data(), hrec.size(), cudaMemcpyHostToDevice, s));
+  const Segment* d_seg = (const Segment*)(rec + tb + ab + ib);
+  launch_axpy_batched(1, d_seg, nprob, maxn, s);  // FP64 -> FP32 start slices
+  MG_CUDA(launch_sequential_batched((const LevelTables*)rec, (const SeqArgs*)(rec + tb), (const BatchTile*)(rec + tb + ab),
+                                    nprob, nullptr, 0, 0, buf, batched_smem(buf, 0, region), s));
+  launch_axpy_batched(3, d_seg + nprob, nprob, maxn, s);  // FP32 -> FP64 final slices
+  MG_CUDA(cudaGetLastError());
+  // the host record must outlive the copy
+  MG_CUDA(cudaStreamSynchronize(s));
+  cudaFreeAsync(rec, s);
+  cudaFreeAsync(f, s);
+  MG_CUDA(cudaStreamSynchronize(s));
+  int timed_out = 0;
+  MG_CUDA(cudaMemcpy(&timed_out, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (timed_out) return fail(MGRIT_ETIMEOUT, "a bounded device wait gave up (TMA staging did not complete)");
+  return MGRIT_OK;
 }
 
 void mgrit_destroy_batched(mgrit_batch* b) { delete b; }

@@ -56,3 +56,24 @@ def test_phases_without_launches_are_left_out():
     s["phase_launches"]["fine32_res"] = 0
     _, others = bench.roofline(s, WL, 6686.1, "measured", 17, None)
     assert [o["phase"] for o in others] == ["coarse"]
+
+
+def test_batched_bookkeeping_sums_the_problems_over_their_cycles():
+    import workloads as W
+
+    probs = W.batched_problems(4)
+    iters = [3, 5, 2, 4]
+    w = bench.batch_phase_work("fine32_res", probs, iters)
+    want = sum(it * (q.nx * q.nt * 6 + (q.nt // q.m) * q.nx * 8) for q, it in zip(probs, iters))
+    assert w["bytes"] == want and w["fp"] == 32
+    lv = bench.batch_levels(probs[0])
+    # coarsen by m while the level has more than one step and m divides it (1024 / 8: 128, 16, 2)
+    assert lv[0] == probs[0].nt and (lv[-1] <= 1 or lv[-1] % probs[0].m) and all(a == b * probs[0].m for a, b in zip(lv, lv[1:]))
+    ph_ms = {"fine64_res": 40.0, "fine32_res": 10.0, "coarse": 30.0, "coarsest": 5.0, "departure": 20.0}
+    ph_n = {"fine64_res": 5, "fine32_res": 25, "coarse": 100, "coarsest": 5, "departure": 4}
+    dom, others = bench.batch_roofline(ph_ms, ph_n, probs, iters, 6686.1, "measured", None)
+    assert dom["phase"] == "fine64_res" and [o["phase"] for o in others] == ["coarse", "fine32_res", "coarsest"]
+    assert dom["avg_launch_ms"] == pytest.approx(8.0)
+    f32 = [o for o in others if o["phase"] == "fine32_res"][0]
+    assert f32["achieved"] == pytest.approx(want / 10e-3 / 1e9)
+    assert f32["algorithmic_bytes_per_launch"] == pytest.approx(want / 25)
