@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "mgrit_sl.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mgrit_[a-z_]+|sl_step_sequential)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(mgrit_[a-z_]+|sl_step_[a-z_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
