@@ -720,6 +720,18 @@ def run_reference_batched(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def host_mem_available() -> int | None:
+    """MemAvailable of /proc/meminfo in bytes (None if unknown)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
 def run_batched(args) -> None:
     import torch
 
@@ -833,7 +845,11 @@ def run_batched(args) -> None:
                       "mgrit_over_sequential": seq_ms / ms,
                       "fp32_sequential_vs_mgrit_final_slice_max_rel_diff": fixed}
         # end to end through the host-buffer entry point: inputs from pinned host memory, every solution back
+        need = sum((q.nt + 1) * q.nx * 8 for q in probs)
+        avail = host_mem_available()
         try:
+            if avail is not None and avail < 2 * need:
+                raise RuntimeError("not enough host memory to pin the solutions")
             u0_pin = [torch.from_numpy(u).pin_memory() for u in u0_h]
             ic_pin = [torch.from_numpy(ic).pin_memory() for ic in inits_c]
             out_pin = [torch.empty(q.nt + 1, q.nx, dtype=torch.float64, pin_memory=True) for q in probs]
