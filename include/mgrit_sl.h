@@ -115,6 +115,10 @@ typedef struct {
   double diverge_ratio; /* MGRIT_EDIVERGED once a residual norm exceeds this multiple of the first
                        (default 1e3); 0: only a non-finite norm ends the iteration (rediscretised coarse
                        operators can grow the residual for many cycles before converging) */
+  int fine_only;    /* 1D only.  0 (default): the whole MGRIT hierarchy.  1: only what sequential stepping
+                       needs -- the fine departure points and the fine level's gather tables (in the
+                       handle's precision); sl_step_sequential, sl_step_sequential_batched and
+                       mgrit_apply_step at level 0 work, the solves return MGRIT_EUNSUPPORTED. */
   int test_wait_cycles; /* testing the timeout path only; 0 (default): off.  > 0: in every 1D FP32 pass
                        whose tables are staged into shared memory by bulk copies, each CTA's first bounded
                        wait is made on a barrier that nothing completes, with this limit in SM cycles, so
@@ -287,7 +291,9 @@ void mgrit_destroy(mgrit_handle* h);
 /*
  * Batched independent 1D problems (each as in mgrit_setup, levels chosen by the rule of mgrit_setup):
  * grids[q], waves[q], orders[q], ms[q] for q < nprob; the shared options must select the FP32-bulk mode
- * (precision 1) and the corrected coarse operator.  mgrit_solve_batched runs the V-cycles of all problems
+ * (precision 1; precision 0 only with fine_only, for FP64 sequential stepping) and the corrected coarse
+ * operator.  A fine_only batch sets up the fine levels alone (sl_step_sequential_batched; its solves return
+ * MGRIT_EUNSUPPORTED).  mgrit_solve_batched runs the V-cycles of all problems
  * in lockstep with one kernel launch per cycle phase over (problem, interval) tiles; each problem stops
  * when its own residual criterion is met (a per-problem mask).  d_u0[q], d_u_init[q] (or NULL),
  * d_u_out[q] as in mgrit_solve; stats: NULL or an array of nprob.  MGRIT_ENOTCONVERGED if any problem did
@@ -314,8 +320,9 @@ mgrit_status mgrit_solve_batched_host(mgrit_batch* b, const double* const* h_u0,
                                       double* const* h_u_out, mgrit_stats* stats);
 /*
  * Sequential SL time stepping of every problem of the batch (eq. (one-step) with g = 0), the comparator
- * of the batched solve: u_{n+1} = S_{p,r}^{(t_n, dt)} u_n on each problem's fine level, FP32 (the batch's
- * bulk precision), all problems in one launch (one CTA per problem, slice in shared memory).
+ * of the batched solve: u_{n+1} = S_{p,r}^{(t_n, dt)} u_n on each problem's fine level, all problems in one
+ * launch (one CTA per problem, slice in shared memory): FP32 on FP32-bulk batches, FP64 on fine_only batches
+ * set up with precision 0 (mgrit_setup_batched accepts precision 0 only with fine_only).
  * d_u0[q] [N] FP64 start slices; d_u_out[q] [N] FP64 final slices.  Returns once done.
  */
 mgrit_status sl_step_sequential_batched(mgrit_batch* b, const double* const* d_u0, double* const* d_u_out);

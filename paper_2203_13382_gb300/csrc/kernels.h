@@ -27,10 +27,11 @@ void launch_backtrack_2d(const double* sx_prev, const double* sy_prev, const dou
                          int m, int ntc, int nx, int p, double* sx_out, double* sy_out, double* gx_out, double* gy_out,
                          cudaStream_t st);
 
-// Gather tables of one level from its offsets: shift[n][i] = (E - (p+1)/2 - i) mod nx and either the
-// FP64 Lagrange weights w64[n][a][i] (a = 0..p) or the FP32 distance eps32[n][i].
+// Gather tables of one level from its offsets: shift[n][i] = (E - (p+1)/2 - i) mod nx, and any of the
+// FP64 Lagrange weights w64[n][a][i] (a = 0..p), the FP32 distance eps32[n][i] and the rest
+// eps_lo[n][i] = eps - eps32 rounded to FP32 (NULL: not written).
 void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, uint16_t* shift, double* w64,
-                         float* eps32, cudaStream_t st);
+                         float* eps32, float* eps_lo, cudaStream_t st);
 
 // Block-PCR coefficients of the on-the-fly FP32 correction solve (p <= 3): per step, from the FP32 sigma
 // rows [nt][nx], record_floats(nx, p) floats into out [nt][record].
@@ -72,6 +73,10 @@ struct LevelTables {
   const uint16_t* shift;  // [nt][npts] (2D: x then y blocks)
   const double* w64;      // [nt][p+1][npts] or NULL
   const float* eps32;     // [nt][npts] or NULL (2D: x then y blocks)
+  const float* eps_lo;    // level 0 of FP32-bulk handles: eps - eps32 rounded to FP32 ([nt][npts]) or NULL
+  // df = 1: a level-0 FP64 pass of the FP32-bulk cycle, run in FP32 pairs from (eps32, eps_lo) instead of
+  // FP64 weights (df32.cuh); its tables are staged like the FP32 levels' (gather_stage = 1)
+  int df;
   long long table_stride; // elements per step row of shift / eps32 (npts)
   int nt;                 // steps on this level (for 2D block offsets)
   // correction solver (coarse levels, corrected operator); NULL for the plain SL step

@@ -8,6 +8,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "df32.cuh"
 #include "kernels.h"
 #include "solver_layout.cuh"
 
@@ -910,25 +911,25 @@ __device__ __forceinline__ void apply_gather_T(const LevelTables& T, int row, co
   }
 }
 
-// FP32 levels stage each step's tables into shared memory: a double buffer of (eps row, shift row and,
-// for coarse levels factorised on the fly, sigma row), each buffer filled one step ahead by TMA bulk
-// copies that complete on its mbarrier; then, on coarse levels, the exchange area of the solve.
-// Byte offsets from the 128-aligned start of the region: buffer b starts at b * per_buf with eps at
-// +0, shift at +e, sigma at +e+h; the two barriers at `bars`.
+// FP32 levels stage each step's tables into shared memory: a double buffer of (eps row, shift row and a
+// third row: sigma for coarse levels factorised on the fly, eps_lo for the FP32-pair passes), each buffer
+// filled one step ahead by TMA bulk copies that complete on its mbarrier; then, on coarse levels, the
+// exchange area of the solve.  Byte offsets from the 128-aligned start of the region: buffer b starts at
+// b * per_buf with eps at +0, shift at +e, the third row at +e+h; the barriers at `bars`.
 struct StageLayout {
   unsigned e, h, per_buf, cf, bars, xch, total, tx;  // tx: table bytes copied per step
 };
-MGRIT_HD StageLayout stage_layout(int nx, int p, int otf, unsigned cf_floats) {
+MGRIT_HD StageLayout stage_layout(int nx, int p, int otf, unsigned cf_floats, int df = 0) {
   StageLayout o;
   o.e = ((unsigned)nx * 4u + 127u) & ~127u;
   o.h = ((unsigned)nx * 2u + 127u) & ~127u;
-  o.per_buf = o.e + o.h + (otf ? o.e : 0u);
+  o.per_buf = o.e + o.h + ((otf || df) ? o.e : 0u);
   o.cf = 2 * o.per_buf;  // one buffer of block-PCR coefficients (otf levels with stored coefficients)
   o.bars = o.cf + ((cf_floats * 4u + 127u) & ~127u);
   o.xch = o.bars + 128;
   const int B = (p + 1) / 2, P = nx / (B <= 2 ? 16 : 8);  // partitions of the on-the-fly solve
   o.total = o.xch + (otf ? (unsigned)((3 * B * B + B) * P * 4) : 0u);
-  o.tx = (unsigned)nx * (otf ? 10u : 6u);
+  o.tx = (unsigned)nx * ((otf || df) ? 10u : 6u);
   return o;
 }
 
@@ -965,7 +966,7 @@ __device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, co
   s.test_wait = 0;
   if (!T.gather_stage) return s;
   s.test_wait = T.test_wait;
-  s.lay = stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u);
+  s.lay = stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u, T.df);
   s.base = smem + ((used + 127) & ~(size_t)127);
   if (threadIdx.x == 0) {
     mbar_init(s.bar(0), 1);
@@ -987,6 +988,8 @@ __device__ __forceinline__ void stage_issue(const Stage& s, const LevelTables& T
   bulk_copy_g2s(d + s.lay.e, T.shift + (size_t)row * T.table_stride, nx * 2u, s.bar(b));
   if (otf)
     bulk_copy_g2s(d + s.lay.e + s.lay.h, (const float*)T.solver + (size_t)row * T.solver_stride, nx * 4u, s.bar(b));
+  else if (T.df)
+    bulk_copy_g2s(d + s.lay.e + s.lay.h, T.eps_lo + (size_t)row * T.table_stride, nx * 4u, s.bar(b));
 }
 
 // Thread 0: bulk copy of the block-PCR coefficient record of step `row` (completes on bar(2)).
@@ -1265,6 +1268,119 @@ __global__ void __launch_bounds__(slice_threads<P, R, COARSE>(),
   relax_body<P, R, COARSE, TRANS, slice_threads<P, R, COARSE>()>(T, a, blockIdx.x, buf, smem_raw);
 }
 
+// ---- level-0 FP64 passes of the FP32-bulk cycle in FP32 pairs --------------------------------------
+//
+// The exact C-point residual of the FP64 iterate (MODE_RES), and the final post F-relaxation into the
+// FP64 solution (MODE_POST), with the fine SL step of Sec. 2.1 evaluated in FP32 pairs (df32.cuh, about
+// 48 bits): the slice lives in shared memory as (hi, lo) pairs, the tables of a step (eps hi, shift,
+// eps lo) are staged by TMA one step ahead, and the Lagrange weights are formed in registers.  FP64
+// appears only where the interval meets FP64 data: the start slice, the C-point residual, the F-point
+// stores.
+
+// dst[i] = (S_n src)_i for the points of this thread, src with its periodic halo (src[nx + t] = src[t]).
+template <int P, int NT>
+__device__ __forceinline__ void apply_gather_df(const float* __restrict__ eh, const float* __restrict__ el,
+                                                const uint16_t* __restrict__ sh, const float2* __restrict__ src,
+                                                float2* __restrict__ dst, int nx) {
+#pragma unroll 2
+  for (int q = 0; q < kPts; ++q) {
+    const int i = threadIdx.x + q * NT;
+    if (i < nx) {
+      const df32 v = df_interp<P>(df32{eh[i], el[i]}, src + wrap_pow2(i + (int)sh[i], nx));
+      dst[i] = make_float2(v.h, v.l);
+    }
+  }
+}
+
+template <int P, int NT>
+__device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxArgs& a, int j, int buf,
+                                              unsigned char* smem_raw) {
+  float2* src = reinterpret_cast<float2*>(smem_raw);
+  float2* dst = src + buf;
+  double* red = reinterpret_cast<double*>(dst + buf);
+  const int nx = T.nx;
+  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(float2) + 64 * sizeof(double), T, false);
+  stage_prefetch_first<P, false>(stg, T, (j < a.J && a.nsteps > 0) ? j * a.m : -1);
+  {
+    const double* st = a.start ? (const double*)a.start + (size_t)j * a.start_stride : nullptr;
+    const double* co = a.corr ? (const double*)a.corr + (size_t)j * a.corr_stride : nullptr;
+    double* wb = a.start_wb ? (double*)a.start_wb + (size_t)j * a.wb_stride : nullptr;
+    for (int i = threadIdx.x; i < nx; i += NT) {
+      double v = st ? st[i] : 0.0;
+      if (co) v += co[i];
+      const df32 d = df_from_double(v);
+      src[i] = make_float2(d.h, d.l);
+      if (wb) wb[i] = v;
+    }
+  }
+  write_halo(src, nx);
+  __syncthreads();
+  if (j >= a.J) return;  // extra CTA: only the correction of the last C-point
+  double sq = 0.0;
+  for (int k = 0; k < a.nsteps; ++k) {
+    const int n = j * a.m + k;
+    const int next_n = k + 1 < a.nsteps ? n + 1 : -1;
+    if (!stage_acquire(stg, T, n, next_n, false)) return;
+    const int b = stg.cur;
+    apply_gather_df<P, NT>(stg.eps(b), stg.sig(b), stg.sh(b), src, dst, nx);
+    __syncthreads();
+    stg.cur ^= 1;
+    stg.pending = next_n;
+    const bool last = (k == a.m - 1);
+    if (!last) {
+      if (a.fstore) {  // F-point of the FP64 solution
+        double* fs = (double*)a.fstore + (size_t)(n + 1) * nx;
+        for (int i = threadIdx.x; i < nx; i += NT) {
+          const float2 v = dst[i];
+          fs[i] = df_to_double(df32{v.x, v.y});
+        }
+      }
+    } else if (a.mode == MODE_FC) {
+      double* co = (double*)a.cout + (size_t)(j + 1) * a.c_stride;
+      for (int i = threadIdx.x; i < nx; i += NT) {
+        const float2 v = dst[i];
+        co[i] = df_to_double(df32{v.x, v.y});
+      }
+    } else {  // MODE_RES: r = S^m u_C(j) - u_C(j+1), in FP64 from the pair
+      const double* ci = a.cin ? (const double*)a.cin + (size_t)(j + 1) * a.c_stride : nullptr;
+      const double* cc = a.cin_corr ? (const double*)a.cin_corr + (size_t)(j + 1) * a.corr_stride : nullptr;
+      double* ro = a.rout ? (double*)a.rout + (size_t)(j + 1) * a.r_stride : nullptr;
+      float* ro32 = a.rout32 ? a.rout32 + (size_t)(j + 1) * a.r_stride : nullptr;
+      for (int i = threadIdx.x; i < nx; i += NT) {
+        const float2 d = dst[i];
+        double v = df_to_double(df32{d.x, d.y});
+        if (cc) v -= (ci ? ci[i] : 0.0) + cc[i];
+        else if (ci) v -= ci[i];
+        if (ro) ro[i] = v;
+        if (ro32) ro32[i] = (float)v;
+        if (a.norm_partial) sq += v * v;
+      }
+    }
+    bool ahead_ok = true;
+    if (k + 1 < a.nsteps) {
+      write_halo(dst, nx);
+      ahead_ok = stage_wait_ahead(stg);
+    }
+    if (__syncthreads_or(!ahead_ok)) {
+      stage_abandon(stg, T, false);
+      return;
+    }
+    float2* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (a.mode == MODE_RES && a.norm_partial) {
+    const double tot = block_sum(sq, red);
+    if (threadIdx.x == 0) a.norm_partial[j] = tot;
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kSliceThreads, 1) k_relax_df_1d(LevelTables T, RelaxArgs a, int buf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  relax_body_df<P, kSliceThreads>(T, a, blockIdx.x, buf, smem_raw);
+}
+
 // u0: [nx] start slice; out: store_all ? [(N+1)][nx] (row 0 = u0) : [nx] (the final slice).
 template <int P, typename R, bool COARSE, bool TRANS, int NT>
 __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, const R* g, const R* u0, R* out_all,
@@ -1338,6 +1454,22 @@ __global__ void __launch_bounds__(NT, (COARSE ? 1 : (std::is_same<R, float>::val
   }
 }
 
+// The FP32-pair level-0 passes of every problem of a batch (one tile per interval).
+__global__ void __launch_bounds__(kSliceThreads, 1)
+    k_relax_batched_df(const LevelTables* __restrict__ tabs, const RelaxArgs* __restrict__ args,
+                       const BatchTile* __restrict__ tiles, const int* __restrict__ active, int buf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BatchTile t = tiles[blockIdx.x];
+  if (active && !active[t.problem]) return;
+  const LevelTables T = tabs[t.table];
+  const RelaxArgs a = args[t.args];
+  switch (T.p) {
+    case 1: relax_body_df<1, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
+    case 3: relax_body_df<3, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
+    default: relax_body_df<5, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
+  }
+}
+
 template <typename R, bool COARSE>
 __global__ void __launch_bounds__(kSliceThreads, 1) k_sequential_batched(const LevelTables* __restrict__ tabs,
                                                                          const SeqArgs* __restrict__ args,
@@ -1387,7 +1519,7 @@ size_t smem_bytes(int buf, const LevelTables& T, bool coarse) {
   size_t b = 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double);
   if (T.gather_stage)
     b = ((b + 127) & ~(size_t)127) +
-        stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u).total;
+        stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u, T.df).total;
   return b;
 }
 
@@ -1409,6 +1541,25 @@ cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_
   if (T.p == 3) MGRIT_LAUNCH_RELAX(3)
   MGRIT_LAUNCH_RELAX(5)
 #undef MGRIT_LAUNCH_RELAX
+}
+
+cudaError_t relax_df_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_t st) {
+  const int buf = buffer_elems(T, false);
+  const size_t sm = smem_bytes<float2>(buf, T, false);
+  const int grid = a.J + (a.extra_cta ? 1 : 0);
+  if (grid <= 0) return cudaSuccess;
+#define MGRIT_LAUNCH_DF(PP)                                                                                \
+  {                                                                                                        \
+    cudaError_t e = cudaFuncSetAttribute(k_relax_df_1d<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                         (int)sm);                                                         \
+    if (e != cudaSuccess) return e;                                                                        \
+    k_relax_df_1d<PP><<<grid, kSliceThreads, sm, st>>>(T, a, buf);                                         \
+    return cudaGetLastError();                                                                             \
+  }
+  if (T.p == 1) MGRIT_LAUNCH_DF(1)
+  if (T.p == 3) MGRIT_LAUNCH_DF(3)
+  MGRIT_LAUNCH_DF(5)
+#undef MGRIT_LAUNCH_DF
 }
 
 template <typename R, bool COARSE, bool TR>
@@ -1518,6 +1669,10 @@ __global__ void k_axpy_convert(int kind, const void* __restrict__ x, void* __res
 
 cudaError_t launch_relax_1d(const LevelTables& T, const RelaxArgs& a, int is_double, cudaStream_t st) {
   const bool coarse = T.solver != nullptr;
+  if (T.df) {  // level-0 FP64 pass of an FP32-bulk handle: FP32 pairs
+    if (!is_double || coarse || T.trans || !T.eps_lo) return cudaErrorInvalidValue;
+    return relax_df_dispatch(T, a, st);
+  }
   if (T.trans) {
     if (!is_double) return cudaErrorInvalidValue;
     return coarse ? relax_dispatch<double, true, true>(T, a, st) : relax_dispatch<double, false, true>(T, a, st);
@@ -1620,7 +1775,7 @@ void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem
   *buf = b;
   *smem = is_double ? smem_bytes<double>(b, T, coarse) : smem_bytes<float>(b, T, coarse);
   *region = T.gather_stage
-                ? stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u).total
+                ? stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u, T.df).total
                 : 0;
 }
 
@@ -1654,6 +1809,14 @@ cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_a
                                  int ntiles, const int* d_active, int is_double, int coarse, int buf, size_t smem,
                                  int threads, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
+  if (is_double == 2) {  // FP32-pair level-0 passes
+    if (coarse) return cudaErrorInvalidValue;
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_relax_batched_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_relax_batched_df<<<ntiles, kSliceThreads, smem, st>>>(d_tabs, d_args, d_tiles, d_active, buf);
+    return cudaGetLastError();
+  }
   if (is_double) {
     if (coarse) return launch_batched_nt<double, true, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
     return launch_batched_nt<double, false, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);

@@ -46,6 +46,7 @@ struct Level {
   uint16_t* shift = nullptr;
   double* w64 = nullptr;
   float* eps32 = nullptr;
+  float* eps_lo = nullptr;  // level 0 of 1D FP32-bulk handles: the FP32 pairs of its FP64 passes
   void* solver = nullptr;   // stored factorisation (FP64 coarse levels)
   float* sig32 = nullptr;   // sigma as FP32 rows (FP32 coarse levels, factorised on the fly)
   float* pcr32 = nullptr;   // FP32 coarse levels, p <= 3: block-PCR coefficients of every step
@@ -261,6 +262,8 @@ struct mgrit_handle {
     T.shift = L.shift;
     T.w64 = L.w64;
     T.eps32 = L.eps32;
+    T.eps_lo = L.eps_lo;
+    T.df = 0;
     T.table_stride = npts;
     T.nt = L.nt;
     // 2D: sigma for the GMRES correction solves, FP32 copy on FP32 levels
@@ -285,6 +288,11 @@ struct mgrit_handle {
       T.trans = 1;
       T.reverse = 1;
       if (T.solver && grid.dim == 1) T.solver = L.solverT;  // 2D: GMRES with M^T on the same sigma
+      return T;
+    }
+    if (l == 0 && is_double && L.eps_lo) {  // the FP64 passes of level 0 in FP32 pairs (staged tables)
+      T.df = 1;
+      T.gather_stage = 1;
       return T;
     }
     if (grid.dim == 1 && !is_double) {
@@ -540,6 +548,7 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->relax = 0;
   opt->cluster_coarse = 1;
   opt->diverge_ratio = 1e3;
+  opt->fine_only = 0;
   opt->test_wait_cycles = 0;
   return MGRIT_OK;
 }
@@ -598,6 +607,8 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
     return fail(MGRIT_EINVAL, "cluster_coarse must be 0, 1, 2, 4, 8 or 16");
   if (!(opt.diverge_ratio >= 0.0)) return fail(MGRIT_EINVAL, "diverge_ratio must be >= 0");
   if (opt.test_wait_cycles < 0) return fail(MGRIT_EINVAL, "test_wait_cycles must be >= 0");
+  if (opt.fine_only != 0 && opt.fine_only != 1) return fail(MGRIT_EINVAL, "fine_only must be 0 or 1");
+  if (opt.fine_only && grid->dim != 1) return fail(MGRIT_EUNSUPPORTED, "fine_only handles are 1D");
   if (levels < 0 || levels == 1) return fail(MGRIT_EINVAL, "levels must be 0 or >= 2");
   std::vector<int> fac = factors(grid->nt, m, opt.m_first, levels, opt.max_coarsest);
   if (fac.empty()) return fail(MGRIT_EINVAL, "nt does not allow a coarse level with this m");
@@ -627,8 +638,9 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
     delete h;
     return s;
   };
-  // levels
-  h->levels.resize(fac.size() + 1);
+  // levels (fine_only: the fine level alone)
+  const bool fine_only = opt.fine_only != 0;
+  h->levels.resize(fine_only ? 1 : fac.size() + 1);
   h->levels[0].nt = grid->nt;
   for (size_t l = 1; l < h->levels.size(); ++l) {
     h->levels[l].m = fac[l - 1];
@@ -642,10 +654,14 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
     L.is_double = (fp32 && !(cf64 && l > 0)) ? 0 : 1;
     if ((st = h->alloc(&L.s64, rows)) != MGRIT_OK) return cleanup_fail(st);
     if ((st = h->alloc(&L.shift, rows)) != MGRIT_OK) return cleanup_fail(st);
-    const bool need64 = L.is_double || l == 0;  // FP64 levels read precomputed weights (2D: per axis)
+    // FP64 levels read precomputed weights (2D: per axis); level 0 of a 1D FP32-bulk handle runs its FP64
+    // passes in FP32 pairs from eps32 and eps_lo instead
+    const bool pairs = l == 0 && fp32 && dim == 1 && !fine_only;
+    const bool need64 = L.is_double || (l == 0 && !pairs);
     const bool need32 = !L.is_double;
     if (need64 && (st = h->alloc(&L.w64, rows * (p + 1))) != MGRIT_OK) return cleanup_fail(st);
     if (need32 && (st = h->alloc(&L.eps32, rows)) != MGRIT_OK) return cleanup_fail(st);
+    if (pairs && (st = h->alloc(&L.eps_lo, rows)) != MGRIT_OK) return cleanup_fail(st);
     if (l > 0) {
       if ((st = h->alloc(&L.sigma, rows)) != MGRIT_OK) return cleanup_fail(st);
       const size_t full = (size_t)(L.nt + 1) * np;
@@ -671,7 +687,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
       }
     }
   }
-  const int J1 = h->J1();
+  const int J1 = fine_only ? 1 : h->J1();
   if (dim == 2) {  // work buffers of the 2D passes
     size_t jmax = (size_t)J1, jc = 1;
     for (size_t l = 1; l + 1 < h->levels.size(); ++l)
@@ -744,7 +760,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
       for (int c = 0; c < dim; ++c)
         launch_build_tables(L.s64 + c * blk, L.nt, nx, np, p, L.shift + c * blk,
                             L.w64 ? L.w64 + (size_t)c * blk * (p + 1) : nullptr, L.eps32 ? L.eps32 + c * blk : nullptr,
-                            s);
+                            L.eps_lo ? L.eps_lo + c * blk : nullptr, s);
       h->phase_end(MGRIT_PHASE_TABLES, ev, dim);
     }
     if (l > 0 && L.solver) {
@@ -794,6 +810,7 @@ namespace {
 mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_kind, const double* d_u_init,
                         cudaMemcpyKind init_kind, double* d_u_out, mgrit_stats* stats,
                         const double* d_final_ref = nullptr, double final_tol = 0.0) {
+  if (h->levels.size() < 2) return fail(MGRIT_EUNSUPPORTED, "a fine_only handle has no MGRIT hierarchy");
   const double t0 = now_ms();
   cudaStream_t s = h->stream;
   const int np = h->npts;
@@ -1048,7 +1065,7 @@ mgrit_status sl_step_sequential(mgrit_handle* h, const double* d_u0, double* d_u
   const double t0 = now_ms();
   const int np = h->npts, nt = h->grid.nt;
   cudaStream_t s = h->stream;
-  LevelTables T = h->tables(0, 1);
+  LevelTables T = h->tables(0, h->opt.precision == 0 ? 1 : 0);  // the tables of the stepping precision
   T.solver = nullptr;
   h->reset_call_counters();
   const int ev = h->phase_begin();
@@ -1140,6 +1157,7 @@ mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, cons
   if (!h || !d_u_target || !d_C_checkpoints || !d_dJ_du0 || !d_dJ_dparams)
     return fail(MGRIT_EINVAL, "NULL argument");
   if (h->opt.precision != 0) return fail(MGRIT_EUNSUPPORTED, "the adjoint solve needs an FP64 handle (precision 0)");
+  if (h->levels.size() < 2) return fail(MGRIT_EUNSUPPORTED, "a fine_only handle has no MGRIT hierarchy");
   MG_TRY(ensure_adjoint(h));
   cudaStream_t s = h->stream;
   const int np = h->npts, nt = h->grid.nt, m1 = h->levels[1].m, J = h->J1();
@@ -1524,7 +1542,8 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
   mgrit_options opt;
   if (opt_in) opt = *opt_in;
   else mgrit_default_options(&opt);
-  if (opt.precision != 1) return fail(MGRIT_EUNSUPPORTED, "batched solves run the FP32-bulk mode (precision 1)");
+  if (opt.precision != 1 && !(opt.fine_only && opt.precision == 0))
+    return fail(MGRIT_EUNSUPPORTED, "batched solves run the FP32-bulk mode (precision 1)");
   if (opt.relax != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves run FCF relaxation (relax 0)");
   if (opt.coarse_fp64 != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves run FP32 coarse levels (coarse_fp64 0)");
   if (opt.coarse_op != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves use the corrected coarse operator");
@@ -1577,8 +1596,12 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     delete b;
     return fail(MGRIT_ENOMEM, "batched workspace allocation failed");
   }
-  // phases of one cycle
-  b->down.push_back(add_relax_phase(b, 1, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+  if (opt.fine_only) {  // sequential stepping only: no cycle phases
+    *out = b;
+    return MGRIT_OK;
+  }
+  // phases of one cycle (the level-0 FP64 passes in FP32 pairs: is_double = 2)
+  b->down.push_back(add_relax_phase(b, 2, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
     mgrit_handle* h = b->hs[q];
     const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
     T = h->tables(0, 1);
@@ -1660,7 +1683,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
       return true;
     }, b->up);
   b->final_args_off = (int)b->args.size();
-  b->final_post = add_relax_phase(b, 1, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+  b->final_post = add_relax_phase(b, 2, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
     mgrit_handle* h = b->hs[q];
     const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
     T = h->tables(0, 1);
@@ -1730,6 +1753,7 @@ int batch_phase_index(const mgrit_batch::Phase& ph) {
 // ignored), else the full (nt + 1) x N iterate.  d_out[q] are device arrays.
 mgrit_status batched_solve_impl(mgrit_batch* b, const double* const* u0, const double* const* init,
                                 cudaMemcpyKind kind, bool init_compact, double* const* d_out, mgrit_stats* stats) {
+  if (b->opt.fine_only) return fail(MGRIT_EUNSUPPORTED, "a fine_only batch has no MGRIT hierarchy");
   const double t0 = now_ms();
   cudaStream_t s = b->stream;
   const int nprob = (int)b->hs.size();
@@ -1955,10 +1979,11 @@ mgrit_status sl_step_sequential_batched(mgrit_batch* b, const double* const* d_u
   for (int q = 0; q < nprob; ++q)
     if (!d_u0[q] || !d_u_out[q]) return fail(MGRIT_EINVAL, "NULL problem buffer");
   cudaStream_t s = b->stream;
+  const int dbl = b->opt.precision == 0;  // FP64 (fine_only batches of precision 0) or FP32 stepping
   size_t total = 0;
   for (mgrit_handle* h : b->hs) total += h->npts;
-  float* f = nullptr;  // FP32 start slices, then the final slices
-  MG_CUDA(scratch_alloc((void**)&f, 2 * total * sizeof(float), s));
+  float* f = nullptr;  // FP32 stepping: the start slices, then the final slices
+  if (!dbl) MG_CUDA(scratch_alloc((void**)&f, 2 * total * sizeof(float), s));
   std::vector<LevelTables> tabs(nprob);
   std::vector<SeqArgs> args(nprob);
   std::vector<BatchTile> tiles(nprob);
@@ -1969,18 +1994,19 @@ mgrit_status sl_step_sequential_batched(mgrit_batch* b, const double* const* d_u
   long long maxn = 0;
   for (int q = 0; q < nprob; ++q) {
     mgrit_handle* h = b->hs[q];
-    tabs[q] = h->tables(0, 0);
+    tabs[q] = h->tables(0, dbl);
     tabs[q].solver = nullptr;
     tabs[q].err = b->d_err;
-    args[q] = SeqArgs{h->grid.nt, nullptr, f + off, f + total + off, 0};
+    if (dbl) args[q] = SeqArgs{h->grid.nt, nullptr, d_u0[q], d_u_out[q], 0};
+    else args[q] = SeqArgs{h->grid.nt, nullptr, f + off, f + total + off, 0};
     tiles[q] = BatchTile{q, q, 0, q};
-    seg[q] = Segment{d_u0[q], f + off, nullptr, h->npts};
-    seg[nprob + q] = Segment{f + total + off, d_u_out[q], nullptr, h->npts};
+    seg[q] = Segment{d_u0[q], f ? f + off : nullptr, nullptr, h->npts};
+    seg[nprob + q] = Segment{f ? f + total + off : nullptr, d_u_out[q], nullptr, h->npts};
     off += h->npts;
     maxn = std::max(maxn, (long long)h->npts);
     int bq;
     size_t smq, rq;
-    relax_smem_need(tabs[q], 0, &bq, &smq, &rq);
+    relax_smem_need(tabs[q], dbl, &bq, &smq, &rq);
     buf = std::max(buf, bq);
     region = std::max(region, rq);
   }
@@ -1997,15 +2023,15 @@ mgrit_status sl_step_sequential_batched(mgrit_batch* b, const double* const* d_u
   MG_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), s));
   MG_CUDA(cudaMemcpyAsync(rec, hrec.data(), hrec.size(), cudaMemcpyHostToDevice, s));
   const Segment* d_seg = (const Segment*)(rec + tb + ab + ib);
-  launch_axpy_batched(1, d_seg, nprob, maxn, s);  // FP64 -> FP32 start slices
+  if (!dbl) launch_axpy_batched(1, d_seg, nprob, maxn, s);  // FP64 -> FP32 start slices
   MG_CUDA(launch_sequential_batched((const LevelTables*)rec, (const SeqArgs*)(rec + tb), (const BatchTile*)(rec + tb + ab),
-                                    nprob, nullptr, 0, 0, buf, batched_smem(buf, 0, region), s));
-  launch_axpy_batched(3, d_seg + nprob, nprob, maxn, s);  // FP32 -> FP64 final slices
+                                    nprob, nullptr, dbl, 0, buf, batched_smem(buf, dbl, region), s));
+  if (!dbl) launch_axpy_batched(3, d_seg + nprob, nprob, maxn, s);  // FP32 -> FP64 final slices
   MG_CUDA(cudaGetLastError());
   // the host record must outlive the copy
   MG_CUDA(cudaStreamSynchronize(s));
   cudaFreeAsync(rec, s);
-  cudaFreeAsync(f, s);
+  if (f) cudaFreeAsync(f, s);
   MG_CUDA(cudaStreamSynchronize(s));
   int timed_out = 0;
   MG_CUDA(cudaMemcpy(&timed_out, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -545,7 +545,7 @@ void launch_backtrack_2d(const double* sx_prev, const double* sy_prev, const dou
 // One step row (blockIdx.y) of one level: shift, and the FP64 weights and / or the FP32 distance.
 template <int P>
 __global__ void k_build_tables(const double* __restrict__ s, int nx, int npts_row, uint16_t* __restrict__ shift,
-                               double* __restrict__ w64, float* __restrict__ eps32) {
+                               double* __restrict__ w64, float* __restrict__ eps32, float* __restrict__ eps_lo) {
   const int pt = blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= npts_row) return;
   const size_t row = blockIdx.y, idx = row * npts_row + pt;
@@ -561,6 +561,7 @@ __global__ void k_build_tables(const double* __restrict__ s, int nx, int npts_ro
   const int fli = (int)fl;
   shift[idx] = (uint16_t)((-fli - L) & (nx - 1));
   if (eps32) eps32[idx] = (float)eps;
+  if (eps_lo) eps_lo[idx] = (float)(eps - (double)(float)eps);
   if (w64) {
     double w[P + 1];
     lagrange_weights<P, double>(eps, w);
@@ -570,7 +571,7 @@ __global__ void k_build_tables(const double* __restrict__ s, int nx, int npts_ro
 }
 
 void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, uint16_t* shift, double* w64,
-                         float* eps32, cudaStream_t st) {
+                         float* eps32, float* eps_lo, cudaStream_t st) {
   const int bs = 256;
   // rows in chunks of 65535 (grid y limit)
   for (int r0 = 0; r0 < nt; r0 += 65535) {
@@ -579,9 +580,10 @@ void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, u
     dim3 g((unsigned)((npts_row + bs - 1) / bs), (unsigned)rows);
     double* w = w64 ? w64 + o * (p + 1) : nullptr;
     float* e = eps32 ? eps32 + o : nullptr;
-    if (p == 1) k_build_tables<1><<<g, bs, 0, st>>>(s + o, nx, npts_row, shift + o, w, e);
-    else if (p == 3) k_build_tables<3><<<g, bs, 0, st>>>(s + o, nx, npts_row, shift + o, w, e);
-    else k_build_tables<5><<<g, bs, 0, st>>>(s + o, nx, npts_row, shift + o, w, e);
+    float* el = eps_lo ? eps_lo + o : nullptr;
+    if (p == 1) k_build_tables<1><<<g, bs, 0, st>>>(s + o, nx, npts_row, shift + o, w, e, el);
+    else if (p == 3) k_build_tables<3><<<g, bs, 0, st>>>(s + o, nx, npts_row, shift + o, w, e, el);
+    else k_build_tables<5><<<g, bs, 0, st>>>(s + o, nx, npts_row, shift + o, w, e, el);
   }
 }
 
