@@ -1454,8 +1454,10 @@ __global__ void __launch_bounds__(NT, (COARSE ? 1 : (std::is_same<R, float>::val
   }
 }
 
-// The FP32-pair level-0 passes of every problem of a batch (one tile per interval).
-__global__ void __launch_bounds__(kSliceThreads, 1)
+// The FP32-pair level-0 passes of every problem of a batch (one tile per interval), NT threads a CTA
+// (slices of at most kPts * NT points), as the FP32 batched passes.
+template <int NT>
+__global__ void __launch_bounds__(NT, kSliceThreads / NT)
     k_relax_batched_df(const LevelTables* __restrict__ tabs, const RelaxArgs* __restrict__ args,
                        const BatchTile* __restrict__ tiles, const int* __restrict__ active, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1464,9 +1466,9 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
   const LevelTables T = tabs[t.table];
   const RelaxArgs a = args[t.args];
   switch (T.p) {
-    case 1: relax_body_df<1, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
-    case 3: relax_body_df<3, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
-    default: relax_body_df<5, kSliceThreads>(T, a, t.j, buf, smem_raw); break;
+    case 1: relax_body_df<1, NT>(T, a, t.j, buf, smem_raw); break;
+    case 3: relax_body_df<3, NT>(T, a, t.j, buf, smem_raw); break;
+    default: relax_body_df<5, NT>(T, a, t.j, buf, smem_raw); break;
   }
 }
 
@@ -1791,6 +1793,16 @@ cudaError_t launch_batched_nt(const LevelTables* d_tabs, const RelaxArgs* d_args
   return cudaGetLastError();
 }
 
+template <int NT>
+cudaError_t launch_batched_df(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles, int ntiles,
+                              const int* d_active, int buf, size_t smem, cudaStream_t st) {
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_relax_batched_df<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_relax_batched_df<NT><<<ntiles, NT, smem, st>>>(d_tabs, d_args, d_tiles, d_active, buf);
+  return cudaGetLastError();
+}
+
 template <bool CC>
 cudaError_t launch_batched_f32(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles, int ntiles,
                                const int* d_active, int buf, size_t smem, int threads, cudaStream_t st) {
@@ -1811,11 +1823,13 @@ cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_a
   if (ntiles <= 0) return cudaSuccess;
   if (is_double == 2) {  // FP32-pair level-0 passes
     if (coarse) return cudaErrorInvalidValue;
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_relax_batched_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_relax_batched_df<<<ntiles, kSliceThreads, smem, st>>>(d_tabs, d_args, d_tiles, d_active, buf);
-    return cudaGetLastError();
+    switch (threads) {
+      case 32: return launch_batched_df<32>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+      case 64: return launch_batched_df<64>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+      case 128: return launch_batched_df<128>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+      case 256: return launch_batched_df<256>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+      default: return launch_batched_df<kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+    }
   }
   if (is_double) {
     if (coarse) return launch_batched_nt<double, true, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);

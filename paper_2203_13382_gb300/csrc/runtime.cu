@@ -1328,7 +1328,8 @@ struct mgrit_batch {
     int threads;    // CTA size of an FP32 relaxation phase (its tiles' slices hold at most 8 * threads points)
   };
   std::vector<Phase> down, up;
-  Phase final_post{};
+  std::vector<Phase> final_post;  // the post F-relaxation into the outputs, one launch per CTA size
+  std::vector<int> final_args;     // per problem: its RelaxArgs of the final post F-relaxation
   std::vector<BatchTile> tiles;
   std::vector<LevelTables> tabs;
   std::vector<RelaxArgs> args;
@@ -1428,7 +1429,7 @@ mgrit_status tune_tile_order(mgrit_batch* b, const mgrit_grid* grids, const mgri
       const std::vector<BatchTile> built(b->tiles.begin() + ph->tile_off, b->tiles.begin() + ph->tile_off + ph->ntiles);
       const std::vector<BatchTile> sorted = longest_first(*ph);
       // candidates: tile order x CTA size (FP32 phases: the class size and up to two doublings, <= 512)
-      const int max_shift = ph->is_double ? 0 : (ph->threads <= 128 ? 2 : (ph->threads <= 256 ? 1 : 0));
+      const int max_shift = ph->is_double == 1 ? 0 : (ph->threads <= 128 ? 2 : (ph->threads <= 256 ? 1 : 0));
       float best_t = 1e30f;
       int best_code = 0;
       for (int c = 0; c < 2; ++c) {
@@ -1517,11 +1518,11 @@ mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F 
   return ph;
 }
 
-// The phases of one relaxation pass: FP64 passes in one launch of 512-thread CTAs, FP32 passes in one
-// launch per CTA size (cta_threads), each over the problems of that size.
+// The phases of one relaxation pass: FP64 passes in one launch of 512-thread CTAs, FP32 and FP32-pair
+// (is_double = 2) passes in one launch per CTA size (cta_threads), each over the problems of that size.
 template <class F>
 void add_relax_phases(mgrit_batch* b, int is_double, int coarse, F per_problem, std::vector<mgrit_batch::Phase>& list) {
-  if (is_double) {
+  if (is_double == 1) {
     list.push_back(add_relax_phase(b, is_double, coarse, per_problem));
     return;
   }
@@ -1601,7 +1602,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     return MGRIT_OK;
   }
   // phases of one cycle (the level-0 FP64 passes in FP32 pairs: is_double = 2)
-  b->down.push_back(add_relax_phase(b, 2, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+  add_relax_phases(b, 2, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
     mgrit_handle* h = b->hs[q];
     const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
     T = h->tables(0, 1);
@@ -1611,7 +1612,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     a.rout32 = h->EC;  // e_C = r in FP32
     nt = J;
     return true;
-  }));
+  }, b->down);
   add_relax_phases(b, 0, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
     mgrit_handle* h = b->hs[q];
     const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
@@ -1683,7 +1684,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
       return true;
     }, b->up);
   b->final_args_off = (int)b->args.size();
-  b->final_post = add_relax_phase(b, 2, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
+  add_relax_phases(b, 2, 0, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {
     mgrit_handle* h = b->hs[q];
     const int np = h->npts, m1 = h->levels[1].m, J = h->J1();
     T = h->tables(0, 1);
@@ -1692,7 +1693,10 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     a.wb_stride = (long long)m1 * np; a.extra_cta = 1;  // start_wb / fstore set per call
     nt = J + 1;
     return true;
-  });
+  }, b->final_post);
+  b->final_args.assign(b->hs.size(), -1);
+  for (const auto& ph : b->final_post)
+    for (int t = 0; t < ph.ntiles; ++t) b->final_args[b->tiles[ph.tile_off + t].problem] = b->tiles[ph.tile_off + t].args;
   auto up = [&](void** d, const void* h, size_t bytes) -> bool {
     if (bytes == 0) return true;
     if (cudaMalloc(d, bytes) != cudaSuccess) return false;
@@ -1717,7 +1721,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     b->setup_launches += h->setup_launches;
   }
   if (opt.profile) {  // two events per launch of one cycle (phases, batched update, sum) and the final pass
-    b->ev.resize(2 * (b->down.size() + b->up.size() + 3));
+    b->ev.resize(2 * (b->down.size() + b->up.size() + b->final_post.size() + 2));
     for (auto& e : b->ev)
       if (cudaEventCreate(&e) != cudaSuccess) {
         cudaGetLastError();
@@ -1769,7 +1773,7 @@ mgrit_status batched_solve_impl(mgrit_batch* b, const double* const* u0, const d
     else
       MG_CUDA(cudaMemsetAsync(h->X + np, 0, (size_t)J * np * sizeof(double), s));
     // per-call output pointers of the final post F-relaxation
-    RelaxArgs& a = b->args[b->final_args_off + q];
+    RelaxArgs& a = b->args[b->final_args[q]];
     a.start_wb = d_out[q];
     a.fstore = d_out[q];
   }
@@ -1899,7 +1903,7 @@ mgrit_status batched_solve_impl(mgrit_batch* b, const double* const* u0, const d
   // every problem: post F-relaxation into its output
   for (int q = 0; q < nprob; ++q) b->h_active[q] = 1;
   MG_CUDA(cudaMemcpyAsync(b->d_active, b->h_active, nprob * sizeof(int), cudaMemcpyHostToDevice, s));
-  MG_TRY(run(b->final_post, MGRIT_PHASE_FINE64_POST));
+  for (auto& ph : b->final_post) MG_TRY(run(ph, MGRIT_PHASE_FINE64_POST));
   MG_CUDA(cudaStreamSynchronize(s));
   ev_collect();
   int timed_out = 0;
