@@ -101,7 +101,8 @@ typedef struct {
   int gmres_maxit;  /* 2D coarse correction solves: GMRES from a zero guess with at most this many
                        iterations (default 10, at most 10) ... */
   double gmres_rtol;/* ... stopped at this relative residual (default 1e-2): the paper's setting for
-                       multilevel and 2D runs (Sec. 3.4, 4.3).  1D correction solves are exact. */
+                       multilevel and 2D runs (Sec. 3.4, 4.3).  1D correction solves are exact unless
+                       solve_mode = 1. */
   int relax;        /* 0 (default): FCF relaxation on every level (Sec. 2.2, the paper's runs);
                        1: F-relaxation only on every level -- with two levels this is Parareal
                        (Sec. 2.2), which after k cycles reproduces the first k coarse intervals of
@@ -119,6 +120,12 @@ typedef struct {
                        needs -- the fine departure points and the fine level's gather tables (in the
                        handle's precision); sl_step_sequential, sl_step_sequential_batched and
                        mgrit_apply_step at level 0 work, the solves return MGRIT_EUNSUPPORTED. */
+  int solve_mode;   /* correction solves [I - diag(sigma) D]^{-1} of 1D coarse levels: 0 (default) exact
+                       (partitioned banded solver); 1: the paper's inexact solve (Sec. 3.3, 3.4), GMRES
+                       from a zero guess with gmres_maxit / gmres_rtol as in 2D (two-level runs of Table 1:
+                       10 iterations, gmres_rtol = 0; multilevel: rtol 1e-2 or 10 iterations) -- FP64 coarse
+                       levels only (precision 0, or coarse_fp64 = 1), single problems, no adjoint.  2D
+                       correction solves always take GMRES (gmres_maxit, gmres_rtol). */
   int test_wait_cycles; /* testing the timeout path only; 0 (default): off.  > 0: in every 1D FP32 pass
                        whose tables are staged into shared memory by bulk copies, each CTA's first bounded
                        wait is made on a barrier that nothing completes, with this limit in SM cycles, so

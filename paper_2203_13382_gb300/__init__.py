@@ -51,7 +51,7 @@ class MgritOptions(ctypes.Structure):
                 ("m_first", ctypes.c_int), ("coarse_fp64", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
                 ("relax", ctypes.c_int), ("cluster_coarse", ctypes.c_int), ("diverge_ratio", ctypes.c_double),
-                ("fine_only", ctypes.c_int), ("test_wait_cycles", ctypes.c_int)]
+                ("fine_only", ctypes.c_int), ("solve_mode", ctypes.c_int), ("test_wait_cycles", ctypes.c_int)]
 
 
 PHASES = ["departure", "backtrack", "tables", "factor", "fine64_fc", "fine64_res", "fine64_post", "fine32_res",

@@ -86,6 +86,36 @@ __global__ void __launch_bounds__(kThreads2d) k_step2d(LevelTables T, const R* _
   if (fstore) fstore[(size_t)(n + 1) * N + pt] = acc;
 }
 
+// 1D: dst[j] = S_{n(j)} src[j] (+ g[n(j)+1]) on slices in global memory (the coarse passes that solve the
+// correction by GMRES, solve_mode 1).  FP64 weights from the table, FP32 from eps; the summation order of
+// the shared-memory gather (apply_gather), so both give the same values.
+template <int P, typename R>
+__global__ void __launch_bounds__(kThreads2d) k_step1d_g(LevelTables T, const R* __restrict__ src, R* __restrict__ dst,
+                                                         int m, int k, int n0, const R* __restrict__ g, int add_g,
+                                                         R* __restrict__ fstore) {
+  const int j = blockIdx.y;
+  const int nx = T.nx;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  const int n = m > 0 ? j * m + k : n0;
+  R w[P + 1];
+  if constexpr (std::is_same<R, float>::value) {
+    lagrange_weights<P, float>(__ldg(T.eps32 + (size_t)n * nx + i), w);
+  } else {
+    const double* wr = T.w64 + (size_t)n * (P + 1) * nx + i;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) w[a] = __ldg(wr + (size_t)a * nx);
+  }
+  const int b = i + (int)__ldg(T.shift + (size_t)n * nx + i);
+  const R* s = src + (size_t)j * nx;
+  R acc = w[0] * s[wrap_pow2(b, nx)];
+#pragma unroll
+  for (int a = 1; a <= P; ++a) acc += w[a] * s[wrap_pow2(b + a, nx)];
+  if (add_g && g) acc += g[(size_t)(n + 1) * nx + i];
+  dst[(size_t)j * nx + i] = acc;
+  if (fstore) fstore[(size_t)(n + 1) * nx + i] = acc;
+}
+
 // Transposed step dst[j] = S_row^T src[j] (+ g[n(j)+1]), FP64, row = nt-1-n(j) when T.reverse.  Target
 // node (X, Y) receives w_a(eps_i) w_b(nu_i) src_i from every arrival point i whose stencil base node
 // is (X - a, Y - b); the arrival points of each base node are read from the sorted buckets, so the sum
@@ -159,6 +189,28 @@ __device__ __forceinline__ R apply_M(const R* x, const R* sx, const R* sy, long 
   return x[pt] - sx[pt] * dxv - sy[pt] * dyv;
 }
 
+// 1D (the paper's solve on 1D coarse levels, solve_mode 1): y = M x with M = I - diag(s) D, and
+// y = M^T x = x - D diag(s) x (D is symmetric).
+template <int B, typename R>
+__device__ __forceinline__ R apply_M1d(const R* x, const R* sg, long long pt, int nx) {
+  const int i = (int)pt;
+  R dv = (R)0;
+#pragma unroll
+  for (int o = -B; o <= B; ++o) dv += (R)dstencil_int<B>(o) * x[wrap_pow2(i + o, nx)];
+  return x[pt] - sg[pt] * dv;
+}
+template <int B, typename R>
+__device__ __forceinline__ R apply_MT1d(const R* x, const R* sg, long long pt, int nx) {
+  const int i = (int)pt;
+  R dv = (R)0;
+#pragma unroll
+  for (int o = -B; o <= B; ++o) {
+    const int q = wrap_pow2(i + o, nx);
+    dv += (R)dstencil_int<B>(o) * sg[q] * x[q];
+  }
+  return x[pt] - dv;
+}
+
 // y = M^T x = x - (I (x) D) diag(sx) x - (D (x) I) diag(sy) x (D is symmetric).
 template <int B, typename R>
 __device__ __forceinline__ R apply_MT(const R* x, const R* sx, const R* sy, long long pt, int nx) {
@@ -192,10 +244,10 @@ __device__ __forceinline__ double cta_dot(const R* a, const R* b, long long N, d
 }
 
 // Arnoldi step with an unnormalised basis: the stored vectors are u_t with v_t = s_t u_t.  Pass A forms
-// w = s_k M u_k row by row (M^T for TRANS), stores it, and accumulates the raw projections <u_t, w>,
-// t = 0..k, in R per thread and warp, the warp partials summed in FP64 into hsum[0..k] (all threads see
-// them).  Rows [lo, hi).
-template <int B, typename R, bool TRANS>
+// w = s_k M u_k row by row (M^T for TRANS; DIM = 1: the 1D operator with sigma sx), stores it, and
+// accumulates the raw projections <u_t, w>, t = 0..k, in R per thread and warp, the warp partials summed
+// in FP64 into hsum[0..k] (all threads see them).  Rows [lo, hi).
+template <int B, typename R, bool TRANS, int DIM = 2>
 __device__ __forceinline__ void cta_apply_project(const R* uk, const R* sx, const R* sy, int nx, const R* V, long long N,
                                                   R* w, int kk, long long lo, long long hi, R sk,
                                                   double (*wpart)[11], double* hsum) {
@@ -203,7 +255,10 @@ __device__ __forceinline__ void cta_apply_project(const R* uk, const R* sx, cons
 #pragma unroll
   for (int t = 0; t < 10; ++t) acc[t] = (R)0;
   for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
-    const R wq = sk * (TRANS ? apply_MT<B, R>(uk, sx, sy, q, nx) : apply_M<B, R>(uk, sx, sy, q, nx));
+    R mq;
+    if constexpr (DIM == 1) mq = TRANS ? apply_MT1d<B, R>(uk, sx, q, nx) : apply_M1d<B, R>(uk, sx, q, nx);
+    else mq = TRANS ? apply_MT<B, R>(uk, sx, sy, q, nx) : apply_M<B, R>(uk, sx, sy, q, nx);
+    const R wq = sk * mq;
     w[q] = wq;
 #pragma unroll
     for (int t = 0; t < 10; ++t)
@@ -249,10 +304,11 @@ __device__ __forceinline__ double cta_subtract_sumsq(const R* V, long long N, R*
 
 // One CTA per interval j: b (= rhs, in place -> solution) of the system of step n(j) = n0 + j*m
 // (row nt_rev - 1 - n(j) when nt_rev > 0; TRANS solves with M^T).  basis: [J][kmax + 1][N] scratch.
+// DIM = 1: the 1D system I - diag(sigma_x) D of nx unknowns (sigma_y unused).
 // GMRES (Arnoldi with classical Gram-Schmidt: the projections on all basis vectors in one pass over w,
 // then one update pass; Givens rotations), zero initial guess, stop when the least-squares residual
 // <= rtol ||b|| or after kmax iterations.
-template <int B, typename R, bool TRANS>
+template <int B, typename R, bool TRANS, int DIM = 2>
 __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restrict__ sigma_x,
                                                         const R* __restrict__ sigma_y, int nx, int n0, int m,
                                                         int nt_rev, R* __restrict__ bx_all, R* __restrict__ basis,
@@ -262,7 +318,7 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restr
   __shared__ double cs[10], sn[10], gv[11], yv[10];
   __shared__ double wpart[32][11];
   __shared__ double hsum[11];
-  const long long N = (long long)nx * nx;
+  const long long N = DIM == 1 ? (long long)nx : (long long)nx * nx;
   const int j = blockIdx.x;
   const int n = nt_rev > 0 ? nt_rev - 1 - (n0 + j * m) : n0 + j * m;
   const R* sx = sigma_x + (size_t)n * N;
@@ -285,7 +341,7 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restr
     R* w = V + (size_t)(kk + 1) * N;
     // classical Gram-Schmidt in two passes: w = M v_k with the projections on all basis vectors, then
     // the update with the norm of the result
-    cta_apply_project<B, R, TRANS>(uk, sx, sy, nx, V, N, w, kk, 0, N, (R)sc[kk], wpart, hsum);
+    cta_apply_project<B, R, TRANS, DIM>(uk, sx, sy, nx, V, N, w, kk, 0, N, (R)sc[kk], wpart, hsum);
     if ((int)threadIdx.x <= kk) {
       const double h = sc[threadIdx.x] * hsum[threadIdx.x];
       H[threadIdx.x][kk] = h;
@@ -454,10 +510,15 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const R*
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-// J systems of step index n0 (+ j m): one CTA each, or, when J leaves SMs idle, a cluster of CTAs each.
-template <int B, typename R, bool TRANS>
+// J systems of step index n0 (+ j m): one CTA each, or, when J leaves SMs idle, a cluster of CTAs each
+// (2D).  DIM = 1: the 1D systems, one CTA each (sig holds sigma only, [nt][nx]).
+template <int B, typename R, bool TRANS, int DIM = 2>
 cudaError_t launch_gmres(const R* sig, long long N, int nt, int nx, int n0, int m, int ntr, R* b, R* basis,
                          int kmax, double rtol, int J, cudaStream_t st) {
+  if constexpr (DIM == 1) {
+    k_gmres2d<B, R, TRANS, 1><<<J, gmres_threads<R>(), 0, st>>>(sig, sig, nx, n0, m, ntr, b, basis, kmax, rtol);
+    return cudaGetLastError();
+  }
   int C = 1;
   while (C < 16 && J * C * 2 <= 152) C *= 2;
   if (C > 1) {
@@ -564,6 +625,25 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
   const bool coarse = T.solver != nullptr;
   const int addg_in_step = coarse ? 0 : 1;
   const int n_first = m > 0 ? k : n0;
+  if (T.npts == T.nx) {  // 1D coarse levels solved by GMRES (solve_mode 1)
+    if (T.trans) return cudaErrorNotSupported;
+#define MGRIT_STEP1D(PP) k_step1d_g<PP, R><<<grid, kThreads2d, 0, st>>>(T, src, dst, m, k, n0, g, addg_in_step, coarse ? nullptr : fstore)
+    if (T.p == 1) MGRIT_STEP1D(1);
+    else if (T.p == 3) MGRIT_STEP1D(3);
+    else MGRIT_STEP1D(5);
+#undef MGRIT_STEP1D
+    if (coarse) {
+      const R* sig = (const R*)T.solver;  // sigma [nt][nx]
+      const int B = (T.p + 1) / 2;
+      cudaError_t e;
+      if (B == 1) e = launch_gmres<1, R, false, 1>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
+      else if (B == 2) e = launch_gmres<2, R, false, 1>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
+      else e = launch_gmres<3, R, false, 1>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
+      if (e != cudaSuccess) return e;
+      k_add_rows<R><<<grid, kThreads2d, 0, st>>>(dst, g, m, k, n0, N, fstore);
+    }
+    return cudaGetLastError();
+  }
   if (T.trans) {  // Phi^T = S^T M^{-T}: the correction solve (in place on src), then the transposed step
     if constexpr (std::is_same<R, double>::value) {
       if (coarse) {

@@ -145,6 +145,7 @@ struct mgrit_handle {
   mgrit_options opt;
   cudaStream_t stream = nullptr;
   int device = 0;  // CUDA device current at setup (the handle's workspace lives there)
+  bool gmres1d = false;  // solve_mode 1 on a 1D handle: coarse levels solve their correction by GMRES
   int npts = 0;
   std::vector<Level> levels;
   std::vector<void*> allocs;
@@ -268,7 +269,8 @@ struct mgrit_handle {
     T.nt = L.nt;
     // 2D: sigma for the GMRES correction solves, FP32 copy on FP32 levels
     T.solver = (l > 0 && opt.coarse_op == 0)
-                   ? (grid.dim == 2 ? (!is_double && L.sig32 ? (const void*)L.sig32 : (const void*)L.sigma) : L.solver)
+                   ? ((grid.dim == 2 || gmres1d) ? (!is_double && L.sig32 ? (const void*)L.sig32 : (const void*)L.sigma)
+                                                 : L.solver)
                    : nullptr;
     T.solver_stride = L.solver_stride;
     T.s64 = L.s64;
@@ -347,7 +349,7 @@ std::vector<int> factors(int nt, int m, int m_first, int levels, int max_coarses
 mgrit_status relax(mgrit_handle* h, int l, int is_double, const RelaxArgs& a, int phase) {
   LevelTables T = h->tables(l, is_double);
   const int ev = h->phase_begin();
-  if (h->grid.dim == 2) MG_CUDA(launch_relax_2d(T, a, h->s2d, is_double, h->stream));
+  if (h->grid.dim == 2 || (h->gmres1d && l > 0)) MG_CUDA(launch_relax_2d(T, a, h->s2d, is_double, h->stream));
   else MG_CUDA(launch_relax_1d(T, a, is_double, h->stream));
   h->phase_end(phase, ev, 1);
   return MGRIT_OK;
@@ -365,7 +367,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
   const int np = h->npts;
   const int dbl = L.is_double;
   if (l == (int)h->levels.size() - 1) {  // coarsest: sequential stepping (Sec. 2.2)
-    if (h->grid.dim == 1 && dbl && h->opt.cluster_coarse && h->opt.coarse_op == 0 && !h->trans_mode) {
+    if (h->grid.dim == 1 && dbl && h->opt.cluster_coarse && h->opt.coarse_op == 0 && !h->trans_mode && !h->gmres1d) {
       // FP64: one interval of nt steps through the relaxation pass (FC: F-points stored, the last step
       // is the C-point), which splits the slice over a thread-block cluster
       RelaxArgs a = args0();
@@ -382,7 +384,8 @@ mgrit_status coarse_cycle(mgrit_handle* h, int l) {
     }
     LevelTables T = h->tables(l, dbl);
     const int ev = h->phase_begin();
-    if (h->grid.dim == 2) MG_CUDA(launch_sequential_2d(T, L.nt, L.G, nullptr, L.E, 1, h->s2d, dbl, h->stream));
+    if (h->grid.dim == 2 || h->gmres1d)
+      MG_CUDA(launch_sequential_2d(T, L.nt, L.G, nullptr, L.E, 1, h->s2d, dbl, h->stream));
     else MG_CUDA(launch_sequential_1d(T, L.nt, L.G, nullptr, L.E, 1, dbl, h->stream));
     h->phase_end(MGRIT_PHASE_COARSEST, ev, 1);
     return MGRIT_OK;
@@ -549,6 +552,7 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->cluster_coarse = 1;
   opt->diverge_ratio = 1e3;
   opt->fine_only = 0;
+  opt->solve_mode = 0;
   opt->test_wait_cycles = 0;
   return MGRIT_OK;
 }
@@ -608,6 +612,9 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
   if (!(opt.diverge_ratio >= 0.0)) return fail(MGRIT_EINVAL, "diverge_ratio must be >= 0");
   if (opt.test_wait_cycles < 0) return fail(MGRIT_EINVAL, "test_wait_cycles must be >= 0");
   if (opt.fine_only != 0 && opt.fine_only != 1) return fail(MGRIT_EINVAL, "fine_only must be 0 or 1");
+  if (opt.solve_mode != 0 && opt.solve_mode != 1) return fail(MGRIT_EINVAL, "solve_mode must be 0 or 1");
+  if (opt.solve_mode == 1 && grid->dim == 1 && opt.precision == 1 && !opt.coarse_fp64)
+    return fail(MGRIT_EUNSUPPORTED, "1D GMRES correction solves (solve_mode 1) need FP64 coarse levels");
   if (opt.fine_only && grid->dim != 1) return fail(MGRIT_EUNSUPPORTED, "fine_only handles are 1D");
   if (levels < 0 || levels == 1) return fail(MGRIT_EINVAL, "levels must be 0 or >= 2");
   std::vector<int> fac = factors(grid->nt, m, opt.m_first, levels, opt.max_coarsest);
@@ -628,6 +635,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
     return fail(MGRIT_ECUDA, "cudaGetDevice failed");
   }
   h->npts = grid->dim == 2 ? grid->nx * grid->nx : grid->nx;
+  h->gmres1d = grid->dim == 1 && opt.solve_mode == 1 && opt.coarse_op == 0;
   const int nx = grid->nx, np = h->npts, dim = grid->dim;
   const double hgrid = (grid->xmax - grid->xmin) / nx;
   const double dt = grid->cfl * hgrid;
@@ -671,7 +679,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
       if (opt.coarse_op == 0 && dim == 2 && !L.is_double &&
           (st = h->alloc(&L.sig32, rows)) != MGRIT_OK)  // FP32 sigma of the FP32 GMRES solves
         return cleanup_fail(st);
-      if (opt.coarse_op == 0 && dim == 1) {
+      if (opt.coarse_op == 0 && dim == 1 && !h->gmres1d) {
         L.P = nx / 8;
         if (L.is_double) {
           L.solver_stride = solver_reals(nx, p);
@@ -688,11 +696,11 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
     }
   }
   const int J1 = fine_only ? 1 : h->J1();
-  if (dim == 2) {  // work buffers of the 2D passes
+  if (dim == 2 || h->gmres1d) {  // work buffers of the passes over slices in global memory (2D, 1D GMRES)
     size_t jmax = (size_t)J1, jc = 1;
     for (size_t l = 1; l + 1 < h->levels.size(); ++l)
       jc = std::max(jc, (size_t)(h->levels[l].nt / h->levels[l + 1].m));
-    jmax = std::max(jmax, jc);
+    jmax = dim == 2 ? std::max(jmax, jc) : jc;  // 1D: only the coarse passes use these slices
     const size_t rsz = (fp32 && !cf64) ? sizeof(float) : sizeof(double);  // coarse GMRES basis
     h->s2d.kmax = opt.gmres_maxit;
     h->s2d.rtol = opt.gmres_rtol;
@@ -1158,6 +1166,7 @@ mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, cons
     return fail(MGRIT_EINVAL, "NULL argument");
   if (h->opt.precision != 0) return fail(MGRIT_EUNSUPPORTED, "the adjoint solve needs an FP64 handle (precision 0)");
   if (h->levels.size() < 2) return fail(MGRIT_EUNSUPPORTED, "a fine_only handle has no MGRIT hierarchy");
+  if (h->gmres1d) return fail(MGRIT_EUNSUPPORTED, "the 1D adjoint uses exact correction solves (solve_mode 0)");
   MG_TRY(ensure_adjoint(h));
   cudaStream_t s = h->stream;
   const int np = h->npts, nt = h->grid.nt, m1 = h->levels[1].m, J = h->J1();
@@ -1231,7 +1240,8 @@ mgrit_status mgrit_apply_step(mgrit_handle* h, int level, int n0, int count, con
   const int dbl = L.is_double;
   LevelTables T = h->tables(level, dbl);
   if (dbl) {
-    if (h->grid.dim == 2) MG_CUDA(launch_apply_steps_2d(T, n0, count, d_in, d_out, h->s2d, 1, s));
+    if (h->grid.dim == 2 || (h->gmres1d && level > 0))
+      MG_CUDA(launch_apply_steps_2d(T, n0, count, d_in, d_out, h->s2d, 1, s));
     else MG_CUDA(launch_apply_steps_1d(T, n0, count, d_in, d_out, 1, s));
   } else {
     float *fi = nullptr, *fo = nullptr;
@@ -1290,7 +1300,8 @@ mgrit_status mgrit_apply_step_noalloc(mgrit_handle* h, int level, int n0, int co
   const int dbl = L.is_double;
   LevelTables T = h->tables(level, dbl);
   if (dbl) {
-    if (h->grid.dim == 2) MG_CUDA(launch_apply_steps_2d(T, n0, count, d_in, d_out, h->s2d, 1, s));
+    if (h->grid.dim == 2 || (h->gmres1d && level > 0))
+      MG_CUDA(launch_apply_steps_2d(T, n0, count, d_in, d_out, h->s2d, 1, s));
     else MG_CUDA(launch_apply_steps_1d(T, n0, count, d_in, d_out, 1, s));
   } else {
     float* stage = nullptr;
@@ -1548,6 +1559,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
   if (opt.relax != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves run FCF relaxation (relax 0)");
   if (opt.coarse_fp64 != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves run FP32 coarse levels (coarse_fp64 0)");
   if (opt.coarse_op != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves use the corrected coarse operator");
+  if (opt.solve_mode != 0) return fail(MGRIT_EUNSUPPORTED, "batched solves use exact correction solves (solve_mode 0)");
   for (int q = 0; q < nprob; ++q)
     if (grids[q].dim != 1) return fail(MGRIT_EUNSUPPORTED, "batched solves are 1D");
   const double t0 = now_ms();
