@@ -126,6 +126,11 @@ typedef struct {
                        10 iterations, gmres_rtol = 0; multilevel: rtol 1e-2 or 10 iterations) -- FP64 coarse
                        levels only (precision 0, or coarse_fp64 = 1), single problems, no adjoint.  2D
                        correction solves always take GMRES (gmres_maxit, gmres_rtol). */
+  int coarse_band;  /* 1D FP32 coarse levels.  1 (default): where the separator block of M^{-1} (M = I -
+                       diag(sigma) D, 8-row partitions) falls below 1e-9 of its diagonal blocks beyond at
+                       most 4 partitions, setup stores it as a band and each correction solve applies it in
+                       one banded product; 0 (or where the band would be wider): block cyclic reduction of
+                       the separator system (p <= 3) or the on-the-fly factorisation (p = 5). */
   int test_wait_cycles; /* testing the timeout path only; 0 (default): off.  > 0: in every 1D FP32 pass
                        whose tables are staged into shared memory by bulk copies, each CTA's first bounded
                        wait is made on a barrier that nothing completes, with this limit in SM cycles, so
@@ -262,6 +267,10 @@ mgrit_status mgrit_adjoint_solve(mgrit_handle* h, const double* d_u_target, cons
 
 /* Number of levels and, for a level l, its step count and coarsening factor (0 on level 0). */
 mgrit_status mgrit_level_info(const mgrit_handle* h, int level, int* nt_level, int* m_level);
+
+/* Half-width, in 8-row partitions, of the banded separator inverse that level l's FP32 correction solves
+ * apply (mgrit_options.coarse_band); 0 where the level solves otherwise. */
+mgrit_status mgrit_level_band(const mgrit_handle* h, int level, int* half_width);
 
 /* Departure offsets s[n][pt] = (x_pt - xi_pt) / h of level l in grid units (2D: x then y
  * component blocks, each [nt_l x N]); d_out has nt_l * N (2D: 2 * nt_l * N) doubles. */

@@ -51,7 +51,8 @@ class MgritOptions(ctypes.Structure):
                 ("m_first", ctypes.c_int), ("coarse_fp64", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
                 ("relax", ctypes.c_int), ("cluster_coarse", ctypes.c_int), ("diverge_ratio", ctypes.c_double),
-                ("fine_only", ctypes.c_int), ("solve_mode", ctypes.c_int), ("test_wait_cycles", ctypes.c_int)]
+                ("fine_only", ctypes.c_int), ("solve_mode", ctypes.c_int), ("coarse_band", ctypes.c_int),
+                ("test_wait_cycles", ctypes.c_int)]
 
 
 PHASES = ["departure", "backtrack", "tables", "factor", "fine64_fc", "fine64_res", "fine64_post", "fine32_res",
@@ -99,6 +100,7 @@ _SIGNATURES = {
     "mgrit_adjoint_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(MgritStats)]),
     "mgrit_level_info": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
+    "mgrit_level_band": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mgrit_copy_offsets": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "mgrit_copy_sigma": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "mgrit_apply_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
@@ -203,6 +205,12 @@ class Handle:
         m = ctypes.c_int()
         _check(load_library().mgrit_level_info(self._h(), level, ctypes.byref(nt), ctypes.byref(m)), "level_info")
         return nt.value, m.value
+
+    def level_band(self, level: int) -> int:
+        """Half-width of the banded separator inverse of this level's FP32 correction solves (0: none)."""
+        w = ctypes.c_int()
+        _check(load_library().mgrit_level_band(self._h(), level, ctypes.byref(w)), "mgrit_level_band")
+        return w.value
 
     @property
     def nlevels(self) -> int:

@@ -38,6 +38,15 @@ void launch_build_tables(const double* s, int nt, int nx, int npts_row, int p, u
 unsigned pcr_record_size(int nx, int p);
 cudaError_t launch_pcr_coef(const float* sig32, int nt, int nx, int p, float* out, cudaStream_t st);
 
+// The banded separator inverse of the FP32 correction solves (8-row partitions, nx / 8 in 16 .. 512):
+// per step a record of band_record_size floats, offsets -kBandMaxHalfWidth .. kBandMaxHalfWidth in rows of
+// band_row_size floats, probed from the FP32 sigma rows [nt][nx]; ind[t], t = 1..7, is raised to the
+// largest entry at partition distance t relative to the diagonal blocks (ind zeroed before).
+constexpr int kBandMaxHalfWidth = 4;
+unsigned band_record_size(int nx, int p);
+unsigned band_row_size(int nx, int p);
+cudaError_t launch_sep_band(const float* sig32, int nt, int nx, int p, float* rec, float* ind, cudaStream_t st);
+
 // Factorisation of M = I - diag(sigma) D_{p+1} (periodic, half-bandwidth b = (p+1)/2) for each of nt
 // steps (layout: solver_layout.cuh), FP64, solver_reals(nx, p) values per step (FP64 coarse levels and
 // the adjoint's M^T; FP32 levels use launch_pcr_coef).  flag (device int) is set to 1 if a pivot is too
@@ -94,6 +103,13 @@ struct LevelTables {
   // pcr_record_floats floats a step, FP32), staged per step into shared memory; NULL: formed on the fly
   const float* pcr;
   unsigned pcr_floats;
+  // otf levels: the coefficient record staged per step, cf_floats floats from cf_src + row * cf_stride
+  // (0: none).  band > 0: the banded separator inverse of half-width `band` partitions (8-row partitions,
+  // relax_kernels.cu corr_solve_band); band = 0 with a record: the block-PCR coefficients above.
+  int band;
+  const float* cf_src;
+  unsigned cf_stride;
+  unsigned cf_floats;
   // adjoint: trans = 1 applies Phi^T (coarse: (M^{-1} S)^T = S^T M^{-T}, `solver` then holds the
   // factorisation of M^T); reverse = 1 maps step n to table row nt - 1 - n; frange[row] = floor range.
   int trans;

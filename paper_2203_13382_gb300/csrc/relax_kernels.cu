@@ -22,7 +22,7 @@ constexpr int kPts = 8;  // points per thread: nx <= kPts * threads (4096 for 51
 // Threads of the slice-resident kernels (one CTA per interval).  Measured on the 4096-point coarse
 // levels: 512 threads at one CTA per SM beat 256 threads at two (longer per-thread gathers and
 // register spills of the on-the-fly solve outweigh the second CTA).
-template <int P, typename R, bool COARSE>
+template <int P, typename R, int COARSE>
 constexpr int slice_threads() {
   return kSliceThreads;
 }
@@ -880,6 +880,207 @@ __device__ __forceinline__ bool corr_solve_coef(float* __restrict__ x, const flo
   return true;
 }
 
+// ---- banded separator inverse (FP32 coarse levels) --------------------------------------------------
+//
+// With 8-row partitions (one per thread, B separator rows first, Q = 8 - B interior rows) the separator
+// unknowns satisfy the Schur system S x_S = g, and S^{-1} is the separator block of M^{-1}, whose entries
+// decay exponentially away from the diagonal (M = I - diag(sigma) D is close to a diagonally dominant
+// M-matrix on the coarse levels).  Where S^{-1} is below 1e-9 of its diagonal blocks beyond a few
+// partitions, it is stored as a band of half-width W <= kBandMax partitions (setup: k_sep_band probes
+// it), and the separator solve is one banded product instead of the block cyclic reduction: two block
+// barriers instead of one per reduction level, every thread a partition.
+
+constexpr int kBandMax = kBandMaxHalfWidth;  // largest stored half-bandwidth, in partitions
+constexpr int kBandColours = 16; // probe colours of k_sep_band (partition index mod 16)
+
+// Floats of one band row (one offset d: B*B blocks for every partition), padded to 16 bytes, and of a
+// whole step record (offsets -kBandMax .. kBandMax; layout [d][a * B + c][partition]).
+MGRIT_HD unsigned band_row_floats(int nx, int p) {
+  const int B = (p + 1) / 2;
+  return ((unsigned)(B * B * (nx / 8)) + 3u) & ~3u;
+}
+MGRIT_HD unsigned band_record_floats(int nx, int p) { return (2 * kBandMax + 1) * band_row_floats(nx, p); }
+
+// x <- M^{-1} x with 8-row partitions: the interior rows solved from sigma (banded LU, no pivoting), the
+// separator right-hand sides g_k, x_S(k) = sum_{|d| <= W} Sinv[k][d] g_{k+d} (band `bd`: the W-trimmed
+// record, [d + W][a * B + c][k], rows of `row` floats), then the interiors again with the separators
+// known.  X: exchange area of 2 B P floats.  The band is being filled by a bulk copy that completes on
+// cf_bar (parity cf_par); the wait comes after the first interior solve.  Once every thread has read
+// the band, thread 0 calls issue_next().  Returns false (all threads) if the bounded wait gave up.
+template <int B, typename IssueNext>
+__device__ __forceinline__ bool corr_solve_band(float* __restrict__ x, const float* __restrict__ sig,
+                                                const float* __restrict__ bd, int W, unsigned row,
+                                                float* __restrict__ X, int nx, uint64_t* cf_bar, uint32_t cf_par,
+                                                IssueNext issue_next) {
+  constexpr int PR = kPartRows, Q = PR - B;
+  const int P = nx / PR;
+  const int k = threadIdx.x;
+  const bool act = k < P;
+  const int g0 = k * PR;
+  float xp[PR], sg[PR] = {};  // sg is read only by the partition threads, after their loads
+  float gk[B];
+  auto M = [&](int rr, int o) -> float { return (o == 0 ? 1.f : 0.f) - sg[rr] * dcoef<B>(o); };
+  auto interior_solve = [&](float (&v)[Q]) {
+    float l[Q][B], U[Q][B + 1], piv[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      float a[2 * B + 1];
+#pragma unroll
+      for (int c = -B; c <= B; ++c) a[c + B] = (r + c >= 0 && r + c < Q) ? M(B + r, c) : 0.f;
+#pragma unroll
+      for (int t = B; t >= 1; --t) {
+        if (r - t < 0) continue;
+        const float lt = a[B - t] * piv[r - t];
+        l[r][t - 1] = lt;
+#pragma unroll
+        for (int c = 1; c <= B; ++c)
+          if (-t + c <= B) a[-t + c + B] -= lt * U[r - t][c];
+      }
+      piv[r] = __frcp_rn(a[B]);
+#pragma unroll
+      for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
+#pragma unroll
+      for (int t = 1; t <= B; ++t)
+        if (r - t >= 0) v[r] -= l[r][t - 1] * v[r - t];
+    }
+#pragma unroll
+    for (int r = Q - 1; r >= 0; --r) {
+#pragma unroll
+      for (int t = 1; t <= B; ++t)
+        if (r + t < Q) v[r] -= U[r][t] * v[r + t];
+      v[r] *= piv[r];
+    }
+  };
+  float* G = X + (size_t)B * P;  // separator right-hand sides of every partition
+  if (act) {
+    load_part<float>(x + g0, xp);
+    load_part<float>(sig + g0, sg);
+    float y[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) y[r] = xp[B + r];
+    interior_solve(y);
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      X[(size_t)a * P + k] = y[Q - B + a];  // tail of y, read by partition k + 1
+      gk[a] = y[a];                          // head of y, used below
+    }
+  }
+  const bool cf_ok = mbar_wait_bounded(cf_bar, cf_par, kWaitLimitCycles);
+  if (__syncthreads_or(!cf_ok)) return false;
+  if (act) {
+    const int km = (k + P - 1) & (P - 1);
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      float v = xp[a];
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const float ct = c >= a ? M(a, c - B - a) : 0.f;
+        const float ch = c <= a ? M(a, B + c - a) : 0.f;
+        v -= ct * X[(size_t)c * P + km] + ch * gk[c];
+      }
+      G[(size_t)a * P + k] = v;
+    }
+  }
+  __syncthreads();
+  float xs[B];
+  if (act) {
+#pragma unroll
+    for (int a = 0; a < B; ++a) xs[a] = 0.f;
+    for (int d = -W; d <= W; ++d) {
+      const int kd = (k + d) & (P - 1);
+      const float* br = bd + (size_t)(d + W) * row + k;
+      float gv[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) gv[c] = G[(size_t)c * P + kd];
+#pragma unroll
+      for (int a = 0; a < B; ++a)
+#pragma unroll
+        for (int c = 0; c < B; ++c) xs[a] += br[(size_t)(a * B + c) * P] * gv[c];
+    }
+    // the separators go to the area of the y tails, which every thread last read before the barrier above
+#pragma unroll
+    for (int a = 0; a < B; ++a) X[(size_t)a * P + k] = xs[a];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) issue_next();  // every band entry of this step has been read
+  if (act) {
+    const int kp = (k + 1) & (P - 1);
+    float xn[B];
+#pragma unroll
+    for (int a = 0; a < B; ++a) xn[a] = X[(size_t)a * P + kp];
+    // interior: A x_I = b_I - M[I, S_k] x_S(k) - M[I, S_{k+1}] x_S(k+1)
+    float v[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      float w = xp[B + r];
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const int ov = c - B - r, ow = Q - r + c;
+        if (ov >= -B) w -= M(B + r, ov) * xs[c];
+        if (ow <= B) w -= M(B + r, ow) * xn[c];
+      }
+      v[r] = w;
+    }
+    interior_solve(v);
+#pragma unroll
+    for (int a = 0; a < B; ++a) xp[a] = xs[a];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) xp[B + r] = v[r];
+    store_part<float>(x + g0, xp);
+  }
+  __syncthreads();
+  return true;
+}
+
+// Setup, one CTA per step row of an FP32 coarse level (nx / 8 >= 32 partitions, blockDim.x >= nx / 8):
+// probes S^{-1} = (M^{-1}) restricted to the separator rows with the on-the-fly solve of 8-row
+// partitions.  For every colour col < 16 and separator component c, x = M^{-1} e with e = 1 on row c of
+// the separator of every partition k == col (mod 16); the value at separator row a of partition k' is
+// the entry Sinv[(k', a), (k, c)] of the probe partition k = k' + d, |d| < 8, nearest to k' (the other
+// probe partitions are 16 or more away, where S^{-1} is negligible wherever the band is used).  Entries
+// |d| <= kBandMax go to the record; ind[|d|], |d| = 1..7, receives the largest |Sinv[k'][d]| over
+// max |Sinv[k'][0]| of this level (atomicMax on the bits of non-negative floats).
+template <int B>
+__global__ void __launch_bounds__(512) k_sep_band(const float* __restrict__ sig_all, int nx, float* __restrict__ rec_all,
+                                                  unsigned rec_stride, unsigned row, float* __restrict__ ind) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* x = reinterpret_cast<float*>(smem_raw);
+  float* sig = x + nx;
+  float* X = sig + nx;
+  const int P = nx / kPartRows;
+  const int k = threadIdx.x;
+  const float* sg = sig_all + (size_t)blockIdx.x * nx;
+  float* rec = rec_all + (size_t)blockIdx.x * rec_stride;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) sig[i] = sg[i];
+  float dmax = 0.f, tmax[8] = {};
+  for (int col = 0; col < kBandColours; ++col) {
+    for (int c = 0; c < B; ++c) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) x[i] = 0.f;
+      __syncthreads();
+      if (k < P && (k & (kBandColours - 1)) == col) x[k * kPartRows + c] = 1.f;
+      __syncthreads();
+      corr_solve_otf<B, kPartRows>(x, sig, X, nx);
+      if (k < P) {
+        int d = (col - k) & (kBandColours - 1);  // probe partition k + d, d in [-7, 8]
+        if (d > kBandColours / 2) d -= kBandColours;
+#pragma unroll
+        for (int a = 0; a < B; ++a) {
+          const float v = x[k * kPartRows + a];
+          if (d >= -kBandMax && d <= kBandMax) rec[(size_t)(d + kBandMax) * row + (size_t)(a * B + c) * P + k] = v;
+          const int ad = d < 0 ? -d : d;
+          if (ad == 0) dmax = fmaxf(dmax, fabsf(v));
+          else if (ad < 8) tmax[ad] = fmaxf(tmax[ad], fabsf(v));
+        }
+      }
+    }
+  }
+  if (k < P && dmax > 0.f) {
+#pragma unroll
+    for (int t = 1; t < 8; ++t) atomicMax(reinterpret_cast<int*>(ind) + t, __float_as_int(tmax[t] / dmax));
+  }
+}
+
 // Rows per partition of the on-the-fly solve: 16 for B <= 2 (half the partitions of the stored layout,
 // so one PCR level less and half the reduction work), 8 for B = 3 (register budget).
 template <int B>
@@ -928,7 +1129,8 @@ MGRIT_HD StageLayout stage_layout(int nx, int p, int otf, unsigned cf_floats, in
   o.bars = o.cf + ((cf_floats * 4u + 127u) & ~127u);
   o.xch = o.bars + 128;
   const int B = (p + 1) / 2, P = nx / (B <= 2 ? 16 : 8);  // partitions of the on-the-fly solve
-  o.total = o.xch + (otf ? (unsigned)((3 * B * B + B) * P * 4) : 0u);
+  const unsigned x_otf = (unsigned)((3 * B * B + B) * P * 4), x_band = (unsigned)(2 * B * (nx / 8) * 4);
+  o.total = o.xch + (otf ? (x_otf > x_band ? x_otf : x_band) : 0u);
   o.tx = (unsigned)nx * ((otf || df) ? 10u : 6u);
   return o;
 }
@@ -966,7 +1168,7 @@ __device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, co
   s.test_wait = 0;
   if (!T.gather_stage) return s;
   s.test_wait = T.test_wait;
-  s.lay = stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u, T.df);
+  s.lay = stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf ? T.cf_floats : 0u, T.df);
   s.base = smem + ((used + 127) & ~(size_t)127);
   if (threadIdx.x == 0) {
     mbar_init(s.bar(0), 1);
@@ -992,25 +1194,26 @@ __device__ __forceinline__ void stage_issue(const Stage& s, const LevelTables& T
     bulk_copy_g2s(d + s.lay.e + s.lay.h, T.eps_lo + (size_t)row * T.table_stride, nx * 4u, s.bar(b));
 }
 
-// Thread 0: bulk copy of the block-PCR coefficient record of step `row` (completes on bar(2)).
+// Thread 0: bulk copy of the coefficient record of step `row` (the banded separator inverse or the
+// block-PCR coefficients; completes on bar(2)).
 __device__ __forceinline__ void stage_issue_cf(const Stage& s, const LevelTables& T, int row) {
-  const unsigned bytes = T.pcr_floats * 4u;
+  const unsigned bytes = T.cf_floats * 4u;
   fence_proxy_async_smem();
   mbar_arrive_expect_tx(s.bar(2), bytes);
-  bulk_copy_g2s(s.cf(), T.pcr + (size_t)row * T.pcr_floats, bytes, s.bar(2));
+  bulk_copy_g2s(s.cf(), T.cf_src + (size_t)row * T.cf_stride, bytes, s.bar(2));
 }
 
 // Thread 0 issues the copies of a CTA's first step n right after stage_init, so that they overlap the
 // load of the start slice (FP32 levels; coarse levels with stored coefficients also the record).
-template <int P, bool COARSE>
+template <int P, int COARSE>
 __device__ __forceinline__ void stage_prefetch_first(Stage& s, const LevelTables& T, int n) {
   if (!s.base || n < 0) return;
   if (threadIdx.x == 0) {
     stage_issue(s, T, n, s.cur, COARSE);
-    if (COARSE && (P + 1) / 2 <= 2) stage_issue_cf(s, T, n);
+    if (COARSE && T.cf_floats) stage_issue_cf(s, T, n);
   }
   s.pending = n;
-  if (COARSE && (P + 1) / 2 <= 2) s.cf_pending = n;
+  if (COARSE && T.cf_floats) s.cf_pending = n;
 }
 
 // Issues the next step's copies (and this step's if it was not prefetched), then waits for buffer
@@ -1071,7 +1274,7 @@ __device__ __forceinline__ void stage_abandon(const Stage& s, const LevelTables&
 // One full step src -> dst (Phi, or Psi with the correction solve), given the prefetched gather table.
 // next_n: the step this CTA takes after this one (-1: none), whose sigma row is prefetched.
 // Returns false if a bounded wait gave up (the caller then stops; the flag T.err is set).
-template <int P, typename R, bool COARSE, bool TRANS, int NT>
+template <int P, typename R, int COARSE, bool TRANS, int NT>
 __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R* dst, const LevelTables& T, int n,
                                           Stage& stg, int next_n) {
   constexpr int B = (P + 1) / 2;
@@ -1090,8 +1293,9 @@ __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R*
     return true;
   }
   if constexpr (std::is_same<R, float>::value) {  // tables staged by TMA; coarse: factorised on the fly
-    // p <= 3: the stored block-PCR coefficients (every FP32 coarse level has them); p = 5: on the fly
-    constexpr bool coef = COARSE && B <= 2;
+    // a staged coefficient record: the banded separator inverse (COARSE == 2) or, p <= 3, the block-PCR
+    // coefficients; without one (p = 5 levels without a band) the matrix is factorised on the fly
+    constexpr bool coef = COARSE == 2 || (COARSE == 1 && B <= 2);
     if (coef && threadIdx.x == 0 && stg.cf_pending != n) stage_issue_cf(stg, T, n);
     if (!stage_acquire(stg, T, n, next_n, COARSE)) {
       if (coef && threadIdx.x == 0) mbar_wait_bounded(stg.bar(2), (stg.phase >> 2) & 1u, kWaitLimitCycles);
@@ -1104,10 +1308,17 @@ __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R*
       if constexpr (coef) {
         const uint32_t par = (stg.phase >> 2) & 1u;
         stg.phase ^= 4u;
-        const bool ok = corr_solve_coef<B, otf_rows<B>()>((float*)dst, stg.sig(b), stg.cf(), stg.xch(), T.nx, stg.bar(2),
-                                                          par, [&]() {
-                                                            if (next_n >= 0) stage_issue_cf(stg, T, next_n);
-                                                          });
+        auto issue_next = [&]() {
+          if (next_n >= 0) stage_issue_cf(stg, T, next_n);
+        };
+        bool ok;
+        if constexpr (COARSE == 2) {  // the banded separator inverse
+          ok = corr_solve_band<B>((float*)dst, stg.sig(b), stg.cf(), T.band, band_row_floats(T.nx, T.p), stg.xch(),
+                                  T.nx, stg.bar(2), par, issue_next);
+        } else {
+          ok = corr_solve_coef<B, otf_rows<B>()>((float*)dst, stg.sig(b), stg.cf(), stg.xch(), T.nx, stg.bar(2), par,
+                                                 issue_next);
+        }
         if (!ok) {  // nothing of the next step's record was issued; the current one may still land
           if (threadIdx.x == 0) {
             atomicExch(T.err, 1);
@@ -1141,7 +1352,7 @@ __device__ __forceinline__ bool full_step(const GatherRegs<P, R>& gr, R* src, R*
 
 // Fine-level kernels keep two (FP32: shared memory of the staged tables) or three (FP64) CTAs per SM.
 // The pass of interval j (one CTA); also the body of the batched kernel.
-template <int P, typename R, bool COARSE, bool TRANS, int NT>
+template <int P, typename R, int COARSE, bool TRANS, int NT>
 __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs& a, int j, int buf,
                                            unsigned char* smem_raw) {
   constexpr int kP = kPts;  // points per thread (nx <= kPts * NT)
@@ -1243,7 +1454,7 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
         ahead_ok = stage_wait_ahead(stg);
       }
       if (__syncthreads_or(!ahead_ok)) {
-        stage_abandon(stg, T, COARSE && (P + 1) / 2 <= 2);
+        stage_abandon(stg, T, COARSE && T.cf_floats > 0);
         return;
       }
     } else {
@@ -1259,7 +1470,7 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
   }
 }
 
-template <int P, typename R, bool COARSE, bool TRANS>
+template <int P, typename R, int COARSE, bool TRANS>
 __global__ void __launch_bounds__(slice_threads<P, R, COARSE>(),
                                   COARSE ? (slice_threads<P, R, COARSE>() == 256 ? 2 : 1)
                                          : (std::is_same<R, float>::value ? 2 : 3))
@@ -1382,7 +1593,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_relax_df_1d(LevelTables T,
 }
 
 // u0: [nx] start slice; out: store_all ? [(N+1)][nx] (row 0 = u0) : [nx] (the final slice).
-template <int P, typename R, bool COARSE, bool TRANS, int NT>
+template <int P, typename R, int COARSE, bool TRANS, int NT>
 __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, const R* g, const R* u0, R* out_all,
                                                 int store_all, int buf, unsigned char* smem_raw) {
   R* src = reinterpret_cast<R*>(smem_raw);
@@ -1424,7 +1635,7 @@ __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, con
   }
 }
 
-template <int P, typename R, bool COARSE, bool TRANS>
+template <int P, typename R, int COARSE, bool TRANS>
 __global__ void __launch_bounds__(slice_threads<P, R, COARSE>()) k_sequential_1d(LevelTables T, int N, const R* g,
                                                                                  const R* u0, R* out_all,
                                                                                  int store_all, int buf) {
@@ -1438,7 +1649,7 @@ __global__ void __launch_bounds__(slice_threads<P, R, COARSE>()) k_sequential_1d
 // NT threads a CTA (FP32 tiles of slices up to kPts * NT points; FP64 tiles use 512): a smaller CTA for
 // the problems with shorter slices, so that more of their intervals are resident on an SM at once.  The
 // minimum CTAs per SM scale with 512 / NT, keeping the register budget a thread of the 512-thread kernel.
-template <typename R, bool COARSE, int NT>
+template <typename R, int COARSE, int NT>
 __global__ void __launch_bounds__(NT, (COARSE ? 1 : (std::is_same<R, float>::value ? 2 : 3)) * (kSliceThreads / NT))
     k_relax_batched(const LevelTables* __restrict__ tabs, const RelaxArgs* __restrict__ args,
                     const BatchTile* __restrict__ tiles, const int* __restrict__ active, int buf) {
@@ -1472,7 +1683,7 @@ __global__ void __launch_bounds__(NT, kSliceThreads / NT)
   }
 }
 
-template <typename R, bool COARSE>
+template <typename R, int COARSE>
 __global__ void __launch_bounds__(kSliceThreads, 1) k_sequential_batched(const LevelTables* __restrict__ tabs,
                                                                          const SeqArgs* __restrict__ args,
                                                                          const BatchTile* __restrict__ tiles,
@@ -1489,7 +1700,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sequential_batched(const L
   }
 }
 
-template <int P, typename R, bool COARSE, bool TRANS>
+template <int P, typename R, int COARSE, bool TRANS>
 __global__ void __launch_bounds__(slice_threads<P, R, COARSE>()) k_apply_1d(LevelTables T, int n0, const R* in,
                                                                             R* out, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1521,11 +1732,11 @@ size_t smem_bytes(int buf, const LevelTables& T, bool coarse) {
   size_t b = 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double);
   if (T.gather_stage)
     b = ((b + 127) & ~(size_t)127) +
-        stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u, T.df).total;
+        stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf ? T.cf_floats : 0u, T.df).total;
   return b;
 }
 
-template <typename R, bool COARSE, bool TR>
+template <typename R, int COARSE, bool TR>
 cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
   const size_t sm = smem_bytes<R>(buf, T, COARSE);
@@ -1564,7 +1775,7 @@ cudaError_t relax_df_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStre
 #undef MGRIT_LAUNCH_DF
 }
 
-template <typename R, bool COARSE, bool TR>
+template <typename R, int COARSE, bool TR>
 cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, const void* u0, void* u, int store_all,
                                 cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
@@ -1583,7 +1794,7 @@ cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, cons
 #undef MGRIT_LAUNCH_SEQ
 }
 
-template <typename R, bool COARSE, bool TR>
+template <typename R, int COARSE, bool TR>
 cudaError_t apply_dispatch(const LevelTables& T, int n0, int count, const void* in, void* out, cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
   const size_t sm = smem_bytes<R>(buf, T, COARSE);
@@ -1677,7 +1888,7 @@ cudaError_t launch_relax_1d(const LevelTables& T, const RelaxArgs& a, int is_dou
   }
   if (T.trans) {
     if (!is_double) return cudaErrorInvalidValue;
-    return coarse ? relax_dispatch<double, true, true>(T, a, st) : relax_dispatch<double, false, true>(T, a, st);
+    return coarse ? relax_dispatch<double, 1, true>(T, a, st) : relax_dispatch<double, 0, true>(T, a, st);
   }
   if (is_double && coarse && T.cluster) {
     const int C = cluster_relax_size(T, a);
@@ -1688,8 +1899,9 @@ cudaError_t launch_relax_1d(const LevelTables& T, const RelaxArgs& a, int is_dou
     }
   }
   if (is_double)
-    return coarse ? relax_dispatch<double, true, false>(T, a, st) : relax_dispatch<double, false, false>(T, a, st);
-  return coarse ? relax_dispatch<float, true, false>(T, a, st) : relax_dispatch<float, false, false>(T, a, st);
+    return coarse ? relax_dispatch<double, 1, false>(T, a, st) : relax_dispatch<double, 0, false>(T, a, st);
+  if (coarse) return T.band ? relax_dispatch<float, 2, false>(T, a, st) : relax_dispatch<float, 1, false>(T, a, st);
+  return relax_dispatch<float, 0, false>(T, a, st);
 }
 
 cudaError_t launch_sequential_1d(const LevelTables& T, int N, const void* g, const void* u0, void* u, int store_all,
@@ -1697,14 +1909,16 @@ cudaError_t launch_sequential_1d(const LevelTables& T, int N, const void* g, con
   const bool coarse = T.solver != nullptr;
   if (T.trans) {
     if (!is_double) return cudaErrorInvalidValue;
-    return coarse ? sequential_dispatch<double, true, true>(T, N, g, u0, u, store_all, st)
-                  : sequential_dispatch<double, false, true>(T, N, g, u0, u, store_all, st);
+    return coarse ? sequential_dispatch<double, 1, true>(T, N, g, u0, u, store_all, st)
+                  : sequential_dispatch<double, 0, true>(T, N, g, u0, u, store_all, st);
   }
   if (is_double)
-    return coarse ? sequential_dispatch<double, true, false>(T, N, g, u0, u, store_all, st)
-                  : sequential_dispatch<double, false, false>(T, N, g, u0, u, store_all, st);
-  return coarse ? sequential_dispatch<float, true, false>(T, N, g, u0, u, store_all, st)
-                : sequential_dispatch<float, false, false>(T, N, g, u0, u, store_all, st);
+    return coarse ? sequential_dispatch<double, 1, false>(T, N, g, u0, u, store_all, st)
+                  : sequential_dispatch<double, 0, false>(T, N, g, u0, u, store_all, st);
+  if (coarse)
+    return T.band ? sequential_dispatch<float, 2, false>(T, N, g, u0, u, store_all, st)
+                  : sequential_dispatch<float, 1, false>(T, N, g, u0, u, store_all, st);
+  return sequential_dispatch<float, 0, false>(T, N, g, u0, u, store_all, st);
 }
 
 cudaError_t launch_apply_steps_1d(const LevelTables& T, int n0, int count, const void* in, void* out, int is_double,
@@ -1713,14 +1927,16 @@ cudaError_t launch_apply_steps_1d(const LevelTables& T, int n0, int count, const
   if (count <= 0) return cudaSuccess;
   if (T.trans) {
     if (!is_double) return cudaErrorInvalidValue;
-    return coarse ? apply_dispatch<double, true, true>(T, n0, count, in, out, st)
-                  : apply_dispatch<double, false, true>(T, n0, count, in, out, st);
+    return coarse ? apply_dispatch<double, 1, true>(T, n0, count, in, out, st)
+                  : apply_dispatch<double, 0, true>(T, n0, count, in, out, st);
   }
   if (is_double)
-    return coarse ? apply_dispatch<double, true, false>(T, n0, count, in, out, st)
-                  : apply_dispatch<double, false, false>(T, n0, count, in, out, st);
-  return coarse ? apply_dispatch<float, true, false>(T, n0, count, in, out, st)
-                : apply_dispatch<float, false, false>(T, n0, count, in, out, st);
+    return coarse ? apply_dispatch<double, 1, false>(T, n0, count, in, out, st)
+                  : apply_dispatch<double, 0, false>(T, n0, count, in, out, st);
+  if (coarse)
+    return T.band ? apply_dispatch<float, 2, false>(T, n0, count, in, out, st)
+                  : apply_dispatch<float, 1, false>(T, n0, count, in, out, st);
+  return apply_dispatch<float, 0, false>(T, n0, count, in, out, st);
 }
 
 void launch_sum(const double* v, int count, double* out, cudaStream_t st) { k_sum<<<1, 1024, 0, st>>>(v, count, out); }
@@ -1777,13 +1993,13 @@ void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem
   *buf = b;
   *smem = is_double ? smem_bytes<double>(b, T, coarse) : smem_bytes<float>(b, T, coarse);
   *region = T.gather_stage
-                ? stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf && T.pcr ? T.pcr_floats : 0u, T.df).total
+                ? stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf ? T.cf_floats : 0u, T.df).total
                 : 0;
 }
 
 namespace {
 
-template <typename R, bool CC, int NT>
+template <typename R, int CC, int NT>
 cudaError_t launch_batched_nt(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles, int ntiles,
                               const int* d_active, int buf, size_t smem, cudaStream_t st) {
   auto kern = k_relax_batched<R, CC, NT>;
@@ -1803,7 +2019,7 @@ cudaError_t launch_batched_df(const LevelTables* d_tabs, const RelaxArgs* d_args
   return cudaGetLastError();
 }
 
-template <bool CC>
+template <int CC>
 cudaError_t launch_batched_f32(const LevelTables* d_tabs, const RelaxArgs* d_args, const BatchTile* d_tiles, int ntiles,
                                const int* d_active, int buf, size_t smem, int threads, cudaStream_t st) {
   switch (threads) {
@@ -1832,11 +2048,12 @@ cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_a
     }
   }
   if (is_double) {
-    if (coarse) return launch_batched_nt<double, true, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
-    return launch_batched_nt<double, false, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+    if (coarse) return launch_batched_nt<double, 1, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
+    return launch_batched_nt<double, 0, kSliceThreads>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, st);
   }
-  if (coarse) return launch_batched_f32<true>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, threads, st);
-  return launch_batched_f32<false>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, threads, st);
+  if (coarse == 2) return launch_batched_f32<2>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, threads, st);
+  if (coarse) return launch_batched_f32<1>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, threads, st);
+  return launch_batched_f32<0>(d_tabs, d_args, d_tiles, ntiles, d_active, buf, smem, threads, st);
 }
 
 cudaError_t launch_sequential_batched(const LevelTables* d_tabs, const SeqArgs* d_args, const BatchTile* d_tiles,
@@ -1852,11 +2069,12 @@ cudaError_t launch_sequential_batched(const LevelTables* d_tabs, const SeqArgs* 
     return cudaGetLastError();                                                                                     \
   }
   if (is_double) {
-    if (coarse) MGRIT_BSEQ(double, true)
-    MGRIT_BSEQ(double, false)
+    if (coarse) MGRIT_BSEQ(double, 1)
+    MGRIT_BSEQ(double, 0)
   }
-  if (coarse) MGRIT_BSEQ(float, true)
-  MGRIT_BSEQ(float, false)
+  if (coarse == 2) MGRIT_BSEQ(float, 2)
+  if (coarse) MGRIT_BSEQ(float, 1)
+  MGRIT_BSEQ(float, 0)
 #undef MGRIT_BSEQ
 }
 
@@ -1892,6 +2110,27 @@ cudaError_t launch_gradient_a_1d(const LevelTables& T, const double* s64, const 
 }
 
 unsigned pcr_record_size(int nx, int p) { return pcr_record_floats(nx, p); }
+unsigned band_record_size(int nx, int p) { return band_record_floats(nx, p); }
+unsigned band_row_size(int nx, int p) { return band_row_floats(nx, p); }
+
+cudaError_t launch_sep_band(const float* sig32, int nt, int nx, int p, float* rec, float* ind, cudaStream_t st) {
+  const int B = (p + 1) / 2, P = nx / kPartRows;
+  if (P < kBandColours || P > 512) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)2 * nx * sizeof(float) + (size_t)(3 * B * B + B) * P * sizeof(float);
+  const unsigned stride = band_record_floats(nx, p), row = band_row_floats(nx, p);
+  cudaError_t e = cudaSuccess;
+#define MGRIT_BAND(BB)                                                                                     \
+  {                                                                                                        \
+    e = cudaFuncSetAttribute(k_sep_band<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+    if (e != cudaSuccess) return e;                                                                        \
+    k_sep_band<BB><<<nt, P, smem, st>>>(sig32, nx, rec, stride, row, ind);                                 \
+  }
+  if (B == 1) MGRIT_BAND(1)
+  else if (B == 2) MGRIT_BAND(2)
+  else MGRIT_BAND(3)
+#undef MGRIT_BAND
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pcr_coef(const float* sig32, int nt, int nx, int p, float* out, cudaStream_t st) {
   const int B = (p + 1) / 2;

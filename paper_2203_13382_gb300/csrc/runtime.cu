@@ -51,6 +51,9 @@ struct Level {
   float* sig32 = nullptr;   // sigma as FP32 rows (FP32 coarse levels, factorised on the fly)
   float* pcr32 = nullptr;   // FP32 coarse levels, p <= 3: block-PCR coefficients of every step
   unsigned pcr_floats = 0;
+  float* band32 = nullptr;  // FP32 coarse levels: the banded separator inverse of every step (probed in setup)
+  float* band_ind = nullptr;  // [8] its decay indicator (k_sep_band)
+  int band_w = 0;           // half-bandwidth in use (0: block PCR / on the fly), chosen in setup_finish
   size_t solver_stride = 0;
   int P = 0;
   int is_double = 1;  // arithmetic of this level's cycle
@@ -279,6 +282,10 @@ struct mgrit_handle {
     T.gather_stage = 0;
     T.pcr = nullptr;
     T.pcr_floats = 0;
+    T.band = 0;
+    T.cf_src = nullptr;
+    T.cf_stride = 0;
+    T.cf_floats = 0;
     T.trans = 0;
     T.reverse = 0;
     T.frange = L.frange;
@@ -305,6 +312,17 @@ struct mgrit_handle {
         T.solver_stride = (size_t)grid.nx;
         T.pcr = L.pcr32;  // p <= 3: the block-PCR coefficients precomputed in setup
         T.pcr_floats = L.pcr_floats;
+        if (L.band_w > 0) {  // the banded separator inverse, rows -W .. W of the stored record
+          const unsigned row = band_row_size(grid.nx, order);
+          T.band = L.band_w;
+          T.cf_src = L.band32 + (size_t)(kBandMaxHalfWidth - L.band_w) * row;
+          T.cf_stride = band_record_size(grid.nx, order);
+          T.cf_floats = (unsigned)(2 * L.band_w + 1) * row;
+        } else if (L.pcr32) {
+          T.cf_src = L.pcr32;
+          T.cf_stride = L.pcr_floats;
+          T.cf_floats = L.pcr_floats;
+        }
       }
     }
     return T;
@@ -553,6 +571,7 @@ mgrit_status mgrit_default_options(mgrit_options* opt) {
   opt->diverge_ratio = 1e3;
   opt->fine_only = 0;
   opt->solve_mode = 0;
+  opt->coarse_band = 1;
   opt->test_wait_cycles = 0;
   return MGRIT_OK;
 }
@@ -573,6 +592,32 @@ static mgrit_status setup_finish(mgrit_handle** out) {
     delete h;
     *out = nullptr;
     return fail(MGRIT_ESINGULAR, "a correction matrix has a (near) zero pivot");
+  }
+  // half-bandwidth of each FP32 coarse level's separator inverse: the smallest W <= kBandMaxHalfWidth
+  // beyond which every entry is below 1e-9 of its diagonal block, and whose record fits the shared memory
+  // of the relaxation kernel; else the block PCR (p <= 3) or the on-the-fly factorisation (p = 5)
+  for (size_t l = 1; l < h->levels.size(); ++l) {
+    Level& L = h->levels[l];
+    if (!L.band_ind) continue;
+    float ind[8] = {};
+    if (cudaMemcpy(ind, L.band_ind, sizeof(ind), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    int W = 0;
+    for (int w = 1; w <= kBandMaxHalfWidth && !W; ++w) {
+      bool ok = true;
+      for (int t = w + 1; t < 8; ++t) ok = ok && ind[t] < 1e-9f;  // NaN fails
+      if (ok) W = w;
+    }
+    for (; W > 0; --W) {  // the record of the step must fit next to the slices and staged rows
+      L.band_w = W;
+      int buf;
+      size_t smem, region;
+      relax_smem_need(h->tables((int)l, 0), 0, &buf, &smem, &region);
+      if (smem <= 227 * 1024) break;
+    }
+    L.band_w = W;
   }
   h->collect_phase_times();
   h->setup_launches = h->call_launches;
@@ -613,6 +658,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
   if (opt.test_wait_cycles < 0) return fail(MGRIT_EINVAL, "test_wait_cycles must be >= 0");
   if (opt.fine_only != 0 && opt.fine_only != 1) return fail(MGRIT_EINVAL, "fine_only must be 0 or 1");
   if (opt.solve_mode != 0 && opt.solve_mode != 1) return fail(MGRIT_EINVAL, "solve_mode must be 0 or 1");
+  if (opt.coarse_band != 0 && opt.coarse_band != 1) return fail(MGRIT_EINVAL, "coarse_band must be 0 or 1");
   if (opt.solve_mode == 1 && grid->dim == 1 && opt.precision == 1 && !opt.coarse_fp64)
     return fail(MGRIT_EUNSUPPORTED, "1D GMRES correction solves (solve_mode 1) need FP64 coarse levels");
   if (opt.fine_only && grid->dim != 1) return fail(MGRIT_EUNSUPPORTED, "fine_only handles are 1D");
@@ -690,6 +736,10 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
           if (p <= 3) {
             L.pcr_floats = pcr_record_size(nx, p);
             if ((st = h->alloc(&L.pcr32, (size_t)L.nt * L.pcr_floats)) != MGRIT_OK) return cleanup_fail(st);
+          }
+          if (opt.coarse_band && nx / 8 >= 16) {  // 8-row partitions, 16 probe colours
+            if ((st = h->alloc(&L.band32, (size_t)L.nt * band_record_size(nx, p))) != MGRIT_OK) return cleanup_fail(st);
+            if ((st = h->alloc(&L.band_ind, 8)) != MGRIT_OK) return cleanup_fail(st);
           }
         }
       }
@@ -780,7 +830,11 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
       const int ev = h->phase_begin();
       launch_axpy_convert(1, L.sigma, L.sig32, nullptr, (long long)L.nt * np * dim, s);
       if (L.pcr32) launch_pcr_coef(L.sig32, L.nt, nx, p, L.pcr32, s);
-      h->phase_end(MGRIT_PHASE_FACTOR, ev, L.pcr32 ? 2 : 1);
+      if (L.band32) {
+        cudaMemsetAsync(L.band_ind, 0, 8 * sizeof(float), s);
+        launch_sep_band(L.sig32, L.nt, nx, p, L.band32, L.band_ind, s);
+      }
+      h->phase_end(MGRIT_PHASE_FACTOR, ev, (L.pcr32 ? 2 : 1) + (L.band32 ? 1 : 0));
     }
     if ((st = launch_fail("setup")) != MGRIT_OK) return st;
   }
@@ -1210,6 +1264,13 @@ mgrit_status mgrit_level_info(const mgrit_handle* h, int level, int* nt_level, i
   return MGRIT_OK;
 }
 
+mgrit_status mgrit_level_band(const mgrit_handle* h, int level, int* half_width) {
+  if (!h || !half_width) return fail(MGRIT_EINVAL, "NULL argument");
+  if (level < 0 || level >= (int)h->levels.size()) return fail(MGRIT_EINVAL, "level out of range");
+  *half_width = h->levels[level].band_w;
+  return MGRIT_OK;
+}
+
 mgrit_status mgrit_copy_offsets(const mgrit_handle* h, int level, double* d_out) {
   if (!h || !d_out) return fail(MGRIT_EINVAL, "NULL argument");
   if (level < 0 || level >= (int)h->levels.size()) return fail(MGRIT_EINVAL, "level out of range");
@@ -1503,6 +1564,8 @@ int cta_threads(int nx) {
   return t < 32 ? 32 : (t > 512 ? 512 : t);
 }
 
+// coarse: 0 fine-level tiles; 1 coarse tiles solved by block PCR or on the fly; 2 coarse tiles with the
+// banded separator inverse (each kind is its own kernel instantiation, so a phase takes one of them).
 template <class F>
 mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F per_problem, int threads = 0) {
   mgrit_batch::Phase ph{0, is_double, coarse, (int)b->tiles.size(), 0, 0, 0, 0, 0, threads ? threads : 512};
@@ -1512,6 +1575,7 @@ mgrit_batch::Phase add_relax_phase(mgrit_batch* b, int is_double, int coarse, F 
     RelaxArgs a;
     int ntile = 0;
     if (!per_problem(q, T, a, ntile)) continue;
+    if (coarse && (T.band > 0 ? 2 : 1) != coarse) continue;
     T.err = b->d_err;
     const int ti = (int)b->tabs.size(), ai = (int)b->args.size();
     b->tabs.push_back(T);
@@ -1537,10 +1601,11 @@ void add_relax_phases(mgrit_batch* b, int is_double, int coarse, F per_problem, 
     list.push_back(add_relax_phase(b, is_double, coarse, per_problem));
     return;
   }
-  for (int t : {512, 256, 128, 64, 32}) {
-    mgrit_batch::Phase ph = add_relax_phase(b, is_double, coarse, per_problem, t);
-    if (ph.ntiles) list.push_back(ph);
-  }
+  for (int t : {512, 256, 128, 64, 32})
+    for (int c : coarse ? std::initializer_list<int>{2, 1} : std::initializer_list<int>{0}) {
+      mgrit_batch::Phase ph = add_relax_phase(b, is_double, c, per_problem, t);
+      if (ph.ntiles) list.push_back(ph);
+    }
 }
 
 }  // namespace
@@ -1657,28 +1722,31 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
         nt = J;
         return true;
       }, b->down);
-    // coarsest levels reached at this depth: sequential solves
-    mgrit_batch::Phase ph{1, 0, 1, (int)b->tiles.size(), 0, 0, 0, 0, 0, 512};
-    for (int q = 0; q < nprob; ++q) {
-      mgrit_handle* h = b->hs[q];
-      if ((int)h->levels.size() - 1 != d) continue;
-      Level& L = h->levels[d];
-      LevelTables T = h->tables(d, 0);
-      T.err = b->d_err;
-      SeqArgs sa{L.nt, L.G, nullptr, L.E, 1};
-      const int ti = (int)b->tabs.size(), ai = (int)b->seqs.size();
-      b->tabs.push_back(T);
-      b->seqs.push_back(sa);
-      int buf;
-      size_t smem, region;
-      relax_smem_need(T, 0, &buf, &smem, &region);
-      ph.buf = std::max(ph.buf, buf);
-      ph.region = std::max(ph.region, region);
-      b->tiles.push_back(BatchTile{ti, ai, 0, q});
+    // coarsest levels reached at this depth: sequential solves (band and other solves in separate phases)
+    for (int cs : {2, 1}) {
+      mgrit_batch::Phase ph{1, 0, cs, (int)b->tiles.size(), 0, 0, 0, 0, 0, 512};
+      for (int q = 0; q < nprob; ++q) {
+        mgrit_handle* h = b->hs[q];
+        if ((int)h->levels.size() - 1 != d) continue;
+        Level& L = h->levels[d];
+        LevelTables T = h->tables(d, 0);
+        if ((T.band > 0 ? 2 : 1) != cs) continue;
+        T.err = b->d_err;
+        SeqArgs sa{L.nt, L.G, nullptr, L.E, 1};
+        const int ti = (int)b->tabs.size(), ai = (int)b->seqs.size();
+        b->tabs.push_back(T);
+        b->seqs.push_back(sa);
+        int buf;
+        size_t smem, region;
+        relax_smem_need(T, 0, &buf, &smem, &region);
+        ph.buf = std::max(ph.buf, buf);
+        ph.region = std::max(ph.region, region);
+        b->tiles.push_back(BatchTile{ti, ai, 0, q});
+      }
+      ph.ntiles = (int)b->tiles.size() - ph.tile_off;
+      ph.smem = batched_smem(ph.buf, 0, ph.region);
+      if (ph.ntiles) b->down.push_back(ph);
     }
-    ph.ntiles = (int)b->tiles.size() - ph.tile_off;
-    ph.smem = batched_smem(ph.buf, 0, ph.region);
-    if (ph.ntiles) b->down.push_back(ph);
   }
   for (int d = maxL - 2; d >= 1; --d)
     add_relax_phases(b, 0, 1, [&](int q, LevelTables& T, RelaxArgs& a, int& nt) {

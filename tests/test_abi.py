@@ -92,6 +92,7 @@ def test_host_only_calls(lib):
     ("test_wait_cycles", -1, 1, b"test_wait_cycles"),
     ("fine_only", 2, 1, b"fine_only"),
     ("solve_mode", 2, 1, b"solve_mode"),
+    ("coarse_band", 2, 1, b"coarse_band"),
 ])
 def test_option_errors_are_reported_before_any_cuda_call(lib, field, value, status, msg):
     """Every option is range-checked by mgrit_setup before it touches the device (here: no GPU at all)."""
@@ -164,6 +165,7 @@ def test_null_handles_are_argument_errors(lib):
         lambda: lib.mgrit_solve_to_reference(None, None, None, None, None, 0.0, ctypes.byref(st)),
         lambda: lib.mgrit_adjoint_solve(None, None, None, None, None, ctypes.byref(st)),
         lambda: lib.mgrit_level_info(None, 0, ctypes.byref(a), ctypes.byref(b)),
+        lambda: lib.mgrit_level_band(None, 0, ctypes.byref(a)),
         lambda: lib.mgrit_copy_offsets(None, 0, None),
         lambda: lib.mgrit_copy_sigma(None, 0, None),
         lambda: lib.mgrit_apply_step(None, 0, 0, 1, None, None),
