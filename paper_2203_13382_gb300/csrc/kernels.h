@@ -84,7 +84,7 @@ struct LevelTables {
   const float* eps32;     // [nt][npts] or NULL (2D: x then y blocks)
   const float* eps_lo;    // level 0 of FP32-bulk handles: eps - eps32 rounded to FP32 ([nt][npts]) or NULL
   // df = 1: a level-0 FP64 pass of the FP32-bulk cycle, run in FP32 pairs from (eps32, eps_lo) instead of
-  // FP64 weights (df32.cuh); its tables are staged like the FP32 levels' (gather_stage = 1)
+  // FP64 weights (df32.cuh), reading its tables straight from global memory
   int df;
   long long table_stride; // elements per step row of shift / eps32 (npts)
   int nt;                 // steps on this level (for 2D block offsets)
@@ -242,10 +242,11 @@ void launch_fill_zero(void* y, long long bytes, cudaStream_t st);
 struct Scratch2d {
   void* cur;
   void* nxt;
-  void* basis;     // [J][kmax + 1][npts]
+  void* basis;     // [J][kmax + 1][npts] ([J][kmax + 2][npts] with restarts > 1)
   int kmax;        // GMRES iterations at most (<= 10)
   double rtol;     // GMRES relative residual
   double* partial; // [J][64]
+  int restarts;    // 1: one GMRES(kmax) cycle (the paper's inexact solve); > 1: restarted cycles to rtol
 };
 
 // 2D passes with the same semantics as launch_relax_1d / launch_sequential_1d / launch_apply_steps_1d

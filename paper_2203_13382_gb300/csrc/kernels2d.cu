@@ -303,16 +303,18 @@ __device__ __forceinline__ double cta_subtract_sumsq(const R* V, long long N, R*
 }
 
 // One CTA per interval j: b (= rhs, in place -> solution) of the system of step n(j) = n0 + j*m
-// (row nt_rev - 1 - n(j) when nt_rev > 0; TRANS solves with M^T).  basis: [J][kmax + 1][N] scratch.
-// DIM = 1: the 1D system I - diag(sigma_x) D of nx unknowns (sigma_y unused).
-// GMRES (Arnoldi with classical Gram-Schmidt: the projections on all basis vectors in one pass over w,
-// then one update pass; Givens rotations), zero initial guess, stop when the least-squares residual
-// <= rtol ||b|| or after kmax iterations.
+// (row nt_rev - 1 - n(j) when nt_rev > 0; TRANS solves with M^T).  basis: [J][kmax + 1][N] scratch
+// ([J][kmax + 2][N] with restarts > 1).  DIM = 1: the 1D system I - diag(sigma_x) D of nx unknowns
+// (sigma_y unused).  GMRES (Arnoldi with classical Gram-Schmidt: the projections on all basis vectors in
+// one pass over w, then one update pass; Givens rotations), zero initial guess, stop when the
+// least-squares residual <= rtol ||b|| or after kmax iterations.  restarts > 1 (the exact solves of
+// solve_mode 2): up to that many GMRES(kmax) cycles, each from the residual b - M x of the solution
+// accumulated so far (the extra scratch vector), until the true residual is <= rtol ||b||.
 template <int B, typename R, bool TRANS, int DIM = 2>
 __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restrict__ sigma_x,
                                                         const R* __restrict__ sigma_y, int nx, int n0, int m,
                                                         int nt_rev, R* __restrict__ bx_all, R* __restrict__ basis,
-                                                        int kmax, double rtol) {
+                                                        int kmax, double rtol, int restarts = 1) {
   __shared__ double red[40];
   __shared__ double H[11][10];
   __shared__ double cs[10], sn[10], gv[11], yv[10];
@@ -324,11 +326,36 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restr
   const R* sx = sigma_x + (size_t)n * N;
   const R* sy = sigma_y + (size_t)n * N;
   R* b = bx_all + (size_t)j * N;
-  R* V = basis + (size_t)j * (kmax + 1) * N;
-  const double beta = sqrt(cta_dot<R>(b, b, N, red));
-  if (beta == 0.0) return;  // x = 0
+  const int nvec = restarts > 1 ? kmax + 2 : kmax + 1;
+  R* V = basis + (size_t)j * nvec * N;
+  R* xacc = restarts > 1 ? V + (size_t)(kmax + 1) * N : nullptr;  // the accumulated solution
+  const double beta0 = sqrt(cta_dot<R>(b, b, N, red));
+  if (beta0 == 0.0) return;  // x = 0
+  const double target = rtol * beta0;
   __shared__ double sc[11], cf[10];  // v_t = sc[t] u_t; projection coefficients of the update pass
-  for (long long q = threadIdx.x; q < N; q += blockDim.x) V[q] = b[q];  // u_0 = b, v_0 = b / beta
+  for (long long q = threadIdx.x; q < N; q += blockDim.x) {
+    V[q] = b[q];  // u_0 = b, v_0 = b / beta
+    if (xacc) xacc[q] = (R)0;
+  }
+  double beta = beta0;
+  for (int cyc = 0; cyc < restarts; ++cyc) {
+  if (cyc > 0) {  // restart from the true residual of the accumulated solution
+    __syncthreads();
+    R rr = (R)0;
+    for (long long q = threadIdx.x; q < N; q += blockDim.x) {
+      R mq;
+      if constexpr (DIM == 1) mq = TRANS ? apply_MT1d<B, R>(xacc, sx, q, nx) : apply_M1d<B, R>(xacc, sx, q, nx);
+      else mq = TRANS ? apply_MT<B, R>(xacc, sx, sy, q, nx) : apply_M<B, R>(xacc, sx, sy, q, nx);
+      const R r = b[q] - mq;
+      V[q] = r;
+      rr += r * r;
+    }
+    const double t = block_sum_r<R>(rr, red);
+    if (threadIdx.x == 0) red[34] = t;
+    __syncthreads();
+    beta = sqrt(red[34]);
+    if (!(beta > target)) break;  // converged (or a non-finite residual: stop)
+  }
   if (threadIdx.x == 0) {
     gv[0] = beta;
     for (int t = 1; t <= kmax; ++t) gv[t] = 0.0;
@@ -372,7 +399,7 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restr
     }
     __syncthreads();
     kused = kk + 1;
-    if (red[36] <= rtol * beta || !(hn > 0.0)) break;
+    if (red[36] <= target || !(hn > 0.0)) break;
   }
   if (threadIdx.x == 0) {  // back substitution R y = g
     for (int t = kused - 1; t >= 0; --t) {
@@ -387,8 +414,13 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d(const R* __restr
   for (long long q = threadIdx.x; q < N; q += blockDim.x) {
     R x = (R)0;
     for (int t = 0; t < kused; ++t) x += yr[t] * V[(size_t)t * N + q];
-    b[q] = x;
+    if (xacc) xacc[q] += x;
+    else b[q] = x;
   }
+  if (!xacc) return;
+  }
+  __syncthreads();
+  for (long long q = threadIdx.x; q < N; q += blockDim.x) b[q] = xacc[q];
 }
 
 // The same GMRES with one system spread over a thread-block cluster of C CTAs (C = gridDim / J): CTA
@@ -514,9 +546,10 @@ __global__ void __launch_bounds__(gmres_threads<R>()) k_gmres2d_cluster(const R*
 // (2D).  DIM = 1: the 1D systems, one CTA each (sig holds sigma only, [nt][nx]).
 template <int B, typename R, bool TRANS, int DIM = 2>
 cudaError_t launch_gmres(const R* sig, long long N, int nt, int nx, int n0, int m, int ntr, R* b, R* basis,
-                         int kmax, double rtol, int J, cudaStream_t st) {
-  if constexpr (DIM == 1) {
-    k_gmres2d<B, R, TRANS, 1><<<J, gmres_threads<R>(), 0, st>>>(sig, sig, nx, n0, m, ntr, b, basis, kmax, rtol);
+                         int kmax, double rtol, int J, cudaStream_t st, int restarts = 1) {
+  if (DIM == 1 || restarts > 1) {  // one CTA per system (restarted solves keep their solution in scratch)
+    k_gmres2d<B, R, TRANS, DIM><<<J, gmres_threads<R>(), 0, st>>>(sig, DIM == 1 ? sig : sig + (size_t)nt * N, nx, n0, m,
+                                                                   ntr, b, basis, kmax, rtol, restarts);
     return cudaGetLastError();
   }
   int C = 1;
@@ -636,9 +669,9 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
       const R* sig = (const R*)T.solver;  // sigma [nt][nx]
       const int B = (T.p + 1) / 2;
       cudaError_t e;
-      if (B == 1) e = launch_gmres<1, R, false, 1>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
-      else if (B == 2) e = launch_gmres<2, R, false, 1>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
-      else e = launch_gmres<3, R, false, 1>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
+      if (B == 1) e = launch_gmres<1, R, false, 1>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st, S.restarts);
+      else if (B == 2) e = launch_gmres<2, R, false, 1>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st, S.restarts);
+      else e = launch_gmres<3, R, false, 1>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st, S.restarts);
       if (e != cudaSuccess) return e;
       k_add_rows<R><<<grid, kThreads2d, 0, st>>>(dst, g, m, k, n0, N, fstore);
     }
@@ -652,13 +685,13 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
         cudaError_t e;
         if (B == 1)
           e = launch_gmres<1, double, true>(sig, N, T.nt, T.nx, n_first, m, ntr, src, (double*)S.basis, S.kmax, S.rtol,
-                                            J, st);
+                                            J, st, S.restarts);
         else if (B == 2)
           e = launch_gmres<2, double, true>(sig, N, T.nt, T.nx, n_first, m, ntr, src, (double*)S.basis, S.kmax, S.rtol,
-                                            J, st);
+                                            J, st, S.restarts);
         else
           e = launch_gmres<3, double, true>(sig, N, T.nt, T.nx, n_first, m, ntr, src, (double*)S.basis, S.kmax, S.rtol,
-                                            J, st);
+                                            J, st, S.restarts);
         if (e != cudaSuccess) return e;
       }
       if (T.p == 1) k_step2d_T<1><<<grid, kThreads2d, 0, st>>>(T, src, dst, m, k, n0, g, fstore);
@@ -679,9 +712,9 @@ cudaError_t step_all(const LevelTables& T, const Scratch2d& S, R* src, R* dst, i
     const R* sig = (const R*)T.solver;
     const int B = (T.p + 1) / 2;
     cudaError_t e;
-    if (B == 1) e = launch_gmres<1, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
-    else if (B == 2) e = launch_gmres<2, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
-    else e = launch_gmres<3, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st);
+    if (B == 1) e = launch_gmres<1, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st, S.restarts);
+    else if (B == 2) e = launch_gmres<2, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st, S.restarts);
+    else e = launch_gmres<3, R, false>(sig, N, T.nt, T.nx, n_first, m, 0, dst, (R*)S.basis, S.kmax, S.rtol, J, st, S.restarts);
     if (e != cudaSuccess) return e;
     k_add_rows<R><<<grid, kThreads2d, 0, st>>>(dst, g, m, k, n0, N, fstore);
   }

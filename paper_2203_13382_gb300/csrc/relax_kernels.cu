@@ -1483,10 +1483,11 @@ __global__ void __launch_bounds__(slice_threads<P, R, COARSE>(),
 //
 // The exact C-point residual of the FP64 iterate (MODE_RES), and the final post F-relaxation into the
 // FP64 solution (MODE_POST), with the fine SL step of Sec. 2.1 evaluated in FP32 pairs (df32.cuh, about
-// 48 bits): the slice lives in shared memory as (hi, lo) pairs, the tables of a step (eps hi, shift,
-// eps lo) are staged by TMA one step ahead, and the Lagrange weights are formed in registers.  FP64
-// appears only where the interval meets FP64 data: the start slice, the C-point residual, the F-point
-// stores.
+// 48 bits): the slice lives in shared memory as (hi, lo) pairs and the Lagrange weights are formed in
+// registers from the step's eps (hi, lo) and shift rows, which are read straight from global memory
+// (coalesced); with the slices alone in shared memory and at most 64 registers a thread, two 512-thread
+// CTAs share an SM, whose warps hide the loads.  FP64 appears only where the interval meets FP64 data:
+// the start slice, the C-point residual, the F-point stores.  Level 0 adds no right-hand side (g = 0).
 
 // dst[i] = (S_n src)_i for the points of this thread, src with its periodic halo (src[nx + t] = src[t]).
 template <int P, int NT>
@@ -1497,7 +1498,7 @@ __device__ __forceinline__ void apply_gather_df(const float* __restrict__ eh, co
   for (int q = 0; q < kPts; ++q) {
     const int i = threadIdx.x + q * NT;
     if (i < nx) {
-      const df32 v = df_interp<P>(df32{eh[i], el[i]}, src + wrap_pow2(i + (int)sh[i], nx));
+      const df32 v = df_interp<P>(df32{__ldg(eh + i), __ldg(el + i)}, src + wrap_pow2(i + (int)__ldg(sh + i), nx));
       dst[i] = make_float2(v.h, v.l);
     }
   }
@@ -1510,8 +1511,6 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
   float2* dst = src + buf;
   double* red = reinterpret_cast<double*>(dst + buf);
   const int nx = T.nx;
-  Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(float2) + 64 * sizeof(double), T, false);
-  stage_prefetch_first<P, false>(stg, T, (j < a.J && a.nsteps > 0) ? j * a.m : -1);
   {
     const double* st = a.start ? (const double*)a.start + (size_t)j * a.start_stride : nullptr;
     const double* co = a.corr ? (const double*)a.corr + (size_t)j * a.corr_stride : nullptr;
@@ -1530,13 +1529,9 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
   double sq = 0.0;
   for (int k = 0; k < a.nsteps; ++k) {
     const int n = j * a.m + k;
-    const int next_n = k + 1 < a.nsteps ? n + 1 : -1;
-    if (!stage_acquire(stg, T, n, next_n, false)) return;
-    const int b = stg.cur;
-    apply_gather_df<P, NT>(stg.eps(b), stg.sig(b), stg.sh(b), src, dst, nx);
+    const size_t row = (size_t)n * T.table_stride;
+    apply_gather_df<P, NT>(T.eps32 + row, T.eps_lo + row, T.shift + row, src, dst, nx);
     __syncthreads();
-    stg.cur ^= 1;
-    stg.pending = next_n;
     const bool last = (k == a.m - 1);
     if (!last) {
       if (a.fstore) {  // F-point of the FP64 solution
@@ -1567,15 +1562,8 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
         if (a.norm_partial) sq += v * v;
       }
     }
-    bool ahead_ok = true;
-    if (k + 1 < a.nsteps) {
-      write_halo(dst, nx);
-      ahead_ok = stage_wait_ahead(stg);
-    }
-    if (__syncthreads_or(!ahead_ok)) {
-      stage_abandon(stg, T, false);
-      return;
-    }
+    if (k + 1 < a.nsteps) write_halo(dst, nx);
+    __syncthreads();
     float2* t = src;
     src = dst;
     dst = t;
@@ -1587,7 +1575,7 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
 }
 
 template <int P>
-__global__ void __launch_bounds__(kSliceThreads, 1) k_relax_df_1d(LevelTables T, RelaxArgs a, int buf) {
+__global__ void __launch_bounds__(kSliceThreads, 2) k_relax_df_1d(LevelTables T, RelaxArgs a, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   relax_body_df<P, kSliceThreads>(T, a, blockIdx.x, buf, smem_raw);
 }
@@ -1668,7 +1656,7 @@ __global__ void __launch_bounds__(NT, (COARSE ? 1 : (std::is_same<R, float>::val
 // The FP32-pair level-0 passes of every problem of a batch (one tile per interval), NT threads a CTA
 // (slices of at most kPts * NT points), as the FP32 batched passes.
 template <int NT>
-__global__ void __launch_bounds__(NT, kSliceThreads / NT)
+__global__ void __launch_bounds__(NT, 2 * kSliceThreads / NT)
     k_relax_batched_df(const LevelTables* __restrict__ tabs, const RelaxArgs* __restrict__ args,
                        const BatchTile* __restrict__ tiles, const int* __restrict__ active, int buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

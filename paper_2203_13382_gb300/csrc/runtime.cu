@@ -299,9 +299,9 @@ struct mgrit_handle {
       if (T.solver && grid.dim == 1) T.solver = L.solverT;  // 2D: GMRES with M^T on the same sigma
       return T;
     }
-    if (l == 0 && is_double && L.eps_lo) {  // the FP64 passes of level 0 in FP32 pairs (staged tables)
+    if (l == 0 && is_double && L.eps_lo) {  // the FP64 passes of level 0 in FP32 pairs (tables from global)
       T.df = 1;
-      T.gather_stage = 1;
+      T.gather_stage = 0;
       return T;
     }
     if (grid.dim == 1 && !is_double) {
@@ -657,7 +657,9 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
   if (!(opt.diverge_ratio >= 0.0)) return fail(MGRIT_EINVAL, "diverge_ratio must be >= 0");
   if (opt.test_wait_cycles < 0) return fail(MGRIT_EINVAL, "test_wait_cycles must be >= 0");
   if (opt.fine_only != 0 && opt.fine_only != 1) return fail(MGRIT_EINVAL, "fine_only must be 0 or 1");
-  if (opt.solve_mode != 0 && opt.solve_mode != 1) return fail(MGRIT_EINVAL, "solve_mode must be 0 or 1");
+  if (opt.solve_mode < 0 || opt.solve_mode > 2) return fail(MGRIT_EINVAL, "solve_mode must be 0, 1 or 2");
+  if (opt.solve_mode == 2 && grid->dim == 2 && opt.precision == 1 && !opt.coarse_fp64)
+    return fail(MGRIT_EUNSUPPORTED, "exact 2D correction solves (solve_mode 2) need FP64 coarse levels");
   if (opt.coarse_band != 0 && opt.coarse_band != 1) return fail(MGRIT_EINVAL, "coarse_band must be 0 or 1");
   if (opt.solve_mode == 1 && grid->dim == 1 && opt.precision == 1 && !opt.coarse_fp64)
     return fail(MGRIT_EUNSUPPORTED, "1D GMRES correction solves (solve_mode 1) need FP64 coarse levels");
@@ -754,10 +756,17 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
     const size_t rsz = (fp32 && !cf64) ? sizeof(float) : sizeof(double);  // coarse GMRES basis
     h->s2d.kmax = opt.gmres_maxit;
     h->s2d.rtol = opt.gmres_rtol;
+    h->s2d.restarts = 1;
+    if (opt.solve_mode == 2) {  // exact 2D correction solves: restarted GMRES(10) to 1e-13
+      h->s2d.kmax = 10;
+      h->s2d.rtol = 1e-13;
+      h->s2d.restarts = 200;
+    }
     if ((st = h->alloc((char**)&h->s2d.cur, jmax * np * sizeof(double))) != MGRIT_OK) return cleanup_fail(st);
     if ((st = h->alloc((char**)&h->s2d.nxt, jmax * np * sizeof(double))) != MGRIT_OK) return cleanup_fail(st);
     if (opt.coarse_op == 0 &&
-        (st = h->alloc((char**)&h->s2d.basis, jc * (opt.gmres_maxit + 1) * np * rsz)) != MGRIT_OK)
+        (st = h->alloc((char**)&h->s2d.basis, jc * (h->s2d.kmax + (h->s2d.restarts > 1 ? 2 : 1)) * np * rsz)) !=
+            MGRIT_OK)
       return cleanup_fail(st);
     if ((st = h->alloc(&h->s2d.partial, jmax * 64)) != MGRIT_OK) return cleanup_fail(st);
   }
@@ -1601,9 +1610,12 @@ void add_relax_phases(mgrit_batch* b, int is_double, int coarse, F per_problem, 
     list.push_back(add_relax_phase(b, is_double, coarse, per_problem));
     return;
   }
+  // coarse passes: the band tiles and the others in separate launches (their kernels differ)
+  const int kinds[2] = {coarse ? 2 : 0, 1};
+  const int nkinds = coarse ? 2 : 1;
   for (int t : {512, 256, 128, 64, 32})
-    for (int c : coarse ? std::initializer_list<int>{2, 1} : std::initializer_list<int>{0}) {
-      mgrit_batch::Phase ph = add_relax_phase(b, is_double, c, per_problem, t);
+    for (int i = 0; i < nkinds; ++i) {
+      mgrit_batch::Phase ph = add_relax_phase(b, is_double, kinds[i], per_problem, t);
       if (ph.ntiles) list.push_back(ph);
     }
 }

@@ -91,7 +91,7 @@ def test_host_only_calls(lib):
     ("diverge_ratio", -1.0, 1, b"diverge_ratio"),
     ("test_wait_cycles", -1, 1, b"test_wait_cycles"),
     ("fine_only", 2, 1, b"fine_only"),
-    ("solve_mode", 2, 1, b"solve_mode"),
+    ("solve_mode", 3, 1, b"solve_mode"),
     ("coarse_band", 2, 1, b"coarse_band"),
 ])
 def test_option_errors_are_reported_before_any_cuda_call(lib, field, value, status, msg):
