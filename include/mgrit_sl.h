@@ -127,7 +127,7 @@ typedef struct {
                        levels only (precision 0, or coarse_fp64 = 1), single problems, no adjoint.
                        2D correction solves take GMRES(gmres_maxit, gmres_rtol) in modes 0 and 1;
                        2: exact solves everywhere -- 1D as mode 0, 2D restarted GMRES(10) to a relative
-                       residual of 1e-13 (FP64 coarse levels only), which keeps MGRIT a linear iteration. */
+                       residual of 1e-14 (FP64 coarse levels only), which keeps MGRIT a linear iteration. */
   int coarse_band;  /* 1D FP32 coarse levels.  1 (default): where the separator block of M^{-1} (M = I -
                        diag(sigma) D, 8-row partitions) falls below 1e-9 of its diagonal blocks beyond at
                        most 4 partitions, setup stores it as a band and each correction solve applies it in

@@ -757,10 +757,10 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
     h->s2d.kmax = opt.gmres_maxit;
     h->s2d.rtol = opt.gmres_rtol;
     h->s2d.restarts = 1;
-    if (opt.solve_mode == 2) {  // exact 2D correction solves: restarted GMRES(10) to 1e-13
+    if (opt.solve_mode == 2) {  // exact 2D correction solves: restarted GMRES(10) to 1e-14
       h->s2d.kmax = 10;
-      h->s2d.rtol = 1e-13;
-      h->s2d.restarts = 200;
+      h->s2d.rtol = 1e-14;
+      h->s2d.restarts = 100;
     }
     if ((st = h->alloc((char**)&h->s2d.cur, jmax * np * sizeof(double))) != MGRIT_OK) return cleanup_fail(st);
     if ((st = h->alloc((char**)&h->s2d.nxt, jmax * np * sizeof(double))) != MGRIT_OK) return cleanup_fail(st);

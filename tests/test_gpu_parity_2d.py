@@ -5,7 +5,9 @@ inexact GMRES (zero guess, at most 10 iterations, relative residual 1e-2; Sec. 4
 Tolerances: setup arrays, single steps and sequential stepping agree to 1e-12 (FP64, rounding order
 only).  With the inexact solve the MGRIT iterates depend on rounding inside GMRES, so the converged
 solutions are compared where the theory fixes them: both equal the unique fine-level solution to the
-stopping tolerance (1e-9 relative), with identical iteration counts.
+stopping tolerance (1e-9 relative), with identical iteration counts.  With exact correction solves
+(solve_mode 2: restarted GMRES to 1e-14 on the GPU, sparse LU in the oracle) MGRIT is a linear iteration
+again and the FP64 iterates are compared element by element (1e-12), residual histories included.
 """
 
 import numpy as np
@@ -118,3 +120,17 @@ def test_graph_replay_matches_direct_launches_2d():
         out, st = h.solve(u0, U0)
         outs.append((out.cpu(), st["iterations"]))
     assert torch.equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_mgrit_2d_exact_correction_solves(case):
+    nx, nt, p, m, wave, a, levels = case
+    H = omg.build_hierarchy(osl.Grid(nx, nt, dim=2), osl.WaveSpeed(wave, a=a, a2=a), p, m, levels=levels)
+    h = gpu(*case, solve_mode=2)
+    u0 = W.u0_bumps_2d(nx, W.SEED_C3_BUMPS, 5)
+    U0 = W.initial_iterate(nt, nx * nx)
+    ref = omg.mgrit_solve(H, u0, U0.reshape(nt + 1, nx, nx))
+    out, st = h.solve(torch.from_numpy(u0.ravel().copy()).cuda(), torch.from_numpy(U0).cuda())
+    assert st["converged"] and st["iterations"] == ref.iterations
+    assert rel(out.cpu().numpy(), ref.U.reshape(nt + 1, -1)) < 1e-12
+    assert np.allclose(st["history"], ref.history, rtol=1e-9, atol=0)
