@@ -40,9 +40,9 @@ cudaError_t launch_pcr_coef(const float* sig32, int nt, int nx, int p, float* ou
 
 // The banded separator inverse of the FP32 correction solves (8-row partitions, nx / 8 in 16 .. 512):
 // per step a record of band_record_size floats, offsets -kBandMaxHalfWidth .. kBandMaxHalfWidth in rows of
-// band_row_size floats, probed from the FP32 sigma rows [nt][nx]; ind[t], t = 1..7, is raised to the
+// band_row_size floats, probed from the FP32 sigma rows [nt][nx]; ind[t], t = 1..4, is raised to the
 // largest entry at partition distance t relative to the diagonal blocks (ind zeroed before).
-constexpr int kBandMaxHalfWidth = 4;
+constexpr int kBandMaxHalfWidth = 3;
 unsigned band_record_size(int nx, int p);
 unsigned band_row_size(int nx, int p);
 cudaError_t launch_sep_band(const float* sig32, int nt, int nx, int p, float* rec, float* ind, cudaStream_t st);

@@ -891,7 +891,7 @@ __device__ __forceinline__ bool corr_solve_coef(float* __restrict__ x, const flo
 // barriers instead of one per reduction level, every thread a partition.
 
 constexpr int kBandMax = kBandMaxHalfWidth;  // largest stored half-bandwidth, in partitions
-constexpr int kBandColours = 16; // probe colours of k_sep_band (partition index mod 16)
+constexpr int kBandColours = 8;  // probe colours of k_sep_band (partition index mod 8)
 
 // Floats of one band row (one offset d: B*B blocks for every partition), padded to 16 bytes, and of a
 // whole step record (offsets -kBandMax .. kBandMax; layout [d][a * B + c][partition]).
@@ -1032,52 +1032,226 @@ __device__ __forceinline__ bool corr_solve_band(float* __restrict__ x, const flo
   return true;
 }
 
-// Setup, one CTA per step row of an FP32 coarse level (nx / 8 >= 32 partitions, blockDim.x >= nx / 8):
-// probes S^{-1} = (M^{-1}) restricted to the separator rows with the on-the-fly solve of 8-row
-// partitions.  For every colour col < 16 and separator component c, x = M^{-1} e with e = 1 on row c of
-// the separator of every partition k == col (mod 16); the value at separator row a of partition k' is
-// the entry Sinv[(k', a), (k, c)] of the probe partition k = k' + d, |d| < 8, nearest to k' (the other
-// probe partitions are 16 or more away, where S^{-1} is negligible wherever the band is used).  Entries
-// |d| <= kBandMax go to the record; ind[|d|], |d| = 1..7, receives the largest |Sinv[k'][d]| over
-// max |Sinv[k'][0]| of this level (atomicMax on the bits of non-negative floats).
+// Setup, one CTA per step row of an FP32 coarse level (P = nx / 8 partitions, 16 <= P <= 512, one thread
+// each): the band of S^{-1}, the inverse of the separator Schur system S x_S = g of the 8-row partitions.
+// Each thread forms the Schur blocks (L_k, D_k, U_k) of its separator from sigma (the interior LU and the
+// spikes, as corr_solve_otf does), then S is reduced by block cyclic reduction with all probe right-hand
+// sides at once: e = 1 on separator component c of every partition k == col (mod 8), for the 8 colours
+// and B components (in groups of G colours).  The value at partition k' is Sinv[(k', a), (k' + d, c)] of
+// the probe partition k' + d, d in [-3, 4], nearest to it (the other probe partitions are 8 or more away).
+// Entries |d| <= kBandMax go to the record; ind[t], t = 1..4, is raised to the largest |Sinv[k'][d]|,
+// |d| = t, over the largest diagonal block entry (at t = 4 the two probes k' +- 4 are summed: an upper
+// bound of the tail), by atomicMax on the bits of non-negative floats.
+template <int B>
+constexpr int band_group() { return B <= 2 ? 8 : 2; }
+
 template <int B>
 __global__ void __launch_bounds__(512) k_sep_band(const float* __restrict__ sig_all, int nx, float* __restrict__ rec_all,
                                                   unsigned rec_stride, unsigned row, float* __restrict__ ind) {
+  constexpr int PR = kPartRows, Q = PR - B, BB = B * B;
+  constexpr int G = band_group<B>(), R = G * B;  // colours and right-hand sides of one reduction pass
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* x = reinterpret_cast<float*>(smem_raw);
-  float* sig = x + nx;
-  float* X = sig + nx;
-  const int P = nx / kPartRows;
+  float* X = reinterpret_cast<float*>(smem_raw);  // [3 BB][P] matrix exchange
+  const int P = nx / PR;
+  float* Xg = X + (size_t)3 * BB * P;             // [R B][P] right-hand side exchange
+  const int T = __ffs(P) - 1;
   const int k = threadIdx.x;
-  const float* sg = sig_all + (size_t)blockIdx.x * nx;
+  const bool act = k < P;
+  const float* sgrow = sig_all + (size_t)blockIdx.x * nx;
   float* rec = rec_all + (size_t)blockIdx.x * rec_stride;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) sig[i] = sg[i];
-  float dmax = 0.f, tmax[8] = {};
-  for (int col = 0; col < kBandColours; ++col) {
+  float sg[PR] = {};
+  float L0[BB], D0[BB], U0[BB];
+  auto M = [&](int rr, int o) -> float { return (o == 0 ? 1.f : 0.f) - sg[rr] * dcoef<B>(o); };
+  float V[Q][B], W[Q][B];
+  if (act) {
+    load_part<float>(sgrow + (size_t)k * PR, sg);
+    // interior LU (rows B .. PR-1 of the partition, no pivoting) and the spikes V = A^{-1} M[I, S_k],
+    // W = A^{-1} M[I, S_{k+1}]
+    float l[Q][B], U[Q][B + 1], piv[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      float a[2 * B + 1];
+#pragma unroll
+      for (int c = -B; c <= B; ++c) a[c + B] = (r + c >= 0 && r + c < Q) ? M(B + r, c) : 0.f;
+#pragma unroll
+      for (int t = B; t >= 1; --t) {
+        if (r - t < 0) continue;
+        const float lt = a[B - t] * piv[r - t];
+        l[r][t - 1] = lt;
+#pragma unroll
+        for (int c = 1; c <= B; ++c)
+          if (-t + c <= B) a[-t + c + B] -= lt * U[r - t][c];
+      }
+      piv[r] = __frcp_rn(a[B]);
+#pragma unroll
+      for (int c = 0; c <= B; ++c) U[r][c] = a[B + c];
+    }
+    auto solve = [&](float (&v)[Q]) {
+#pragma unroll
+      for (int r = 0; r < Q; ++r)
+#pragma unroll
+        for (int t = 1; t <= B; ++t)
+          if (r - t >= 0) v[r] -= l[r][t - 1] * v[r - t];
+#pragma unroll
+      for (int r = Q - 1; r >= 0; --r) {
+#pragma unroll
+        for (int t = 1; t <= B; ++t)
+          if (r + t < Q) v[r] -= U[r][t] * v[r + t];
+        v[r] *= piv[r];
+      }
+    };
+#pragma unroll
     for (int c = 0; c < B; ++c) {
+      float v[Q], w[Q];
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        const int ov = c - B - r, ow = Q - r + c;
+        v[r] = ov >= -B ? M(B + r, ov) : 0.f;
+        w[r] = ow <= B ? M(B + r, ow) : 0.f;
+      }
+      solve(v);
+      solve(w);
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        V[r][c] = v[r];
+        W[r][c] = w[r];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < B; ++a)
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        X[(size_t)(a * B + c) * P + k] = V[Q - B + a][c];
+        X[(size_t)(BB + a * B + c) * P + k] = W[Q - B + a][c];
+      }
+  }
+  __syncthreads();
+  if (act) {  // the Schur blocks of separator k: couplings to S_{k-1}, S_k, S_{k+1}
+    const int km = (k + P - 1) & (P - 1);
+    float Vt[BB], Wt[BB];
+#pragma unroll
+    for (int e = 0; e < BB; ++e) {
+      Vt[e] = X[(size_t)e * P + km];
+      Wt[e] = X[(size_t)(BB + e) * P + km];
+    }
+#pragma unroll
+    for (int a = 0; a < B; ++a)
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        float lv = 0.f, dv = M(a, c - a), uv = 0.f;
+#pragma unroll
+        for (int c2 = 0; c2 < B; ++c2) {
+          const float ct = c2 >= a ? M(a, c2 - B - a) : 0.f;
+          const float ch = c2 <= a ? M(a, B + c2 - a) : 0.f;
+          lv -= ct * Vt[c2 * B + c];
+          dv -= ct * Wt[c2 * B + c] + ch * V[c2][c];
+          uv -= ch * W[c2][c];
+        }
+        L0[a * B + c] = lv;
+        D0[a * B + c] = dv;
+        U0[a * B + c] = uv;
+      }
+  }
+  float dmax = 0.f, tmax[5] = {};
+  for (int col0 = 0; col0 < kBandColours; col0 += G) {
+    float Lk[BB], Dk[BB], Uk[BB], gk[R][B];
+#pragma unroll
+    for (int e = 0; e < BB; ++e) {
+      Lk[e] = L0[e];
+      Dk[e] = D0[e];
+      Uk[e] = U0[e];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int a = 0; a < B; ++a) gk[r][a] = (act && (k & (kBandColours - 1)) == col0 + r / B && a == r % B) ? 1.f : 0.f;
+    for (int t = 0; t < T; ++t) {
+      __syncthreads();  // the previous level's (or pass's) reads of the exchange are done
+      if (act) {
+        float Di[BB];
+        inv_small<B>(Dk, Di);
+#pragma unroll
+        for (int e = 0; e < BB; ++e) {
+          X[(size_t)e * P + k] = Di[e];
+          X[(size_t)(BB + e) * P + k] = Lk[e];
+          X[(size_t)(2 * BB + e) * P + k] = Uk[e];
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int a = 0; a < B; ++a) Xg[(size_t)(r * B + a) * P + k] = gk[r][a];
+      }
       __syncthreads();
-      for (int i = threadIdx.x; i < nx; i += blockDim.x) x[i] = 0.f;
-      __syncthreads();
-      if (k < P && (k & (kBandColours - 1)) == col) x[k * kPartRows + c] = 1.f;
-      __syncthreads();
-      corr_solve_otf<B, kPartRows>(x, sig, X, nx);
-      if (k < P) {
-        int d = (col - k) & (kBandColours - 1);  // probe partition k + d, d in [-7, 8]
+      if (act) {
+        const int d = 1 << t;
+        const int km = (k - d) & (P - 1), kp = (k + d) & (P - 1);
+        float Dm[BB], Dp[BB], al[BB], ga[BB], tmp[BB], tmp2[BB], n1[BB], n2[BB];
+#pragma unroll
+        for (int e = 0; e < BB; ++e) {
+          Dm[e] = X[(size_t)e * P + km];
+          Dp[e] = X[(size_t)e * P + kp];
+        }
+        mm_small<B>(Lk, Dm, al);
+        mm_small<B>(Uk, Dp, ga);
+#pragma unroll
+        for (int e = 0; e < BB; ++e) {
+          al[e] = -al[e];
+          ga[e] = -ga[e];
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int a = 0; a < B; ++a) {
+            float v = gk[r][a];
+#pragma unroll
+            for (int c = 0; c < B; ++c)
+              v += al[a * B + c] * Xg[(size_t)(r * B + c) * P + km] + ga[a * B + c] * Xg[(size_t)(r * B + c) * P + kp];
+            gk[r][a] = v;
+          }
+#pragma unroll
+        for (int e = 0; e < BB; ++e) {
+          tmp[e] = X[(size_t)(2 * BB + e) * P + km];  // U_{k-d}
+          tmp2[e] = X[(size_t)(BB + e) * P + kp];     // L_{k+d}
+        }
+        mm_small<B>(al, tmp, n1);
+        mm_small<B>(ga, tmp2, n2);
+#pragma unroll
+        for (int e = 0; e < BB; ++e) Dk[e] += n1[e] + n2[e];
+#pragma unroll
+        for (int e = 0; e < BB; ++e) {
+          tmp[e] = X[(size_t)(BB + e) * P + km];       // L_{k-d}
+          tmp2[e] = X[(size_t)(2 * BB + e) * P + kp];  // U_{k+d}
+        }
+        mm_small<B>(al, tmp, Lk);
+        mm_small<B>(ga, tmp2, Uk);
+      }
+    }
+    if (act) {  // x = (L + D + U)^{-1} g: the columns of S^{-1} on this separator
+      float F[BB], Fi[BB];
+#pragma unroll
+      for (int e = 0; e < BB; ++e) F[e] = Lk[e] + Dk[e] + Uk[e];
+      inv_small<B>(F, Fi);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = r % B;
+        int d = (col0 + r / B - k) & (kBandColours - 1);  // probe partition k + d, d in [-3, 4]
         if (d > kBandColours / 2) d -= kBandColours;
+        const int ad = d < 0 ? -d : d;
 #pragma unroll
         for (int a = 0; a < B; ++a) {
-          const float v = x[k * kPartRows + a];
-          if (d >= -kBandMax && d <= kBandMax) rec[(size_t)(d + kBandMax) * row + (size_t)(a * B + c) * P + k] = v;
-          const int ad = d < 0 ? -d : d;
+          float v = 0.f;
+#pragma unroll
+          for (int c2 = 0; c2 < B; ++c2) v += Fi[a * B + c2] * gk[r][c2];
+          if (ad <= kBandMax) rec[(size_t)(d + kBandMax) * row + (size_t)(a * B + c) * P + k] = v;
           if (ad == 0) dmax = fmaxf(dmax, fabsf(v));
-          else if (ad < 8) tmax[ad] = fmaxf(tmax[ad], fabsf(v));
+          else tmax[ad] = fmaxf(tmax[ad], fabsf(v));
         }
       }
     }
   }
-  if (k < P && dmax > 0.f) {
+  if (act && dmax > 0.f) {
 #pragma unroll
-    for (int t = 1; t < 8; ++t) atomicMax(reinterpret_cast<int*>(ind) + t, __float_as_int(tmax[t] / dmax));
+    for (int t = 1; t <= 4; ++t) atomicMax(reinterpret_cast<int*>(ind) + t, __float_as_int(tmax[t] / dmax));
   }
 }
 
@@ -2103,8 +2277,9 @@ unsigned band_row_size(int nx, int p) { return band_row_floats(nx, p); }
 
 cudaError_t launch_sep_band(const float* sig32, int nt, int nx, int p, float* rec, float* ind, cudaStream_t st) {
   const int B = (p + 1) / 2, P = nx / kPartRows;
-  if (P < kBandColours || P > 512) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)2 * nx * sizeof(float) + (size_t)(3 * B * B + B) * P * sizeof(float);
+  if (P < 16 || P > 512) return cudaErrorInvalidValue;
+  const int R = (B <= 2 ? 8 : 2) * B;
+  const size_t smem = (size_t)(3 * B * B + R * B) * P * sizeof(float);
   const unsigned stride = band_record_floats(nx, p), row = band_row_floats(nx, p);
   cudaError_t e = cudaSuccess;
 #define MGRIT_BAND(BB)                                                                                     \

@@ -52,7 +52,7 @@ struct Level {
   float* pcr32 = nullptr;   // FP32 coarse levels, p <= 3: block-PCR coefficients of every step
   unsigned pcr_floats = 0;
   float* band32 = nullptr;  // FP32 coarse levels: the banded separator inverse of every step (probed in setup)
-  float* band_ind = nullptr;  // [8] its decay indicator (k_sep_band)
+  float* band_ind = nullptr;  // [8] its decay indicator (k_sep_band; entries 1..4 used)
   int band_w = 0;           // half-bandwidth in use (0: block PCR / on the fly), chosen in setup_finish
   size_t solver_stride = 0;
   int P = 0;
@@ -594,7 +594,7 @@ static mgrit_status setup_finish(mgrit_handle** out) {
     return fail(MGRIT_ESINGULAR, "a correction matrix has a (near) zero pivot");
   }
   // half-bandwidth of each FP32 coarse level's separator inverse: the smallest W <= kBandMaxHalfWidth
-  // beyond which every entry is below 1e-9 of its diagonal block, and whose record fits the shared memory
+  // beyond which every probed entry is below 1e-9 of the diagonal blocks, and whose record fits the shared memory
   // of the relaxation kernel; else the block PCR (p <= 3) or the on-the-fly factorisation (p = 5)
   for (size_t l = 1; l < h->levels.size(); ++l) {
     Level& L = h->levels[l];
@@ -607,7 +607,7 @@ static mgrit_status setup_finish(mgrit_handle** out) {
     int W = 0;
     for (int w = 1; w <= kBandMaxHalfWidth && !W; ++w) {
       bool ok = true;
-      for (int t = w + 1; t < 8; ++t) ok = ok && ind[t] < 1e-9f;  // NaN fails
+      for (int t = w + 1; t <= kBandMaxHalfWidth + 1; ++t) ok = ok && ind[t] < 1e-9f;  // NaN fails
       if (ok) W = w;
     }
     for (; W > 0; --W) {  // the record of the step must fit next to the slices and staged rows
@@ -739,7 +739,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
             L.pcr_floats = pcr_record_size(nx, p);
             if ((st = h->alloc(&L.pcr32, (size_t)L.nt * L.pcr_floats)) != MGRIT_OK) return cleanup_fail(st);
           }
-          if (opt.coarse_band && nx / 8 >= 16) {  // 8-row partitions, 16 probe colours
+          if (opt.coarse_band && nx / 8 >= 16 && nx / 8 <= 512) {  // 8-row partitions, one probe thread each
             if ((st = h->alloc(&L.band32, (size_t)L.nt * band_record_size(nx, p))) != MGRIT_OK) return cleanup_fail(st);
             if ((st = h->alloc(&L.band_ind, 8)) != MGRIT_OK) return cleanup_fail(st);
           }
