@@ -348,9 +348,12 @@ def run_ours(args) -> None:
         dist = dist_mod
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     wl = dict(WORKLOAD)
-    if args.nt:  # a shorter time axis (profiling captures of a small case); not the benchmark workload
+    if args.nt:  # another time axis (profiling captures, the long-axis case); not the benchmark workload
         wl["nt"] = args.nt
-        wl["workload"] = WORKLOAD["workload"].replace(f"nt{WORKLOAD['nt']}", f"nt{args.nt}")
+        wl["workload"] = wl["workload"].replace(f"nt{WORKLOAD['nt']}", f"nt{args.nt}")
+    if args.nx:  # another slice length (the long-axis case nx 512, nt 131072); not the benchmark workload
+        wl["nx"] = args.nx
+        wl["workload"] = wl["workload"].replace(f"nx{WORKLOAD['nx']}", f"nx{args.nx}")
     nx, nt = wl["nx"], wl["nt"]
     dof = nx * nt
     prec = 0 if args.precision == "fp64" else 1
@@ -1076,7 +1079,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the sequential comparator and e2e runs")
     ap.add_argument("--nt", type=int, default=0, help="override nt (small profiling cases only)")
-    ap.add_argument("--nx", type=int, default=0, help="override nx of the 2D workload (small profiling cases only)")
+    ap.add_argument("--nx", type=int, default=0,
+                    help="override nx (1D: another slice length, e.g. the long-axis case; 2D: small profiling cases)")
     ap.add_argument("--workload", choices=["batched", "advection1d", "advection2d", "adjoint2d", "twolevel", "cpu"],
                     default="batched", help="batched (256 problems) is the benchmark; the others measure further rows")
     ap.add_argument("--no-phase-events", action="store_true",

@@ -168,6 +168,13 @@ MGRIT_D void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t*
                : "memory");
 }
 
+// Asks for [src, src + bytes) to be brought into L2 (a hint: nothing to wait for, no shared memory).
+// Issued only for 16-byte aligned addresses and sizes that are a multiple of 16.
+MGRIT_D void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  if (((reinterpret_cast<uintptr_t>(src) | bytes) & 15u) == 0 && bytes > 0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Orders this thread's earlier generic-proxy shared-memory accesses before later async-proxy ones.
 MGRIT_D void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 

@@ -618,6 +618,18 @@ static mgrit_status setup_finish(mgrit_handle** out) {
       if (smem <= 227 * 1024) break;
     }
     L.band_w = W;
+    if (W == 0 && L.pcr_floats && !L.pcr32) {  // band rejected: the block-PCR record after all
+      mgrit_status st = h->alloc(&L.pcr32, (size_t)L.nt * L.pcr_floats);
+      if (st == MGRIT_OK && launch_pcr_coef(L.sig32, L.nt, h->grid.nx, h->order, L.pcr32, h->stream) != cudaSuccess)
+        st = fail(MGRIT_ECUDA, "setup: block-PCR coefficients");
+      if (st == MGRIT_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
+        st = fail(MGRIT_ECUDA, std::string("setup: ") + cudaGetErrorString(cudaGetLastError()));
+      if (st != MGRIT_OK) {
+        delete h;
+        *out = nullptr;
+        return st;
+      }
+    }
   }
   h->collect_phase_times();
   h->setup_launches = h->call_launches;
@@ -735,11 +747,12 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
           if ((st = h->alloc((char**)&L.solver, tot)) != MGRIT_OK) return cleanup_fail(st);
         } else {
           if ((st = h->alloc(&L.sig32, (size_t)L.nt * nx)) != MGRIT_OK) return cleanup_fail(st);
-          if (p <= 3) {
+          const bool probe = opt.coarse_band && nx / 8 >= 16 && nx / 8 <= 512;  // 8-row partitions, a thread each
+          if (p <= 3) {  // with a probed band, the PCR record is built only if the band is rejected (setup_finish)
             L.pcr_floats = pcr_record_size(nx, p);
-            if ((st = h->alloc(&L.pcr32, (size_t)L.nt * L.pcr_floats)) != MGRIT_OK) return cleanup_fail(st);
+            if (!probe && (st = h->alloc(&L.pcr32, (size_t)L.nt * L.pcr_floats)) != MGRIT_OK) return cleanup_fail(st);
           }
-          if (opt.coarse_band && nx / 8 >= 16 && nx / 8 <= 512) {  // 8-row partitions, one probe thread each
+          if (probe) {
             if ((st = h->alloc(&L.band32, (size_t)L.nt * band_record_size(nx, p))) != MGRIT_OK) return cleanup_fail(st);
             if ((st = h->alloc(&L.band_ind, 8)) != MGRIT_OK) return cleanup_fail(st);
           }

@@ -1,8 +1,6 @@
 import os
 import sys
 
-import pytest
-
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -13,13 +11,3 @@ if HERE not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built extension")
-    config.addinivalue_line("markers", "slow: long CPU oracle runs, excluded from the default CPU suite")
-
-
-def pytest_collection_modifyitems(config, items):
-    if os.environ.get("MGRIT_RUN_SLOW") == "1":
-        return
-    skip = pytest.mark.skip(reason="slow oracle run; set MGRIT_RUN_SLOW=1")
-    for item in items:
-        if "slow" in item.keywords:
-            item.add_marker(skip)
