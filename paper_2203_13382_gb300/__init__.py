@@ -100,7 +100,7 @@ _SIGNATURES = {
     "mgrit_adjoint_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(MgritStats)]),
     "mgrit_level_info": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
-    "mgrit_level_band": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "mgrit_level_band": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP]),
     "mgrit_copy_offsets": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "mgrit_copy_sigma": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "mgrit_apply_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
@@ -206,11 +206,13 @@ class Handle:
         _check(load_library().mgrit_level_info(self._h(), level, ctypes.byref(nt), ctypes.byref(m)), "level_info")
         return nt.value, m.value
 
-    def level_band(self, level: int) -> int:
-        """Half-width of the banded separator inverse of this level's FP32 correction solves (0: none)."""
+    def level_band(self, level: int, decay: bool = False):
+        """Half-width of the banded separator inverse of this level's FP32 correction solves (0: none);
+        with decay=True also the probed decay at partition distances 1..4 (a list of 4 floats)."""
         w = ctypes.c_int()
-        _check(load_library().mgrit_level_band(self._h(), level, ctypes.byref(w)), "mgrit_level_band")
-        return w.value
+        d = (ctypes.c_float * 4)()
+        _check(load_library().mgrit_level_band(self._h(), level, ctypes.byref(w), d), "mgrit_level_band")
+        return (w.value, list(d)) if decay else w.value
 
     @property
     def nlevels(self) -> int:

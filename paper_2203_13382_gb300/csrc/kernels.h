@@ -43,6 +43,10 @@ cudaError_t launch_pcr_coef(const float* sig32, int nt, int nx, int p, float* ou
 // band_row_size floats, probed from the FP32 sigma rows [nt][nx]; ind[t], t = 1..4, is raised to the
 // largest entry at partition distance t relative to the diagonal blocks (ind zeroed before).
 constexpr int kBandMaxHalfWidth = 3;
+// Entries of the separator inverse below this fraction of its diagonal blocks are left out of the band:
+// below the unit roundoff of the FP32 solve that applies it (2^-24 = 6e-8), so the truncation adds less
+// than the solve's own rounding.
+constexpr float kBandTolerance = 1e-8f;
 unsigned band_record_size(int nx, int p);
 unsigned band_row_size(int nx, int p);
 cudaError_t launch_sep_band(const float* sig32, int nt, int nx, int p, float* rec, float* ind, cudaStream_t st);

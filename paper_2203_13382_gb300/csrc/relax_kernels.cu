@@ -885,7 +885,7 @@ __device__ __forceinline__ bool corr_solve_coef(float* __restrict__ x, const flo
 // With 8-row partitions (one per thread, B separator rows first, Q = 8 - B interior rows) the separator
 // unknowns satisfy the Schur system S x_S = g, and S^{-1} is the separator block of M^{-1}, whose entries
 // decay exponentially away from the diagonal (M = I - diag(sigma) D is close to a diagonally dominant
-// M-matrix on the coarse levels).  Where S^{-1} is below 1e-9 of its diagonal blocks beyond a few
+// M-matrix on the coarse levels).  Where S^{-1} is below kBandTolerance of its diagonal blocks beyond a few
 // partitions, it is stored as a band of half-width W <= kBandMax partitions (setup: k_sep_band probes
 // it), and the separator solve is one banded product instead of the block cyclic reduction: two block
 // barriers instead of one per reduction level, every thread a partition.
@@ -1294,7 +1294,7 @@ __device__ __forceinline__ void apply_gather_T(const LevelTables& T, int row, co
 struct StageLayout {
   unsigned e, h, per_buf, cf, bars, xch, total, tx;  // tx: table bytes copied per step
 };
-MGRIT_HD StageLayout stage_layout(int nx, int p, int otf, unsigned cf_floats, int df = 0) {
+MGRIT_HD StageLayout stage_layout(int nx, int p, int otf, unsigned cf_floats, int df = 0, int band = 0) {
   StageLayout o;
   o.e = ((unsigned)nx * 4u + 127u) & ~127u;
   o.h = ((unsigned)nx * 2u + 127u) & ~127u;
@@ -1304,7 +1304,7 @@ MGRIT_HD StageLayout stage_layout(int nx, int p, int otf, unsigned cf_floats, in
   o.xch = o.bars + 128;
   const int B = (p + 1) / 2, P = nx / (B <= 2 ? 16 : 8);  // partitions of the on-the-fly solve
   const unsigned x_otf = (unsigned)((3 * B * B + B) * P * 4), x_band = (unsigned)(2 * B * (nx / 8) * 4);
-  o.total = o.xch + (otf ? (x_otf > x_band ? x_otf : x_band) : 0u);
+  o.total = o.xch + (otf ? (band ? x_band : (x_otf > x_band ? x_otf : x_band)) : 0u);
   o.tx = (unsigned)nx * ((otf || df) ? 10u : 6u);
   return o;
 }
@@ -1342,7 +1342,7 @@ __device__ __forceinline__ Stage stage_init(unsigned char* smem, size_t used, co
   s.test_wait = 0;
   if (!T.gather_stage) return s;
   s.test_wait = T.test_wait;
-  s.lay = stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf ? T.cf_floats : 0u, T.df);
+  s.lay = stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf ? T.cf_floats : 0u, T.df, coarse && T.otf && T.band > 0);
   s.base = smem + ((used + 127) & ~(size_t)127);
   if (threadIdx.x == 0) {
     mbar_init(s.bar(0), 1);
@@ -1664,15 +1664,31 @@ __global__ void __launch_bounds__(slice_threads<P, R, COARSE>(),
 // the start slice, the C-point residual, the F-point stores.  Level 0 adds no right-hand side (g = 0).
 
 // dst[i] = (S_n src)_i for the points of this thread, src with its periodic halo (src[nx + t] = src[t]).
+// All of the thread's table loads are issued before the first interpolation, so a warp waits for the
+// step's rows once rather than once per point.
 template <int P, int NT>
 __device__ __forceinline__ void apply_gather_df(const float* __restrict__ eh, const float* __restrict__ el,
                                                 const uint16_t* __restrict__ sh, const float2* __restrict__ src,
                                                 float2* __restrict__ dst, int nx) {
-#pragma unroll 2
+  float h[kPts], l[kPts];
+  int s[kPts];
+#pragma unroll
+  for (int q = 0; q < kPts; ++q) {
+    const int i = threadIdx.x + q * NT;
+    h[q] = 0.f;
+    l[q] = 0.f;
+    s[q] = 0;
+    if (i < nx) {
+      h[q] = __ldg(eh + i);
+      l[q] = __ldg(el + i);
+      s[q] = (int)__ldg(sh + i);
+    }
+  }
+#pragma unroll
   for (int q = 0; q < kPts; ++q) {
     const int i = threadIdx.x + q * NT;
     if (i < nx) {
-      const df32 v = df_interp<P>(df32{__ldg(eh + i), __ldg(el + i)}, src + wrap_pow2(i + (int)__ldg(sh + i), nx));
+      const df32 v = df_interp<P>(df32{h[q], l[q]}, src + wrap_pow2(i + s[q], nx));
       dst[i] = make_float2(v.h, v.l);
     }
   }
@@ -1692,7 +1708,7 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
     for (int i = threadIdx.x; i < nx; i += NT) {
       double v = st ? st[i] : 0.0;
       if (co) v += co[i];
-      const df32 d = df_from_double(v);
+      const df32 d = df_from_double_int(v);
       src[i] = make_float2(d.h, d.l);
       if (wb) wb[i] = v;
     }
@@ -1741,15 +1757,23 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
       const double* cc = a.cin_corr ? (const double*)a.cin_corr + (size_t)(j + 1) * a.corr_stride : nullptr;
       double* ro = a.rout ? (double*)a.rout + (size_t)(j + 1) * a.r_stride : nullptr;
       float* ro32 = a.rout32 ? a.rout32 + (size_t)(j + 1) * a.r_stride : nullptr;
+      float qh = 0.f, ql = 0.f;  // this thread's sum of squares, as an FP32 pair
       for (int i = threadIdx.x; i < nx; i += NT) {
         const float2 d = dst[i];
-        double v = df_to_double(df32{d.x, d.y});
-        if (cc) v -= (ci ? ci[i] : 0.0) + cc[i];
-        else if (ci) v -= ci[i];
-        if (ro) ro[i] = v;
-        if (ro32) ro32[i] = (float)v;
-        if (a.norm_partial) sq += v * v;
+        df32 r{d.x, d.y};
+        if (cc) {  // F-relaxation with a pending correction: in FP64
+          r = df_from_double_int(df_to_double(r) - ((ci ? ci[i] : 0.0) + cc[i]));
+        } else if (ci) {
+          r = df_sub(r, df_from_double_int(ci[i]));
+        }
+        if (ro) ro[i] = df_to_double(r);
+        if (ro32) ro32[i] = __fadd_rn(r.h, r.l);
+        if (a.norm_partial) {
+          const float p = __fmul_rn(r.h, r.h);
+          df_acc(qh, ql, df32{p, __fmaf_rn(r.h, r.h, -p)});
+        }
       }
+      sq += (double)qh + (double)ql;
     }
     if (k + 1 < a.nsteps) write_halo(dst, nx);
     __syncthreads();
@@ -1909,7 +1933,7 @@ size_t smem_bytes(int buf, const LevelTables& T, bool coarse) {
   size_t b = 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double);
   if (T.gather_stage)
     b = ((b + 127) & ~(size_t)127) +
-        stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf ? T.cf_floats : 0u, T.df).total;
+        stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf ? T.cf_floats : 0u, T.df, coarse && T.otf && T.band > 0).total;
   return b;
 }
 
@@ -2170,7 +2194,7 @@ void relax_smem_need(const LevelTables& T, int is_double, int* buf, size_t* smem
   *buf = b;
   *smem = is_double ? smem_bytes<double>(b, T, coarse) : smem_bytes<float>(b, T, coarse);
   *region = T.gather_stage
-                ? stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf ? T.cf_floats : 0u, T.df).total
+                ? stage_layout(T.nx, T.p, coarse && T.otf, coarse && T.otf ? T.cf_floats : 0u, T.df, coarse && T.otf && T.band > 0).total
                 : 0;
 }
 

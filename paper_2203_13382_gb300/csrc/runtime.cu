@@ -54,6 +54,7 @@ struct Level {
   float* band32 = nullptr;  // FP32 coarse levels: the banded separator inverse of every step (probed in setup)
   float* band_ind = nullptr;  // [8] its decay indicator (k_sep_band; entries 1..4 used)
   int band_w = 0;           // half-bandwidth in use (0: block PCR / on the fly), chosen in setup_finish
+  float band_decay[4] = {};  // the probed indicator at partition distances 1..4 (host copy)
   size_t solver_stride = 0;
   int P = 0;
   int is_double = 1;  // arithmetic of this level's cycle
@@ -594,8 +595,8 @@ static mgrit_status setup_finish(mgrit_handle** out) {
     return fail(MGRIT_ESINGULAR, "a correction matrix has a (near) zero pivot");
   }
   // half-bandwidth of each FP32 coarse level's separator inverse: the smallest W <= kBandMaxHalfWidth
-  // beyond which every probed entry is below 1e-9 of the diagonal blocks, and whose record fits the shared memory
-  // of the relaxation kernel; else the block PCR (p <= 3) or the on-the-fly factorisation (p = 5)
+  // beyond which every probed entry is below kBandTolerance of the diagonal blocks, if its record fits the
+  // shared memory of the relaxation kernel; else the block PCR (p <= 3) or the on-the-fly factorisation (p = 5)
   for (size_t l = 1; l < h->levels.size(); ++l) {
     Level& L = h->levels[l];
     if (!L.band_ind) continue;
@@ -604,18 +605,19 @@ static mgrit_status setup_finish(mgrit_handle** out) {
       cudaGetLastError();
       continue;
     }
+    for (int t = 0; t < 4; ++t) L.band_decay[t] = ind[t + 1];
     int W = 0;
     for (int w = 1; w <= kBandMaxHalfWidth && !W; ++w) {
       bool ok = true;
-      for (int t = w + 1; t <= kBandMaxHalfWidth + 1; ++t) ok = ok && ind[t] < 1e-9f;  // NaN fails
+      for (int t = w + 1; t <= kBandMaxHalfWidth + 1; ++t) ok = ok && ind[t] < kBandTolerance;  // NaN fails
       if (ok) W = w;
     }
-    for (; W > 0; --W) {  // the record of the step must fit next to the slices and staged rows
+    if (W > 0) {  // the record of the step must fit next to the slices and staged rows
       L.band_w = W;
       int buf;
       size_t smem, region;
       relax_smem_need(h->tables((int)l, 0), 0, &buf, &smem, &region);
-      if (smem <= 227 * 1024) break;
+      if (smem > 227 * 1024) W = 0;
     }
     L.band_w = W;
     if (W == 0 && L.pcr_floats && !L.pcr32) {  // band rejected: the block-PCR record after all
@@ -1286,10 +1288,12 @@ mgrit_status mgrit_level_info(const mgrit_handle* h, int level, int* nt_level, i
   return MGRIT_OK;
 }
 
-mgrit_status mgrit_level_band(const mgrit_handle* h, int level, int* half_width) {
+mgrit_status mgrit_level_band(const mgrit_handle* h, int level, int* half_width, float* decay) {
   if (!h || !half_width) return fail(MGRIT_EINVAL, "NULL argument");
   if (level < 0 || level >= (int)h->levels.size()) return fail(MGRIT_EINVAL, "level out of range");
   *half_width = h->levels[level].band_w;
+  if (decay)
+    for (int t = 0; t < 4; ++t) decay[t] = h->levels[level].band_decay[t];
   return MGRIT_OK;
 }
 

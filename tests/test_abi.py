@@ -165,7 +165,7 @@ def test_null_handles_are_argument_errors(lib):
         lambda: lib.mgrit_solve_to_reference(None, None, None, None, None, 0.0, ctypes.byref(st)),
         lambda: lib.mgrit_adjoint_solve(None, None, None, None, None, ctypes.byref(st)),
         lambda: lib.mgrit_level_info(None, 0, ctypes.byref(a), ctypes.byref(b)),
-        lambda: lib.mgrit_level_band(None, 0, ctypes.byref(a)),
+        lambda: lib.mgrit_level_band(None, 0, ctypes.byref(a), None),
         lambda: lib.mgrit_copy_offsets(None, 0, None),
         lambda: lib.mgrit_copy_sigma(None, 0, None),
         lambda: lib.mgrit_apply_step(None, 0, 0, 1, None, None),

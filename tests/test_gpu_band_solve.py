@@ -2,16 +2,24 @@
 
 On 1D FP32 coarse levels M = I - diag(sigma) D_{p+1} (eq. (Phi_multilevel)) is solved with 8-row
 partitions whose separator system is inverted by a stored band of S^{-1} = (M^{-1}) restricted to the
-separators, probed in setup and kept only where it is exact to 1e-9 of its diagonal blocks.  A coarse step
-with the band must equal the FP64 coarse step within the FP32 tolerance of the single-step parity tests and
-the step with the block cyclic reduction (coarse_band = 0); the band must actually be in use on the levels
-whose sigma is moderate; MGRIT with and without the band takes the same number of cycles.
+separators, probed in setup and kept only where the entries it leaves out are below 1e-8 of its diagonal
+blocks (under the FP32 unit roundoff of the solve that applies it).
+- The probed decay of S^{-1} equals the oracle's: M^{-1} formed densely from the oracle's sigma of every
+  step, its separator blocks at partition distance t = 1..3 relative to the diagonal block of the same
+  partition (FP32 probe: 1e-3 relative where the ratio is above 1e-6), and the band width the setup chose is
+  the smallest one whose left-out entries are under the tolerance.
+- A coarse step with the band equals the FP64 coarse step within the FP32 tolerance of the single-step parity
+  tests and the step with the block cyclic reduction (coarse_band = 0); the band is in use on the levels
+  whose sigma is moderate; MGRIT with and without the band takes the same number of cycles.
 """
 
 import numpy as np
 import pytest
 
 import workloads as W
+from oracle import coarse as oco
+from oracle import mgrit as omg
+from oracle import semi_lagrangian as osl
 
 pytestmark = pytest.mark.gpu
 
@@ -74,3 +82,44 @@ def test_mgrit_with_and_without_the_band(p):
     assert res[1][1] == res[0][1]
     assert rel(res[1][0], res[0][0]) < 1e-9  # both at a 1e-10 residual of the same FP64 system
     assert any(w > 0 for w in res[1][2])
+
+
+def oracle_decay(sigma_rows, nx, p):
+    """max over steps and partitions k of max_{a,c} |S^{-1}[(k,a),(k+-t,c)]| / max_{a,c} |S^{-1}[(k,a),(k,c)]|
+    for t = 1..3, S^{-1} the separator rows and columns (the first B rows of each 8-row partition) of M^{-1}."""
+    B, P = (p + 1) // 2, nx // 8
+    sep = np.array([k * 8 + a for k in range(P) for a in range(B)])
+    out = np.zeros(3)
+    for sig in sigma_rows:
+        Minv = np.linalg.inv(oco.correction_matrix_1d(sig, p).toarray())
+        S = Minv[np.ix_(sep, sep)].reshape(P, B, P, B)
+        for k in range(P):
+            dmax = np.abs(S[k, :, k, :]).max()
+            for t in range(1, 4):
+                v = max(np.abs(S[k, :, (k + t) % P, :]).max(), np.abs(S[k, :, (k - t) % P, :]).max())
+                out[t - 1] = max(out[t - 1], v / dmax)
+    return out
+
+
+@pytest.mark.parametrize("p", [1, 3, 5])
+def test_probed_decay_matches_the_oracle(p):
+    nx, nt, m = 256, 256, 4
+    kw = dict(wave="sin_kx_cos_t", a=0.5, k=2.0)
+    H = omg.build_hierarchy(osl.Grid(nx, nt), osl.WaveSpeed("sin_kx_cos_t", a=0.5, k=2.0), p, m)
+    h = mg.mgrit_setup(nx, nt, p, m, precision=1, **kw)
+    assert h.nlevels == H.nlevels
+    for level in range(1, h.nlevels):
+        W_gpu, dec = h.level_band(level, decay=True)
+        if nx // 8 < 16 or not any(dec):
+            continue
+        ref = oracle_decay(H.levels[level].sigma, nx, p)
+        for t in range(3):
+            if ref[t] > 1e-6:
+                assert abs(dec[t] - ref[t]) <= 1e-3 * ref[t], (level, t + 1, dec[t], ref[t])
+            else:
+                assert dec[t] <= 1e-6 + 2.0 * ref[t], (level, t + 1, dec[t], ref[t])
+        # the chosen width: the smallest whose left-out entries (distances W+1 .. 4) are under 1e-8, or 0
+        need = next((w for w in range(1, 4) if all(d < 1e-8 for d in dec[w:])), 0)
+        assert W_gpu in (need, 0), (level, W_gpu, need, dec)
+        print(f"p={p} level {level}: band {W_gpu}, probed {['%.2e' % d for d in dec]}, oracle {['%.2e' % r for r in ref]}")
+    h.destroy()
