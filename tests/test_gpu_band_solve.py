@@ -6,8 +6,9 @@ separators, probed in setup and kept only where the entries it leaves out are be
 blocks (under the FP32 unit roundoff of the solve that applies it).
 - The probed decay of S^{-1} equals the oracle's: M^{-1} formed densely from the oracle's sigma of every
   step, its separator blocks at partition distance t = 1..3 relative to the diagonal block of the same
-  partition (FP32 probe: 1e-3 relative where the ratio is above 1e-6), and the band width the setup chose is
-  the smallest one whose left-out entries are under the tolerance.
+  partition, summed as the probe's eight colours sum them (partitions 8 apart share a colour; FP32 probe:
+  1e-3 relative where the ratio is above 1e-6), and the band width the setup chose is the smallest one whose
+  left-out entries are under the tolerance.
 - A coarse step with the band equals the FP64 coarse step within the FP32 tolerance of the single-step parity
   tests and the step with the block cyclic reduction (coarse_band = 0); the band is in use on the levels
   whose sigma is moderate; MGRIT with and without the band takes the same number of cycles.
@@ -85,18 +86,22 @@ def test_mgrit_with_and_without_the_band(p):
 
 
 def oracle_decay(sigma_rows, nx, p):
-    """max over steps and partitions k of max_{a,c} |S^{-1}[(k,a),(k+-t,c)]| / max_{a,c} |S^{-1}[(k,a),(k,c)]|
-    for t = 1..3, S^{-1} the separator rows and columns (the first B rows of each 8-row partition) of M^{-1}."""
+    """What the probe measures, from the exact inverse: S^{-1} is the separator rows and columns (the first B
+    rows of each 8-row partition) of M^{-1}; a probe of colour c (unit right-hand sides on every partition
+    = c mod 8) returns at partition k the sum of S^{-1}[k, q] over the partitions q = c (mod 8).  Ratio at
+    distance t = 1..3: the largest such sum for q = k +- t (mod 8) over the one for q = k (mod 8), maximised
+    over k and the steps."""
     B, P = (p + 1) // 2, nx // 8
     sep = np.array([k * 8 + a for k in range(P) for a in range(B)])
     out = np.zeros(3)
     for sig in sigma_rows:
         Minv = np.linalg.inv(oco.correction_matrix_1d(sig, p).toarray())
         S = Minv[np.ix_(sep, sep)].reshape(P, B, P, B)
+        alias = np.stack([S[:, :, c::8, :].sum(axis=2) for c in range(8)], axis=1)  # [k][colour][a][c]
         for k in range(P):
-            dmax = np.abs(S[k, :, k, :]).max()
+            dmax = np.abs(alias[k, k % 8]).max()
             for t in range(1, 4):
-                v = max(np.abs(S[k, :, (k + t) % P, :]).max(), np.abs(S[k, :, (k - t) % P, :]).max())
+                v = max(np.abs(alias[k, (k + t) % 8]).max(), np.abs(alias[k, (k - t) % 8]).max())
                 out[t - 1] = max(out[t - 1], v / dmax)
     return out
 
