@@ -505,6 +505,7 @@ def run_ours(args) -> None:
             "config": {**wl, "precision": args.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2: per-step gather tables alone exceed 2 GB"},
             "iterations": iters[0], "iterations_all_steps": sorted(set(iters)),
+            "device_bytes": int(stats[0]["device_bytes"]),
             "setup_ms_per_step": float(np.median([st["setup_ms"] for st in stats])),
             "solve_only_ms_per_step": float(np.median([st["solve_ms"] for st in stats])),
             "solve_only_value": dof / (float(np.median([st["solve_ms"] for st in stats])) / 1e3),
@@ -781,6 +782,10 @@ def run_batched(args) -> None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     wl = dict(WORKLOAD_BATCH)
     probs = W.batched_problems(wl["problems"])
+    if args.problems and args.problems < wl["problems"]:  # the first problems of the draw (profiling captures only)
+        probs = probs[:args.problems]
+        wl["workload"] += f"_first{args.problems}"
+        wl["problems_used"] = args.problems
     specs = [dict(nx=q.nx, nt=q.nt, order=q.order, m=q.m, a=q.a, k=float(q.k)) for q in probs]
     u0_h, rows, inits_c = batch_inputs(probs)
     u0s = [torch.from_numpy(u).cuda() for u in u0_h]
@@ -935,6 +940,7 @@ def run_batched(args) -> None:
             "config": {**wl, "dof": dof, "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (per-step gather tables of the batch exceed 10 GB)"},
             "iterations_min_max": [min(iters), max(iters)], "converged": conv,
+            "device_bytes": int(sum(x["device_bytes"] for x in stats[0])),
             "setup_ms_per_step": float(np.median([max(x["setup_ms"] for x in st) for st in stats])),
             "comparator": comparator, "roofline": roof, "roofline_others": roof_others, "cpu_baseline": cpu,
             "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
@@ -1083,6 +1089,8 @@ def main():
                     help="override nx (1D: another slice length, e.g. the long-axis case; 2D: small profiling cases)")
     ap.add_argument("--workload", choices=["batched", "advection1d", "advection2d", "adjoint2d", "twolevel", "cpu"],
                     default="batched", help="batched (256 problems) is the benchmark; the others measure further rows")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="batched: use only the first N problems of the 256 (small profiling cases only)")
     ap.add_argument("--no-phase-events", action="store_true",
                     help="skip the second, instrumented timed region (phase table from one solve)")
     args = ap.parse_args()

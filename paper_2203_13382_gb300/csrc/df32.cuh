@@ -30,38 +30,6 @@ MGRIT_D df32 df_from_double(double x) {
 
 MGRIT_D double df_to_double(df32 a) { return __dadd_rn((double)a.h, (double)a.l); }
 
-// The same pair as df_from_double, formed with integer operations on the FP64 bit pattern (GB300 runs
-// FP64 instructions, conversions included, at 1/64 of the FP32 rate).  h = x rounded to nearest-even at
-// 24 bits: the top 24 significand bits plus the rounding carry, the exponent rebiased; the remainder
-// (the low 29 bits, minus 2^29 when h rounded up) is an exact integer r, and l = r * 2^(e - 1075)
-// rounded to FP32 by one integer-to-float conversion and an exact scaling by a power of two.  Equal to
-// df_from_double wherever 2^-74 <= |x| < 2^127; zero (and subnormal) inputs give (0, 0); other
-// magnitudes take df_from_double.
-MGRIT_D df32 df_from_double_int(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7ff);
-  if (e == 0) return {0.f, 0.f};
-  if (e < 949 || e >= 1023 + 127) return df_from_double(x);
-  const unsigned long long m = (b & 0xfffffffffffffULL) | (1ULL << 52);  // 53-bit significand
-  unsigned hm = (unsigned)(m >> 29);                                      // 24 bits
-  int r = (int)(m & 0x1fffffffULL);                                       // low 29 bits
-  if (r > (1 << 28) || (r == (1 << 28) && (hm & 1u))) {
-    ++hm;
-    r -= 1 << 29;
-  }
-  int ef = e - 1023 + 127;
-  if (hm == (1u << 24)) {  // the carry reached the next binade
-    hm >>= 1;
-    ++ef;
-  }
-  const unsigned sign = (unsigned)(b >> 63) << 31;
-  const float h = __uint_as_float(sign | ((unsigned)ef << 23) | (hm & 0x7fffffu));
-  // 2^(e - 1075) as an FP32 power of two (normal for e >= 949)
-  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
-  const float l = __fmul_rn(__int2float_rn(sign ? -r : r), scale);
-  return {h, l};
-}
-
 // c - e for an integer c with |c| >= 1 and 0 <= e.h < 1 (so |c| >= |e.h|: Fast2Sum), not renormalised.
 MGRIT_D df32 df_int_minus(float c, df32 e) {
   const float s = __fsub_rn(c, e.h);
@@ -98,14 +66,6 @@ MGRIT_D void df_acc(float& sh, float& sl, df32 t) {
 MGRIT_D df32 df_norm(float h, float l) {
   const float s = __fadd_rn(h, l);
   return {s, __fsub_rn(l, __fsub_rn(s, h))};
-}
-
-// a - b (TwoSum of the high parts, the low parts added to the error, renormalised by Fast2Sum).
-MGRIT_D df32 df_sub(df32 a, df32 b) {
-  const float s = __fsub_rn(a.h, b.h);
-  const float bb = __fsub_rn(s, a.h);
-  const float err = __fsub_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fadd_rn(b.h, bb));
-  return df_norm(s, __fadd_rn(err, __fsub_rn(a.l, b.l)));
 }
 
 // (-1)^{P-a} C(P, a): the integer numerators of the Lagrange basis coefficients 1 / prod_{b != a} (a - b)

@@ -1708,7 +1708,7 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
     for (int i = threadIdx.x; i < nx; i += NT) {
       double v = st ? st[i] : 0.0;
       if (co) v += co[i];
-      const df32 d = df_from_double_int(v);
+      const df32 d = df_from_double(v);
       src[i] = make_float2(d.h, d.l);
       if (wb) wb[i] = v;
     }
@@ -1757,23 +1757,15 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
       const double* cc = a.cin_corr ? (const double*)a.cin_corr + (size_t)(j + 1) * a.corr_stride : nullptr;
       double* ro = a.rout ? (double*)a.rout + (size_t)(j + 1) * a.r_stride : nullptr;
       float* ro32 = a.rout32 ? a.rout32 + (size_t)(j + 1) * a.r_stride : nullptr;
-      float qh = 0.f, ql = 0.f;  // this thread's sum of squares, as an FP32 pair
       for (int i = threadIdx.x; i < nx; i += NT) {
         const float2 d = dst[i];
-        df32 r{d.x, d.y};
-        if (cc) {  // F-relaxation with a pending correction: in FP64
-          r = df_from_double_int(df_to_double(r) - ((ci ? ci[i] : 0.0) + cc[i]));
-        } else if (ci) {
-          r = df_sub(r, df_from_double_int(ci[i]));
-        }
-        if (ro) ro[i] = df_to_double(r);
-        if (ro32) ro32[i] = __fadd_rn(r.h, r.l);
-        if (a.norm_partial) {
-          const float p = __fmul_rn(r.h, r.h);
-          df_acc(qh, ql, df32{p, __fmaf_rn(r.h, r.h, -p)});
-        }
+        double v = df_to_double(df32{d.x, d.y});
+        if (cc) v -= (ci ? ci[i] : 0.0) + cc[i];
+        else if (ci) v -= ci[i];
+        if (ro) ro[i] = v;
+        if (ro32) ro32[i] = (float)v;
+        if (a.norm_partial) sq += v * v;
       }
-      sq += (double)qh + (double)ql;
     }
     if (k + 1 < a.nsteps) write_halo(dst, nx);
     __syncthreads();
