@@ -11,17 +11,20 @@ namespace mgrit {
 
 // ---- setup (setup_kernels.cu) ------------------------------------------------------------------
 
-// Fine departure offsets s[n][i] = (x_i - xi) / h, one backward ERK-r step (Sec. 2.1).
+// Fine departure offsets s[n][i] = (x_i - xi) / h, one backward ERK-r step (Sec. 2.1); pairs: the
+// spatially varying speeds evaluated in FP32 pairs (FP32-bulk handles), else FP64.
 void launch_departure_1d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* s,
-                         cudaStream_t st);
+                         bool pairs, cudaStream_t st);
 // 2D: sx, sy each [nt][nx*nx], row-major (y slow).
 void launch_departure_2d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* sx,
                          double* sy, cudaStream_t st);
 
 // Coarse offsets by backtracking (eq. (coarse_depart_interp)) plus phi / sigma (eq. (nu_p_def)).
-// s_prev [m*ntc][nx], sigma_prev [m*ntc][nx] or NULL (level 1); outputs [ntc][nx].
-void launch_backtrack_1d(const double* s_prev, const double* sigma_prev, int m, int ntc, int nx, int p, double* s_out,
-                         double* sigma_out, cudaStream_t st);
+// s_prev [m*ntc][nx], sigma_prev [m*ntc][nx] or NULL (level 1); eh_prev / el_prev [m*ntc][nx]: the fine
+// level's eps as FP32 pairs, or NULL (the sum of f over the fine steps then comes from s_prev in FP64);
+// outputs [ntc][nx].
+void launch_backtrack_1d(const double* s_prev, const double* sigma_prev, const float* eh_prev, const float* el_prev,
+                         int m, int ntc, int nx, int p, double* s_out, double* sigma_out, cudaStream_t st);
 // 2D bilinear backtracking (Sec. SM6); sigma_x / sigma_y per component.
 void launch_backtrack_2d(const double* sx_prev, const double* sy_prev, const double* gx_prev, const double* gy_prev,
                          int m, int ntc, int nx, int p, double* sx_out, double* sy_out, double* gx_out, double* gy_out,

@@ -819,7 +819,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
       Level& L0 = h->levels[0];
       launch_departure_2d(wp, p, nx, grid->nt, grid->xmin, hgrid, dt, L0.s64, L0.s64 + (size_t)L0.nt * np, s);
     } else {
-      launch_departure_1d(wp, p, nx, grid->nt, grid->xmin, hgrid, dt, h->levels[0].s64, s);
+      launch_departure_1d(wp, p, nx, grid->nt, grid->xmin, hgrid, dt, h->levels[0].s64, opt.precision == 1, s);
     }
     h->phase_end(MGRIT_PHASE_DEPARTURE, ev, 1);
   }
@@ -834,7 +834,8 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
         launch_backtrack_2d(Lp.s64, Lp.s64 + pblk, l > 1 ? Lp.sigma : nullptr, l > 1 ? Lp.sigma + pblk : nullptr, L.m,
                             L.nt, nx, p, L.s64, L.s64 + blk, L.sigma, L.sigma + blk, s);
       else
-        launch_backtrack_1d(Lp.s64, l > 1 ? Lp.sigma : nullptr, L.m, L.nt, nx, p, L.s64, L.sigma, s);
+        launch_backtrack_1d(Lp.s64, l > 1 ? Lp.sigma : nullptr, Lp.eps_lo ? Lp.eps32 : nullptr, Lp.eps_lo, L.m, L.nt,
+                            nx, p, L.s64, L.sigma, s);
       h->phase_end(MGRIT_PHASE_BACKTRACK, ev, 1);
     }
     {

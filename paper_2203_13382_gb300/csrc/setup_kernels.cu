@@ -3,6 +3,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "df32.cuh"
 #include "kernels.h"
 #include "physics.cuh"
 #include "solver_layout.cuh"
@@ -132,6 +133,112 @@ __global__ void __launch_bounds__(256) k_departure_1d(WaveParams w, int nx, int 
   }
 }
 
+// ---- the same departure points in FP32 pairs (FP32-bulk handles, the spatially varying 1D speeds) ----
+//
+// GB300 runs FP64 at 1/64 of the FP32 rate, and the ERK stages above are FP64-bound.  Here every stage
+// runs on the FP32 pipes in FP32 pairs (df32.cuh: Dekker's product, Knuth's TwoSum), about 46 significant
+// bits after the rounding of a few dozen operations -- far inside the 1e-11 to which departure offsets are
+// checked, and of the order of the FP32-pair level-0 residual these handles use anyway.  FP64 remains
+// where a value enters once per node or row: sin / cos of the node's spatial phase, the stage time factors
+// and the offset stored.
+
+// a + b, renormalised (TwoSum of the high parts, the low parts added to its error).
+MGRIT_D df32 dep_add(df32 a, df32 b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  return df_norm(s, __fadd_rn(err, __fadd_rn(a.l, b.l)));
+}
+
+// a * b renormalised.
+MGRIT_D df32 dep_mul(df32 a, df32 b) {
+  const df32 p = df_mul(a, b);
+  return df_norm(p.h, p.l);
+}
+
+// sin t, cos t of a pair |t| < 2^-7: sin t = t (1 + t^2 (-1/6 + t^2/120)) with the t^3 term in pairs, and
+// cos t = 1 - t^2/2 + t^4 (1/24 - t^2/720) with t^2/2 in pairs; the parts left in FP32 (t^5/120, t^4/24 and
+// beyond) and the truncated terms are below 1e-17.
+MGRIT_D void dep_small_sincos(df32 t, df32& st, df32& ct) {
+  constexpr float m6h = (float)(-1.0 / 6.0);
+  constexpr float m6l = (float)(-1.0 / 6.0 - (double)(float)(-1.0 / 6.0));
+  const df32 t2 = dep_mul(t, t);
+  const float q = t2.h;
+  const df32 c1 = dep_add(df32{m6h, m6l}, df32{__fmul_rn(q, 1.f / 120.f), 0.f});
+  st = dep_add(t, dep_mul(t, dep_mul(t2, c1)));
+  const float cc = __fmul_rn(__fmul_rn(q, q), __fmaf_rn(q, -1.f / 720.f, 1.f / 24.f));
+  ct = dep_add(df32{1.f, 0.f}, dep_add(df32{-0.5f * t2.h, -0.5f * t2.l}, df32{cc, 0.f}));
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_departure_1d_df(WaveParams w, int nx, int nt, double xmin, double h,
+                                                         double dt, double* __restrict__ s) {
+  using Tb = ErkTab<R>;
+  constexpr int S = Tb::S;
+  __shared__ float2 tf[kDepSteps][S];  // the stage time factors as pairs (kind 3: a cos(2 pi t))
+  const int n0 = blockIdx.y * kDepSteps;
+  for (int q = threadIdx.x; q < kDepSteps * S; q += blockDim.x) {
+    const int nb = q / S, st = q % S;
+    const double c = cos(kTwoPi * ((n0 + nb + 1) * dt - Tb::c(st) * dt));
+    const df32 v = df_from_double(w.kind == 3 ? w.a * c : c);
+    tf[nb][st] = make_float2(v.h, v.l);
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  const double x = xmin + h * i;
+  const double kw = (w.kind == 3) ? kTwoPi * w.k : kTwoPi;
+  double Sx64, Cx64;
+  sincos(kw * x, &Sx64, &Cx64);
+  const df32 Sx = df_from_double(Sx64), Cx = df_from_double(Cx64);
+  df32 pa[S][S], pb[S];
+#pragma unroll
+  for (int st = 0; st < S; ++st) {
+#pragma unroll
+    for (int j = 0; j < S; ++j) pa[st][j] = df_from_double(kw * dt * Tb::a(st, j));
+    pb[st] = df_from_double(Tb::b(st) * dt / h);
+  }
+  const int nend = min(kDepSteps, nt - n0);
+  for (int nb = 0; nb < nend; ++nb) {
+    df32 k[S];
+#pragma unroll
+    for (int st = 0; st < S; ++st) {
+      const float2 t2 = tf[nb][st];
+      const df32 tfp{t2.x, t2.y};
+      df32 a;
+      if (st == 0) {  // the first stage point is the arrival node itself
+        a = w.kind == 2 ? dep_mul(tfp, Cx) : dep_add(df32{1.f, 0.f}, dep_mul(tfp, Sx));
+      } else {
+        df32 ph{0.f, 0.f};  // kw (x - stage point)
+#pragma unroll
+        for (int j = 0; j < st; ++j)
+          if (Tb::a(st, j) != 0.0) ph = dep_add(ph, dep_mul(pa[st][j], k[j]));
+        df32 sth, cth;
+        if (fabsf(ph.h) < 0.0078125f) {
+          dep_small_sincos(ph, sth, cth);
+        } else {  // large phase steps (coarse grids): FP64
+          double s64, c64;
+          small_sincos(df_to_double(ph), s64, c64);
+          sth = df_from_double(s64);
+          cth = df_from_double(c64);
+        }
+        if (w.kind == 2) {  // cos(2 pi t) cos(2 pi (x - d))
+          a = dep_mul(tfp, dep_add(dep_mul(Cx, cth), dep_mul(Sx, sth)));
+        } else {  // 1 + a sin(2 pi k (x - d)) cos(2 pi t)
+          const df32 cs = dep_mul(Cx, sth);
+          a = dep_add(df32{1.f, 0.f}, dep_mul(tfp, dep_add(dep_mul(Sx, cth), df32{-cs.h, -cs.l})));
+        }
+      }
+      k[st] = a;
+    }
+    df32 sv{0.f, 0.f};
+#pragma unroll
+    for (int st = 0; st < S; ++st)
+      if (Tb::b(st) != 0.0) sv = dep_add(sv, dep_mul(pb[st], k[st]));
+    s[(size_t)(n0 + nb) * nx + i] = df_to_double(sv);
+  }
+}
+
 // 2D: arrival node (i, j) of the steps n0 .. n0 + kDepSteps - 1 (blockIdx.y).  The node's sin / cos of
 // the spatial phases are formed once; at a stage point (x - dx, y - dy) they follow by angle addition with
 // a small-angle series, and the time factors of the stages are shared by the block.
@@ -214,9 +321,15 @@ __global__ void __launch_bounds__(256) k_departure_2d(WaveParams w, int nx, int 
 }
 
 void launch_departure_1d(const WaveParams& w, int r, int nx, int nt, double xmin, double h, double dt, double* s,
-                         cudaStream_t st) {
+                         bool pairs, cudaStream_t st) {
   const int bs = 256;
   dim3 grid((unsigned)((nx + bs - 1) / bs), (unsigned)((nt + kDepSteps - 1) / kDepSteps));
+  if (pairs && (w.kind == 2 || w.kind == 3)) {
+    if (r == 1) k_departure_1d_df<1><<<grid, bs, 0, st>>>(w, nx, nt, xmin, h, dt, s);
+    else if (r == 3) k_departure_1d_df<3><<<grid, bs, 0, st>>>(w, nx, nt, xmin, h, dt, s);
+    else k_departure_1d_df<5><<<grid, bs, 0, st>>>(w, nx, nt, xmin, h, dt, s);
+    return;
+  }
   if (r == 1) k_departure_1d<1><<<grid, bs, 0, st>>>(w, nx, nt, xmin, h, dt, s);
   else if (r == 3) k_departure_1d<3><<<grid, bs, 0, st>>>(w, nx, nt, xmin, h, dt, s);
   else k_departure_1d<5><<<grid, bs, 0, st>>>(w, nx, nt, xmin, h, dt, s);
@@ -416,9 +529,31 @@ MGRIT_D double f_prod(double z) {
   return out;
 }
 
-// One coarse step row n (blockIdx.y) of arrival nodes i.
+// f_prod of an FP32 pair z (about 44 significant bits): Horner's rule on the integer coefficients with
+// pair products (Dekker) and the constant added by TwoSum, renormalised every step (df32.cuh).
 template <int P>
-__global__ void k_backtrack_1d(const double* __restrict__ s_prev, const double* __restrict__ sig_prev, int m, int nx,
+MGRIT_D df32 f_prod_df(df32 z) {
+  constexpr FProdCoef<P> k{};
+  df32 out{1.f, 0.f};
+#pragma unroll
+  for (int d = P; d >= 0; --d) {
+    const df32 t = df_mul(out, z);
+    const float c = (float)k.c[d];
+    const float s = __fadd_rn(t.h, c);
+    const float bb = __fsub_rn(s, t.h);
+    const float err = __fadd_rn(__fsub_rn(t.h, __fsub_rn(s, bb)), __fsub_rn(c, bb));
+    out = df_norm(s, __fadd_rn(err, t.l));
+  }
+  return out;
+}
+
+// One coarse step row n (blockIdx.y) of arrival nodes i.  eh_prev / el_prev (or null): the FP32 pair
+// (eps_hi, eps_lo) of the fine level's eps rows, when that level keeps them (level 0 of the FP32-bulk
+// mode); the sum of f over the m fine steps is then formed in FP32 pairs on the FP32 pipes instead of
+// from s_prev in FP64 (GB300 runs FP64 at 1/64 of the FP32 rate).
+template <int P>
+__global__ void k_backtrack_1d(const double* __restrict__ s_prev, const double* __restrict__ sig_prev,
+                               const float* __restrict__ eh_prev, const float* __restrict__ el_prev, int m, int nx,
                                double* __restrict__ s_out, double* __restrict__ sig_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nx) return;
@@ -438,10 +573,18 @@ __global__ void k_backtrack_1d(const double* __restrict__ s_prev, const double* 
   const size_t idx = (size_t)n * nx + i;
   s_out[idx] = sc;
   double ff = 0.0, gs = 0.0;
-  for (int k = 0; k < m; ++k) {
-    ff += f_prod<P>(frac_eps(s_prev[base + (size_t)k * nx + i]));
-    if (sig_prev) gs += sig_prev[base + (size_t)k * nx + i];
+  if (eh_prev) {
+    float fh = 0.f, fl = 0.f;
+    for (int k = 0; k < m; ++k) {
+      const size_t q = base + (size_t)k * nx + i;
+      df_acc(fh, fl, f_prod_df<P>(df32{eh_prev[q], el_prev[q]}));
+    }
+    ff = (double)fh + (double)fl;
+  } else {
+    for (int k = 0; k < m; ++k) ff += f_prod<P>(frac_eps(s_prev[base + (size_t)k * nx + i]));
   }
+  if (sig_prev)
+    for (int k = 0; k < m; ++k) gs += sig_prev[base + (size_t)k * nx + i];
   double inv_fact = 1.0;
 #pragma unroll
   for (int b = 2; b <= P + 1; ++b) inv_fact /= b;
@@ -449,19 +592,21 @@ __global__ void k_backtrack_1d(const double* __restrict__ s_prev, const double* 
   sig_out[idx] = sig_prev ? gs + phi : phi;
 }
 
-void launch_backtrack_1d(const double* s_prev, const double* sigma_prev, int m, int ntc, int nx, int p, double* s_out,
-                         double* sigma_out, cudaStream_t st) {
+void launch_backtrack_1d(const double* s_prev, const double* sigma_prev, const float* eh_prev, const float* el_prev,
+                         int m, int ntc, int nx, int p, double* s_out, double* sigma_out, cudaStream_t st) {
   const int bs = 256;
   for (int r0 = 0; r0 < ntc; r0 += 65535) {
     const int rows = min(65535, ntc - r0);
     dim3 g((unsigned)((nx + bs - 1) / bs), (unsigned)rows);
     const double* sp = s_prev + (size_t)m * r0 * nx;
     const double* gp = sigma_prev ? sigma_prev + (size_t)m * r0 * nx : nullptr;
+    const float* eh = (eh_prev && el_prev) ? eh_prev + (size_t)m * r0 * nx : nullptr;
+    const float* el = (eh_prev && el_prev) ? el_prev + (size_t)m * r0 * nx : nullptr;
     double* so = s_out + (size_t)r0 * nx;
     double* go = sigma_out + (size_t)r0 * nx;
-    if (p == 1) k_backtrack_1d<1><<<g, bs, 0, st>>>(sp, gp, m, nx, so, go);
-    else if (p == 3) k_backtrack_1d<3><<<g, bs, 0, st>>>(sp, gp, m, nx, so, go);
-    else k_backtrack_1d<5><<<g, bs, 0, st>>>(sp, gp, m, nx, so, go);
+    if (p == 1) k_backtrack_1d<1><<<g, bs, 0, st>>>(sp, gp, eh, el, m, nx, so, go);
+    else if (p == 3) k_backtrack_1d<3><<<g, bs, 0, st>>>(sp, gp, eh, el, m, nx, so, go);
+    else k_backtrack_1d<5><<<g, bs, 0, st>>>(sp, gp, eh, el, m, nx, so, go);
   }
 }
 
