@@ -168,6 +168,15 @@ MGRIT_D void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t*
                : "memory");
 }
 
+// Programmatic dependent launch (sm_90+).  A kernel launched with programmatic stream serialization may
+// start while the kernel before it on the stream is still running: it does its independent prologue
+// (barrier set-up, bulk copies of set-up tables) and then waits in pdl_wait until that kernel has finished
+// and its writes are visible; nothing that kernel writes, or reads, is touched before the wait.
+// pdl_trigger lets the next kernel start once every CTA of this one has called it.  Both are no-ops for a
+// kernel launched without the attribute.
+MGRIT_D void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+MGRIT_D void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Asks for [src, src + bytes) to be brought into L2 (a hint: nothing to wait for, no shared memory).
 // Issued only for 16-byte aligned addresses and sizes that are a multiple of 16.
 MGRIT_D void bulk_prefetch_l2(const void* src, uint32_t bytes) {

@@ -30,6 +30,21 @@ MGRIT_D df32 df_from_double(double x) {
 
 MGRIT_D double df_to_double(df32 a) { return __dadd_rn((double)a.h, (double)a.l); }
 
+// (double)x for an FP32 x by moving its bits (exact: rebiased exponent, significand shifted into place);
+// zero keeps its sign, subnormal, infinite and NaN inputs take the conversion instruction.
+MGRIT_D double float_to_double_bits(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)sign);
+  if (e == 0 || e == 0xffu) return (double)x;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// df_to_double with the two conversions done by float_to_double_bits (one FP64 instruction, the add).
+MGRIT_D double df_to_double_bits(df32 a) { return __dadd_rn(float_to_double_bits(a.h), float_to_double_bits(a.l)); }
+
 // c - e for an integer c with |c| >= 1 and 0 <= e.h < 1 (so |c| >= |e.h|: Fast2Sum), not renormalised.
 MGRIT_D df32 df_int_minus(float c, df32 e) {
   const float s = __fsub_rn(c, e.h);

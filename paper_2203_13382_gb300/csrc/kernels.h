@@ -23,8 +23,10 @@ void launch_departure_2d(const WaveParams& w, int r, int nx, int nt, double xmin
 // s_prev [m*ntc][nx], sigma_prev [m*ntc][nx] or NULL (level 1); eh_prev / el_prev [m*ntc][nx]: the fine
 // level's eps as FP32 pairs, or NULL (the sum of f over the fine steps then comes from s_prev in FP64);
 // outputs [ntc][nx].
+// pairs: FP32-pair arithmetic for the composition and the sum of f (FP32-bulk handles), else FP64.
 void launch_backtrack_1d(const double* s_prev, const double* sigma_prev, const float* eh_prev, const float* el_prev,
-                         int m, int ntc, int nx, int p, double* s_out, double* sigma_out, cudaStream_t st);
+                         bool pairs, int m, int ntc, int nx, int p, double* s_out, double* sigma_out,
+                         cudaStream_t st);
 // 2D bilinear backtracking (Sec. SM6); sigma_x / sigma_y per component.
 void launch_backtrack_2d(const double* sx_prev, const double* sy_prev, const double* gx_prev, const double* gy_prev,
                          int m, int ntc, int nx, int p, double* sx_out, double* sy_out, double* gx_out, double* gy_out,
@@ -160,6 +162,8 @@ struct RelaxArgs {
   void* rout;          // MODE_RES: residual output (stride r_stride)
   float* rout32;       // MODE_RES, FP64 passes: optional FP32 copy of the residual (stride r_stride)
   int rout_f64;        // MODE_RES, FP32 passes: rout holds doubles (an FP64 coarse level's right-hand side)
+  int rout_value;      // MODE_RES, FP32-pair passes: rout receives the propagated C value S^m u_C(j) (the
+                       // C-relaxed value, residual + current value) instead of the residual
   long long c_stride;
   long long r_stride;
   int g_at_c;          // MODE_RES: add g at the C-point
@@ -229,7 +233,7 @@ cudaError_t launch_relax_batched(const LevelTables* d_tabs, const RelaxArgs* d_a
 cudaError_t launch_sequential_batched(const LevelTables* d_tabs, const SeqArgs* d_args, const BatchTile* d_tiles,
                                       int ntiles, const int* d_active, int is_double, int coarse, int buf,
                                       size_t smem, cudaStream_t st);
-// launch_axpy_convert over many segments in one launch (kinds 1, 3, 5 and 0 = copy); segments of
+// launch_axpy_convert over many segments in one launch (kinds 1, 3, 5, 8 and 0 = copy); segments of
 // inactive problems have n = 0.
 void launch_axpy_batched(int kind, const Segment* d_seg, int nseg, long long maxn, cudaStream_t st);
 // out = sum of seg.x[0 .. n) (doubles, fixed order) written to *(double*)seg.y, one CTA per segment.
@@ -240,7 +244,8 @@ void launch_sum(const double* v, int count, double* out, cudaStream_t st);
 // out[0] = sum_i (a[i] + b[i] - ref[i])^2 over n values (b may be NULL), fixed order.
 void launch_dist2(const double* a, const double* b, const double* ref, long long n, double* out, cudaStream_t st);
 // Elementwise update with type conversion: kind 0: y = x (d); 1: y(f) = x(d); 2: y(d) += x(f);
-// 3: y(d) = x(f); 4: y(d) += x(d); 5: y(d) += x(d) + z(f); 6: y(d) = x(d) - z(d); 7: y(d) += x(d) + z(d).
+// 3: y(d) = x(f); 4: y(d) += x(d); 5: y(d) += x(d) + z(f); 6: y(d) = x(d) - z(d); 7: y(d) += x(d) + z(d);
+// 8: y(d) = x(d) + z(f); 9: y(d) = x(d) + z(d).
 void launch_axpy_convert(int kind, const void* x, void* y, const void* z, long long n, cudaStream_t st);
 // zero fill
 void launch_fill_zero(void* y, long long bytes, cudaStream_t st);

@@ -1537,6 +1537,8 @@ __device__ __forceinline__ void relax_body(const LevelTables& T, const RelaxArgs
   Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), T, COARSE);
   if constexpr (std::is_same<R, float>::value)
     stage_prefetch_first<P, COARSE>(stg, T, (j < a.J && a.nsteps > 0) ? j * a.m : -1);
+  pdl_trigger();
+  pdl_wait();  // the set-up tables above are read-only; everything below depends on the previous kernel
   {
     const R* st = a.start ? (const R*)a.start + (size_t)j * a.start_stride : nullptr;
     const R* co = a.corr ? (const R*)a.corr + (size_t)j * a.corr_stride : nullptr;
@@ -1701,19 +1703,6 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
   float2* dst = src + buf;
   double* red = reinterpret_cast<double*>(dst + buf);
   const int nx = T.nx;
-  {
-    const double* st = a.start ? (const double*)a.start + (size_t)j * a.start_stride : nullptr;
-    const double* co = a.corr ? (const double*)a.corr + (size_t)j * a.corr_stride : nullptr;
-    double* wb = a.start_wb ? (double*)a.start_wb + (size_t)j * a.wb_stride : nullptr;
-    for (int i = threadIdx.x; i < nx; i += NT) {
-      double v = st ? st[i] : 0.0;
-      if (co) v += co[i];
-      const df32 d = df_from_double(v);
-      src[i] = make_float2(d.h, d.l);
-      if (wb) wb[i] = v;
-    }
-  }
-  write_halo(src, nx);
   // the table rows of a step are read once, straight from global memory: they are asked into L2 two
   // steps ahead (three bulk prefetches a step, one thread each), so the gather's loads hit L2
   auto prefetch_rows = [&](int k) {
@@ -1728,6 +1717,21 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
     prefetch_rows(0);
     prefetch_rows(1);
   }
+  pdl_trigger();
+  pdl_wait();  // the tables are read-only; the slices and C-point arrays come from the previous kernel
+  {
+    const double* st = a.start ? (const double*)a.start + (size_t)j * a.start_stride : nullptr;
+    const double* co = a.corr ? (const double*)a.corr + (size_t)j * a.corr_stride : nullptr;
+    double* wb = a.start_wb ? (double*)a.start_wb + (size_t)j * a.wb_stride : nullptr;
+    for (int i = threadIdx.x; i < nx; i += NT) {
+      double v = st ? st[i] : 0.0;
+      if (co) v += co[i];
+      const df32 d = df_from_double(v);
+      src[i] = make_float2(d.h, d.l);
+      if (wb) wb[i] = v;
+    }
+  }
+  write_halo(src, nx);
   __syncthreads();
   if (j >= a.J) return;  // extra CTA: only the correction of the last C-point
   double sq = 0.0;
@@ -1743,7 +1747,7 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
         double* fs = (double*)a.fstore + (size_t)(n + 1) * nx;
         for (int i = threadIdx.x; i < nx; i += NT) {
           const float2 v = dst[i];
-          fs[i] = df_to_double(df32{v.x, v.y});
+          fs[i] = df_to_double_bits(df32{v.x, v.y});
         }
       }
     } else if (a.mode == MODE_FC) {
@@ -1759,10 +1763,11 @@ __device__ __forceinline__ void relax_body_df(const LevelTables& T, const RelaxA
       float* ro32 = a.rout32 ? a.rout32 + (size_t)(j + 1) * a.r_stride : nullptr;
       for (int i = threadIdx.x; i < nx; i += NT) {
         const float2 d = dst[i];
-        double v = df_to_double(df32{d.x, d.y});
+        const double pv = df_to_double(df32{d.x, d.y});
+        double v = pv;
         if (cc) v -= (ci ? ci[i] : 0.0) + cc[i];
         else if (ci) v -= ci[i];
-        if (ro) ro[i] = v;
+        if (ro) ro[i] = a.rout_value ? pv : v;
         if (ro32) ro32[i] = (float)v;
         if (a.norm_partial) sq += v * v;
       }
@@ -1794,6 +1799,8 @@ __device__ __forceinline__ void sequential_body(const LevelTables& T, int N, con
   const int nx = T.nx;
   Stage stg = stage_init(smem_raw, 2 * (size_t)buf * sizeof(R) + 64 * sizeof(double), T, COARSE);
   if constexpr (std::is_same<R, float>::value) stage_prefetch_first<P, COARSE>(stg, T, N > 0 ? 0 : -1);
+  pdl_trigger();
+  pdl_wait();  // u0 and g come from the previous kernel
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const R v = u0 ? u0[i] : (R)0;
     src[i] = v;
@@ -1929,6 +1936,24 @@ size_t smem_bytes(int buf, const LevelTables& T, bool coarse) {
   return b;
 }
 
+// Launches kern with programmatic stream serialization (see pdl_wait): it may begin its prologue while the
+// previous kernel on the stream finishes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename R, int COARSE, bool TR>
 cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_t st) {
   const int buf = buffer_elems(T, COARSE);
@@ -1940,8 +1965,8 @@ cudaError_t relax_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStream_
     auto kern = k_relax_1d<PP, R, COARSE, TR>;                                                                 \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
     if (e != cudaSuccess) return e;                                                                        \
-    kern<<<grid, slice_threads<PP, R, COARSE>(), sm, st>>>(T, a, buf);                                                      \
-    return cudaGetLastError();                                                                             \
+    e = launch_pdl(kern, (unsigned)grid, (unsigned)slice_threads<PP, R, COARSE>(), sm, st, T, a, buf);      \
+    return e != cudaSuccess ? e : cudaGetLastError();                                                      \
   }
   if (T.p == 1) MGRIT_LAUNCH_RELAX(1)
   if (T.p == 3) MGRIT_LAUNCH_RELAX(3)
@@ -1959,8 +1984,8 @@ cudaError_t relax_df_dispatch(const LevelTables& T, const RelaxArgs& a, cudaStre
     cudaError_t e = cudaFuncSetAttribute(k_relax_df_1d<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                          (int)sm);                                                         \
     if (e != cudaSuccess) return e;                                                                        \
-    k_relax_df_1d<PP><<<grid, kSliceThreads, sm, st>>>(T, a, buf);                                         \
-    return cudaGetLastError();                                                                             \
+    e = launch_pdl(k_relax_df_1d<PP>, (unsigned)grid, (unsigned)kSliceThreads, sm, st, T, a, buf);         \
+    return e != cudaSuccess ? e : cudaGetLastError();                                                      \
   }
   if (T.p == 1) MGRIT_LAUNCH_DF(1)
   if (T.p == 3) MGRIT_LAUNCH_DF(3)
@@ -1978,8 +2003,9 @@ cudaError_t sequential_dispatch(const LevelTables& T, int N, const void* g, cons
     auto kern = k_sequential_1d<PP, R, COARSE, TR>;                                                            \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
     if (e != cudaSuccess) return e;                                                                        \
-    kern<<<1, slice_threads<PP, R, COARSE>(), sm, st>>>(T, N, (const R*)g, (const R*)u0, (R*)u, store_all, buf);            \
-    return cudaGetLastError();                                                                             \
+    e = launch_pdl(kern, 1u, (unsigned)slice_threads<PP, R, COARSE>(), sm, st, T, N, (const R*)g, (const R*)u0, \
+                   (R*)u, store_all, buf);                                                                 \
+    return e != cudaSuccess ? e : cudaGetLastError();                                                      \
   }
   if (T.p == 1) MGRIT_LAUNCH_SEQ(1)
   if (T.p == 3) MGRIT_LAUNCH_SEQ(3)
@@ -2067,6 +2093,8 @@ __global__ void k_axpy_convert(int kind, const void* __restrict__ x, void* __res
     case 4: ((double*)y)[i] += ((const double*)x)[i]; break;
     case 5: ((double*)y)[i] += ((const double*)x)[i] + (double)((const float*)z)[i]; break;
     case 7: ((double*)y)[i] += ((const double*)x)[i] + ((const double*)z)[i]; break;
+    case 8: ((double*)y)[i] = ((const double*)x)[i] + float_to_double_bits(((const float*)z)[i]); break;
+    case 9: ((double*)y)[i] = ((const double*)x)[i] + ((const double*)z)[i]; break;
     default: ((double*)y)[i] = ((const double*)x)[i] - ((const double*)z)[i]; break;
   }
 }
@@ -2164,6 +2192,7 @@ __global__ void k_axpy_batched(int kind, const Segment* __restrict__ seg) {
       case 1: ((float*)sg.y)[i] = (float)((const double*)sg.x)[i]; break;
       case 3: ((double*)sg.y)[i] = (double)((const float*)sg.x)[i]; break;
       case 5: ((double*)sg.y)[i] += ((const double*)sg.x)[i] + (double)((const float*)sg.z)[i]; break;
+      case 8: ((double*)sg.y)[i] = ((const double*)sg.x)[i] + float_to_double_bits(((const float*)sg.z)[i]); break;
       default: ((double*)sg.y)[i] = ((const double*)sg.x)[i]; break;
     }
   }

@@ -725,8 +725,8 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
     if ((st = h->alloc(&L.s64, rows)) != MGRIT_OK) return cleanup_fail(st);
     if ((st = h->alloc(&L.shift, rows)) != MGRIT_OK) return cleanup_fail(st);
     // FP64 levels read precomputed weights (2D: per axis); level 0 of a 1D FP32-bulk handle runs its FP64
-    // passes in FP32 pairs from eps32 and eps_lo instead
-    const bool pairs = l == 0 && fp32 && dim == 1 && !fine_only;
+    // passes in FP32 pairs from eps32 and eps_lo instead (fine_only handles too: their FP64 single steps)
+    const bool pairs = l == 0 && fp32 && dim == 1;
     const bool need64 = L.is_double || (l == 0 && !pairs);
     const bool need32 = !L.is_double;
     if (need64 && (st = h->alloc(&L.w64, rows * (p + 1))) != MGRIT_OK) return cleanup_fail(st);
@@ -834,8 +834,8 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
         launch_backtrack_2d(Lp.s64, Lp.s64 + pblk, l > 1 ? Lp.sigma : nullptr, l > 1 ? Lp.sigma + pblk : nullptr, L.m,
                             L.nt, nx, p, L.s64, L.s64 + blk, L.sigma, L.sigma + blk, s);
       else
-        launch_backtrack_1d(Lp.s64, l > 1 ? Lp.sigma : nullptr, Lp.eps_lo ? Lp.eps32 : nullptr, Lp.eps_lo, L.m, L.nt,
-                            nx, p, L.s64, L.sigma, s);
+        launch_backtrack_1d(Lp.s64, l > 1 ? Lp.sigma : nullptr, Lp.eps_lo ? Lp.eps32 : nullptr, Lp.eps_lo,
+                            opt.precision == 1, L.m, L.nt, nx, p, L.s64, L.sigma, s);
       h->phase_end(MGRIT_PHASE_BACKTRACK, ev, 1);
     }
     {
@@ -1001,6 +1001,9 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
         return enqueue_norm(h, J);
       }
       a.rout32 = h->EC;  // C-relaxation of the error equation from a zero guess gives e_C = r (FP32)
+      // FP32-pair residual pass (1D): r64 receives the C-relaxed value S^m u_C(j) = u_C(j+1) + r(j+1)
+      const bool cval = h->levels[0].eps_lo != nullptr;
+      a.rout_value = cval ? 1 : 0;
       MG_TRY(relax(h, 0, 1, a, MGRIT_PHASE_FINE64_RES));
       // F-relaxation + residual of the error equation in FP32
       a = args0();
@@ -1016,10 +1019,15 @@ mgrit_status solve_impl(mgrit_handle* h, const double* d_u0, cudaMemcpyKind u0_k
       a.norm_partial = h->norm_partial;
       MG_TRY(relax(h, 0, 0, a, MGRIT_PHASE_FINE32_RES));
       MG_TRY(coarse_cycle(h, 1));
-      // u_C += r + E_1
+      // u_C += r + E_1 (with the C-relaxed values: u_C(j) = r64(j) + E_1(j), j >= 1; u_C(0) stays u0)
       {
         const int ev = h->phase_begin();
-        launch_axpy_convert(L1.is_double ? 7 : 5, h->r64, h->X, L1.E, (long long)(J + 1) * np, s);
+        if (cval)
+          launch_axpy_convert(L1.is_double ? 9 : 8, h->r64 + np, h->X + np,
+                              L1.is_double ? (const void*)((const double*)L1.E + np) : (const void*)((const float*)L1.E + np),
+                              (long long)J * np, s);
+        else
+          launch_axpy_convert(L1.is_double ? 7 : 5, h->r64, h->X, L1.E, (long long)(J + 1) * np, s);
         h->phase_end(MGRIT_PHASE_MISC, ev, 1);
       }
     }
@@ -1717,6 +1725,7 @@ mgrit_status mgrit_setup_batched(int nprob, const mgrit_grid* grids, const mgrit
     a.m = m1; a.J = J; a.nsteps = m1; a.mode = MODE_RES;
     a.start = h->X; a.start_stride = np; a.cin = h->X; a.c_stride = np; a.rout = h->r64; a.r_stride = np;
     a.rout32 = h->EC;  // e_C = r in FP32
+    a.rout_value = 1;  // r64 receives the C-relaxed value S^m u_C(j) = u_C(j+1) + r(j+1)
     nt = J;
     return true;
   }, b->down);
@@ -1936,7 +1945,7 @@ mgrit_status batched_solve_impl(mgrit_batch* b, const double* const* u0, const d
     for (auto& ph : b->down) MG_TRY(run(ph, batch_phase_index(ph)));  // down[0]: FP64 residual, e_C = r
     for (auto& ph : b->up) MG_TRY(run(ph, MGRIT_PHASE_COARSE));
     int e = ev_begin();
-    launch_axpy_batched(5, b->d_seg + nprob, nprob, b->maxn_all, s);  // u_C += r + E_1
+    launch_axpy_batched(8, b->d_seg + nprob, nprob, b->maxn_all, s);  // u_C = S^m u_C + E_1 (= u_C + r + E_1)
     ev_end(e, MGRIT_PHASE_MISC);
     e = ev_begin();
     launch_sum_batched(b->d_seg + 2 * nprob, nprob, s);
@@ -1951,10 +1960,10 @@ mgrit_status batched_solve_impl(mgrit_batch* b, const double* const* u0, const d
   for (int k = 0; k < b->opt.max_iter && n_active > 0; ++k) {
     for (int q = 0; q < nprob; ++q) {
       mgrit_handle* h = b->hs[q];
-      const long long n = active[q] ? (long long)(h->J1() + 1) * h->npts : 0;
+      const long long n = active[q] ? (long long)h->J1() * h->npts : 0;  // C-points 1 .. J
       b->h_active[q] = active[q];
       b->h_seg[q] = Segment{nullptr, nullptr, nullptr, 0};
-      b->h_seg[nprob + q] = Segment{h->r64, h->X, h->levels[1].E, n};
+      b->h_seg[nprob + q] = Segment{h->r64 + h->npts, h->X + h->npts, (const float*)h->levels[1].E + h->npts, n};
       b->h_seg[2 * nprob + q] = Segment{h->norm_partial, b->d_norms + q, nullptr, active[q] ? (long long)h->J1() : 0};
     }
     MG_CUDA(cudaMemcpyAsync(b->d_active, b->h_active, nprob * sizeof(int), cudaMemcpyHostToDevice, s));

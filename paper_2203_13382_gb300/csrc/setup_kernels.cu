@@ -495,6 +495,80 @@ void launch_departure_da_2d(const WaveParams& w, int r, int nx, int nt, double x
 // K2: backtracking (Sec. 3.3.1 eq. (coarse_depart_interp); Sec. SM6) and phi / sigma (eq. (nu_p_def))
 // ------------------------------------------------------------------------------------------------
 
+// floor(s) and eps = s - floor(s) as an FP32 pair (eh = eps rounded to nearest-even at 24 bits, el = the
+// rest rounded the same way), from the bit pattern of s with integer operations only (GB300 runs FP64,
+// conversions included, at 1/64 of the FP32 rate).  With E the unbiased exponent of s and m its 53-bit
+// significand, eps = G 2^-k: for 1 <= |s| < 2^30 the k = 52 - E fraction bits of m (complemented to
+// 2^k when s < 0), for 0 < s < 1 all of m with k = 52 - E.  Then eh takes the top 24 bits of G with the
+// rounding carry and el the signed remainder.  Every case the function accepts gives the values of the
+// FP64 route (eps is exact in FP64 there); it returns false for the rest (-1 < s < 0, |s| >= 2^30,
+// 0 < eps < 2^-74), which take the FP64 route.
+MGRIT_D bool split_offset_int(double s, int& fl, float& eh, float& el) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const bool neg = (b >> 63) != 0;
+  if (e == 0) {
+    if (neg) return false;
+    fl = 0;  // +0 or a positive subnormal: eps below 2^-1022, taken as 0
+    eh = el = 0.f;
+    return true;
+  }
+  const int E = e - 1023;
+  if (E >= 30) return false;
+  const unsigned long long m = (b & 0xfffffffffffffULL) | (1ULL << 52);
+  const int k = 52 - E;
+  unsigned long long G;
+  if (E >= 0) {
+    const long long I = (long long)(m >> k);
+    G = m & ((1ULL << k) - 1);
+    if (!neg) {
+      fl = (int)I;
+    } else if (G) {
+      fl = -(int)I - 1;
+      G = (1ULL << k) - G;
+    } else {
+      fl = -(int)I;
+    }
+  } else {
+    if (neg) return false;
+    fl = 0;
+    G = m;
+  }
+  if (G == 0) {
+    eh = el = 0.f;
+    return true;
+  }
+  const int lead = 63 - __clzll((long long)G);
+  int ex = lead - k;  // eps in [2^ex, 2^(ex+1))
+  if (ex < -74) return false;
+  unsigned hm;
+  int r = 0;  // G = hm 2^d + r
+  int d = lead - 23;
+  if (d <= 0) {
+    hm = (unsigned)(G << (-d));
+    d = 0;
+  } else {
+    hm = (unsigned)(G >> d);
+    const unsigned long long rem = G & ((1ULL << d) - 1);
+    const unsigned long long half = 1ULL << (d - 1);
+    long long rr = (long long)rem;
+    if (rem > half || (rem == half && (hm & 1u))) {
+      ++hm;
+      rr -= 1LL << d;
+    }
+    r = (int)rr;
+    if (hm == (1u << 24)) {
+      hm >>= 1;
+      ++ex;
+    }
+  }
+  eh = __uint_as_float(((unsigned)(ex + 127) << 23) | (hm & 0x7fffffu));
+  // el = r 2^-k: r has at most 29 bits, so its conversion rounds as the FP64 route does, and 2^-k is a
+  // normal FP32 power of two (k = lead - ex <= 52 + 74)
+  el = r == 0 ? 0.f : __fmul_rn(__int2float_rn(r), __uint_as_float((unsigned)(127 - k) << 23));
+  return true;
+}
+
 // eps = s - floor(s) in [0, 1) (east-neighbour distance, eq. (depart_decompose)).
 MGRIT_D double frac_eps(double s) {
   double e = s - floor(s);
@@ -547,39 +621,100 @@ MGRIT_D df32 f_prod_df(df32 z) {
   return out;
 }
 
-// One coarse step row n (blockIdx.y) of arrival nodes i.  eh_prev / el_prev (or null): the FP32 pair
-// (eps_hi, eps_lo) of the fine level's eps rows, when that level keeps them (level 0 of the FP32-bulk
-// mode); the sum of f over the m fine steps is then formed in FP32 pairs on the FP32 pipes instead of
-// from s_prev in FP64 (GB300 runs FP64 at 1/64 of the FP32 rate).
+// s = fl + eps with eps as an FP32 pair: the integer route where it applies, else FP64.
+MGRIT_D void offset_parts(double s, int& fl, df32& eps) {
+  float eh, el;
+  if (split_offset_int(s, fl, eh, el)) {
+    eps = df32{eh, el};
+    return;
+  }
+  double f = floor(s), e = s - f;
+  if (e >= 1.0) {
+    e -= 1.0;
+    f += 1.0;
+  }
+  fl = (int)f;
+  eps = df_from_double(e);
+}
+
+// a - e for an integer a (|a| < 2^24) and a pair 0 <= e < 1, renormalised.
+MGRIT_D df32 int_minus_pair(int a, df32 e) {
+  const float c = (float)a;
+  const float s = __fsub_rn(c, e.h);
+  const float bb = __fsub_rn(s, c);
+  const float err = __fsub_rn(__fsub_rn(c, __fsub_rn(s, bb)), __fadd_rn(e.h, bb));
+  return df_norm(s, __fsub_rn(err, e.l));
+}
+
+// One coarse step row n (blockIdx.y) of arrival nodes i.  pairs (FP32-bulk handles): the composition of
+// the fine maps and the sum of f over the m fine steps are formed in FP32 pairs on the FP32 pipes, each
+// fine offset split into its integer floor and its eps pair by integer operations (GB300 runs FP64 at
+// 1/64 of the FP32 rate); the coarse offset keeps about 46 bits (1e-11 of a 650-cell offset on the
+// deepest level of the 4096 x 16384 workload).  Otherwise FP64 throughout.  eh_prev / el_prev (or null):
+// the fine level's eps pair rows where that level keeps them (level 0 of the FP32-bulk mode).
 template <int P>
 __global__ void k_backtrack_1d(const double* __restrict__ s_prev, const double* __restrict__ sig_prev,
-                               const float* __restrict__ eh_prev, const float* __restrict__ el_prev, int m, int nx,
-                               double* __restrict__ s_out, double* __restrict__ sig_out) {
+                               const float* __restrict__ eh_prev, const float* __restrict__ el_prev, int pairs,
+                               int m, int nx, double* __restrict__ s_out, double* __restrict__ sig_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nx) return;
   const int n = blockIdx.y;
   const size_t base = (size_t)m * n * nx;
   // position of the coarse characteristic relative to x_i in grid units; c^{(m-1)} = f^{(m-1)}
-  double c = -s_prev[base + (size_t)(m - 1) * nx + i];
-  for (int k = m - 2; k >= 0; --k) {
-    const double* row = s_prev + base + (size_t)k * nx;
-    const double xE = ceil(c);  // east node of c (the node itself if c lies on one)
-    const int E = i + (int)xE;
-    const double fE = xE - row[wrap_pow2(E, nx)];
-    const double fW = (xE - 1.0) - row[wrap_pow2(E - 1, nx)];
-    c = (fE - fW) * (c - xE) + fE;
+  double sc;
+  if (pairs) {
+    int fl;
+    df32 e;
+    offset_parts(s_prev[base + (size_t)(m - 1) * nx + i], fl, e);
+    df32 c = int_minus_pair(-fl, e);  // -(fl + eps)
+    for (int k = m - 2; k >= 0; --k) {
+      const double* row = s_prev + base + (size_t)k * nx;
+      // east node of c (the node itself if c lies on one): ceil of the high part unless c sits just above
+      // an integer high part
+      float ce = ceilf(c.h);
+      if (ce == c.h && c.l > 0.f) ce += 1.f;
+      const int xE = (int)ce;
+      const int E = i + xE;
+      int fE_i, fW_i;
+      df32 eE, eW;
+      offset_parts(row[wrap_pow2(E, nx)], fE_i, eE);
+      offset_parts(row[wrap_pow2(E - 1, nx)], fW_i, eW);
+      const df32 fE = int_minus_pair(xE - fE_i, eE);      // xE - s[E]
+      const df32 fW = int_minus_pair(xE - 1 - fW_i, eW);  // (xE - 1) - s[E - 1]
+      const df32 slope = dep_add(fE, df32{-fW.h, -fW.l});
+      const df32 t = dep_add(c, df32{-ce, 0.f});           // c - xE
+      c = dep_add(dep_mul(slope, t), fE);
+    }
+    sc = -df_to_double(c);
+  } else {
+    double c = -s_prev[base + (size_t)(m - 1) * nx + i];
+    for (int k = m - 2; k >= 0; --k) {
+      const double* row = s_prev + base + (size_t)k * nx;
+      const double xE = ceil(c);  // east node of c (the node itself if c lies on one)
+      const int E = i + (int)xE;
+      const double fE = xE - row[wrap_pow2(E, nx)];
+      const double fW = (xE - 1.0) - row[wrap_pow2(E - 1, nx)];
+      c = (fE - fW) * (c - xE) + fE;
+    }
+    sc = -c;
   }
-  const double sc = -c;
   const size_t idx = (size_t)n * nx + i;
   s_out[idx] = sc;
   double ff = 0.0, gs = 0.0;
-  if (eh_prev) {
-    float fh = 0.f, fl = 0.f;
+  if (eh_prev || pairs) {
+    float fh = 0.f, fq = 0.f;
     for (int k = 0; k < m; ++k) {
       const size_t q = base + (size_t)k * nx + i;
-      df_acc(fh, fl, f_prod_df<P>(df32{eh_prev[q], el_prev[q]}));
+      df32 e;
+      if (eh_prev) {
+        e = df32{eh_prev[q], el_prev[q]};
+      } else {
+        int fl;
+        offset_parts(s_prev[q], fl, e);
+      }
+      df_acc(fh, fq, f_prod_df<P>(e));
     }
-    ff = (double)fh + (double)fl;
+    ff = (double)fh + (double)fq;
   } else {
     for (int k = 0; k < m; ++k) ff += f_prod<P>(frac_eps(s_prev[base + (size_t)k * nx + i]));
   }
@@ -593,7 +728,8 @@ __global__ void k_backtrack_1d(const double* __restrict__ s_prev, const double* 
 }
 
 void launch_backtrack_1d(const double* s_prev, const double* sigma_prev, const float* eh_prev, const float* el_prev,
-                         int m, int ntc, int nx, int p, double* s_out, double* sigma_out, cudaStream_t st) {
+                         bool pairs, int m, int ntc, int nx, int p, double* s_out, double* sigma_out,
+                         cudaStream_t st) {
   const int bs = 256;
   for (int r0 = 0; r0 < ntc; r0 += 65535) {
     const int rows = min(65535, ntc - r0);
@@ -604,9 +740,9 @@ void launch_backtrack_1d(const double* s_prev, const double* sigma_prev, const f
     const float* el = (eh_prev && el_prev) ? el_prev + (size_t)m * r0 * nx : nullptr;
     double* so = s_out + (size_t)r0 * nx;
     double* go = sigma_out + (size_t)r0 * nx;
-    if (p == 1) k_backtrack_1d<1><<<g, bs, 0, st>>>(sp, gp, eh, el, m, nx, so, go);
-    else if (p == 3) k_backtrack_1d<3><<<g, bs, 0, st>>>(sp, gp, eh, el, m, nx, so, go);
-    else k_backtrack_1d<5><<<g, bs, 0, st>>>(sp, gp, eh, el, m, nx, so, go);
+    if (p == 1) k_backtrack_1d<1><<<g, bs, 0, st>>>(sp, gp, eh, el, pairs ? 1 : 0, m, nx, so, go);
+    else if (p == 3) k_backtrack_1d<3><<<g, bs, 0, st>>>(sp, gp, eh, el, pairs ? 1 : 0, m, nx, so, go);
+    else k_backtrack_1d<5><<<g, bs, 0, st>>>(sp, gp, eh, el, pairs ? 1 : 0, m, nx, so, go);
   }
 }
 
@@ -695,13 +831,23 @@ __global__ void k_build_tables(const double* __restrict__ s, int nx, int npts_ro
   if (pt >= npts_row) return;
   const size_t row = blockIdx.y, idx = row * npts_row + pt;
   const double sv = s[idx];
+  constexpr int L = (P + 1) / 2;
+  if (!w64) {  // FP32 tables: floor and the eps pair by integer operations where they apply
+    int fl;
+    float eh, el;
+    if (split_offset_int(sv, fl, eh, el)) {
+      shift[idx] = (uint16_t)((-fl - L) & (nx - 1));
+      eps32[idx] = eh;
+      if (eps_lo) eps_lo[idx] = el;
+      return;
+    }
+  }
   double fl = floor(sv);
   double eps = sv - fl;
   if (eps >= 1.0) {
     eps -= 1.0;
     fl += 1.0;
   }
-  constexpr int L = (P + 1) / 2;
   // first stencil node E - L with E = i - floor(s); stored as an offset from i, modulo nx (a power of two)
   const int fli = (int)fl;
   shift[idx] = (uint16_t)((-fli - L) & (nx - 1));
