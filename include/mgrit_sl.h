@@ -130,10 +130,11 @@ typedef struct {
                        residual of 1e-14 (FP64 coarse levels only), which keeps MGRIT a linear iteration. */
   int coarse_band;  /* 1D FP32 coarse levels.  1 (default): where the separator block of M^{-1} (M = I -
                        diag(sigma) D, 8-row partitions) falls below 1e-8 of its diagonal blocks (under the
-                       FP32 unit roundoff of the solve) beyond at most 3 partitions, setup stores it as a
-                       band and each correction solve applies it in one banded product; 0 (or where the band
-                       would be wider or its record does not fit in shared memory): block cyclic reduction of
-                       the separator system (p <= 3) or the on-the-fly factorisation (p = 5). */
+                       FP32 unit roundoff of the solve) beyond at most 6 partitions (probed with 8 colours,
+                       and again with 16 where the decay is slower), setup stores it as a band and each
+                       correction solve applies it in one banded product; 0 (or where the band would be wider
+                       or its record does not fit in shared memory): block cyclic reduction of the separator
+                       system (p <= 3) or the on-the-fly factorisation (p = 5). */
   int test_wait_cycles; /* testing the timeout path only; 0 (default): off.  > 0: in every 1D FP32 pass
                        whose tables are staged into shared memory by bulk copies, each CTA's first bounded
                        wait is made on a barrier that nothing completes, with this limit in SM cycles, so
@@ -273,9 +274,9 @@ mgrit_status mgrit_level_info(const mgrit_handle* h, int level, int* nt_level, i
 
 /* Half-width, in 8-row partitions, of the banded separator inverse that level l's FP32 correction solves
  * apply (mgrit_options.coarse_band); 0 where the level solves otherwise.  decay (NULL or 4 floats): the
- * probed decay of that inverse, decay[t - 1] = the largest entry at partition distance t (t = 4: the sum of
- * the two entries at +-4) over the largest diagonal-block entry, maximised over the level's steps; zeros
- * where the level was not probed. */
+ * decay of that inverse from the first (8-colour) probe, decay[t - 1] = the largest entry at partition
+ * distance t (t = 4: the sum of the two entries at +-4) over the largest diagonal-block entry, maximised
+ * over the level's steps; zeros where the level was not probed. */
 mgrit_status mgrit_level_band(const mgrit_handle* h, int level, int* half_width, float* decay);
 
 /* Departure offsets s[n][pt] = (x_pt - xi_pt) / h of level l in grid units (2D: x then y

@@ -45,16 +45,18 @@ cudaError_t launch_pcr_coef(const float* sig32, int nt, int nx, int p, float* ou
 
 // The banded separator inverse of the FP32 correction solves (8-row partitions, nx / 8 in 16 .. 512):
 // per step a record of band_record_size floats, offsets -kBandMaxHalfWidth .. kBandMaxHalfWidth in rows of
-// band_row_size floats, probed from the FP32 sigma rows [nt][nx]; ind[t], t = 1..4, is raised to the
-// largest entry at partition distance t relative to the diagonal blocks (ind zeroed before).
-constexpr int kBandMaxHalfWidth = 3;
+// band_row_size floats, probed from the FP32 sigma rows [nt][nx] with 8 colours (offsets up to 3 stored;
+// ind[t], t = 1..4) or 16 colours (offsets up to 6; ind[t], t = 1..8): ind[t] is raised to the largest
+// entry at partition distance t relative to the diagonal blocks (ind zeroed before).
+constexpr int kBandMaxHalfWidth = 6;
 // Entries of the separator inverse below this fraction of its diagonal blocks are left out of the band:
 // below the unit roundoff of the FP32 solve that applies it (2^-24 = 6e-8), so the truncation adds less
 // than the solve's own rounding.
 constexpr float kBandTolerance = 1e-8f;
 unsigned band_record_size(int nx, int p);
 unsigned band_row_size(int nx, int p);
-cudaError_t launch_sep_band(const float* sig32, int nt, int nx, int p, float* rec, float* ind, cudaStream_t st);
+cudaError_t launch_sep_band(const float* sig32, int nt, int nx, int p, int colours, float* rec, float* ind,
+                            cudaStream_t st);
 
 // Factorisation of M = I - diag(sigma) D_{p+1} (periodic, half-bandwidth b = (p+1)/2) for each of nt
 // steps (layout: solver_layout.cuh), FP64, solver_reals(nx, p) values per step (FP64 coarse levels and

@@ -891,7 +891,6 @@ __device__ __forceinline__ bool corr_solve_coef(float* __restrict__ x, const flo
 // barriers instead of one per reduction level, every thread a partition.
 
 constexpr int kBandMax = kBandMaxHalfWidth;  // largest stored half-bandwidth, in partitions
-constexpr int kBandColours = 8;  // probe colours of k_sep_band (partition index mod 8)
 
 // Floats of one band row (one offset d: B*B blocks for every partition), padded to 16 bytes, and of a
 // whole step record (offsets -kBandMax .. kBandMax; layout [d][a * B + c][partition]).
@@ -1036,18 +1035,20 @@ __device__ __forceinline__ bool corr_solve_band(float* __restrict__ x, const flo
 // each): the band of S^{-1}, the inverse of the separator Schur system S x_S = g of the 8-row partitions.
 // Each thread forms the Schur blocks (L_k, D_k, U_k) of its separator from sigma (the interior LU and the
 // spikes, as corr_solve_otf does), then S is reduced by block cyclic reduction with all probe right-hand
-// sides at once: e = 1 on separator component c of every partition k == col (mod 8), for the 8 colours
-// and B components (in groups of G colours).  The value at partition k' is Sinv[(k', a), (k' + d, c)] of
-// the probe partition k' + d, d in [-3, 4], nearest to it (the other probe partitions are 8 or more away).
-// Entries |d| <= kBandMax go to the record; ind[t], t = 1..4, is raised to the largest |Sinv[k'][d]|,
-// |d| = t, over the largest diagonal block entry (at t = 4 the two probes k' +- 4 are summed: an upper
-// bound of the tail), by atomicMax on the bits of non-negative floats.
+// sides at once: e = 1 on separator component c of every partition k == col (mod NC), for the NC colours
+// (8 or 16) and B components (in groups of G colours).  The value at partition k' is
+// Sinv[(k', a), (k' + d, c)] of the probe partition k' + d, d in [1 - NC/2, NC/2], nearest to it (the other
+// probe partitions are NC or more away).  Entries |d| <= min(NC/2 - 1, kBandMax) go to the record;
+// ind[t], t = 1..NC/2, is raised to the largest |Sinv[k'][d]|, |d| = t, over the largest diagonal block
+// entry (at t = NC/2 the two probes k' +- NC/2 are summed: an upper bound of the tail), by atomicMax on the
+// bits of non-negative floats.
 template <int B>
 constexpr int band_group() { return B <= 2 ? 8 : 2; }
 
-template <int B>
+template <int B, int NC>
 __global__ void __launch_bounds__(512) k_sep_band(const float* __restrict__ sig_all, int nx, float* __restrict__ rec_all,
                                                   unsigned rec_stride, unsigned row, float* __restrict__ ind) {
+  constexpr int RMAX = (NC / 2 - 1) < kBandMax ? (NC / 2 - 1) : kBandMax;  // recorded offsets
   constexpr int PR = kPartRows, Q = PR - B, BB = B * B;
   constexpr int G = band_group<B>(), R = G * B;  // colours and right-hand sides of one reduction pass
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1152,8 +1153,8 @@ __global__ void __launch_bounds__(512) k_sep_band(const float* __restrict__ sig_
         U0[a * B + c] = uv;
       }
   }
-  float dmax = 0.f, tmax[5] = {};
-  for (int col0 = 0; col0 < kBandColours; col0 += G) {
+  float dmax = 0.f, tmax[NC / 2 + 1] = {};
+  for (int col0 = 0; col0 < NC; col0 += G) {
     float Lk[BB], Dk[BB], Uk[BB], gk[R][B];
 #pragma unroll
     for (int e = 0; e < BB; ++e) {
@@ -1164,7 +1165,7 @@ __global__ void __launch_bounds__(512) k_sep_band(const float* __restrict__ sig_
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int a = 0; a < B; ++a) gk[r][a] = (act && (k & (kBandColours - 1)) == col0 + r / B && a == r % B) ? 1.f : 0.f;
+      for (int a = 0; a < B; ++a) gk[r][a] = (act && (k & (NC - 1)) == col0 + r / B && a == r % B) ? 1.f : 0.f;
     for (int t = 0; t < T; ++t) {
       __syncthreads();  // the previous level's (or pass's) reads of the exchange are done
       if (act) {
@@ -1234,15 +1235,15 @@ __global__ void __launch_bounds__(512) k_sep_band(const float* __restrict__ sig_
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int c = r % B;
-        int d = (col0 + r / B - k) & (kBandColours - 1);  // probe partition k + d, d in [-3, 4]
-        if (d > kBandColours / 2) d -= kBandColours;
+        int d = (col0 + r / B - k) & (NC - 1);  // probe partition k + d, d in [1 - NC/2, NC/2]
+        if (d > NC / 2) d -= NC;
         const int ad = d < 0 ? -d : d;
 #pragma unroll
         for (int a = 0; a < B; ++a) {
           float v = 0.f;
 #pragma unroll
           for (int c2 = 0; c2 < B; ++c2) v += Fi[a * B + c2] * gk[r][c2];
-          if (ad <= kBandMax) rec[(size_t)(d + kBandMax) * row + (size_t)(a * B + c) * P + k] = v;
+          if (ad <= RMAX) rec[(size_t)(d + kBandMax) * row + (size_t)(a * B + c) * P + k] = v;
           if (ad == 0) dmax = fmaxf(dmax, fabsf(v));
           else tmax[ad] = fmaxf(tmax[ad], fabsf(v));
         }
@@ -1251,7 +1252,7 @@ __global__ void __launch_bounds__(512) k_sep_band(const float* __restrict__ sig_
   }
   if (act && dmax > 0.f) {
 #pragma unroll
-    for (int t = 1; t <= 4; ++t) atomicMax(reinterpret_cast<int*>(ind) + t, __float_as_int(tmax[t] / dmax));
+    for (int t = 1; t <= NC / 2; ++t) atomicMax(reinterpret_cast<int*>(ind) + t, __float_as_int(tmax[t] / dmax));
   }
 }
 
@@ -2335,22 +2336,29 @@ unsigned pcr_record_size(int nx, int p) { return pcr_record_floats(nx, p); }
 unsigned band_record_size(int nx, int p) { return band_record_floats(nx, p); }
 unsigned band_row_size(int nx, int p) { return band_row_floats(nx, p); }
 
-cudaError_t launch_sep_band(const float* sig32, int nt, int nx, int p, float* rec, float* ind, cudaStream_t st) {
+cudaError_t launch_sep_band(const float* sig32, int nt, int nx, int p, int colours, float* rec, float* ind,
+                            cudaStream_t st) {
   const int B = (p + 1) / 2, P = nx / kPartRows;
-  if (P < 16 || P > 512) return cudaErrorInvalidValue;
+  if (P < 16 || P > 512 || (colours != 8 && colours != 16)) return cudaErrorInvalidValue;
   const int R = (B <= 2 ? 8 : 2) * B;
   const size_t smem = (size_t)(3 * B * B + R * B) * P * sizeof(float);
   const unsigned stride = band_record_floats(nx, p), row = band_row_floats(nx, p);
   cudaError_t e = cudaSuccess;
-#define MGRIT_BAND(BB)                                                                                     \
+#define MGRIT_BAND(BB, NCC)                                                                                \
   {                                                                                                        \
-    e = cudaFuncSetAttribute(k_sep_band<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+    e = cudaFuncSetAttribute(k_sep_band<BB, NCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                        \
-    k_sep_band<BB><<<nt, P, smem, st>>>(sig32, nx, rec, stride, row, ind);                                 \
+    k_sep_band<BB, NCC><<<nt, P, smem, st>>>(sig32, nx, rec, stride, row, ind);                            \
   }
-  if (B == 1) MGRIT_BAND(1)
-  else if (B == 2) MGRIT_BAND(2)
-  else MGRIT_BAND(3)
+  if (colours == 8) {
+    if (B == 1) MGRIT_BAND(1, 8)
+    else if (B == 2) MGRIT_BAND(2, 8)
+    else MGRIT_BAND(3, 8)
+  } else {
+    if (B == 1) MGRIT_BAND(1, 16)
+    else if (B == 2) MGRIT_BAND(2, 16)
+    else MGRIT_BAND(3, 16)
+  }
 #undef MGRIT_BAND
   return cudaGetLastError();
 }

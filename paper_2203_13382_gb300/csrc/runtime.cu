@@ -52,7 +52,7 @@ struct Level {
   float* pcr32 = nullptr;   // FP32 coarse levels, p <= 3: block-PCR coefficients of every step
   unsigned pcr_floats = 0;
   float* band32 = nullptr;  // FP32 coarse levels: the banded separator inverse of every step (probed in setup)
-  float* band_ind = nullptr;  // [8] its decay indicator (k_sep_band; entries 1..4 used)
+  float* band_ind = nullptr;  // [32] its decay indicators (k_sep_band): 8 colours at 1..4, 16 colours at 17..24
   int band_w = 0;           // half-bandwidth in use (0: block PCR / on the fly), chosen in setup_finish
   float band_decay[4] = {};  // the probed indicator at partition distances 1..4 (host copy)
   size_t solver_stride = 0;
@@ -594,31 +594,63 @@ static mgrit_status setup_finish(mgrit_handle** out) {
     *out = nullptr;
     return fail(MGRIT_ESINGULAR, "a correction matrix has a (near) zero pivot");
   }
-  // half-bandwidth of each FP32 coarse level's separator inverse: the smallest W <= kBandMaxHalfWidth
-  // beyond which every probed entry is below kBandTolerance of the diagonal blocks, if its record fits the
-  // shared memory of the relaxation kernel; else the block PCR (p <= 3) or the on-the-fly factorisation (p = 5)
+  // half-bandwidth of each FP32 coarse level's separator inverse: the smallest W beyond which every probed
+  // entry is below kBandTolerance of the diagonal blocks, if its record fits the shared memory of the
+  // relaxation kernel; else the block PCR (p <= 3) or the on-the-fly factorisation (p = 5).  The 8-colour
+  // probe of the setup decides W <= 3 (entries probed to distance 4); levels it rejects, where a band of
+  // half-width kBandMaxHalfWidth would still fit, are probed again with 16 colours (W <= 6, entries to 8),
+  // all such levels at once before one synchronisation.
+  auto fits = [&](size_t l, int w) {
+    Level& L = h->levels[l];
+    L.band_w = w;
+    int buf;
+    size_t smem, region;
+    relax_smem_need(h->tables((int)l, 0), 0, &buf, &smem, &region);
+    L.band_w = 0;
+    return smem <= 227 * 1024;
+  };
+  auto choose = [](const float* ind, int wmax, int tmax) {
+    for (int w = 1; w <= wmax; ++w) {
+      bool under = true;
+      for (int t = w + 1; t <= tmax; ++t) under = under && ind[t] < kBandTolerance;  // NaN fails
+      if (under) return w;
+    }
+    return 0;
+  };
+  std::vector<int> widths(h->levels.size(), 0);
+  std::vector<char> reprobe(h->levels.size(), 0);
+  bool any16 = false;
   for (size_t l = 1; l < h->levels.size(); ++l) {
     Level& L = h->levels[l];
     if (!L.band_ind) continue;
-    float ind[8] = {};
+    float ind[5] = {};
     if (cudaMemcpy(ind, L.band_ind, sizeof(ind), cudaMemcpyDeviceToHost) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     for (int t = 0; t < 4; ++t) L.band_decay[t] = ind[t + 1];
-    int W = 0;
-    for (int w = 1; w <= kBandMaxHalfWidth && !W; ++w) {
-      bool ok = true;
-      for (int t = w + 1; t <= kBandMaxHalfWidth + 1; ++t) ok = ok && ind[t] < kBandTolerance;  // NaN fails
-      if (ok) W = w;
+    int W = choose(ind, 3, 4);
+    if (W > 0 && !fits(l, W)) W = 0;
+    widths[l] = W;
+    if (W == 0 && fits(l, kBandMaxHalfWidth) &&
+        launch_sep_band(L.sig32, L.nt, h->grid.nx, h->order, 16, L.band32, L.band_ind + 16, h->stream) ==
+            cudaSuccess) {
+      reprobe[l] = 1;
+      any16 = true;
     }
-    if (W > 0) {  // the record of the step must fit next to the slices and staged rows
-      L.band_w = W;
-      int buf;
-      size_t smem, region;
-      relax_smem_need(h->tables((int)l, 0), 0, &buf, &smem, &region);
-      if (smem > 227 * 1024) W = 0;
-    }
+  }
+  if (any16 && cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    std::fill(reprobe.begin(), reprobe.end(), 0);
+  }
+  for (size_t l = 1; l < h->levels.size(); ++l) {
+    Level& L = h->levels[l];
+    if (!L.band_ind) continue;
+    int W = widths[l];
+    float ind16[9] = {};
+    if (reprobe[l] && cudaMemcpy(ind16, L.band_ind + 16, sizeof(ind16), cudaMemcpyDeviceToHost) == cudaSuccess)
+      W = choose(ind16, kBandMaxHalfWidth, 8);
+    cudaGetLastError();
     L.band_w = W;
     if (W == 0 && L.pcr_floats && !L.pcr32) {  // band rejected: the block-PCR record after all
       mgrit_status st = h->alloc(&L.pcr32, (size_t)L.nt * L.pcr_floats);
@@ -756,7 +788,7 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
           }
           if (probe) {
             if ((st = h->alloc(&L.band32, (size_t)L.nt * band_record_size(nx, p))) != MGRIT_OK) return cleanup_fail(st);
-            if ((st = h->alloc(&L.band_ind, 8)) != MGRIT_OK) return cleanup_fail(st);
+            if ((st = h->alloc(&L.band_ind, 32)) != MGRIT_OK) return cleanup_fail(st);  // [0, 5) and [16, 25)
           }
         }
       }
@@ -856,8 +888,8 @@ static mgrit_status setup_impl(const mgrit_grid* grid, const mgrit_wavespeed* wa
       launch_axpy_convert(1, L.sigma, L.sig32, nullptr, (long long)L.nt * np * dim, s);
       if (L.pcr32) launch_pcr_coef(L.sig32, L.nt, nx, p, L.pcr32, s);
       if (L.band32) {
-        cudaMemsetAsync(L.band_ind, 0, 8 * sizeof(float), s);
-        launch_sep_band(L.sig32, L.nt, nx, p, L.band32, L.band_ind, s);
+        cudaMemsetAsync(L.band_ind, 0, 32 * sizeof(float), s);
+        launch_sep_band(L.sig32, L.nt, nx, p, 8, L.band32, L.band_ind, s);
       }
       h->phase_end(MGRIT_PHASE_FACTOR, ev, (L.pcr32 ? 2 : 1) + (L.band32 ? 1 : 0));
     }

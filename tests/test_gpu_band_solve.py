@@ -2,8 +2,9 @@
 
 On 1D FP32 coarse levels M = I - diag(sigma) D_{p+1} (eq. (Phi_multilevel)) is solved with 8-row
 partitions whose separator system is inverted by a stored band of S^{-1} = (M^{-1}) restricted to the
-separators, probed in setup and kept only where the entries it leaves out are below 1e-8 of its diagonal
-blocks (under the FP32 unit roundoff of the solve that applies it).
+separators, probed in setup (8 colours, and 16 where the decay is slower) and kept only where the entries
+it leaves out are below 1e-8 of its diagonal blocks (under the FP32 unit roundoff of the solve that applies
+it).
 - The probed decay of S^{-1} equals the oracle's: M^{-1} formed densely from the oracle's sigma of every
   step, its separator blocks at partition distance t = 1..3 relative to the diagonal block of the same
   partition, summed as the probe's eight colours sum them (partitions 8 apart share a colour; FP32 probe:
@@ -123,8 +124,9 @@ def test_probed_decay_matches_the_oracle(p):
                 assert abs(dec[t] - ref[t]) <= 1e-3 * ref[t], (level, t + 1, dec[t], ref[t])
             else:
                 assert dec[t] <= 1e-6 + 2.0 * ref[t], (level, t + 1, dec[t], ref[t])
-        # the chosen width: the smallest whose left-out entries (distances W+1 .. 4) are under 1e-8, or 0
+        # the chosen width: the smallest whose left-out entries (distances W+1 .. 4) are under 1e-8, or 0;
+        # levels this first probe rejects are probed again with 16 colours (widths up to 6)
         need = next((w for w in range(1, 4) if all(d < 1e-8 for d in dec[w:])), 0)
-        assert W_gpu in (need, 0), (level, W_gpu, need, dec)
+        assert W_gpu in (need, 0) or need == 0, (level, W_gpu, need, dec)
         print(f"p={p} level {level}: band {W_gpu}, probed {['%.2e' % d for d in dec]}, oracle {['%.2e' % r for r in ref]}")
     h.destroy()
