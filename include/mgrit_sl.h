@@ -300,8 +300,7 @@ mgrit_status mgrit_apply_step(mgrit_handle* h, int level, int n0, int count, con
  * staged through an 8 MiB buffer in file-scope device memory that every GPU loading this library
  * holds until the process exits; count * N must not exceed 1048576 (MGRIT_EINVAL otherwise, before
  * any launch).  Every call looks up that buffer's address on the current device (cudaGetSymbolAddress),
- * and the current device must be the handle's device (MGRIT_EINVAL otherwise, before any launch).  The
- * call ends with a stream synchronisation, so it cannot be made while its stream is being captured.
+ * and the current device must be the handle's device (MGRIT_EINVAL otherwise, before any launch).
  * All calls share the buffer: calls that overlap on the GPU (other streams, other threads, other
  * handles) race; calls issued one after another are safe, as each call overwrites every staged value
  * it reads.  Synchronous.
